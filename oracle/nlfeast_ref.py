@@ -1,0 +1,365 @@
+"""Plain FP64 CPU oracle of nonlinear FEAST (NLFEAST).
+
+Gavin, Miedlar, Polizzi, "FEAST Eigensolver for Nonlinear Eigenvalue Problems"
+(arXiv 1801.09794).  Every function names the passage it follows.
+
+TEST INFRASTRUCTURE ONLY.  This package is imported by ``tests/``, by
+``__graft_entry__.smoke()`` (to check the GPU result) and by ``bench.py``'s
+CPU-baseline / reference leg.  The GPU library never imports, links or calls
+it, and it shares no code with the GPU library: both consume only the seeded
+problems of ``workloads/``.
+
+Everything is complex128 / float64 on the host, written for readability and
+not for speed: numpy/scipy LAPACK routines (LU, QR, QZ) serve as single steps.
+
+Readings of points the paper leaves open (each is also listed in the design doc):
+
+* Quadrature (Algorithm 1 inputs; Step 4): the contour is
+  z(theta) = c + ra*cos(theta) + i*rb*sin(theta), theta in [0, 2*pi)
+  (a circle when ra == rb), and omega_j = w_j * z'(theta_j) / (2*pi*i),
+  i.e. the 1/(2*pi*i) factor of the integral is folded into the weights.
+  Default rule: Gauss-Legendre with n_c points on [0, 2*pi].
+* Step 4's right factor (z_j I - Lambda)^{-1} is diagonal, so it scales
+  column i by 1/(z_j - lambda_i).
+* Step 2 "closest to the interior of C": rank by the normalised radius
+  rho(lambda) = |((Re(lambda - c))/ra, (Im(lambda - c))/rb)|_2, with a
+  stable sort on (rho, Re lambda, Im lambda); inside means rho < 1.
+* Step 3's test is the relative residual
+  ||T(lambda_i) x_i||_2 / sum_t |scale_t f_t(lambda_i)| * ||A_t||_2 with
+  ||x_i||_2 = 1, over the Ritz values strictly inside C, where ||A_t||_2 is
+  estimated by 30 power iterations on A^H A from the normalised all-ones
+  vector (identity: 1).  The iteration count counts executions of Step 1,
+  and the test is not taken before one filter application.
+* Step 1 for polynomial T: the projected matrix polynomial is linearised in
+  the first companion form (Sec. 2, the k = 2 pencil there, generalised to
+  degree k) and solved by QZ; the Ritz vector is the last block of the pencil
+  eigenvector.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+__all__ = [
+    "quadrature", "filter_function", "f_value", "assemble", "power_norm2",
+    "term_norms", "projected_coefficients", "companion", "reduced_eig",
+    "normalized_radius", "select", "ritz_vectors", "block_residual",
+    "relative_residuals", "filter_update", "orthonormalize", "factor_nodes",
+    "nlfeast", "brute_force_eigs", "winding_count", "shift_invert_nearest",
+    "SingularNode",
+]
+
+
+class SingularNode(ArithmeticError):
+    """A Ritz value coincides with a quadrature node (Step 4 divides by z_j - lambda_i)."""
+
+
+# --------------------------------------------------------------------------
+# Contour and quadrature (Algorithm 1, inputs; Step 4)
+# --------------------------------------------------------------------------
+def quadrature(center, ra, rb, nc, rule="gl"):
+    """Nodes z_j and weights omega_j with sum_j omega_j g(z_j) ~ (1/(2 pi i)) oint g(z) dz.
+
+    Algorithm 1 takes "a set of n_c quadrature nodes and weights"; Step 4 sums
+    omega_j * (...) * (z_j I - Lambda)^{-1}.  The parametrisation and the rule are
+    the readings stated in the module docstring.
+    """
+    if nc < 1:
+        raise ValueError("nc must be positive")
+    if rule == "gl":
+        x, w = np.polynomial.legendre.leggauss(nc)
+        theta = np.pi * (x + 1.0)
+        wt = np.pi * w
+    elif rule == "trapezoid":
+        theta = 2.0 * np.pi * (np.arange(nc) + 0.5) / nc
+        wt = np.full(nc, 2.0 * np.pi / nc)
+    elif rule == "gl_halves":
+        if nc % 2:
+            raise ValueError("gl_halves needs an even nc")
+        x, w = np.polynomial.legendre.leggauss(nc // 2)
+        t0 = 0.5 * np.pi * (x + 1.0)
+        theta = np.concatenate([t0, t0 + np.pi])
+        wt = np.concatenate([0.5 * np.pi * w, 0.5 * np.pi * w])
+    else:
+        raise ValueError(f"unknown rule {rule!r}")
+    z = center + ra * np.cos(theta) + 1j * rb * np.sin(theta)
+    dz = -ra * np.sin(theta) + 1j * rb * np.cos(theta)
+    omega = wt * dz / (2j * np.pi)
+    return z.astype(np.complex128), omega.astype(np.complex128)
+
+
+def filter_function(lam, z, omega):
+    """Scalar filter f(lambda) = sum_j omega_j / (z_j - lambda): the coefficient of
+    x_i in column i of Step 4 (it approximates 1 inside C and 0 outside)."""
+    lam = np.atleast_1d(np.asarray(lam, dtype=np.complex128))
+    return (omega[None, :] / (z[None, :] - lam[:, None])).sum(axis=1)
+
+
+# --------------------------------------------------------------------------
+# The matrix function T (Sec. 2: T(lambda) = sum_i lambda^i A_i; Sec. 6 for
+# non-polynomial f)
+# --------------------------------------------------------------------------
+def f_value(term, z):
+    """Scalar function of one term: lambda**p or exp(-tau*lambda), times its scale."""
+    z = np.asarray(z, dtype=np.complex128)
+    if term["kind"] == "pow":
+        v = z ** term["p"]
+    elif term["kind"] == "exp":
+        v = np.exp(-term["tau"] * z)
+    else:
+        raise ValueError(term["kind"])
+    return term["scale"] * v
+
+
+def assemble(problem, z):
+    """T(z) = sum_t scale_t f_t(z) A_t as a dense matrix (A_t None = identity)."""
+    n = problem["n"]
+    T = np.zeros((n, n), dtype=np.complex128)
+    for t in problem["terms"]:
+        c = complex(f_value(t, z))
+        if t["A"] is None:
+            T[np.diag_indices(n)] += c
+        else:
+            T += c * t["A"]
+    return T
+
+
+def power_norm2(A, iters=30):
+    """||A||_2 estimated by `iters` power steps on A^H A from ones/sqrt(n)."""
+    if A is None:
+        return 1.0
+    n = A.shape[1]
+    v = np.full(n, 1.0 / np.sqrt(n), dtype=np.complex128)
+    s = 0.0
+    for _ in range(iters):
+        w = A.conj().T @ (A @ v)
+        s = np.linalg.norm(w)
+        if s == 0.0:
+            return 0.0
+        v = w / s
+    return float(np.sqrt(s))
+
+
+def term_norms(problem, iters=30):
+    return np.array([power_norm2(t["A"], iters) for t in problem["terms"]])
+
+
+# --------------------------------------------------------------------------
+# Step 1: projected problem Q^H T(lambda) Q y = 0, solved by linearisation
+# --------------------------------------------------------------------------
+def projected_coefficients(problem, Q):
+    """Ahat_p = sum_{t: f_t = lambda^p} scale_t Q^H A_t Q, p = 0..k (Step 1)."""
+    k = max(t["p"] for t in problem["terms"] if t["kind"] == "pow")
+    m = Q.shape[1]
+    Ahat = [np.zeros((m, m), dtype=np.complex128) for _ in range(k + 1)]
+    for t in problem["terms"]:
+        if t["kind"] != "pow":
+            raise NotImplementedError("projected_coefficients is for polynomial T")
+        AQ = Q if t["A"] is None else t["A"] @ Q
+        Ahat[t["p"]] += t["scale"] * (Q.conj().T @ AQ)
+    return Ahat
+
+
+def companion(Ahat):
+    """First companion form L(lambda) = L0 + lambda*L1 of sum_p lambda^p Ahat_p.
+
+    Sec. 2 writes it for k = 2 as lambda*[[A2, 0], [0, I]] + [[A1, A0], [-I, 0]]
+    with eigenvectors [lambda x; x]; for degree k the first block row holds
+    A_{k-1} .. A_0, the sub-diagonal blocks are -I, and L1 = diag(A_k, I, .., I).
+    The eigenvector is [lambda^{k-1} y; ...; lambda y; y].
+    """
+    k = len(Ahat) - 1
+    m = Ahat[0].shape[0]
+    N = k * m
+    L0 = np.zeros((N, N), dtype=np.complex128)
+    L1 = np.zeros((N, N), dtype=np.complex128)
+    for b in range(k):
+        L0[0:m, b * m:(b + 1) * m] = Ahat[k - 1 - b]
+    for b in range(1, k):
+        L0[b * m:(b + 1) * m, (b - 1) * m:b * m] = -np.eye(m)
+        L1[b * m:(b + 1) * m, b * m:(b + 1) * m] = np.eye(m)
+    L1[0:m, 0:m] = Ahat[k]
+    return L0, L1
+
+
+def reduced_eig(Ahat):
+    """All eigenpairs of the projected polynomial (Step 1) by QZ on the companion.
+
+    Returns eigenvalues (k*m,) and the vectors y (m, k*m) taken from the last
+    block of each pencil eigenvector.
+    """
+    L0, L1 = companion(Ahat)
+    m = Ahat[0].shape[0]
+    lam, Z = sla.eig(L0, -L1)
+    return lam, Z[-m:, :]
+
+
+def normalized_radius(lam, center, ra, rb):
+    """rho(lambda) of the Step 2 reading; rho < 1 means inside C."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    d = lam - center
+    with np.errstate(invalid="ignore", over="ignore"):
+        rho = np.sqrt((d.real / ra) ** 2 + (d.imag / rb) ** 2)
+    rho = np.where(np.isfinite(rho), rho, np.inf)
+    return rho
+
+
+def select(lam, center, ra, rb, m0):
+    """Step 2: indices of the m0 Ritz values closest to the interior of C."""
+    rho = normalized_radius(lam, center, ra, rb)
+    re = np.where(np.isfinite(lam.real), lam.real, np.inf)
+    im = np.where(np.isfinite(lam.imag), lam.imag, np.inf)
+    order = np.lexsort((im, re, rho))
+    return order[:m0]
+
+
+def ritz_vectors(Q, Y):
+    """X = Q Y with unit columns (Step 2)."""
+    X = Q @ Y
+    return X / np.linalg.norm(X, axis=0)[None, :]
+
+
+# --------------------------------------------------------------------------
+# Step 3: block residual and its test
+# --------------------------------------------------------------------------
+def block_residual(problem, X, lam):
+    """T(X, Lambda) = sum_t A_t X diag(scale_t f_t(lambda_i)) (Sec. 4.2, the block
+    residual function; for a polynomial sum_i A_i X Lambda^i)."""
+    R = np.zeros_like(X)
+    for t in problem["terms"]:
+        fx = f_value(t, lam)
+        AX = X if t["A"] is None else t["A"] @ X
+        R += AX * fx[None, :]
+    return R
+
+
+def relative_residuals(problem, R, lam, norms):
+    """||r_i||_2 / sum_t |scale_t f_t(lambda_i)| ||A_t||_2 (the Step 3 reading)."""
+    den = np.zeros(len(lam))
+    for t, nt in zip(problem["terms"], norms):
+        den += np.abs(f_value(t, lam)) * nt
+    return np.linalg.norm(R, axis=0) / den
+
+
+# --------------------------------------------------------------------------
+# Step 4: the contour-quadrature filter
+# --------------------------------------------------------------------------
+def factor_nodes(problem, z):
+    """LU factors of T(z_j) for every node (fixed shifts, so done once per contour)."""
+    return [sla.lu_factor(assemble(problem, zj)) for zj in z]
+
+
+def filter_update(lus, z, omega, X, lam, R):
+    """Step 4: Q = sum_j omega_j (X - T(z_j)^{-1} T(X, Lambda)) (z_j I - Lambda)^{-1}."""
+    Q = np.zeros_like(X)
+    for lu, zj, wj in zip(lus, z, omega):
+        d = zj - lam
+        if np.any(d == 0):
+            raise SingularNode("Ritz value on a quadrature node")
+        Yj = sla.lu_solve(lu, R)
+        Q += (X - Yj) * (wj / d)[None, :]
+    return Q
+
+
+def orthonormalize(Q):
+    """Steps 0 and 5: orthonormal basis of span(Q) by Householder QR."""
+    q, _ = np.linalg.qr(Q, mode="reduced")
+    return q
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1
+# --------------------------------------------------------------------------
+def nlfeast(problem, contour, m0, X0, tol=1e-10, maxit=50, lus=None, norms=None):
+    """Algorithm 1 (NLFEAST for T(lambda)x = 0), polynomial T.
+
+    contour: {"center": complex, "ra": float, "rb": float, "nc": int, "rule": str}.
+    Returns a dict with the m0 selected Ritz values ``lam`` and unit vectors ``X``,
+    their relative residuals ``relres``, the ``inside`` mask, the iteration count
+    ``iters`` (executions of Step 1), ``converged`` and the per-iteration maximum
+    relative residual over the inside pairs ``history``.
+    """
+    c, ra, rb = complex(contour["center"]), float(contour["ra"]), float(contour["rb"])
+    z, omega = quadrature(c, ra, rb, int(contour["nc"]), contour.get("rule", "gl"))
+    if lus is None:
+        lus = factor_nodes(problem, z)
+    if norms is None:
+        norms = term_norms(problem)
+    Q = orthonormalize(np.asarray(X0, dtype=np.complex128))          # Step 0
+    history = []
+    converged = False
+    it = 0
+    for it in range(1, maxit + 1):
+        Ahat = projected_coefficients(problem, Q)                      # Step 1
+        lam_all, Y_all = reduced_eig(Ahat)
+        sel = select(lam_all, c, ra, rb, m0)                           # Step 2
+        lam = lam_all[sel]
+        X = ritz_vectors(Q, Y_all[:, sel])
+        R = block_residual(problem, X, lam)                            # Step 3
+        rr = relative_residuals(problem, R, lam, norms)
+        ins = normalized_radius(lam, c, ra, rb) < 1.0
+        history.append(float(rr[ins].max()) if ins.any() else 0.0)
+        if it > 1 and np.all(rr[ins] <= tol):
+            converged = True
+            break
+        if it == maxit:
+            break
+        Q = orthonormalize(filter_update(lus, z, omega, X, lam, R))    # Steps 4, 5
+    return {"lam": lam, "X": X, "relres": rr, "inside": ins, "iters": it,
+            "converged": converged, "history": history, "norms": norms,
+            "abs_res": np.linalg.norm(R, axis=0)}
+
+
+# --------------------------------------------------------------------------
+# Brute-force references used to pin the oracle and to build test contours
+# --------------------------------------------------------------------------
+def _power_matrices(problem):
+    n = problem["n"]
+    k = max(t["p"] for t in problem["terms"])
+    mats = [np.zeros((n, n), dtype=np.complex128) for _ in range(k + 1)]
+    for t in problem["terms"]:
+        if t["kind"] != "pow":
+            raise NotImplementedError
+        mats[t["p"]] += t["scale"] * (np.eye(n) if t["A"] is None else t["A"])
+    return mats
+
+
+def brute_force_eigs(problem):
+    """Every eigenvalue of a small polynomial problem: QZ on the full companion."""
+    L0, L1 = companion(_power_matrices(problem))
+    return sla.eigvals(L0, -L1)
+
+
+def winding_count(problem, center, ra, rb, nsamp=2048):
+    """Number of eigenvalues inside C by the argument principle:
+    (1/2 pi) * total change of arg det T(z) along C, with det T from an LU."""
+    theta = 2.0 * np.pi * np.arange(nsamp + 1) / nsamp
+    zs = center + ra * np.cos(theta) + 1j * rb * np.sin(theta)
+    ph = np.empty(nsamp + 1)
+    for s, zz in enumerate(zs):
+        sign, _ = np.linalg.slogdet(assemble(problem, zz))
+        ph[s] = np.angle(sign)
+    return int(round((np.unwrap(ph)[-1] - ph[0]) / (2.0 * np.pi)))
+
+
+def shift_invert_nearest(problem, sigma, nev):
+    """The nev eigenvalues of a quadratic problem nearest sigma, by shift-invert
+    Arnoldi on the first companion pencil, applying L(sigma)^{-1} through one
+    n x n LU of P(sigma) (no 2n x 2n factorisation)."""
+    from scipy.sparse.linalg import LinearOperator, eigs
+    A0, A1, A2 = _power_matrices(problem)
+    n = problem["n"]
+    lu = sla.lu_factor(sigma * sigma * A2 + sigma * A1 + A0)
+    S = sigma * A2 + A1
+
+    def op(v):
+        v = np.asarray(v).reshape(-1)
+        v1 = A2 @ v[:n]          # L1 [u1; u2] = [A2 u1; u2]
+        v2 = v[n:]
+        u2 = sla.lu_solve(lu, v1 + S @ v2)
+        u1 = sigma * u2 - v2
+        return np.concatenate([u1, u2])
+
+    L = LinearOperator((2 * n, 2 * n), matvec=op, dtype=np.complex128)
+    theta = eigs(L, k=nev, which="LM", return_eigenvectors=False, tol=1e-13,
+                 ncv=min(2 * n, max(2 * nev + 1, 160)))
+    lam = sigma - 1.0 / theta
+    return lam[np.argsort(np.abs(lam - sigma))]
