@@ -1,0 +1,191 @@
+/*
+ * feast_nl.h -- C ABI of a GB300 (sm_103a) library for the contour-quadrature
+ * filter of nonlinear FEAST (Gavin, Miedlar, Polizzi, "FEAST Eigensolver for
+ * Nonlinear Eigenvalue Problems", arXiv 1801.09794).
+ *
+ * Problem (Sec. 2, Eq. NLEVP and the matrix polynomial P(lambda) = sum_i lambda^i A_i):
+ *     find lambda inside a closed contour C and x != 0 with T(lambda) x = 0,
+ *     T(lambda) = sum_t scale_t * f_t(lambda) * A_t,
+ *     f_t(lambda) = lambda^p            (FEAST_NL_POW), or
+ *     f_t(lambda) = exp(-tau*lambda)    (FEAST_NL_EXP, the non-polynomial case of Sec. 6).
+ *
+ * Method (Algorithm 1): node matrices T(z_j) are factored once per contour; each
+ * iteration projects T onto the subspace Q (Step 1), keeps the m0 Ritz pairs
+ * closest to the interior of C (Step 2), tests the residuals (Step 3), applies
+ * the quadrature filter
+ *     Q = sum_j omega_j (X - T(z_j)^{-1} T(X, Lambda)) (z_j I - Lambda)^{-1}   (Step 4)
+ * and orthonormalises Q (Step 5).  All of it runs on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Matrices crossing the ABI are complex128 (interleaved re, im doubles),
+ *     row-major ("C order", as numpy / torch store them).
+ *   - A pointer may be host or device memory; the library asks the CUDA driver
+ *     which one it is (terms say it explicitly with on_device).  The caller
+ *     keeps ownership of every buffer it passes; the library copies inputs
+ *     before returning and never keeps a caller pointer.
+ *   - Every function returns a status (FEAST_NL_OK == 0 on success); no C++
+ *     exception, abort or exit crosses the ABI.  feast_nl_last_error() gives a
+ *     one-line reason for the last failure on the calling thread.
+ *   - A handle is not thread-safe: use one handle per host thread.  Each handle
+ *     works on its own CUDA stream (created by the library, or the caller's).
+ *   - Device memory is owned by the handle and freed by feast_nl_destroy().
+ */
+#ifndef FEAST_NL_H
+#define FEAST_NL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FEAST_NL_OK              0
+#define FEAST_NL_EINVAL          1  /* bad argument (size, pointer, enum, order of calls) */
+#define FEAST_NL_ESINGULAR_NODE  2  /* T(z_j) singular, or a Ritz value equal to a node z_j */
+#define FEAST_NL_ENOT_CONVERGED  3  /* maxit reached; results of the last iterate are readable */
+#define FEAST_NL_ETOO_MANY       4  /* all m0 kept Ritz values are inside C: m0 is too small
+                                       (Algorithm 1 needs fewer than m0 eigenvalues inside) */
+#define FEAST_NL_ENOMEM          5  /* device or host allocation failed */
+#define FEAST_NL_EDEVICE         6  /* CUDA error, or a device-side iteration limit was hit */
+#define FEAST_NL_EUNSUPPORTED    7  /* valid request this build does not implement */
+
+/* ---- enums --------------------------------------------------------------- */
+enum feast_nl_fkind { FEAST_NL_POW = 0, FEAST_NL_EXP = 1 };
+
+/* Arithmetic of the node factorisations and solves (Step 4).  The block residual
+ * T(X, Lambda), the projections Q^H A_t Q, the reduced problem and the
+ * orthonormalisation are FP64-accurate in every mode.
+ *   FEAST_NL_FP64  : LU and solves in FP64.
+ *   FEAST_NL_FP32  : LU and solves in FP32 (complex64).  The filter is a
+ *                    residual inverse iteration (Sec. 4.2), so solve errors scale
+ *                    with ||T(X, Lambda)|| and vanish as the pairs converge. */
+enum feast_nl_precision { FEAST_NL_FP64 = 0, FEAST_NL_FP32 = 1 };
+
+/* Quadrature rule on the parametrised contour z(theta) = c + ra cos(theta) + i rb sin(theta),
+ * omega_j = w_j z'(theta_j) / (2 pi i):
+ *   FEAST_NL_GL        : Gauss-Legendre, nc points on theta in [0, 2 pi]
+ *   FEAST_NL_TRAPEZOID : theta_j = 2 pi (j + 1/2) / nc, w_j = 2 pi / nc
+ *   FEAST_NL_GL_HALVES : Gauss-Legendre, nc/2 points on each half [0, pi], [pi, 2 pi] */
+enum feast_nl_rule { FEAST_NL_GL = 0, FEAST_NL_TRAPEZOID = 1, FEAST_NL_GL_HALVES = 2 };
+
+/* ---- types --------------------------------------------------------------- */
+typedef struct feast_nl_handle feast_nl_handle;   /* opaque */
+
+/* One term scale * f(lambda) * A of T(lambda).
+ *   kind, p, tau : f(lambda) = lambda^p (kind POW, 0 <= p <= 8) or exp(-tau lambda) (kind EXP).
+ *   scale        : complex multiplier (scale_re + i scale_im).
+ *   A            : n x n complex128, row-major with row stride lda (>= n) elements;
+ *                  NULL means the identity matrix.
+ *   on_device    : nonzero if A is device memory of the current CUDA device. */
+typedef struct {
+    int32_t kind;
+    int32_t p;
+    double tau;
+    double scale_re;
+    double scale_im;
+    const void* A;
+    int64_t lda;
+    int32_t on_device;
+    int32_t reserved;
+} feast_nl_term;
+
+/* Summary of a solve (filled by feast_nl_solve). */
+typedef struct {
+    int32_t iters;        /* executions of Step 1 */
+    int32_t n_inside;     /* kept Ritz values strictly inside C */
+    int32_t n_converged;  /* inside pairs with relative residual <= tol */
+    int32_t status;       /* same value feast_nl_solve returned */
+    double max_relres;    /* max relative residual over the inside pairs (0 if none) */
+    double ms_factor;     /* device time of node assembly + LU (0 when reused) */
+    double ms_iterate;    /* device time of all iterations */
+} feast_nl_info;
+
+/* ---- entry points ---------------------------------------------------------- */
+
+/* Create a solver for T(lambda) = sum_t scale_t f_t(lambda) A_t of size n.
+ * Copies every A_t to the device (transposed to the library's column-major
+ * layout) and estimates ||A_t||_2 by 30 power iterations on A^H A from the
+ * normalised all-ones vector (identity terms: 1); these norms scale the
+ * relative residual of Step 3.
+ *   h         : out, the new handle (NULL on failure).
+ *   n         : 1 <= n <= 65536.
+ *   nterms    : 1 <= nterms <= 16.
+ *   precision : enum feast_nl_precision.
+ *   stream    : cudaStream_t to run on, or NULL for a library-owned stream.
+ * Errors: EINVAL, ENOMEM, EDEVICE. */
+int feast_nl_create(feast_nl_handle** h, int64_t n, int32_t nterms,
+                    const feast_nl_term* terms, int32_t precision, void* stream);
+
+/* Set the contour C and its quadrature (Algorithm 1 inputs), assemble every
+ * T(z_j) on the device and LU-factor it with partial pivoting (the shifts are
+ * fixed, so this is done once per contour and reused by every iteration).
+ *   c_re, c_im : center; ra, rb > 0 : semi-axes along the real and imaginary
+ *   axes (a circle when equal); 1 <= nc <= 1024 nodes; rule : enum feast_nl_rule.
+ * Errors: EINVAL, ENOMEM, ESINGULAR_NODE (a zero pivot: a node sits on an
+ * eigenvalue), EDEVICE. */
+int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra,
+                         double rb, int32_t nc, int32_t rule);
+
+/* Run Algorithm 1 with a subspace of m0 columns until every kept Ritz pair
+ * strictly inside C has relative residual
+ *     ||T(lambda_i) x_i||_2 / sum_t |scale_t f_t(lambda_i)| ||A_t||_2 <= tol,  ||x_i||_2 = 1,
+ * (tested after at least one filter application) or maxit executions of Step 1.
+ *   m0   : 1 <= m0 <= min(n, 112).
+ *   X0   : n x m0 complex128 row-major start block (host or device), or NULL to
+ *          draw one on the device from `seed` (complex normal, counter-based).
+ *   info : optional out summary.
+ * Polynomial T only (kind POW); EXP terms return EUNSUPPORTED.
+ * Returns OK, ENOT_CONVERGED, ETOO_MANY, ESINGULAR_NODE, EINVAL, ENOMEM,
+ * EDEVICE.  After OK, ENOT_CONVERGED or ETOO_MANY the last iterate is
+ * readable with feast_nl_get_eigpairs. */
+int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit,
+                   uint64_t seed, const void* X0, feast_nl_info* info);
+
+/* Copy out the kept Ritz pairs of the last solve, in the order of Step 2
+ * (increasing normalised radius).
+ *   capacity    : number of pairs the buffers hold.
+ *   m_out       : out, number of pairs written (<= capacity).
+ *   lambda      : 2*capacity doubles (re, im), host or device; may be NULL.
+ *   X           : n x capacity complex128 row-major (column i = x_i, unit 2-norm),
+ *                 host or device; may be NULL.
+ *   relres      : capacity doubles, host or device; may be NULL.
+ *   inside_only : nonzero to return only the pairs strictly inside C.
+ * Errors: EINVAL (no solve yet, bad capacity), EDEVICE. */
+int feast_nl_get_eigpairs(feast_nl_handle* h, int32_t capacity, int32_t* m_out,
+                          double* lambda, void* X, double* relres, int32_t inside_only);
+
+/* Quadrature nodes and weights in use (2*nc doubles each, host memory). */
+int feast_nl_get_nodes(feast_nl_handle* h, double* z, double* omega);
+
+/* Apply T(z_j)^{-1} with the stored factors of node j to an n x m block
+ * (complex128 row-major, host or device), in the handle's LU precision.
+ * Exposes the node solves of Step 4 for testing. */
+int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R, void* Y);
+
+/* One filter application (Step 4) without orthonormalisation: given unit
+ * Ritz vectors X (n x m) and values lambda (2*m doubles), compute
+ * T(X, Lambda) and Q = sum_j omega_j (X - T(z_j)^{-1} T(X, Lambda)) (z_j I - Lambda)^{-1}.
+ * X, Q: complex128 row-major, host or device; 1 <= m <= min(n, 112). */
+int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X,
+                          const double* lambda, void* Q);
+
+/* Projected coefficients of Step 1 for an n x m block Q (complex128 row-major):
+ * Ahat_p = sum_{t: f_t = lambda^p} scale_t Q^H A_t Q for p = 0..k, written as
+ * (k+1) consecutive m x m complex128 row-major matrices.  kmax_out receives k. */
+int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat,
+                     int32_t* kmax_out);
+
+/* Free the handle and all its device memory.  NULL is ignored. */
+void feast_nl_destroy(feast_nl_handle* h);
+
+/* Static text for a status code. */
+const char* feast_nl_strerror(int status);
+
+/* One-line detail of the last failure on the calling thread ("" if none). */
+const char* feast_nl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEAST_NL_H */

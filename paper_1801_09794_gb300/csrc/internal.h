@@ -1,0 +1,190 @@
+// Internal declarations shared by the library's translation units.
+// Storage convention inside the library: column-major, leading dimension given
+// explicitly, complex numbers interleaved (double2 = complex128, float2 = complex64).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on double2 / float2
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a) { return make_double2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+// c + a*b
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+// c - a*b
+__host__ __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__host__ __device__ __forceinline__ float cabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__host__ __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
+__host__ __device__ __forceinline__ float cabs(float2 a) { return hypotf(a.x, a.y); }
+__host__ __device__ __forceinline__ double cnorm2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float cnorm2(float2 a) { return a.x * a.x + a.y * a.y; }
+// 1/a with scaling against overflow
+__host__ __device__ __forceinline__ double2 crcp(double2 a) {
+    double s = fmax(fabs(a.x), fabs(a.y));
+    if (s == 0.0) return make_double2(0.0, 0.0);
+    double ar = a.x / s, ai = a.y / s, d = (ar * ar + ai * ai) * s;
+    return make_double2(ar / d, -ai / d);
+}
+__host__ __device__ __forceinline__ float2 crcp(float2 a) {
+    float s = fmaxf(fabsf(a.x), fabsf(a.y));
+    if (s == 0.0f) return make_float2(0.0f, 0.0f);
+    float ar = a.x / s, ai = a.y / s, d = (ar * ar + ai * ai) * s;
+    return make_float2(ar / d, -ai / d);
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return a * crcp(b); }
+
+template <typename T> struct cplx_real;
+template <> struct cplx_real<double2> { typedef double type; };
+template <> struct cplx_real<float2> { typedef float type; };
+
+template <typename T> __host__ __device__ __forceinline__ T cmake(double re, double im);
+template <> __host__ __device__ __forceinline__ double2 cmake<double2>(double re, double im) { return make_double2(re, im); }
+template <> __host__ __device__ __forceinline__ float2 cmake<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+__host__ __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__host__ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+template <typename T> __host__ __device__ __forceinline__ T from_d2(double2 a);
+template <> __host__ __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+namespace fnl {
+
+constexpr int kMaxM0 = 112;       // largest subspace the single-CTA reduced kernels hold
+constexpr int kMaxTerms = 16;
+constexpr int kMaxPow = 8;
+
+// Device-side description of one term of T(lambda).
+struct TermDev {
+    int kind;      // 0 pow, 1 exp
+    int p;
+    double tau;
+    double2 scale;
+    double norm;   // ||A_t||_2 estimate (1 for identity)
+    int aidx;      // index into the stacked dense matrices, -1 = identity
+    int pad;
+};
+
+// Per-iteration scalar results written by the device, read by the host.
+struct IterStatus {
+    int n_inside;
+    int n_conv;
+    int flags;         // bit 0: reduced QR hit its limit; bit 1: Ritz value on a node;
+                       // bit 2: Cholesky breakdown; bit 3: Newton fallback used
+    int pad;
+    double max_relres;
+};
+
+// ------------------------------------------------------------------ dense kernels (k_dense.cu)
+// C = alpha * op(A) * B + beta * C, column-major, batched over `batch` with element
+// strides sA, sB, sC.  opA: 0 = A (m x k), 1 = A^H (A stored k x m).
+template <typename T>
+cudaError_t gemm(cudaStream_t st, int opA, int m, int n, int k, T alpha, const T* A, int64_t lda,
+                 int64_t sA, const T* B, int64_t ldb, int64_t sB, T beta, T* C, int64_t ldc,
+                 int64_t sC, int batch);
+// Same product with the k dimension split into `splits` chunks summed in a fixed
+// order through `work` (splits * m * n elements); batch = 1.
+cudaError_t gemm_splitk_d(cudaStream_t st, int opA, int m, int n, int k, double2 alpha,
+                          const double2* A, int64_t lda, const double2* B, int64_t ldb,
+                          double2 beta, double2* C, int64_t ldc, double2* work, int splits);
+
+cudaError_t transpose_rowmajor_to_colmajor(cudaStream_t st, int64_t rows, int64_t cols,
+                                           const double2* src, int64_t lds, double2* dst,
+                                           int64_t ldd);
+cudaError_t transpose_colmajor_to_rowmajor(cudaStream_t st, int64_t rows, int64_t cols,
+                                           const double2* src, int64_t lds, double2* dst,
+                                           int64_t ldd);
+// y = A x (A n x n col-major) and y = A^H x
+cudaError_t gemv_n(cudaStream_t st, int64_t n, const double2* A, const double2* x, double2* y,
+                   double2* work);
+cudaError_t gemv_c(cudaStream_t st, int64_t n, const double2* A, const double2* x, double2* y);
+// out[0] = ||x||_2, x /= out[0] (if nonzero)
+cudaError_t normalize_vec(cudaStream_t st, int64_t n, double2* x, double* out);
+cudaError_t fill_ones(cudaStream_t st, int64_t n, double2* x);
+
+// T(z_j) = sum_t coef[t*nc + j] * A_t + diagc[j] * I for every node j (FP64 arithmetic,
+// result rounded once to T).
+template <typename T>
+cudaError_t assemble_nodes(cudaStream_t st, int64_t n, int nA, const double2* A,
+                           const double2* coef, const double2* diagc, int nc, T* F,
+                           int64_t strideF);
+
+// complex normal start block (counter-based: splitmix64 + Box-Muller), n x m col-major
+cudaError_t random_block(cudaStream_t st, int64_t n, int m, uint64_t seed, double2* X);
+// Y_j <- convert(R) for every node
+template <typename T>
+cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nc, T* Y,
+                          int64_t strideY);
+cudaError_t filter_coefficients(cudaStream_t st, int nc, int m, const double2* z,
+                                const double2* w, const double2* lam, double2* coef,
+                                double2* fsum, IterStatus* status);
+template <typename T>
+cudaError_t accumulate_filter(cudaStream_t st, int64_t n, int m, int nc, const double2* X,
+                              const T* Y, int64_t strideY, const double2* coef,
+                              const double2* fsum, double2* Q);
+// nrm[i] = ||col_i(X)||_2
+cudaError_t column_norms(cudaStream_t st, int64_t n, int m, const double2* X, int64_t ldx,
+                         double* nrm);
+// X[:, i] /= nrm[i]; Ycat[t*m + a, i] = Y[a, i] * scale_t f_t(lam_i) / nrm[i]
+cudaError_t ritz_scale(cudaStream_t st, int64_t n, int m, int nterms, const TermDev* terms,
+                       const double2* lam, const double* nrm, double2* X, const double2* Y,
+                       double2* Ycat);
+// relres_i and the convergence summary
+cudaError_t residual_summary(cudaStream_t st, int m, int nterms, const TermDev* terms,
+                             const double2* lam, const double* rnorm, double c_re, double c_im,
+                             double ra, double rb, double tol, double* relres,
+                             IterStatus* status);
+// Ahat_p = sum_{t: pow p} scale_t G_t  (G = Q^H [W_0 .. W_{T-1}], m x (T m))
+cudaError_t form_reduced(cudaStream_t st, int m, int nterms, int kmax, const TermDev* terms,
+                         const double2* G, double2* Ahat);
+template <typename T>
+cudaError_t to_double(cudaStream_t st, int64_t cnt, const T* src, double2* dst);
+// Y = I (m x m), ones[0..m) = 1
+cudaError_t set_identity(cudaStream_t st, int m, double2* Y, double* ones);
+cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nterms,
+                                const TermDev* terms, const double2* Q, double2* W);
+
+// ------------------------------------------------------------------ LU (k_lu.cu)
+template <typename T>
+cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
+                              int* piv, int nc, int* info);
+template <typename T>
+cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
+                             const int* piv, int nc, T* Y, int64_t strideY, int m);
+template <typename T> int lu_block_size();
+
+// ------------------------------------------------------------------ reduced problem (k_reduced.cu)
+// From Ahat (kmax+1 stacked m x m FP64), compute all k*m eigenvalues of the
+// companion pencil (FP32 Hessenberg QR), keep the m0 with the smallest normalised
+// radius, refine each by Newton's method on the m x m polynomial in FP64, and
+// return lam (m0) and unit vectors Yred (m x m0).
+cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat, int m0,
+                          double c_re, double c_im, double ra, double rb, void* work,
+                          double2* lam, double2* Yred, IterStatus* status);
+size_t reduced_work_bytes(int m, int kmax);
+// Cholesky G = R^H R (with diagonal shift), returns R^{-1} (upper) in Rinv.
+cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_rel,
+                         double2* Rinv, IterStatus* status);
+
+}  // namespace fnl

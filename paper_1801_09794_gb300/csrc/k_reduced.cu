@@ -1,0 +1,730 @@
+// Reduced problem of Steps 1-2 (Algorithm 1) on the GPU, and the small
+// Cholesky factorisation used by the orthonormalisation of Step 5.
+//
+// Step 1 asks for the eigenpairs of the projected polynomial
+//     Ahat(lambda) = sum_p lambda^p Ahat_p   (m x m, Ahat_p = Q^H A_p Q)
+// "by a simple linearization" (Sec. 4.2).  GB300 runs FP64 at ~1/64 of its
+// FP32 rate, and the eigenvalues of the linearisation come from a chain of
+// dependent plane rotations (one SM), so the work is staged:
+//   stage 1: eigenvalues of the block companion matrix
+//            C = [[-Ahat_k^{-1} Ahat_{k-1} ... -Ahat_k^{-1} Ahat_0], [I 0 ..], ...]
+//            (the first companion pencil of Sec. 2 with its leading block
+//            inverted) by Householder reduction to Hessenberg form and the
+//            implicit single-shift complex QR algorithm, in FP32, one CTA;
+//            Step 2 keeps the m Ritz values of smallest normalised radius; each
+//            is refined in FP64 by Newton's method on Ahat(lambda) y = 0 with the
+//            normalisation x^H y = 1 (nonlinear inverse iteration), one CTA per
+//            pair, which also yields the Ritz vector y;
+//   stage 2: only if stage 1 failed (a Newton step left its basin, or two kept
+//            values coincide -- clustered, ill-conditioned Ritz values that FP32
+//            cannot separate), the same companion / Hessenberg / QR / selection
+//            runs in FP64 and Newton polishes from those values.
+// Every stage-2 kernel reads the failure flag on the device and returns at once
+// when it is clear, so the stream never waits on the host.
+// Newton's fixed point is an exact eigenpair of the FP64 projected problem, so
+// the kept pairs carry FP64 accuracy either way.
+#include "internal.h"
+#include <cfloat>
+
+namespace fnl {
+namespace {
+
+template <typename R> struct cx;
+template <> struct cx<float> { typedef float2 type; static __device__ float eps() { return FLT_EPSILON; }
+                               static __device__ float tiny() { return FLT_MIN / FLT_EPSILON; } };
+template <> struct cx<double> { typedef double2 type; static __device__ double eps() { return DBL_EPSILON; }
+                                static __device__ double tiny() { return DBL_MIN / DBL_EPSILON; } };
+
+__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <typename C> __device__ __forceinline__ C cone();
+template <> __device__ __forceinline__ float2 cone<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double2 cone<double2>() { return make_double2(1.0, 0.0); }
+__device__ __forceinline__ float2 cfrom(double2 a, float2*) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 cfrom(double2 a, double2*) { return a; }
+
+template <typename R>
+__device__ typename cx<R>::type csqrt_(typename cx<R>::type z) {
+    typedef typename cx<R>::type C;
+    R r = hypot(z.x, z.y);
+    C out;
+    if (r == (R)0) { out.x = 0; out.y = 0; return out; }
+    R t = sqrt((R)0.5 * (fabs(z.x) + r));
+    if (z.x >= (R)0) { out.x = t; out.y = z.y / ((R)2 * t); }
+    else { out.x = fabs(z.y) / ((R)2 * t); out.y = copysign(t, z.y); }
+    return out;
+}
+
+// Two eigenvalues of [[a, b], [c, d]].
+template <typename R>
+__device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename cx<R>::type c,
+                       typename cx<R>::type d, typename cx<R>::type* e1,
+                       typename cx<R>::type* e2) {
+    typedef typename cx<R>::type C;
+    C h = cscale((R)0.5, a + d);
+    C q = cscale((R)0.5, a - d);
+    C disc = csqrt_<R>(q * q + b * c);
+    *e1 = h + disc;
+    *e2 = h - disc;
+}
+
+constexpr int kRedThreads = 1024;
+// flags word shared by the stages (device memory)
+constexpr int kNeed64 = 1;
+
+// ---------------------------------------------------------------------------
+// companion matrix: LU of Ahat_k, solve for the top block row (precision R).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) companion_kernel(
+    int m, int kmax, const double2* __restrict__ Ahat, typename cx<R>::type* __restrict__ C,
+    typename cx<R>::type* __restrict__ Lk, int* __restrict__ piv, int* redflag, int stage) {
+    typedef typename cx<R>::type CT;
+    if (stage == 2 && !(*redflag & kNeed64)) return;
+    const int N = kmax * m;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t mm = (int64_t)m * m;
+    __shared__ int s_p;
+    if (stage == 1) {
+        __syncthreads();
+        if (tid == 0) *redflag = 0;
+    }
+    for (int64_t e = tid; e < (int64_t)N * N; e += nt) {
+        int r = (int)(e % N), c = (int)(e / N);
+        CT v = czero<CT>();
+        if (r < m) {
+            int b = c / m, cc = c - b * m;
+            v = cfrom(Ahat[(int64_t)(kmax - 1 - b) * mm + r + (int64_t)cc * m], (CT*)nullptr);
+        } else if (c == r - m) {
+            v = cone<CT>();
+        }
+        C[e] = v;
+    }
+    for (int64_t e = tid; e < mm; e += nt) Lk[e] = cfrom(Ahat[(int64_t)kmax * mm + e], (CT*)nullptr);
+    __syncthreads();
+    for (int c = 0; c < m; ++c) {
+        if (tid < 32) {
+            R best = (R)-1;
+            int bi = c;
+            for (int r = c + tid; r < m; r += 32) {
+                R v = cabs1(Lk[r + c * m]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                R ov = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (tid == 0) { s_p = bi; piv[c] = bi; }
+        }
+        __syncthreads();
+        int p = s_p;
+        if (p != c)
+            for (int cc = tid; cc < m; cc += nt) {
+                CT a = Lk[c + cc * m];
+                Lk[c + cc * m] = Lk[p + cc * m];
+                Lk[p + cc * m] = a;
+            }
+        __syncthreads();
+        CT inv = crcp(Lk[c + c * m]);
+        int rem = m - c - 1;
+        for (int r = c + 1 + tid; r < m; r += nt) Lk[r + c * m] = Lk[r + c * m] * inv;
+        __syncthreads();
+        for (int e = tid; e < rem * rem; e += nt) {
+            int r = c + 1 + e % rem, cc = c + 1 + e / rem;
+            Lk[r + cc * m] = cfms(Lk[r + c * m], Lk[c + cc * m], Lk[r + cc * m]);
+        }
+        __syncthreads();
+    }
+    for (int col = tid; col < N; col += nt) {
+        CT* x = C + (int64_t)col * N;   // rows 0..m-1 of column col
+        for (int c = 0; c < m; ++c) {
+            int p = piv[c];
+            if (p != c) { CT t = x[c]; x[c] = x[p]; x[p] = t; }
+        }
+        for (int i = 0; i < m; ++i)
+            for (int r = i + 1; r < m; ++r) x[r] = cfms(Lk[r + i * m], x[i], x[r]);
+        for (int i = m - 1; i >= 0; --i) {
+            x[i] = x[i] * crcp(Lk[i + i * m]);
+            for (int r = 0; r < i; ++r) x[r] = cfms(Lk[r + i * m], x[i], x[r]);
+        }
+        for (int i = 0; i < m; ++i) x[i] = -x[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder reduction of C (N x N, in place) to upper Hessenberg form.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename cx<R>::type* __restrict__ C,
+                                                                 const int* redflag, int stage) {
+    typedef typename cx<R>::type CT;
+    if (stage == 2 && !(*redflag & kNeed64)) return;
+    extern __shared__ unsigned char smem_raw[];
+    CT* sv = reinterpret_cast<CT*>(smem_raw);   // N
+    __shared__ R red[32];
+    __shared__ CT s_alpha;
+    __shared__ R s_beta;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nt >> 5;
+    for (int j = 0; j + 2 < N; ++j) {
+        const int len = N - j - 1;
+        CT* xcol = C + (int64_t)j * N + (j + 1);
+        R s = 0;
+        for (int r = tid; r < len; r += nt) s += cnorm2(xcol[r]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            R t = 0;
+            for (int w = 0; w < nwarps; ++w) t += red[w];
+            CT x0 = xcol[0];
+            R ax0 = cabs(x0);
+            R nx = sqrt(t);
+            R tail = t - ax0 * ax0;
+            if (nx == (R)0 || !(tail > (R)1e-30 * t)) {
+                s_beta = 0;
+            } else {
+                CT ph;
+                if (ax0 > (R)0) { ph.x = x0.x / ax0; ph.y = x0.y / ax0; }
+                else { ph.x = 1; ph.y = 0; }
+                CT alpha;
+                alpha.x = -ph.x * nx;
+                alpha.y = -ph.y * nx;
+                CT v0 = x0 - alpha;
+                s_alpha = alpha;
+                s_beta = (R)2 / (tail + cnorm2(v0));
+                sv[0] = v0;
+            }
+        }
+        __syncthreads();
+        const R beta = s_beta;
+        if (beta == (R)0) continue;
+        for (int r = 1 + tid; r < len; r += nt) sv[r] = xcol[r];
+        __syncthreads();
+        for (int cc = j + 1 + warp; cc < N; cc += nwarps) {
+            CT* col = C + (int64_t)cc * N + (j + 1);
+            CT w = czero<CT>();
+            for (int r = lane; r < len; r += 32) w = cfma(cconj(sv[r]), col[r], w);
+            for (int o = 16; o > 0; o >>= 1) {
+                w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+                w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+            }
+            w = cscale(beta, w);
+            for (int r = lane; r < len; r += 32) col[r] = cfms(sv[r], w, col[r]);
+        }
+        if (tid == 0) xcol[0] = s_alpha;
+        for (int r = 1 + tid; r < len; r += nt) xcol[r] = czero<CT>();
+        __syncthreads();
+        for (int r = tid; r < N; r += nt) {
+            CT w = czero<CT>();
+            for (int c = 0; c < len; ++c) w = cfma(C[r + (int64_t)(j + 1 + c) * N], sv[c], w);
+            w = cscale(beta, w);
+            for (int c = 0; c < len; ++c) {
+                CT* p = C + r + (int64_t)(j + 1 + c) * N;
+                *p = cfms(w, cconj(sv[c]), *p);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// packed Hessenberg storage with one bulge row: column j holds rows 0..j+2
+__device__ __forceinline__ int64_t hoff(int i, int j) { return (int64_t)j * (j + 5) / 2 + i; }
+
+// ---------------------------------------------------------------------------
+// Eigenvalues of the Hessenberg matrix by the implicit single-shift complex QR
+// algorithm (one warp chases the bulge), then Step 2's selection.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) qr_select_kernel(
+    int N, int m0, const typename cx<R>::type* __restrict__ C, typename cx<R>::type* Hglobal,
+    int use_smem, double c_re, double c_im, double ra, double rb, double2* __restrict__ lam0,
+    double* __restrict__ gap, const int* redflag, int stage, IterStatus* status) {
+    typedef typename cx<R>::type CT;
+    if (stage == 2 && !(*redflag & kNeed64)) return;
+    extern __shared__ unsigned char smem_raw[];
+    CT* ev = reinterpret_cast<CT*>(smem_raw);   // N
+    CT* H = use_smem ? ev + N : Hglobal;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    for (int j = tid; j < N; j += nt)
+        for (int i = 0; i <= j + 2; ++i)
+            H[hoff(i, j)] = (i < N && i <= j + 1) ? C[i + (int64_t)j * N] : czero<CT>();
+    __syncthreads();
+    if (tid < 32) {
+        const R eps = cx<R>::eps(), tiny = cx<R>::tiny();
+        int hi = N - 1, its = 0, total = 0;
+        bool failed = false;
+        while (hi >= 0) {
+            if (hi == 0) { if (lane == 0) ev[0] = H[hoff(0, 0)]; break; }
+            int l = 0;
+            for (int base = hi; base >= 1; base -= 32) {
+                int i = base - lane;
+                bool neg = false;
+                if (i >= 1) {
+                    R h = cabs1(H[hoff(i, i - 1)]);
+                    R sd = cabs1(H[hoff(i - 1, i - 1)]) + cabs1(H[hoff(i, i)]);
+                    neg = (h <= eps * sd) || (h <= tiny);
+                }
+                unsigned b = __ballot_sync(0xffffffffu, neg);
+                if (b) { l = base - (__ffs(b) - 1); break; }
+            }
+            if (l > 0 && lane == 0) H[hoff(l, l - 1)] = czero<CT>();
+            __syncwarp();
+            if (l == hi) {
+                if (lane == 0) ev[hi] = H[hoff(hi, hi)];
+                __syncwarp();
+                hi -= 1; its = 0;
+                continue;
+            }
+            if (l == hi - 1) {
+                CT e1, e2;
+                eig2x2<R>(H[hoff(hi - 1, hi - 1)], H[hoff(hi - 1, hi)], H[hoff(hi, hi - 1)],
+                          H[hoff(hi, hi)], &e1, &e2);
+                if (lane == 0) { ev[hi - 1] = e1; ev[hi] = e2; }
+                __syncwarp();
+                hi -= 2; its = 0;
+                continue;
+            }
+            ++its; ++total;
+            if (total > 40 * N) { failed = true; break; }
+            CT mu;
+            CT d = H[hoff(hi, hi)];
+            if (its % 11 == 10) {
+                mu = d;
+                mu.x += (R)0.75 * cabs(H[hoff(hi, hi - 1)]);
+            } else {
+                CT e1, e2;
+                eig2x2<R>(H[hoff(hi - 1, hi - 1)], H[hoff(hi - 1, hi)], H[hoff(hi, hi - 1)], d, &e1, &e2);
+                mu = (cabs1(e1 - d) <= cabs1(e2 - d)) ? e1 : e2;
+            }
+            for (int k = l; k < hi; ++k) {
+                CT x, y;
+                if (k == l) { x = H[hoff(l, l)] - mu; y = H[hoff(l + 1, l)]; }
+                else        { x = H[hoff(k, k - 1)]; y = H[hoff(k + 1, k - 1)]; }
+                R ax = cabs(x), ay = cabs(y);
+                R c;
+                CT s;
+                if (ay == (R)0) { c = 1; s = czero<CT>(); }
+                else if (ax == (R)0) { c = 0; s.x = y.x / ay; s.y = -y.y / ay; }
+                else {
+                    R rho = hypot(ax, ay);
+                    c = ax / rho;
+                    CT ph;
+                    ph.x = x.x / ax;
+                    ph.y = x.y / ax;
+                    s = cscale((R)1 / rho, ph * cconj(y));
+                }
+                const int j0 = (k == l) ? l : k - 1;
+                for (int j = j0 + lane; j <= hi; j += 32) {
+                    CT h1 = H[hoff(k, j)], h2 = H[hoff(k + 1, j)];
+                    H[hoff(k, j)] = cscale(c, h1) + s * h2;
+                    H[hoff(k + 1, j)] = cscale(c, h2) - cconj(s) * h1;
+                }
+                __syncwarp();
+                if (k > l && lane == 0) H[hoff(k + 1, k - 1)] = czero<CT>();
+                __syncwarp();
+                const int i1 = min(k + 2, hi);
+                for (int i = l + lane; i <= i1; i += 32) {
+                    CT h1 = H[hoff(i, k)], h2 = H[hoff(i, k + 1)];
+                    H[hoff(i, k)] = cscale(c, h1) + cconj(s) * h2;
+                    H[hoff(i, k + 1)] = cscale(c, h2) - s * h1;
+                }
+                __syncwarp();
+            }
+        }
+        if (failed) {
+            for (int i = lane; i <= hi; i += 32) ev[i] = H[hoff(i, i)];
+            if (lane == 0) atomicOr(&status->flags, 1);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // Step 2: rank by (rho, Re, Im, index); keep the first m0
+    for (int i = tid; i < N; i += nt) {
+        CT e = ev[i];
+        double ex = e.x, ey = e.y;
+        bool fin = isfinite(ex) && isfinite(ey);
+        double rx = (ex - c_re) / ra, ry = (ey - c_im) / rb;
+        double rho = fin ? sqrt(rx * rx + ry * ry) : INFINITY;
+        double kx = fin ? ex : INFINITY, ky = fin ? ey : INFINITY;
+        int rank = 0;
+        double g = INFINITY;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            CT f = ev[j];
+            double fx = f.x, fy = f.y;
+            bool ffin = isfinite(fx) && isfinite(fy);
+            double sx = (fx - c_re) / ra, sy = (fy - c_im) / rb;
+            double rj = ffin ? sqrt(sx * sx + sy * sy) : INFINITY;
+            double jx = ffin ? fx : INFINITY, jy = ffin ? fy : INFINITY;
+            bool less = (rj < rho) || (rj == rho && (jx < kx || (jx == kx && (jy < ky || (jy == ky && j < i)))));
+            rank += less ? 1 : 0;
+            if (ffin && fin) g = fmin(g, hypot(fx - ex, fy - ey));
+        }
+        if (rank < m0) {
+            lam0[rank] = make_double2(ex, ey);
+            gap[rank] = g;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Newton refinement of one kept Ritz pair per CTA.
+// smem: T (m x m, col-major, LU in place), x, u, xf (m each), piv (m)
+// ---------------------------------------------------------------------------
+constexpr int kNewtonThreads = 256;
+constexpr int kNewtonMax = 8;
+
+__device__ void newton_build(int m, int kmax, const double2* __restrict__ Ahat, double2 lam,
+                             double2* T) {
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
+        double2 v = Ahat[(int64_t)kmax * mm + e];          // Horner in lambda
+        for (int p = kmax - 1; p >= 0; --p) v = cfma(v, lam, Ahat[(int64_t)p * mm + e]);
+        T[e] = v;
+    }
+}
+
+__device__ void newton_lu(int m, double2* T, int* piv, int* s_p) {
+    for (int c = 0; c < m; ++c) {
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = c;
+            for (int r = c + threadIdx.x; r < m; r += 32) {
+                double v = cabs1(T[r + c * m]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (threadIdx.x == 0) { *s_p = bi; piv[c] = bi; }
+        }
+        __syncthreads();
+        int p = *s_p;
+        if (p != c)
+            for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
+                double2 a = T[c + cc * m];
+                T[c + cc * m] = T[p + cc * m];
+                T[p + cc * m] = a;
+            }
+        __syncthreads();
+        double2 d = T[c + c * m];
+        if (d.x == 0.0 && d.y == 0.0) d = make_double2(1e-300, 0.0);
+        double2 inv = crcp(d);
+        int rem = m - c - 1;
+        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) T[r + c * m] = T[r + c * m] * inv;
+        __syncthreads();
+        if (threadIdx.x == 0) T[c + c * m] = d;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            int r = c + 1 + e % rem, cc = c + 1 + e / rem;
+            T[r + cc * m] = cfms(T[r + c * m], T[c + cc * m], T[r + cc * m]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void newton_solve(int m, const double2* T, const int* piv, double2* b) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0)
+            for (int c = 0; c < m; ++c) {
+                int p = piv[c];
+                if (p != c) { double2 t = b[c]; b[c] = b[p]; b[p] = t; }
+            }
+        __syncwarp();
+        for (int i = 0; i < m; ++i) {
+            double2 bi = b[i];
+            for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
+            __syncwarp();
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
+            __syncwarp();
+            double2 bi = b[i];
+            for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        red[32] = t;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
+    int m, int kmax, const double2* __restrict__ Ahat, const double2* __restrict__ lam0,
+    const double* __restrict__ gap, double2* __restrict__ lam, double2* __restrict__ Y,
+    int* redflag, int stage, IterStatus* status) {
+    if (stage == 2 && !(*redflag & kNeed64)) return;
+    extern __shared__ unsigned char smem_raw[];
+    double2* T = reinterpret_cast<double2*>(smem_raw);
+    double2* x = T + (int64_t)m * m;
+    double2* u = x + m;
+    double2* xf = u + m;
+    int* piv = reinterpret_cast<int*>(xf + m);
+    __shared__ double red[33];
+    __shared__ int s_p;
+    const int i = blockIdx.x;
+    const int64_t mm = (int64_t)m * m;
+    const double2 l0 = lam0[i];
+    double2 l = l0;
+    newton_build(m, kmax, Ahat, l, T);
+    __syncthreads();
+    newton_lu(m, T, piv, &s_p);
+    for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = make_double2(1.0, 0.0);
+    __syncthreads();
+    newton_solve(m, T, piv, x);
+    {
+        double s = 0.0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(x[r]);
+        s = sqrt(block_sum(s, red));
+        double inv = (s > 0.0 && isfinite(s)) ? 1.0 / s : 0.0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) { x[r] = inv * x[r]; xf[r] = x[r]; }
+        __syncthreads();
+    }
+    bool ok = true;
+    for (int it = 0; it < kNewtonMax; ++it) {
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {     // u = T'(l) x
+            double2 acc = make_double2(0.0, 0.0);
+            double2 lp = make_double2(1.0, 0.0);
+            for (int p = 1; p <= kmax; ++p) {
+                double2 row = make_double2(0.0, 0.0);
+                const double2* Ap = Ahat + (int64_t)p * mm;
+                for (int c = 0; c < m; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
+                acc = cfma(((double)p) * lp, row, acc);
+                lp = lp * l;
+            }
+            u[r] = acc;
+        }
+        __syncthreads();
+        newton_solve(m, T, piv, u);
+        double dre = 0.0, dim = 0.0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            double2 t = cconj(x[r]) * u[r];
+            dre += t.x;
+            dim += t.y;
+        }
+        dre = block_sum(dre, red);
+        dim = block_sum(dim, red);
+        double2 d = make_double2(dre, dim);
+        if (!(cabs(d) > 0.0) || !isfinite(d.x) || !isfinite(d.y)) { ok = false; break; }
+        double2 delta = crcp(d);
+        double s = 0.0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(u[r]);
+        s = sqrt(block_sum(s, red));
+        double inv = (s > 0.0 && isfinite(s)) ? 1.0 / s : 0.0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = inv * u[r];
+        __syncthreads();
+        l = l - delta;
+        if (cabs(delta) <= 4.0 * DBL_EPSILON * fmax(cabs(l), 1e-300)) break;
+        newton_build(m, kmax, Ahat, l, T);
+        __syncthreads();
+        newton_lu(m, T, piv, &s_p);
+    }
+    const double moved = cabs(l - l0);
+    const double lim = 0.3 * gap[i];
+    if (!ok || !isfinite(l.x) || !isfinite(l.y) || !(moved <= lim)) {
+        l = l0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = xf[r];
+        if (threadIdx.x == 0) {
+            atomicOr(&status->flags, 8);
+            atomicOr(redflag, kNeed64);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lam[i] = l;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) Y[r + (int64_t)i * m] = x[r];
+}
+
+// Two kept Ritz values that coincide after Newton mean stage 1 lost one.
+__global__ void duplicate_check_kernel(int m0, const double2* __restrict__ lam, int* redflag) {
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+        double2 a = lam[i];
+        for (int j = i + 1; j < m0; ++j) {
+            double2 b = lam[j];
+            double d = hypot(a.x - b.x, a.y - b.y);
+            if (d <= 1e-9 * fmax(hypot(a.x, a.y), 1e-300)) atomicOr(redflag, kNeed64);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky G + shift*trace(G)*I = R^H R and R^{-1}, one CTA, FP32 arithmetic:
+// the orthonormalisation only needs a well-conditioned basis of the same span,
+// and Q R^{-1} is applied in FP64 by the caller.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2* __restrict__ G,
+                                                           double shift_rel,
+                                                           double2* __restrict__ Rinv,
+                                                           IterStatus* status) {
+    extern __shared__ unsigned char smem_raw[];
+    float2* R = reinterpret_cast<float2*>(smem_raw);   // m x m col-major (upper used)
+    float2* X = R + m * m;                              // m x m col-major
+    __shared__ float s_tr;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < m; ++i) tr += G[i + (int64_t)i * m].x;
+        s_tr = (float)(shift_rel * tr);
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+        int r = e % m, c = e / m;
+        double2 g = G[e];
+        float2 v = make_float2((float)g.x, (float)g.y);
+        if (r == c) v = make_float2(v.x + s_tr, 0.0f);
+        R[e] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            float d = R[j + j * m].x;
+            if (!(d > 0.0f)) { atomicOr(&status->flags, 4); d = 1e-30f; }
+            R[j + j * m] = make_float2(sqrtf(d), 0.0f);
+        }
+        __syncthreads();
+        float rjj = R[j + j * m].x;
+        for (int c = j + 1 + tid; c < m; c += nt) R[j + c * m] = (1.0f / rjj) * R[j + c * m];
+        __syncthreads();
+        int rem = m - j - 1;
+        for (int e = tid; e < rem * rem; e += nt) {
+            int r = j + 1 + e % rem, c = j + 1 + e / rem;
+            if (r <= c) R[r + c * m] = cfms(cconj(R[j + r * m]), R[j + c * m], R[r + c * m]);
+        }
+        __syncthreads();
+    }
+    for (int c = tid; c < m; c += nt) {
+        float2* x = X + c * m;
+        for (int i = 0; i < m; ++i) x[i] = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
+        for (int i = c; i >= 0; --i) {
+            float2 xi = x[i] * crcp(R[i + i * m]);
+            x[i] = xi;
+            for (int r = 0; r < i; ++r) x[r] = cfms(R[r + i * m], xi, x[r]);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) Rinv[e] = make_double2(X[e].x, X[e].y);
+}
+
+size_t packed_elems(int N) { return (size_t)N * (N + 5) / 2 + 4; }
+constexpr int kMaxSmemPacked = 200 * 1024;
+
+// Workspace layout, every region 256-byte aligned.
+struct RedLayout {
+    size_t c32, lk32, c64, lk64, piv, h32, h64, lam0, gap, flag, total;
+};
+RedLayout red_layout(int m, int kmax) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t N = (size_t)kmax * m;
+    RedLayout L;
+    size_t o = 0;
+    L.c32 = o;  o = al(o + N * N * sizeof(float2));
+    L.lk32 = o; o = al(o + (size_t)m * m * sizeof(float2));
+    L.c64 = o;  o = al(o + N * N * sizeof(double2));
+    L.lk64 = o; o = al(o + (size_t)m * m * sizeof(double2));
+    L.piv = o;  o = al(o + (size_t)m * sizeof(int));
+    L.h32 = o;  o = al(o + packed_elems((int)N) * sizeof(float2));
+    L.h64 = o;  o = al(o + packed_elems((int)N) * sizeof(double2));
+    L.lam0 = o; o = al(o + (size_t)m * sizeof(double2));
+    L.gap = o;  o = al(o + (size_t)m * sizeof(double));
+    L.flag = o; o = al(o + 16);
+    L.total = o;
+    return L;
+}
+
+template <typename R>
+cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2* Ahat, int m0,
+                      double c_re, double c_im, double ra, double rb, unsigned char* base,
+                      const RedLayout& L, IterStatus* status) {
+    typedef typename cx<R>::type CT;
+    const int N = kmax * m;
+    CT* C = reinterpret_cast<CT*>(base + (sizeof(R) == 4 ? L.c32 : L.c64));
+    CT* Lk = reinterpret_cast<CT*>(base + (sizeof(R) == 4 ? L.lk32 : L.lk64));
+    CT* Hg = reinterpret_cast<CT*>(base + (sizeof(R) == 4 ? L.h32 : L.h64));
+    int* piv = reinterpret_cast<int*>(base + L.piv);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
+    double* gap = reinterpret_cast<double*>(base + L.gap);
+    companion_kernel<R><<<1, kRedThreads, 0, st>>>(m, kmax, Ahat, C, Lk, piv, flag, stage);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    hessenberg_kernel<R><<<1, kRedThreads, sizeof(CT) * N, st>>>(N, C, flag, stage);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    size_t hbytes = packed_elems(N) * sizeof(CT);
+    int use_smem = (hbytes + sizeof(CT) * N) <= (size_t)kMaxSmemPacked;
+    size_t smem = sizeof(CT) * N + (use_smem ? hbytes : 0);
+    qr_select_kernel<R><<<1, 256, smem, st>>>(N, m0, C, Hg, use_smem, c_re, c_im, ra, rb, lam0,
+                                              gap, flag, stage, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t reduced_work_bytes(int m, int kmax) { return red_layout(m, kmax).total; }
+
+cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat, int m0,
+                          double c_re, double c_im, double ra, double rb, void* work,
+                          double2* lam, double2* Yred, IterStatus* status) {
+    static bool attr_done = false;
+    cudaError_t e;
+    if (!attr_done) {
+        if ((e = cudaFuncSetAttribute(qr_select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(qr_select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(newton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024)) != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const RedLayout L = red_layout(m, kmax);
+    unsigned char* base = static_cast<unsigned char*>(work);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
+    double* gap = reinterpret_cast<double*>(base + L.gap);
+    const size_t nsm = sizeof(double2) * ((size_t)m * m + 3 * m) + sizeof(int) * m;
+    // stage 1: FP32 eigenvalues, FP64 Newton
+    if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
+    newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 1, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // stage 2 (device-side no-op unless stage 1 flagged a failure)
+    if ((e = run_stage<double>(st, 2, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
+    newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 2, status);
+    return cudaGetLastError();
+}
+
+cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_rel,
+                         double2* Rinv, IterStatus* status) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(chol_inverse_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    size_t smem = sizeof(float2) * 2 * (size_t)m * m;
+    chol_inverse_kernel<<<1, 512, smem, st>>>(m, G, shift_rel, Rinv, status);
+    return cudaGetLastError();
+}
+
+}  // namespace fnl
