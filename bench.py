@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the nonlinear FEAST filter library on one GB300 (or N replicas).
+
+Metric: eigenpairs/s at 1e-10 relative residual.  One step = one whole solve
+of the workload: node assembly + node LU factorisations (set_contour) and
+every iteration of Algorithm 1 until convergence (solve).  An eigenpair counts
+when it lies strictly inside the contour, its relative residual is <= 1e-10 and
+its eigenvalue is within 1e-10 (relative) of the stored reference eigenvalues.
+
+Default workload (qep_mixed_n4096): T(l) = l^2 M + l C + K, n = 4096, complex128
+inputs, 16 Gauss-Legendre nodes on the stored circle holding 64 eigenvalues,
+m0 = 96; node LUs and solves in FP32, everything else FP64-accurate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (the path has no exchange step):
+value = eigenpairs of all ranks / max over ranks of the step time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "eigenpairs/s at 1e-10 rel. residual"
+UNIT = "eigenpairs/s"
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (vector and tensor), nominal
+FP32_SIMT_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 lanes x FMA x 2.07 GHz
+TF32_OVER_BF16 = 1.1 / 2.25
+
+WORKLOADS = {
+    "qep_mixed_n4096": {"gen": "config2_qep", "n": 4096, "precision": "fp32", "tol": 1e-10,
+                        "maxit": 40},
+    "qep_plain_n256": {"gen": "config1_qep", "n": 256, "precision": "fp64", "tol": 1e-10,
+                       "maxit": 60},
+}
+
+
+# ---------------------------------------------------------------------------- ranks
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_over_ranks(value, op, device=None):
+    """All-reduce one float over the default process group (identity when alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------- inputs
+def load_workload(name):
+    import workloads
+    spec = WORKLOADS[name]
+    with open(os.path.join(ROOT, "tests", "golden", "contours.json")) as f:
+        c = json.load(f)[name]
+    problem = getattr(workloads, spec["gen"])(spec["n"], 0)
+    gold = np.array([complex(*x) for x in c["eigs_inside"]])
+    return spec, c, problem, gold
+
+
+def count_good(lam, rr, gold, center, radius, tol=1e-10):
+    """Kept pairs inside the circle with relres <= tol, matched one-to-one to the
+    reference eigenvalues within relative tol."""
+    used = np.zeros(len(gold), dtype=bool)
+    good = 0
+    for lv, r in zip(lam, rr):
+        if abs(lv - center) >= radius or not (r <= tol):
+            continue
+        d = np.abs(gold - lv) / np.abs(gold)
+        d[used] = np.inf
+        j = int(np.argmin(d))
+        if d[j] <= tol:
+            used[j] = True
+            good += 1
+    return good
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+        return out
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+
+        def find(keys, default):
+            for k in keys:
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+            return default, "fallback"
+        hbm, s1 = find(["hbm_gbs", "hbm_GBs", "hbm"], 6800.0)
+        bf16, s2 = find(["bf16_tflops", "bf16"], 1900.0)
+        bf16s, _ = find(["bf16_tflops_sustained"], bf16)
+        return {"hbm_gbs": hbm, "bf16_tflops": bf16, "bf16_tflops_sustained": bf16s,
+                "source": s1 if s1 == s2 else "mixed"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------- roofline
+def phase_work(name, spec, c, iters, nterms_dense):
+    """Algorithmic real flops of one phase over one solve (4M complex counting)."""
+    n, m0, nc = spec["n"], c["m0"], c["nc"]
+    if name == "lu":
+        return nc * (8.0 / 3.0) * n ** 3
+    if name == "apply":
+        return iters * nterms_dense * 8.0 * n * n * m0
+    if name == "solve":
+        return (iters - 1) * nc * 8.0 * n * n * m0
+    if name == "project":
+        return iters * 8.0 * n * m0 * (3 * m0)
+    return None
+
+
+def phase_peak(name, precision, pk, sm_mhz):
+    clk = (sm_mhz or 2070.0) / 2070.0
+    if name in ("lu", "solve") and precision == "fp32":
+        return FP32_SIMT_TFLOPS_AT_MAX * clk, "alu", "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x SM clock"
+    return FP64_NOMINAL_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s"
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1801_09794_gb300 as P
+    spec, c, problem, gold = load_workload(args.workload)
+    center = complex(*c["center"])
+    n, m0 = spec["n"], c["m0"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    # device-resident inputs for the kernel-side value
+    pdev = {"n": n, "terms": []}
+    for t in problem["terms"]:
+        A = t["A"]
+        pdev["terms"].append(dict(t, A=None if A is None else torch.from_numpy(A).to(dev)))
+    torch.cuda.synchronize()
+    s = P.FeastNL(pdev, spec["precision"], stream=stream.cuda_stream)
+    nterms_dense = sum(1 for t in problem["terms"] if t["A"] is not None)
+
+    def step(h):
+        h.set_contour(center, c["ra"], c["rb"], c["nc"], c["rule"])
+        st, info = h.solve(m0, tol=spec["tol"], maxit=spec["maxit"], seed=args.seed,
+                           allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        return info
+
+    for _ in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    barrier()
+    s.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = P.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = []
+    goods = []
+    for _ in range(args.steps):
+        infos.append(step(s))
+        lam, _, rr = s.get_eigpairs(inside_only=True, vectors=False)
+        goods.append(count_good(lam, rr, gold, center, c["ra"]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = P.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = s.get_profile()
+    s.close()
+    barrier()
+    ms_max = reduce_over_ranks(ms, "max", dev)
+    good_total = reduce_over_ranks(min(goods), "sum", dev)
+    value = good_total / (ms_max / 1e3)
+
+    # live per-phase roofline (CUDA events on the library's stream)
+    iters = infos[-1].iters
+    pk = peaks()
+    phases = {}
+    for name, (pms, pl) in prof.items():
+        if pms <= 0:
+            continue
+        w = phase_work(name, spec, c, iters, nterms_dense)
+        ent = {"ms_per_step": pms / args.steps, "launches_per_step": pl / args.steps}
+        if w is not None:
+            tf = w / (pms / args.steps / 1e3) / 1e12
+            peak, bound, why = phase_peak(name, spec["precision"], pk, clk.get("sm_mhz"))
+            ent.update(tflops=tf, peak_tflops=peak, frac=tf / peak, bound=bound)
+        phases[name] = ent
+    dom = max(phases, key=lambda k: phases[k]["ms_per_step"])
+    d = phases[dom]
+    if "tflops" in d:
+        peak, bound, why = phase_peak(dom, spec["precision"], pk, clk.get("sm_mhz"))
+        roof = {"kernel": f"phase '{dom}' (all its launches)", "bound": bound,
+                "achieved": d["tflops"], "peak": peak, "unit": "TFLOP/s", "frac": d["frac"],
+                "traffic": None, "peak_source": why,
+                "launches_per_step": d["launches_per_step"],
+                "avg_launch_ms": d["ms_per_step"] / max(d["launches_per_step"], 1)}
+    else:
+        roof = {"kernel": f"phase '{dom}'", "bound": "latency", "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+    lu = phases.get("lu", {})
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = run_e2e(args, P, torch, problem, spec, c, center, gold, dev)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64 LU + f64",
+           "data": "synthetic (seeded generator, no dataset)",
+           "config": {"workload": args.workload, "n": n, "degree": 2, "nc": c["nc"],
+                      "m0": m0, "count_inside": c["count"], "lu_precision": spec["precision"],
+                      "tol": spec["tol"], "iterations": iters,
+                      "eigenpairs_per_step": min(goods),
+                      "l2": "inputs larger than L2 (A_i 805 MB, node factors 2.1 GB)",
+                      "parallelism": f"replicas x{ws}"},
+           "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                      "reasons": clk["reasons"]},
+           "e2e": e2e, "gpu_launches": int(launches),
+           "roofline": roof,
+           "node_lu_tflops": lu.get("tflops"),
+           "phases": phases, "peaks": pk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, problem, spec, c, center, gold)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(args, P, torch, problem, spec, c, center, gold, dev):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    pinned = {"n": problem["n"], "terms": []}
+    h2d = 0
+    for t in problem["terms"]:
+        A = t["A"]
+        if A is not None:
+            A = torch.from_numpy(A).pin_memory()
+            h2d += A.numel() * 16
+        pinned["terms"].append(dict(t, A=A))
+    m0 = c["m0"]
+    steps = max(1, min(args.steps, 5))
+    times = []
+    goods = []
+    d2h = 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = P.FeastNL(pinned, spec["precision"])
+        h.set_contour(center, c["ra"], c["rb"], c["nc"], c["rule"])
+        h.solve(m0, tol=spec["tol"], maxit=spec["maxit"], seed=args.seed,
+                allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        lam, X, rr = h.get_eigpairs(inside_only=True, vectors=True)
+        h.close()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if i > 0:                      # first call warms the allocator and module
+            times.append(t1 - t0)
+            goods.append(count_good(lam, rr, gold, center, c["ra"]))
+            d2h = X.nbytes + lam.nbytes + rr.nbytes
+    t = reduce_over_ranks(statistics.median(times), "max", dev)
+    g = reduce_over_ranks(min(goods), "sum", dev)
+    return {"value": g / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "s_per_step": t, "steps": steps}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_solve(problem, c, center, spec, X0):
+    import oracle as O
+    t0 = time.perf_counter()
+    r = O.nlfeast(problem, {"center": center, "ra": c["ra"], "rb": c["rb"], "nc": c["nc"],
+                            "rule": c["rule"]}, c["m0"], X0, tol=spec["tol"], maxit=spec["maxit"])
+    return time.perf_counter() - t0, r
+
+
+def cpu_baseline(args, problem, spec, c, center, gold):
+    """The FP64 oracle, as it stands, on the host cores: one whole solve of the
+    workload (node LUs + every iteration), started from the same kind of block."""
+    from workloads import start_block
+    X0 = start_block(problem["n"], c["m0"], args.seed)
+    t, r = oracle_solve(problem, c, center, spec, X0)
+    good = count_good(r["lam"], r["relres"], gold, center, c["ra"])
+    return {"value": good / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"one whole solve of {args.workload} ({r['iters']} iterations, "
+                      f"{c['nc']} node LUs) in {t:.1f} s",
+            "seconds": t}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    spec, c, problem, gold = load_workload(args.workload)
+    center = complex(*c["center"])
+    from workloads import start_block
+    X0 = start_block(problem["n"], c["m0"], args.seed)
+    # each step is one whole oracle solve (~20 s for the default workload), so the
+    # arm caps warm-up at 1 and steps at 3 to end within a few minutes
+    w, k = min(args.warmup, 1), min(args.steps, 3)
+    for _ in range(w):
+        oracle_solve(problem, c, center, spec, X0)
+    ts, goods, iters = [], [], 0
+    for _ in range(k):
+        t, r = oracle_solve(problem, c, center, spec, X0)
+        ts.append(t)
+        goods.append(count_good(r["lam"], r["relres"], gold, center, c["ra"]))
+        iters = r["iters"]
+    t = statistics.mean(ts)
+    v = min(goods) / t
+    sample = f"{k} whole oracle solves of {args.workload} ({iters} iterations each)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": k, "warmup": w, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "n": problem["n"], "nc": c["nc"], "m0": c["m0"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qep_mixed_n4096")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

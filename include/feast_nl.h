@@ -176,6 +176,34 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X,
 int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat,
                      int32_t* kmax_out);
 
+/* ---- measurement ------------------------------------------------------------ */
+/* Phases of the path, for feast_nl_get_profile. */
+enum feast_nl_phase {
+    FEAST_NL_PH_ASSEMBLE = 0,  /* T(z_j) for all nodes                          */
+    FEAST_NL_PH_LU = 1,        /* node LU factorisations                          */
+    FEAST_NL_PH_APPLY = 2,     /* W_t = A_t Q (FP64)                              */
+    FEAST_NL_PH_PROJECT = 3,   /* Q^H W_t and the projected coefficients          */
+    FEAST_NL_PH_REDUCED = 4,   /* reduced eigenproblem, selection, Ritz vectors y */
+    FEAST_NL_PH_RITZ = 5,      /* X = Q Y, T(X, Lambda), residual test            */
+    FEAST_NL_PH_SOLVE = 6,     /* node solves T(z_j)^{-1} T(X, Lambda)            */
+    FEAST_NL_PH_ACCUM = 7,     /* quadrature weights and accumulation into Q      */
+    FEAST_NL_PH_ORTH = 8,      /* orthonormalisation (Steps 0 and 5)              */
+    FEAST_NL_PH_IO = 9,        /* start-block upload                              */
+    FEAST_NL_NPHASES = 10
+};
+
+/* Turn per-phase device timing on (nonzero) or off, and reset its totals.
+ * When on, every phase of set_contour and solve is bracketed by CUDA events
+ * on the handle's stream. */
+int feast_nl_set_profiling(feast_nl_handle* h, int32_t on);
+
+/* Totals since the last feast_nl_set_profiling: device milliseconds and kernel
+ * launches per phase (arrays of nphases entries, host memory, may be NULL). */
+int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_t* launches);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t feast_nl_launch_count(void);
+
 /* Free the handle and all its device memory.  NULL is ignored. */
 void feast_nl_destroy(feast_nl_handle* h);
 

@@ -30,7 +30,9 @@ PRECISIONS = {"fp64": FEAST_NL_FP64, "fp32": FEAST_NL_FP32}
 # every exported symbol of include/feast_nl.h
 EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_nl_get_eigpairs",
            "feast_nl_get_nodes", "feast_nl_node_solve", "feast_nl_filter_apply",
-           "feast_nl_project", "feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error"]
+           "feast_nl_project", "feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
+           "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count"]
+PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
 
 class feast_nl_term(ctypes.Structure):
@@ -80,8 +82,13 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_strerror.restype = ctypes.c_char_p
     lib.feast_nl_last_error.argtypes = []
     lib.feast_nl_last_error.restype = ctypes.c_char_p
+    lib.feast_nl_set_profiling.argtypes = [P, I32]
+    lib.feast_nl_get_profile.argtypes = [P, I32, P, P]
+    lib.feast_nl_launch_count.argtypes = []
+    lib.feast_nl_launch_count.restype = ctypes.c_int64
     for name in EXPORTS:
-        if name not in ("feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error"):
+        if name not in ("feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
+                        "feast_nl_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -93,6 +100,11 @@ def strerror(status):
 
 def last_error():
     return load_library().feast_nl_last_error().decode()
+
+
+def launch_count():
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().feast_nl_launch_count())
 
 
 def _ptr(a):
@@ -194,6 +206,17 @@ class FeastNL:
         m = mo.value
         lamc = lam[0:2 * m:2] + 1j * lam[1:2 * m:2]
         return lamc, (X[:, :m] if vectors else None), rr[:m]
+
+    def set_profiling(self, on=True):
+        _check(self.lib.feast_nl_set_profiling(self.h, int(bool(on))), "feast_nl_set_profiling")
+
+    def get_profile(self):
+        """{phase: (device ms, launches)} accumulated since set_profiling."""
+        ms = np.zeros(len(PHASES))
+        ln = np.zeros(len(PHASES), dtype=np.int64)
+        _check(self.lib.feast_nl_get_profile(self.h, len(PHASES), ms.ctypes.data, ln.ctypes.data),
+               "feast_nl_get_profile")
+        return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(PHASES)}
 
     def get_nodes(self):
         z = np.zeros(2 * self.nc)

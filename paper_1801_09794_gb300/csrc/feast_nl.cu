@@ -159,11 +159,57 @@ struct feast_nl_handle {
     bool have_result = false;
     int m_last = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // optional per-phase device timing
+    struct Mark { int phase; cudaEvent_t a, b; uint64_t l0, l1; };
+    bool prof = false;
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    double prof_ms[FEAST_NL_NPHASES] = {0};
+    int64_t prof_launches[FEAST_NL_NPHASES] = {0};
 
     size_t lu_elem() const { return precision == FEAST_NL_FP64 ? sizeof(double2) : sizeof(float2); }
 };
 
 namespace {
+
+cudaEvent_t prof_event(feast_nl_handle* h) {
+    if (h->pool_used == h->pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->pool.push_back(e);
+    }
+    return h->pool[h->pool_used++];
+}
+// Scoped device-time measurement of one phase (no-op unless profiling is on).
+struct Phase {
+    feast_nl_handle* h;
+    int idx = -1;
+    Phase(feast_nl_handle* hh, int phase) : h(hh) {
+        if (!h->prof) return;
+        cudaEvent_t a = prof_event(h), b = prof_event(h);
+        if (!a || !b) return;
+        cudaEventRecord(a, h->st);
+        h->marks.push_back({phase, a, b, launch_count(), 0});
+        idx = (int)h->marks.size() - 1;
+    }
+    ~Phase() {
+        if (idx < 0) return;
+        cudaEventRecord(h->marks[idx].b, h->st);
+        h->marks[idx].l1 = launch_count();
+    }
+};
+void prof_flush(feast_nl_handle* h) {
+    if (!h->prof || h->marks.empty()) return;
+    cudaStreamSynchronize(h->st);
+    for (auto& mk : h->marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) h->prof_ms[mk.phase] += ms;
+        h->prof_launches[mk.phase] += (int64_t)(mk.l1 - mk.l0);
+    }
+    h->marks.clear();
+    h->pool_used = 0;
+}
 
 void release_workspace(feast_nl_handle* h) {
     dfree(h->dQ); dfree(h->dQt); dfree(h->dX); dfree(h->dR); dfree(h->dW);
@@ -252,6 +298,7 @@ int apply_terms(feast_nl_handle* h, const double2* Q, int m, double2* W) {
 
 // Q <- Q R^{-1} twice (CholQR with a small diagonal shift), columns pre-equilibrated.
 int orthonormalize(feast_nl_handle* h, int m) {
+    Phase ph(h, FEAST_NL_PH_ORTH);
     const int64_t n = h->n;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     CK(column_norms(h->st, n, m, h->dQ, n, h->dNu));
@@ -272,12 +319,22 @@ int ritz_and_residual(feast_nl_handle* h, int m, double tol) {
     const int64_t n = h->n;
     const int T = h->nterms;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-    CKS(apply_terms(h, h->dQ, m, h->dW));
-    CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, h->dQ, n, h->dW, n, zero, h->dG, m,
-                     h->dSplit, h->splits));
-    CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
-    CK(reduced_solve(h->st, m, h->kmax, h->dAhat, m, h->c_re, h->c_im, h->ra, h->rb, h->dRed,
-                     h->dLam, h->dYred, h->dStatus));
+    {
+        Phase ph(h, FEAST_NL_PH_APPLY);
+        CKS(apply_terms(h, h->dQ, m, h->dW));
+    }
+    {
+        Phase ph(h, FEAST_NL_PH_PROJECT);
+        CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, h->dQ, n, h->dW, n, zero, h->dG, m,
+                         h->dSplit, h->splits));
+        CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
+    }
+    {
+        Phase ph(h, FEAST_NL_PH_REDUCED);
+        CK(reduced_solve(h->st, m, h->kmax, h->dAhat, m, h->c_re, h->c_im, h->ra, h->rb, h->dRed,
+                         h->dLam, h->dYred, h->dStatus));
+    }
+    Phase ph(h, FEAST_NL_PH_RITZ);
     CK(gemm<double2>(h->st, 0, (int)n, m, m, one, h->dQ, n, 0, h->dYred, m, 0, zero, h->dX, n, 0,
                      1));
     CK(column_norms(h->st, n, m, h->dX, n, h->dNu));
@@ -293,22 +350,32 @@ int ritz_and_residual(feast_nl_handle* h, int m, double tol) {
 // Step 4 for the current (X, Lambda, R): node solves and weighted accumulation into Q.
 int filter_step(feast_nl_handle* h, int m) {
     const int64_t n = h->n;
-    CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
-                           h->dStatus));
     if (h->precision == FEAST_NL_FP64) {
         double2* Y = static_cast<double2*>(h->dY);
-        CK(broadcast_rhs<double2>(h->st, n, m, h->dR, h->nc, Y, n * m));
-        CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
-                                     static_cast<const double2*>(h->dF), n * n, h->dpiv, h->nc, Y,
-                                     n * m, m));
+        {
+            Phase ph(h, FEAST_NL_PH_SOLVE);
+            CK(broadcast_rhs<double2>(h->st, n, m, h->dR, h->nc, Y, n * m));
+            CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
+                                         static_cast<const double2*>(h->dF), n * n, h->dpiv,
+                                         h->nc, Y, n * m, m));
+        }
+        Phase ph(h, FEAST_NL_PH_ACCUM);
+        CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
+                               h->dStatus));
         CK(accumulate_filter<double2>(h->st, n, m, h->nc, h->dX, Y, n * m, h->dCoef, h->dFsum,
                                       h->dQ));
     } else {
         float2* Y = static_cast<float2*>(h->dY);
-        CK(broadcast_rhs<float2>(h->st, n, m, h->dR, h->nc, Y, n * m));
-        CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
-                                    static_cast<const float2*>(h->dF), n * n, h->dpiv, h->nc, Y,
-                                    n * m, m));
+        {
+            Phase ph(h, FEAST_NL_PH_SOLVE);
+            CK(broadcast_rhs<float2>(h->st, n, m, h->dR, h->nc, Y, n * m));
+            CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
+                                        static_cast<const float2*>(h->dF), n * n, h->dpiv, h->nc,
+                                        Y, n * m, m));
+        }
+        Phase ph(h, FEAST_NL_PH_ACCUM);
+        CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
+                               h->dStatus));
         CK(accumulate_filter<float2>(h->st, n, m, h->nc, h->dX, Y, n * m, h->dCoef, h->dFsum,
                                      h->dQ));
     }
@@ -353,6 +420,28 @@ const char* feast_nl_strerror(int status) {
 
 const char* feast_nl_last_error(void) { return g_last_error.c_str(); }
 
+int64_t feast_nl_launch_count(void) { return (int64_t)launch_count(); }
+
+int feast_nl_set_profiling(feast_nl_handle* h, int32_t on) {
+    CKS(validate_handle(h));
+    h->prof = on != 0;
+    h->marks.clear();
+    h->pool_used = 0;
+    for (int i = 0; i < FEAST_NL_NPHASES; ++i) { h->prof_ms[i] = 0.0; h->prof_launches[i] = 0; }
+    return FEAST_NL_OK;
+}
+
+int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_t* launches) {
+    CKS(validate_handle(h));
+    if (nphases < 0) return fail(FEAST_NL_EINVAL, "nphases < 0");
+    prof_flush(h);
+    for (int i = 0; i < nphases && i < FEAST_NL_NPHASES; ++i) {
+        if (ms) ms[i] = h->prof_ms[i];
+        if (launches) launches[i] = h->prof_launches[i];
+    }
+    return FEAST_NL_OK;
+}
+
 void feast_nl_destroy(feast_nl_handle* h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
@@ -366,6 +455,7 @@ void feast_nl_destroy(feast_nl_handle* h) {
     dfree(h->dinfo);
     dfree(h->dStatus);
     if (h->hStatus) cudaFreeHost(h->hStatus);
+    for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
@@ -580,12 +670,20 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     CK(cudaEventRecord(h->ev0, h->st));
     if (h->precision == FEAST_NL_FP64) {
         double2* F = static_cast<double2*>(h->dF);
-        CK(assemble_nodes<double2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
+        {
+            Phase ph(h, FEAST_NL_PH_ASSEMBLE);
+            CK(assemble_nodes<double2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
+        }
+        Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<double2>(h->st, n, lu_block_size<double2>(), F, n * n, h->dpiv, nc,
                                       h->dinfo));
     } else {
         float2* F = static_cast<float2*>(h->dF);
-        CK(assemble_nodes<float2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
+        {
+            Phase ph(h, FEAST_NL_PH_ASSEMBLE);
+            CK(assemble_nodes<float2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
+        }
+        Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<float2>(h->st, n, lu_block_size<float2>(), F, n * n, h->dpiv, nc,
                                      h->dinfo));
     }
@@ -596,6 +694,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->ms_factor = ms;
+    prof_flush(h);
     dfree(dcoef);
     dfree(ddiag);
     for (int j = 0; j < nc; ++j)
@@ -622,8 +721,11 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     const int m = m0;
     CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
     CK(cudaEventRecord(h->ev0, h->st));
-    if (X0) CKS(load_block(h, X0, m, h->dQ));
-    else CK(random_block(h->st, h->n, m, seed, h->dQ));
+    {
+        Phase ph(h, FEAST_NL_PH_IO);
+        if (X0) CKS(load_block(h, X0, m, h->dQ));
+        else CK(random_block(h->st, h->n, m, seed, h->dQ));
+    }
     CKS(orthonormalize(h, m));                                  // Step 0
     int it = 0;
     bool converged = false;
@@ -652,6 +754,7 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     CK(cudaEventSynchronize(h->ev1));
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    prof_flush(h);
     h->have_result = true;
     h->m_last = m;
     int status = converged ? FEAST_NL_OK : FEAST_NL_ENOT_CONVERGED;

@@ -96,6 +96,10 @@ struct IterStatus {
     double max_relres;
 };
 
+// Process-wide count of kernel launches issued by this library.
+void note_launch(int k = 1);
+uint64_t launch_count();
+
 // ------------------------------------------------------------------ dense kernels (k_dense.cu)
 // C = alpha * op(A) * B + beta * C, column-major, batched over `batch` with element
 // strides sA, sB, sC.  opA: 0 = A (m x k), 1 = A^H (A stored k x m).

@@ -1,8 +1,13 @@
 // Dense building blocks of the filter step: complex GEMM, node assembly,
 // filter accumulation and the bookkeeping of Steps 2-4 (Algorithm 1).
 #include "internal.h"
+#include <atomic>
 
 namespace fnl {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ============================================================================
 // Complex GEMM, SIMT, 64x64 output tile per 256-thread CTA, 4x4 per thread.
@@ -114,6 +119,7 @@ cudaError_t gemm(cudaStream_t st, int opA, int m, int n, int k, T alpha, const T
     if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
     dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, batch);
     int kc = k > 0 ? k : 1;
+    note_launch();
     if (opA == 0)
         gemm_kernel<T, 0><<<grid, 256, 0, st>>>(m, n, k, kc, 1, alpha, A, lda, sA, B, ldb, sB,
                                                 beta, C, ldc, sC);
@@ -142,6 +148,7 @@ cudaError_t gemm_splitk_d(cudaStream_t st, int opA, int m, int n, int k, double2
     dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     int64_t mn = (int64_t)m * n;
+    note_launch();
     if (opA == 0)
         gemm_kernel<double2, 0><<<grid, 256, 0, st>>>(m, n, k, kchunk, splits, one, A, lda, 0, B,
                                                       ldb, 0, zero, work, m, mn);
@@ -150,6 +157,7 @@ cudaError_t gemm_splitk_d(cudaStream_t st, int opA, int m, int n, int k, double2
                                                       ldb, 0, zero, work, m, mn);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    note_launch();
     reduce_splits_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(m, n, splits, alpha, work,
                                                                        beta, C, ldc);
     return cudaGetLastError();
@@ -196,6 +204,7 @@ cudaError_t transpose_rowmajor_to_colmajor(cudaStream_t st, int64_t rows, int64_
                                            int64_t ldd) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    note_launch();
     transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, lds, dst, ldd, 1);
     return cudaGetLastError();
 }
@@ -204,6 +213,7 @@ cudaError_t transpose_colmajor_to_rowmajor(cudaStream_t st, int64_t rows, int64_
                                            int64_t ldd) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    note_launch();
     transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, lds, dst, ldd, 0);
     return cudaGetLastError();
 }
@@ -274,19 +284,24 @@ __global__ void fill_ones_kernel(int64_t n, double2* x) {
 cudaError_t gemv_n(cudaStream_t st, int64_t n, const double2* A, const double2* x, double2* y,
                    double2* work) {
     dim3 grid((unsigned)((n + 127) / 128), kGemvSplit);
+    note_launch();
     gemv_n_kernel<<<grid, 128, 0, st>>>(n, A, x, work);
+    note_launch();
     gemv_n_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, work, y);
     return cudaGetLastError();
 }
 cudaError_t gemv_c(cudaStream_t st, int64_t n, const double2* A, const double2* x, double2* y) {
+    note_launch();
     gemv_c_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, A, x, y);
     return cudaGetLastError();
 }
 cudaError_t normalize_vec(cudaStream_t st, int64_t n, double2* x, double* out) {
+    note_launch();
     normalize_kernel<<<1, 1024, 0, st>>>(n, x, out);
     return cudaGetLastError();
 }
 cudaError_t fill_ones(cudaStream_t st, int64_t n, double2* x) {
+    note_launch();
     fill_ones_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x);
     return cudaGetLastError();
 }
@@ -332,11 +347,11 @@ cudaError_t assemble_nodes(cudaStream_t st, int64_t n, int nA, const double2* A,
     int64_t want = (nn + 255) / 256;
     int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
     switch (nA) {
-        case 1: assemble_kernel<T, 1><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
-        case 2: assemble_kernel<T, 2><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
-        case 3: assemble_kernel<T, 3><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
-        case 4: assemble_kernel<T, 4><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
-        default: assemble_kernel<T, 0><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+        case 1: note_launch(); assemble_kernel<T, 1><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+        case 2: note_launch(); assemble_kernel<T, 2><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+        case 3: note_launch(); assemble_kernel<T, 3><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+        case 4: note_launch(); assemble_kernel<T, 4><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+        default: note_launch(); assemble_kernel<T, 0><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
     }
     return cudaGetLastError();
 }
@@ -414,6 +429,7 @@ __global__ void accumulate_kernel(int64_t n, int m, int nc, const double2* __res
 
 cudaError_t random_block(cudaStream_t st, int64_t n, int m, uint64_t seed, double2* X) {
     int64_t tot = n * m;
+    note_launch();
     random_block_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, seed, X);
     return cudaGetLastError();
 }
@@ -421,6 +437,7 @@ template <typename T>
 cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nc, T* Y,
                           int64_t strideY) {
     int64_t nm = n * m;
+    note_launch();
     broadcast_rhs_kernel<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, R, nc, Y, strideY);
     return cudaGetLastError();
 }
@@ -431,6 +448,7 @@ template cudaError_t broadcast_rhs<float2>(cudaStream_t, int64_t, int, const dou
 cudaError_t filter_coefficients(cudaStream_t st, int nc, int m, const double2* z,
                                 const double2* w, const double2* lam, double2* coef,
                                 double2* fsum, IterStatus* status) {
+    note_launch();
     filter_coef_kernel<<<(m + 127) / 128, 128, 0, st>>>(nc, m, z, w, lam, coef, fsum, status);
     return cudaGetLastError();
 }
@@ -439,6 +457,7 @@ cudaError_t accumulate_filter(cudaStream_t st, int64_t n, int m, int nc, const d
                               const T* Y, int64_t strideY, const double2* coef,
                               const double2* fsum, double2* Q) {
     int64_t nm = n * m;
+    note_launch();
     accumulate_kernel<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(n, m, nc, X, Y, strideY,
                                                                       coef, fsum, Q);
     return cudaGetLastError();
@@ -560,6 +579,7 @@ __global__ void copy_identity_kernel(int64_t nm, int nterms, const TermDev* __re
 
 cudaError_t column_norms(cudaStream_t st, int64_t n, int m, const double2* X, int64_t ldx,
                          double* nrm) {
+    note_launch();
     column_norms_kernel<<<m, 256, 0, st>>>(n, X, ldx, nrm);
     return cudaGetLastError();
 }
@@ -567,18 +587,23 @@ cudaError_t ritz_scale(cudaStream_t st, int64_t n, int m, int nterms, const Term
                        const double2* lam, const double* nrm, double2* X, const double2* Y,
                        double2* Ycat) {
     int64_t nm = n * m;
-    if (nm > 0)
+    if (nm > 0) {
+        note_launch();
         scale_columns_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(n, m, nrm, X);
+    }
     int64_t tot = (int64_t)nterms * m * m;
-    if (tot > 0)
+    if (tot > 0) {
+        note_launch();
         ycat_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, nterms, terms, lam, nrm, Y,
                                                                    Ycat);
+    }
     return cudaGetLastError();
 }
 cudaError_t residual_summary(cudaStream_t st, int m, int nterms, const TermDev* terms,
                              const double2* lam, const double* rnorm, double c_re, double c_im,
                              double ra, double rb, double tol, double* relres,
                              IterStatus* status) {
+    note_launch();
     residual_summary_kernel<<<1, 128, 0, st>>>(m, nterms, terms, lam, rnorm, c_re, c_im, ra, rb,
                                                tol, relres, status);
     return cudaGetLastError();
@@ -586,6 +611,7 @@ cudaError_t residual_summary(cudaStream_t st, int m, int nterms, const TermDev* 
 cudaError_t form_reduced(cudaStream_t st, int m, int nterms, int kmax, const TermDev* terms,
                          const double2* G, double2* Ahat) {
     int64_t tot = (int64_t)(kmax + 1) * m * m;
+    note_launch();
     form_reduced_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, nterms, kmax, terms, G,
                                                                       Ahat);
     return cudaGetLastError();
@@ -593,6 +619,7 @@ cudaError_t form_reduced(cudaStream_t st, int m, int nterms, int kmax, const Ter
 cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nterms,
                                 const TermDev* terms, const double2* Q, double2* W) {
     int64_t nm = n * m;
+    note_launch();
     copy_identity_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, nterms, terms, Q, W);
     return cudaGetLastError();
 }
@@ -614,12 +641,14 @@ __global__ void identity_kernel(int m, double2* __restrict__ Y, double* __restri
 }  // namespace
 template <typename T>
 cudaError_t to_double(cudaStream_t st, int64_t cnt, const T* src, double2* dst) {
+    note_launch();
     to_double_kernel<T><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, src, dst);
     return cudaGetLastError();
 }
 template cudaError_t to_double<double2>(cudaStream_t, int64_t, const double2*, double2*);
 template cudaError_t to_double<float2>(cudaStream_t, int64_t, const float2*, double2*);
 cudaError_t set_identity(cudaStream_t st, int m, double2* Y, double* ones) {
+    note_launch();
     identity_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(m, Y, ones);
     return cudaGetLastError();
 }

@@ -198,10 +198,12 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
     const T minus1 = cmake<T>(-1.0, 0.0), one = cmake<T>(1.0, 0.0);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
+        note_launch();
         lu_panel_kernel<T><<<nc, 1024, 0, st>>>(n, (int)k0, jb, F, n, strideF, piv, info);
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
             dim3 g((unsigned)((rest + kTrsmCols - 1) / kTrsmCols), nc);
+            note_launch();
             swap_trsm_lower_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(
                 n, (int)k0, jb, F, n, strideF, piv, F, n, strideF, (int)(k0 + jb), (int)rest);
             e = gemm<T>(st, 0, (int)rest, (int)rest, jb, minus1, F + (k0 + jb) + k0 * n, n,
@@ -222,6 +224,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     dim3 g((unsigned)((m + kTrsmCols - 1) / kTrsmCols), nc);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
+        note_launch();
         swap_trsm_lower_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(
             n, (int)k0, jb, F, n, strideF, piv, Y, n, strideY, 0, m);
         int64_t rest = n - k0 - jb;
@@ -234,6 +237,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     int64_t last = ((n - 1) / nb) * nb;
     for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
+        note_launch();
         trsm_upper_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(n, (int)k0, jb, F, n, strideF,
                                                                     Y, n, strideY, m);
         if (k0 > 0) {

@@ -663,14 +663,17 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     int* flag = reinterpret_cast<int*>(base + L.flag);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
+    note_launch();
     companion_kernel<R><<<1, kRedThreads, 0, st>>>(m, kmax, Ahat, C, Lk, piv, flag, stage);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    note_launch();
     hessenberg_kernel<R><<<1, kRedThreads, sizeof(CT) * N, st>>>(N, C, flag, stage);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     size_t hbytes = packed_elems(N) * sizeof(CT);
     int use_smem = (hbytes + sizeof(CT) * N) <= (size_t)kMaxSmemPacked;
     size_t smem = sizeof(CT) * N + (use_smem ? hbytes : 0);
+    note_launch();
     qr_select_kernel<R><<<1, 256, smem, st>>>(N, m0, C, Hg, use_smem, c_re, c_im, ra, rb, lam0,
                                               gap, flag, stage, status);
     return cudaGetLastError();
@@ -702,12 +705,15 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     const size_t nsm = sizeof(double2) * ((size_t)m * m + 3 * m) + sizeof(int) * m;
     // stage 1: FP32 eigenvalues, FP64 Newton
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
+    note_launch();
     newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 1, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
     duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 2 (device-side no-op unless stage 1 flagged a failure)
     if ((e = run_stage<double>(st, 2, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
+    note_launch();
     newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 2, status);
     return cudaGetLastError();
 }
@@ -723,6 +729,7 @@ cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_
         attr_done = true;
     }
     size_t smem = sizeof(float2) * 2 * (size_t)m * m;
+    note_launch();
     chol_inverse_kernel<<<1, 512, smem, st>>>(m, G, shift_rel, Rinv, status);
     return cudaGetLastError();
 }
