@@ -204,6 +204,27 @@ int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t feast_nl_launch_count(void);
 
+/* ---- allocation-free Gram product --------------------------------------------
+ * G = Q^H Q for a device-resident n x m block Q.  The paper has no counterpart:
+ * this serves callers that must not touch the CUDA allocator (their device
+ * memory belongs to another framework's pool, or they run where cudaMalloc /
+ * cudaFree would stall or synchronise the device).  It allocates nothing and
+ * needs no handle.
+ *   Q      : device, complex128, COLUMN-major n x m with leading dimension ldq >= n.
+ *   G      : device, complex128, COLUMN-major m x m (leading dimension m), written
+ *            in full (G is Hermitian).
+ *   stream : cudaStream_t or NULL; the call is asynchronous on that stream.
+ * Limits: 1 <= n <= 2^30, 1 <= m, m*m <= 262144 (m <= 512); larger sizes return
+ * EINVAL without touching the GPU.  Q and G must be device pointers (EINVAL).
+ * The split-K partial sums live in one static 4 MiB device array that every GPU
+ * loading this library holds until the process exits; every call overwrites the
+ * partials it reads, so nothing needs clearing, but all calls share that array:
+ * calls that overlap on the GPU (different streams, or other host threads) race.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture. */
+int feast_nl_gram_noalloc(int64_t n, int32_t m, const void* Q, int64_t ldq, void* G,
+                          void* stream);
+
 /* Free the handle and all its device memory.  NULL is ignored. */
 void feast_nl_destroy(feast_nl_handle* h);
 

@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": FEAST_NL_FP64, "fp32": FEAST_NL_FP32}
 EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_nl_get_eigpairs",
            "feast_nl_get_nodes", "feast_nl_node_solve", "feast_nl_filter_apply",
            "feast_nl_project", "feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
-           "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count"]
+           "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count",
+           "feast_nl_gram_noalloc"]
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
 
@@ -86,6 +87,7 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_get_profile.argtypes = [P, I32, P, P]
     lib.feast_nl_launch_count.argtypes = []
     lib.feast_nl_launch_count.restype = ctypes.c_int64
+    lib.feast_nl_gram_noalloc.argtypes = [I64, I32, P, I64, P, P]
     for name in EXPORTS:
         if name not in ("feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
                         "feast_nl_launch_count"):

@@ -18,6 +18,7 @@ using namespace fnl;
 typedef std::complex<double> zd;
 
 static thread_local std::string g_last_error;
+void fnl::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 namespace {
 

@@ -96,6 +96,9 @@ struct IterStatus {
     double max_relres;
 };
 
+// Sets the text returned by feast_nl_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Process-wide count of kernel launches issued by this library.
 void note_launch(int k = 1);
 uint64_t launch_count();
