@@ -741,8 +741,8 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
             std::vector<double> rr(m);
             cudaMemcpy(lam.data(), h->dLam, sizeof(double2) * m, cudaMemcpyDeviceToHost);
             cudaMemcpy(rr.data(), h->dRelres, sizeof(double) * m, cudaMemcpyDeviceToHost);
-            fprintf(stderr, "[feast_nl] it %d inside %d conv %d max_relres %.3e flags %d\n", it,
-                    stt.n_inside, stt.n_conv, stt.max_relres, stt.flags);
+            fprintf(stderr, "[feast_nl] it %d inside %d conv %d max_relres %.3e flags %d qr_sweeps %d\n",
+                    it, stt.n_inside, stt.n_conv, stt.max_relres, stt.flags, stt.qr_sweeps);
             for (int i = 0; i < m; ++i)
                 fprintf(stderr, "    %2d  % .12e % .12e  relres %.3e\n", i, lam[i].x, lam[i].y, rr[i]);
         }

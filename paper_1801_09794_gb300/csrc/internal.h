@@ -92,7 +92,7 @@ struct IterStatus {
     int n_conv;
     int flags;         // bit 0: reduced QR hit its limit; bit 1: Ritz value on a node;
                        // bit 2: Cholesky breakdown; bit 3: Newton fallback used
-    int pad;
+    int qr_sweeps;     // QR sweeps of the last reduced eigenvalue computation
     double max_relres;
 };
 

@@ -72,6 +72,8 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 }
 
 constexpr int kRedThreads = 1024;
+constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (window <= 32)
+constexpr int kMaxCompanion = 1024; // largest companion order (degree * m0)
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
@@ -139,19 +141,42 @@ __global__ void __launch_bounds__(kRedThreads) companion_kernel(
         }
         __syncthreads();
     }
+    // top block row <- -Ahat_k^{-1} (top block row): rows 0..m-1 of every column.
+    // Interchanges per column, then substitution steps parallel over (row, column).
     for (int col = tid; col < N; col += nt) {
-        CT* x = C + (int64_t)col * N;   // rows 0..m-1 of column col
+        CT* x = C + (int64_t)col * N;
         for (int c = 0; c < m; ++c) {
             int p = piv[c];
             if (p != c) { CT t = x[c]; x[c] = x[p]; x[p] = t; }
         }
-        for (int i = 0; i < m; ++i)
-            for (int r = i + 1; r < m; ++r) x[r] = cfms(Lk[r + i * m], x[i], x[r]);
-        for (int i = m - 1; i >= 0; --i) {
-            x[i] = x[i] * crcp(Lk[i + i * m]);
-            for (int r = 0; r < i; ++r) x[r] = cfms(Lk[r + i * m], x[i], x[r]);
+    }
+    __syncthreads();
+    for (int i = 0; i < m - 1; ++i) {
+        const int rows = m - 1 - i;
+        for (int e = tid; e < rows * N; e += nt) {
+            int r = i + 1 + e % rows, col = e / rows;
+            CT* x = C + (int64_t)col * N;
+            x[r] = cfms(Lk[r + i * m], x[i], x[r]);
         }
-        for (int i = 0; i < m; ++i) x[i] = -x[i];
+        __syncthreads();
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        const CT di = crcp(Lk[i + i * m]);
+        for (int col = tid; col < N; col += nt) {
+            CT* x = C + (int64_t)col * N;
+            x[i] = x[i] * di;
+        }
+        __syncthreads();
+        for (int e = tid; e < i * N; e += nt) {
+            int r = e % i, col = e / i;
+            CT* x = C + (int64_t)col * N;
+            x[r] = cfms(Lk[r + i * m], x[i], x[r]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < m * N; e += nt) {
+        int r = e % m, col = e / m;
+        C[r + (int64_t)col * N] = -C[r + (int64_t)col * N];
     }
 }
 
@@ -233,7 +258,6 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
 }
 
 // packed Hessenberg storage with one bulge row: column j holds rows 0..j+2
-__device__ __forceinline__ int64_t hoff(int i, int j) { return (int64_t)j * (j + 5) / 2 + i; }
 
 // ---------------------------------------------------------------------------
 // Eigenvalues of the Hessenberg matrix by the implicit single-shift complex QR
@@ -250,99 +274,172 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
     CT* ev = reinterpret_cast<CT*>(smem_raw);   // N
     CT* H = use_smem ? ev + N : Hglobal;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    __shared__ int coff[kMaxCompanion + 1];   // start of packed column j
+    for (int j = tid; j <= N; j += nt) coff[j] = j * (j + 5) / 2;
+    __syncthreads();
+#define HH(i, j) H[coff[(j)] + (i)]
     for (int j = tid; j < N; j += nt)
         for (int i = 0; i <= j + 2; ++i)
-            H[hoff(i, j)] = (i < N && i <= j + 1) ? C[i + (int64_t)j * N] : czero<CT>();
+            HH(i, j) = (i < N && i <= j + 1) ? C[i + (int64_t)j * N] : czero<CT>();
     __syncthreads();
-    if (tid < 32) {
-        const R eps = cx<R>::eps(), tiny = cx<R>::tiny();
-        int hi = N - 1, its = 0, total = 0;
-        bool failed = false;
-        while (hi >= 0) {
-            if (hi == 0) { if (lane == 0) ev[0] = H[hoff(0, 0)]; break; }
-            int l = 0;
-            for (int base = hi; base >= 1; base -= 32) {
-                int i = base - lane;
-                bool neg = false;
-                if (i >= 1) {
-                    R h = cabs1(H[hoff(i, i - 1)]);
-                    R sd = cabs1(H[hoff(i - 1, i - 1)]) + cabs1(H[hoff(i, i)]);
-                    neg = (h <= eps * sd) || (h <= tiny);
-                }
-                unsigned b = __ballot_sync(0xffffffffu, neg);
-                if (b) { l = base - (__ffs(b) - 1); break; }
+    // Every thread runs the same control flow (deflation tests and shifts are
+    // computed redundantly from shared memory).  Each sweep chases the bulge in
+    // chunks of kQrChunk rotations: warp 0 applies them inside a small window
+    // (the only entries the next rotations read), then the whole CTA applies the
+    // chunk's rotations to the columns right of the window and the rows above
+    // it, each column / row independently.
+    __shared__ R s_c[kQrChunk];
+    __shared__ CT s_s[kQrChunk];
+    __shared__ R s_red[32];
+    const int warp = tid >> 5;
+    const R eps = cx<R>::eps();
+    // deflation: a subdiagonal is negligible below eps times its diagonal
+    // neighbours or below eps ||H||_F (a backward-stable perturbation of H; the
+    // kept values are polished in FP64 afterwards)
+    R hn = 0;
+    for (int j = tid; j < N; j += nt)
+        for (int i = 0; i <= j + 1 && i < N; ++i) hn += cnorm2(HH(i, j));
+    for (int o = 16; o > 0; o >>= 1) hn += __shfl_down_sync(0xffffffffu, hn, o);
+    if (lane == 0) s_red[warp] = hn;
+    __syncthreads();
+    hn = 0;
+    for (int w = 0; w < (nt >> 5); ++w) hn += s_red[w];
+    // (a floor of eps ||H||_F was tried: it roughly halves nothing -- sweeps are
+    //  already ~1.2 per eigenvalue -- and costs FP32 accuracy, so only a tiny floor)
+    const R tiny = fmax(cx<R>::tiny(), eps * eps * sqrt(hn));
+    int hi = N - 1, its = 0, total = 0;
+    bool failed = false;
+    while (hi >= 0) {
+        if (hi == 0) {
+            if (tid == 0) ev[0] = HH(0, 0);
+            break;
+        }
+        int l = 0;
+        for (int base = hi; base >= 1; base -= 32) {
+            int i = base - lane;
+            bool neg = false;
+            if (i >= 1) {
+                R h = cabs1(HH(i, i - 1));
+                R sd = cabs1(HH(i - 1, i - 1)) + cabs1(HH(i, i));
+                neg = (h <= eps * sd) || (h <= tiny);
             }
-            if (l > 0 && lane == 0) H[hoff(l, l - 1)] = czero<CT>();
-            __syncwarp();
-            if (l == hi) {
-                if (lane == 0) ev[hi] = H[hoff(hi, hi)];
-                __syncwarp();
-                hi -= 1; its = 0;
-                continue;
-            }
-            if (l == hi - 1) {
-                CT e1, e2;
-                eig2x2<R>(H[hoff(hi - 1, hi - 1)], H[hoff(hi - 1, hi)], H[hoff(hi, hi - 1)],
-                          H[hoff(hi, hi)], &e1, &e2);
-                if (lane == 0) { ev[hi - 1] = e1; ev[hi] = e2; }
-                __syncwarp();
-                hi -= 2; its = 0;
-                continue;
-            }
-            ++its; ++total;
-            if (total > 40 * N) { failed = true; break; }
-            CT mu;
-            CT d = H[hoff(hi, hi)];
+            unsigned b = __ballot_sync(0xffffffffu, neg);
+            if (b) { l = base - (__ffs(b) - 1); break; }
+        }
+        __syncthreads();
+        if (l > 0 && tid == 0) HH(l, l - 1) = czero<CT>();
+        if (l == hi) {
+            if (tid == 0) ev[hi] = HH(hi, hi);
+            __syncthreads();
+            hi -= 1; its = 0;
+            continue;
+        }
+        if (l == hi - 1) {
+            CT e1, e2;
+            eig2x2<R>(HH(hi - 1, hi - 1), HH(hi - 1, hi), HH(hi, hi - 1),
+                      HH(hi, hi), &e1, &e2);
+            if (tid == 0) { ev[hi - 1] = e1; ev[hi] = e2; }
+            __syncthreads();
+            hi -= 2; its = 0;
+            continue;
+        }
+        ++its; ++total;
+        if (total > 40 * N) { failed = true; break; }
+        CT mu;
+        {
+            CT d = HH(hi, hi);
             if (its % 11 == 10) {
                 mu = d;
-                mu.x += (R)0.75 * cabs(H[hoff(hi, hi - 1)]);
+                mu.x += (R)0.75 * cabs(HH(hi, hi - 1));
             } else {
                 CT e1, e2;
-                eig2x2<R>(H[hoff(hi - 1, hi - 1)], H[hoff(hi - 1, hi)], H[hoff(hi, hi - 1)], d, &e1, &e2);
+                eig2x2<R>(HH(hi - 1, hi - 1), HH(hi - 1, hi), HH(hi, hi - 1), d, &e1, &e2);
                 mu = (cabs1(e1 - d) <= cabs1(e2 - d)) ? e1 : e2;
             }
-            for (int k = l; k < hi; ++k) {
-                CT x, y;
-                if (k == l) { x = H[hoff(l, l)] - mu; y = H[hoff(l + 1, l)]; }
-                else        { x = H[hoff(k, k - 1)]; y = H[hoff(k + 1, k - 1)]; }
-                R ax = cabs(x), ay = cabs(y);
-                R c;
-                CT s;
-                if (ay == (R)0) { c = 1; s = czero<CT>(); }
-                else if (ax == (R)0) { c = 0; s.x = y.x / ay; s.y = -y.y / ay; }
-                else {
-                    R rho = hypot(ax, ay);
-                    c = ax / rho;
-                    CT ph;
-                    ph.x = x.x / ax;
-                    ph.y = x.y / ax;
-                    s = cscale((R)1 / rho, ph * cconj(y));
+        }
+        __syncthreads();
+        for (int k = l; k < hi; k += kQrChunk) {
+            const int kb = min(kQrChunk, hi - k);
+            const int w0 = (k == l) ? l : k - 1;
+            const int w1 = min(k + kb + 1, hi);
+            if (warp == 0) {
+                // the window holds at most kQrChunk + 3 <= 32 rows / columns:
+                // one element per lane in each update
+                for (int r = 0; r < kb; ++r) {
+                    const int kk = k + r;
+                    CT x, y;
+                    if (kk == l) { x = H[coff[l] + l] - mu; y = H[coff[l] + l + 1]; }
+                    else         { x = H[coff[kk - 1] + kk]; y = H[coff[kk - 1] + kk + 1]; }
+                    // G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0)
+                    const R nx = cnorm2(x), ny = cnorm2(y);
+                    R c;
+                    CT s;
+                    if (ny == (R)0) { c = 1; s = czero<CT>(); }
+                    else if (nx == (R)0) { R iy = rsqrt(ny); c = 0; s.x = y.x * iy; s.y = -y.y * iy; }
+                    else {
+                        const R irho = rsqrt(nx + ny), ix = rsqrt(nx);
+                        c = nx * ix * irho;                       // |x| / rho
+                        s = cscale(ix * irho, x * cconj(y));       // (x/|x|) conj(y) / rho
+                    }
+                    if (lane == 0) { s_c[r] = c; s_s[r] = s; }
+                    const int j = ((kk == l) ? l : kk - 1) + lane;
+                    if (j <= w1) {
+                        const int o = coff[j];
+                        CT h1 = H[o + kk], h2 = H[o + kk + 1];
+                        H[o + kk] = cscale(c, h1) + s * h2;
+                        H[o + kk + 1] = (j == kk - 1) ? czero<CT>() : cscale(c, h2) - cconj(s) * h1;
+                    }
+                    __syncwarp();
+                    const int i = w0 + lane;
+                    if (i <= min(kk + 2, hi)) {
+                        const int o0 = coff[kk], o1 = coff[kk + 1];
+                        CT h1 = H[o0 + i], h2 = H[o1 + i];
+                        H[o0 + i] = cscale(c, h1) + cconj(s) * h2;
+                        H[o1 + i] = cscale(c, h2) - s * h1;
+                    }
+                    __syncwarp();
                 }
-                const int j0 = (k == l) ? l : k - 1;
-                for (int j = j0 + lane; j <= hi; j += 32) {
-                    CT h1 = H[hoff(k, j)], h2 = H[hoff(k + 1, j)];
-                    H[hoff(k, j)] = cscale(c, h1) + s * h2;
-                    H[hoff(k + 1, j)] = cscale(c, h2) - cconj(s) * h1;
-                }
-                __syncwarp();
-                if (k > l && lane == 0) H[hoff(k + 1, k - 1)] = czero<CT>();
-                __syncwarp();
-                const int i1 = min(k + 2, hi);
-                for (int i = l + lane; i <= i1; i += 32) {
-                    CT h1 = H[hoff(i, k)], h2 = H[hoff(i, k + 1)];
-                    H[hoff(i, k)] = cscale(c, h1) + cconj(s) * h2;
-                    H[hoff(i, k + 1)] = cscale(c, h2) - s * h1;
-                }
-                __syncwarp();
             }
+            __syncthreads();
+            // deferred: rows k..k+kb of the columns right of the window, and
+            // columns k..k+kb of the rows above it
+            const int nfc = hi - w1, nfr = w0 - l;
+            for (int t = tid; t < nfc + nfr; t += nt) {
+                if (t < nfc) {
+                    const int j = w1 + 1 + t;
+                    CT a = HH(k, j);
+                    for (int r = 0; r < kb; ++r) {
+                        const R c = s_c[r];
+                        const CT s = s_s[r];
+                        CT b = HH(k + r + 1, j);
+                        HH(k + r, j) = cscale(c, a) + s * b;
+                        a = cscale(c, b) - cconj(s) * a;
+                    }
+                    HH(k + kb, j) = a;
+                } else {
+                    const int i = l + (t - nfc);
+                    CT a = HH(i, k);
+                    for (int r = 0; r < kb; ++r) {
+                        const R c = s_c[r];
+                        const CT s = s_s[r];
+                        CT b = HH(i, k + r + 1);
+                        HH(i, k + r) = cscale(c, a) + cconj(s) * b;
+                        a = cscale(c, b) - s * a;
+                    }
+                    HH(i, k + kb) = a;
+                }
+            }
+            __syncthreads();
         }
-        if (failed) {
-            for (int i = lane; i <= hi; i += 32) ev[i] = H[hoff(i, i)];
-            if (lane == 0) atomicOr(&status->flags, 1);
-        }
-        __syncwarp();
     }
     __syncthreads();
+    if (failed) {
+        for (int i = tid; i <= hi; i += nt) ev[i] = HH(i, i);
+        if (tid == 0) atomicOr(&status->flags, 1);
+    }
+    if (tid == 0) status->qr_sweeps = total;
+    __syncthreads();
+    #undef HH
     // Step 2: rank by (rho, Re, Im, index); keep the first m0
     for (int i = tid; i < N; i += nt) {
         CT e = ev[i];
@@ -374,7 +471,7 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
 
 // ---------------------------------------------------------------------------
 // FP64 Newton refinement of one kept Ritz pair per CTA.
-// smem: T (m x m, col-major, LU in place), x, u, xf (m each), piv (m)
+// smem: T (m x m, col-major, LU in place), x, u, xf, a (m each), piv (m)
 // ---------------------------------------------------------------------------
 constexpr int kNewtonThreads = 256;
 constexpr int kNewtonMax = 8;
@@ -479,7 +576,8 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     double2* x = T + (int64_t)m * m;
     double2* u = x + m;
     double2* xf = u + m;
-    int* piv = reinterpret_cast<int*>(xf + m);
+    double2* a = xf + m;
+    int* piv = reinterpret_cast<int*>(a + m);
     __shared__ double red[33];
     __shared__ int s_p;
     const int i = blockIdx.x;
@@ -500,44 +598,62 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         for (int r = threadIdx.x; r < m; r += blockDim.x) { x[r] = inv * x[r]; xf[r] = x[r]; }
         __syncthreads();
     }
+    // Newton on [T(l) y = 0, x^H y = 1] with the Jacobian's T block frozen at the
+    // factorised point (chord iteration); residuals T(l) x and T'(l) x are FP64.
+    // Each step:  a = T(lf)^{-1} T(l) x,  u = T(lf)^{-1} T'(l) x,
+    //             dl = -(x^H a)/(x^H u),  x <- x - a - dl u,  l <- l + dl.
+    // With lf = l this is exactly Newton; the factorisation is refreshed while
+    // the steps are still large.
     bool ok = true;
+    int refreshes = 0;
     for (int it = 0; it < kNewtonMax; ++it) {
-        for (int r = threadIdx.x; r < m; r += blockDim.x) {     // u = T'(l) x
-            double2 acc = make_double2(0.0, 0.0);
-            double2 lp = make_double2(1.0, 0.0);
-            for (int p = 1; p <= kmax; ++p) {
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            double2 v = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
+            for (int p = kmax; p >= 0; --p) {             // Horner for T(l)x and T'(l)x
                 double2 row = make_double2(0.0, 0.0);
                 const double2* Ap = Ahat + (int64_t)p * mm;
                 for (int c = 0; c < m; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
-                acc = cfma(((double)p) * lp, row, acc);
-                lp = lp * l;
+                dv = cfma(dv, l, v);
+                v = cfma(v, l, row);
             }
-            u[r] = acc;
+            a[r] = v;
+            u[r] = dv;
         }
         __syncthreads();
+        newton_solve(m, T, piv, a);
         newton_solve(m, T, piv, u);
-        double dre = 0.0, dim = 0.0;
+        double are = 0.0, aim = 0.0, ure = 0.0, uim = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
-            double2 t = cconj(x[r]) * u[r];
-            dre += t.x;
-            dim += t.y;
+            double2 ta = cconj(x[r]) * a[r], tu = cconj(x[r]) * u[r];
+            are += ta.x; aim += ta.y; ure += tu.x; uim += tu.y;
         }
-        dre = block_sum(dre, red);
-        dim = block_sum(dim, red);
-        double2 d = make_double2(dre, dim);
-        if (!(cabs(d) > 0.0) || !isfinite(d.x) || !isfinite(d.y)) { ok = false; break; }
-        double2 delta = crcp(d);
+        are = block_sum(are, red);
+        aim = block_sum(aim, red);
+        ure = block_sum(ure, red);
+        uim = block_sum(uim, red);
+        double2 xu = make_double2(ure, uim);
+        if (!(cabs(xu) > 0.0) || !isfinite(xu.x) || !isfinite(xu.y)) { ok = false; break; }
+        double2 dl = -(make_double2(are, aim) * crcp(xu));
+        if (!isfinite(dl.x) || !isfinite(dl.y)) { ok = false; break; }
         double s = 0.0;
-        for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(u[r]);
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            double2 nx = x[r] - a[r] - dl * u[r];
+            u[r] = nx;
+            s += cnorm2(nx);
+        }
         s = sqrt(block_sum(s, red));
         double inv = (s > 0.0 && isfinite(s)) ? 1.0 / s : 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = inv * u[r];
         __syncthreads();
-        l = l - delta;
-        if (cabs(delta) <= 4.0 * DBL_EPSILON * fmax(cabs(l), 1e-300)) break;
-        newton_build(m, kmax, Ahat, l, T);
-        __syncthreads();
-        newton_lu(m, T, piv, &s_p);
+        l = l + dl;
+        const double rel = cabs(dl) / fmax(cabs(l), 1e-300);
+        if (rel <= 4.0 * DBL_EPSILON) break;
+        if (rel > 1e-9 && refreshes < 2 && (it == 1 || it == 4)) {
+            newton_build(m, kmax, Ahat, l, T);
+            __syncthreads();
+            newton_lu(m, T, piv, &s_p);
+            ++refreshes;
+        }
     }
     const double moved = cabs(l - l0);
     const double lim = 0.3 * gap[i];
@@ -702,7 +818,7 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     int* flag = reinterpret_cast<int*>(base + L.flag);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
-    const size_t nsm = sizeof(double2) * ((size_t)m * m + 3 * m) + sizeof(int) * m;
+    const size_t nsm = sizeof(double2) * ((size_t)m * m + 4 * m) + sizeof(int) * m;
     // stage 1: FP32 eigenvalues, FP64 Newton
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
