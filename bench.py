@@ -37,7 +37,7 @@ FP32_SIMT_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 lanes
 TF32_OVER_BF16 = 1.1 / 2.25
 
 WORKLOADS = {
-    "qep_mixed_n4096": {"gen": "config2_qep", "n": 4096, "precision": "fp32", "tol": 1e-10,
+    "qep_mixed_n4096": {"gen": "config2_qep", "n": 4096, "precision": "fp32_i8", "tol": 1e-10,
                         "maxit": 40},
     "qep_plain_n256": {"gen": "config1_qep", "n": 256, "precision": "fp64", "tol": 1e-10,
                        "maxit": 60},

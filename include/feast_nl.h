@@ -59,8 +59,14 @@ enum feast_nl_fkind { FEAST_NL_POW = 0, FEAST_NL_EXP = 1 };
  *   FEAST_NL_FP64  : LU and solves in FP64.
  *   FEAST_NL_FP32  : LU and solves in FP32 (complex64).  The filter is a
  *                    residual inverse iteration (Sec. 4.2), so solve errors scale
- *                    with ||T(X, Lambda)|| and vanish as the pairs converge. */
-enum feast_nl_precision { FEAST_NL_FP64 = 0, FEAST_NL_FP32 = 1 };
+ *                    with ||T(X, Lambda)|| and vanish as the pairs converge.
+ *   FEAST_NL_FP32_I8 : as FP32, and the products A_t Q (block residual and
+ *                    projections) run on the BF16 tensor cores through an
+ *                    error-free split into seven 7-bit integer digit slices with
+ *                    power-of-two row / column scales (exact integer sums,
+ *                    recombined in FP64; relative error about 1e-14 of |A||Q|).
+ *                    Needs n <= 22000; larger n falls back to FP64 products. */
+enum feast_nl_precision { FEAST_NL_FP64 = 0, FEAST_NL_FP32 = 1, FEAST_NL_FP32_I8 = 2 };
 
 /* Quadrature rule on the parametrised contour z(theta) = c + ra cos(theta) + i rb sin(theta),
  * omega_j = w_j z'(theta_j) / (2 pi i):

@@ -22,10 +22,10 @@ FEAST_NL_ENOMEM = 5
 FEAST_NL_EDEVICE = 6
 FEAST_NL_EUNSUPPORTED = 7
 FEAST_NL_POW, FEAST_NL_EXP = 0, 1
-FEAST_NL_FP64, FEAST_NL_FP32 = 0, 1
+FEAST_NL_FP64, FEAST_NL_FP32, FEAST_NL_FP32_I8 = 0, 1, 2
 FEAST_NL_GL, FEAST_NL_TRAPEZOID, FEAST_NL_GL_HALVES = 0, 1, 2
 RULES = {"gl": FEAST_NL_GL, "trapezoid": FEAST_NL_TRAPEZOID, "gl_halves": FEAST_NL_GL_HALVES}
-PRECISIONS = {"fp64": FEAST_NL_FP64, "fp32": FEAST_NL_FP32}
+PRECISIONS = {"fp64": FEAST_NL_FP64, "fp32": FEAST_NL_FP32, "fp32_i8": FEAST_NL_FP32_I8}
 
 # every exported symbol of include/feast_nl.h
 EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_nl_get_eigpairs",

@@ -156,6 +156,14 @@ struct feast_nl_handle {
     IterStatus* dStatus = nullptr;
     IterStatus* hStatus = nullptr;  // pinned
     int splits = 1;
+    // digit-split products on the tensor cores (precision FEAST_NL_FP32_I8)
+    int oz_s = 0;
+    OzakiLayout oz;                 // layout for mcap columns
+    unsigned char* dAsl = nullptr;  // nA x s slices of A'
+    double* dSigma = nullptr;       // nA x Mpad row scales
+    unsigned char* dQsl = nullptr;  // s slices of Q'
+    double* dTau = nullptr;         // column scales
+    int* dSlot = nullptr;           // dense index -> term index
     // results of the last solve
     bool have_result = false;
     int m_last = 0;
@@ -219,6 +227,7 @@ void release_workspace(feast_nl_handle* h) {
     dfree(h->dG); dfree(h->dSplit); dfree(h->dAhat); dfree(h->dYred); dfree(h->dYcat);
     dfree(h->dG2); dfree(h->dRinv); dfree(h->dLam); dfree(h->dCoef); dfree(h->dFsum);
     dfree(h->dNu); dfree(h->dRnorm); dfree(h->dRelres); dfree(h->dRed); dfree(h->dStage);
+    dfree(h->dQsl); dfree(h->dTau);
     h->mcap = 0;
     h->have_result = false;
 }
@@ -253,6 +262,13 @@ int ensure_workspace(feast_nl_handle* h, int m) {
     CK(dalloc(&h->dRelres, (size_t)m));
     CK(dalloc(&h->dRed, reduced_work_bytes(m, std::max(h->kmax, 1))));
     CK(dalloc(&h->dStage, (size_t)n * m));
+    if (h->oz_s > 0) {
+        h->oz = ozaki_layout(n, m, h->oz_s);
+        const size_t qb = (size_t)(h->oz.b_slice * h->oz_s) * ozaki_elem_bytes();
+        CK(dalloc(&h->dQsl, qb));
+        CK(cudaMemsetAsync(h->dQsl, 0, qb, h->st));
+        CK(dalloc(&h->dTau, (size_t)m));
+    }
     h->mcap = m;
     return FEAST_NL_OK;
 }
@@ -287,6 +303,15 @@ int store_block(feast_nl_handle* h, const double2* src, int m, void* dst, int64_
 int apply_terms(feast_nl_handle* h, const double2* Q, int m, double2* W) {
     const int64_t n = h->n;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    if (h->oz_s > 0 && h->nA > 0) {
+        // all dense terms at once on the INT8 tensor cores
+        const OzakiLayout L = ozaki_layout(n, m, h->oz_s);
+        CK(ozaki_split_Q(h->st, n, m, h->oz_s, Q, h->dTau, h->dQsl, L));
+        CK(ozaki_gemm(h->st, n, m, L, h->nA, h->dAsl, h->dSigma, h->dQsl, h->dTau, W, h->dSlot,
+                      &h->dStatus->flags));
+        CK(copy_identity_terms(h->st, n, m, h->nterms, h->dTerms, Q, W));
+        return FEAST_NL_OK;
+    }
     for (int t = 0; t < h->nterms; ++t) {
         const HostTerm& ht = h->terms[t];
         if (ht.aidx < 0) continue;
@@ -448,6 +473,9 @@ void feast_nl_destroy(feast_nl_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     release_workspace(h);
     dfree(h->dA);
+    dfree(h->dAsl);
+    dfree(h->dSigma);
+    dfree(h->dSlot);
     dfree(h->dTerms);
     dfree(h->dz);
     dfree(h->dw);
@@ -471,7 +499,7 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
     if (n < 1 || n > 65536) return fail(FEAST_NL_EINVAL, "n must be in [1, 65536]");
     if (nterms < 1 || nterms > kMaxTerms) return fail(FEAST_NL_EINVAL, "nterms must be in [1, 16]");
     if (!terms) return fail(FEAST_NL_EINVAL, "terms is NULL");
-    if (precision != FEAST_NL_FP64 && precision != FEAST_NL_FP32)
+    if (precision != FEAST_NL_FP64 && precision != FEAST_NL_FP32 && precision != FEAST_NL_FP32_I8)
         return fail(FEAST_NL_EINVAL, "unknown precision");
     feast_nl_handle* h = new (std::nothrow) feast_nl_handle();
     if (!h) return fail(FEAST_NL_ENOMEM, "host allocation failed");
@@ -523,6 +551,19 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         (e = dalloc(&h->dStatus, 1)) != cudaSuccess ||
         (e = cudaMallocHost((void**)&h->hStatus, sizeof(IterStatus))) != cudaSuccess)
         return cleanup(fail_cuda(e, "allocation", __LINE__));
+    if (precision == FEAST_NL_FP32_I8 && h->nA > 0 && ozaki_supported(n, kOzakiSlices)) {
+        h->oz_s = kOzakiSlices;
+        const OzakiLayout L = ozaki_layout(n, 1, h->oz_s);
+        std::vector<int> slot;
+        for (int t = 0; t < nterms; ++t)
+            if (h->terms[t].aidx >= 0) slot.push_back(t);
+        if ((e = dalloc(&h->dAsl, (size_t)(L.a_term * h->nA) * ozaki_elem_bytes())) != cudaSuccess ||
+            (e = dalloc(&h->dSigma, (size_t)(L.Mpad * h->nA))) != cudaSuccess ||
+            (e = dalloc(&h->dSlot, slot.size())) != cudaSuccess ||
+            (e = cudaMemcpy(h->dSlot, slot.data(), sizeof(int) * slot.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cleanup(fail_cuda(e, "allocation of digit slices", __LINE__));
+    }
     // copy the coefficients in, transposed to column-major
     double2* stage = nullptr;
     double2 *v = nullptr, *u = nullptr, *gw = nullptr;
@@ -554,6 +595,13 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
             e = transpose_rowmajor_to_colmajor(h->st, n, n, src, tt.lda, dst, n);
         }
         if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "transpose of A", __LINE__)); }
+        if (h->oz_s > 0) {
+            const OzakiLayout L = ozaki_layout(n, 1, h->oz_s);
+            const int a = h->terms[t].aidx;
+            e = ozaki_split_A(h->st, n, h->oz_s, dst, h->dSigma + (int64_t)a * L.Mpad,
+                              h->dAsl + (int64_t)a * L.a_term * ozaki_elem_bytes(), L);
+            if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "digit split of A", __LINE__)); }
+        }
         if (!tt.on_device) {
             // the staging buffer is reused by the next term
             e = cudaStreamSynchronize(h->st);

@@ -172,6 +172,32 @@ cudaError_t set_identity(cudaStream_t st, int m, double2* Y, double* ones);
 cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nterms,
                                 const TermDev* terms, const double2* Q, double2* W);
 
+// ------------------------------------------------------------------ digit-split products (k_ozaki.cu)
+struct OzakiLayout {
+    int s = 0;           // digit slices per operand
+    int64_t Mpad = 0;    // rows of A' padded to the 128-row tile
+    int64_t Kp = 0;      // 2n padded to the 64-byte K stage
+    int64_t Npad = 0;    // 2m padded to the 64-column tile
+    int64_t a_slice = 0, a_term = 0, b_slice = 0;   // elements (BF16)
+};
+// Digit slices per operand: the truncation remainder is below 2^{-7s} of the row /
+// column scale, so s = 7 keeps the products at ~1e-14 relative accuracy.
+constexpr int kOzakiSlices = 7;
+OzakiLayout ozaki_layout(int64_t n, int m, int s);
+bool ozaki_supported(int64_t n, int s);
+// sigma (Mpad doubles) and the s digit slices of A' = [Re A | Im A] (A n x n col-major)
+size_t ozaki_elem_bytes();
+cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, double* sigma,
+                          void* slices, const OzakiLayout& L);
+// tau (m doubles) and the s digit slices of the real embedding of Q (n x m col-major)
+cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double2* Q, double* tau,
+                          void* slices, const OzakiLayout& L);
+// W + term_slot[t] * n * m  <-  A_t Q for t < nterms (complex128, col-major, ld n);
+// a failed internal wait sets bit 4 of *err.
+cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, int nterms,
+                       const void* Aslices, const double* sigma, const void* Qslices,
+                       const double* tau, double2* W, const int* term_slot, int* err);
+
 // ------------------------------------------------------------------ LU (k_lu.cu)
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,

@@ -1,0 +1,454 @@
+// FP64-accurate complex products W = A Q on the BF16 tensor cores (tcgen05).
+//
+// GB300 executes FP64 at ~1.1 TFLOP/s and dense BF16 MMA at ~2 PFLOP/s.  The
+// block residual T(X, Lambda) and the projections Q^H A Q of Algorithm 1 need
+// FP64-level accuracy, and their cost is dominated by the products A_t Q
+// (8 n^2 m0 flops per term and iteration).  They are computed here by an
+// error-free splitting into small-integer digit slices (the idea of Ozaki,
+// Ogita, Oishi and Rump for accurate matrix products, written from its
+// definition):
+//
+//   A' = [Re A | Im A]  (n x 2n, real) and Q' (2n x 2m, real; column 2j is
+//   [Re q_j; -Im q_j], column 2j+1 is [Im q_j; Re q_j]), so A' Q' holds Re W and
+//   Im W column-interleaved;
+//   A'_ik = sigma_i (sum_{p=1..s} a^(p)_ik 2^{-7p} + r_ik),  |r_ik| < 2^{-7s},
+//   Q'_kj = tau_j   (sum_{q=1..s} b^(q)_kj 2^{-7q} + r'_kj), |r'_kj| < 2^{-7s},
+//   a, b integers in [-127, 127] (truncated base-128 digits after scaling by a
+//   power of two strictly above the row / column maximum), stored as BF16,
+//   which holds them exactly;
+//   W'_ij ~= sigma_i tau_j sum_{L=2..s+1} 2^{-7L} S_L(i,j),  S_L = sum_{p+q=L} a^(p) b^(q).
+//
+// Each product of digits is exact in FP32 and an FP32 sum of integers is exact
+// while it stays below 2^24.  The three leading levels L = 2, 3, 4 (at most
+// three slice pairs each) are therefore accumulated in TMEM over 256-element
+// K chunks (3 * 256 * 127^2 < 2^24) and drained into int32 registers after
+// every chunk, which keeps them exact; levels L >= 5 carry weights <= 2^-35 and
+// are accumulated in FP32 over the whole K (relative effect <= 2^-45).  The
+// dropped pairs (p + q > s + 1) and the truncation remainders are below
+// 2^{-7s} of sigma_i (resp. tau_j) per operand entry; with s = 7 the product is
+// accurate to ~1e-14 relative to |A'| |Q'|.
+//
+// Kernel: one CTA (256 threads) per 128 x 48 tile of W'.  K advances in
+// 32-element stages (double-buffered cp.async); thread 0 issues
+// tcgen05.mma.kind::f16 (M = 128, N = 48, K = 16) for every slice pair into
+// its level's TMEM columns and commits each stage to an mbarrier.  Warps w and
+// w + 4 read TMEM lanes 32 (w mod 4) .. and split the 48 columns.  Operand
+// tiles use the canonical K-major layout without swizzle: 8-row x 16-byte core
+// matrices (128 bytes), the four K chunks of a row group side by side
+// (LBO = 128 B along K, SBO = 512 B between row groups).
+#include "internal.h"
+
+#include <cuda_bf16.h>
+
+namespace fnl {
+namespace {
+
+constexpr int kOzM = 128;          // rows of W' per CTA (TMEM lanes)
+constexpr int kOzN = 48;           // columns of W' per CTA
+constexpr int kOzBK = 32;          // K elements (64 bytes) per stage
+constexpr int kOzThreads = 256;
+constexpr int kOzMaxSlices = 8;
+constexpr int kOzExact = 3;        // levels drained exactly (L = 2..4)
+constexpr int kOzChunkStages = 8;  // 8 x 32 = 256 K elements between drains
+constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// tcgen05 shared-memory matrix descriptor, SWIZZLE_NONE, K-major.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;   // descriptor version for the sm_100 family
+    return d;                  // base offset 0, absolute LBO, no swizzle
+}
+
+// Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 cycles and reports it.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(addr, parity)) {
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// 8 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
+    int s, int Mrows, int Kp, const __nv_bfloat16* __restrict__ Aslices, int64_t a_slice_stride,
+    int64_t a_term_stride, const double* __restrict__ sigma, int64_t sigma_term_stride,
+    const __nv_bfloat16* __restrict__ Bslices, int64_t b_slice_stride, const double* __restrict__ tau,
+    double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, const int* __restrict__ term_slot,
+    int ncols_complex, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, colhalf = warp >> 2;     // TMEM lanes / column half
+    const int row0 = blockIdx.x * kOzM;
+    const int col0 = blockIdx.y * kOzN;                    // real column of W'
+    const int term = blockIdx.z;
+    const __nv_bfloat16* A = Aslices + term * a_term_stride;
+    const double* sg = sigma + term * sigma_term_stride;
+    double2* Wt = W + (int64_t)term_slot[term] * w_term_stride;
+    const int a_tile = kOzM * kOzBK * 2;                   // bytes per A slice tile (8 KB)
+    const int b_tile = kOzN * kOzBK * 2;                   // 3 KB
+    const int stage_bytes = s * (a_tile + b_tile);
+    unsigned char* stage[2] = {smem, smem + stage_bytes};
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+
+    const uint32_t idesc = bf16_idesc(kOzM, kOzN);
+    const int nk = Kp / kOzBK;
+    int exact[kOzExact][kOzN / 2];                         // running sums of levels 2..4
+#pragma unroll
+    for (int L = 0; L < kOzExact; ++L)
+#pragma unroll
+        for (int c = 0; c < kOzN / 2; ++c) exact[L][c] = 0;
+    bool ok = true;
+    uint32_t level_init = 0;                               // bit L: level L holds data
+    for (int t = 0; t < nk && ok; ++t) {
+        const int b = t & 1;
+        if (t >= 2) ok = mbar_wait(smem_u32(&mbar[b]), ((t - 2) >> 1) & 1);
+        ok = __syncthreads_and(ok);                          // uniform exit on a timeout
+        if (!ok) break;
+        // ---- load stage t: s A tiles (128 x 32 bf16) and s B tiles (48 x 32 bf16)
+        const int64_t k0 = (int64_t)t * kOzBK;
+        unsigned char* sa = stage[b];
+        unsigned char* sb = stage[b] + s * a_tile;
+        for (int idx = tid; idx < s * (kOzM + kOzN) * 4; idx += kOzThreads) {
+            const int chunk = idx & 3;                     // 16-byte K chunk (8 elements)
+            const int r = idx >> 2;
+            int p, rr;
+            const __nv_bfloat16* src;
+            unsigned char* dst;
+            if (r < s * kOzM) {
+                p = r / kOzM;
+                rr = r - p * kOzM;
+                src = A + p * a_slice_stride + (int64_t)(row0 + rr) * Kp + k0 + chunk * 8;
+                dst = sa + p * a_tile;
+            } else {
+                const int r2 = r - s * kOzM;
+                p = r2 / kOzN;
+                rr = r2 - p * kOzN;
+                src = Bslices + p * b_slice_stride + (int64_t)(col0 + rr) * Kp + k0 + chunk * 8;
+                dst = sb + p * b_tile;
+            }
+            dst += ((rr >> 3) * 4 + chunk) * 128 + (rr & 7) * 16;
+            cp_async16(smem_u32(dst), src);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const bool chunk_start = (t % kOzChunkStages) == 0;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (chunk_start) level_init &= ~((1u << kOzExact) - 1u);   // exact levels restart
+            for (int p = 0; p < s; ++p) {
+                for (int q = 0; p + q <= s - 1; ++q) {
+                    const int L = p + q;
+                    const uint32_t dcol = tmem + (uint32_t)(L * kOzN);
+                    for (int kk = 0; kk < kOzBK / 16; ++kk) {
+                        const uint64_t ad = smem_desc(smem_u32(sa + p * a_tile) + kk * 256, 128, 512);
+                        const uint64_t bd = smem_desc(smem_u32(sb + q * b_tile) + kk * 256, 128, 512);
+                        const uint32_t acc = (level_init >> L) & 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(dcol),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        level_init |= 1u << L;
+                    }
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[b]))
+                : "memory");
+        }
+        // ---- end of a 256-element chunk (or of K): drain the exact levels
+        if ((t % kOzChunkStages) == kOzChunkStages - 1 || t == nk - 1) {
+            ok = mbar_wait(smem_u32(&mbar[b]), (t >> 1) & 1);
+            ok = __syncthreads_and(ok);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) {
+#pragma unroll
+                for (int L = 0; L < kOzExact; ++L) {
+                    if (L >= s) break;
+#pragma unroll
+                    for (int g = 0; g < kOzN / 2 / 8; ++g) {
+                        uint32_t v[8];
+                        tmem_ld8(lane_base + (uint32_t)(L * kOzN + colhalf * (kOzN / 2) + g * 8), v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            exact[L][g * 8 + c] += __float2int_rn(__uint_as_float(v[c]));
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    if (!ok && tid == 0) atomicOr(err, 16);
+    __syncthreads();
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = row0 + quarter * 32 + lane;
+        const double sgm = (row < Mrows) ? sg[row] : 0.0;
+        double acc[kOzN / 2];
+#pragma unroll
+        for (int c = 0; c < kOzN / 2; ++c) acc[c] = 0.0;
+        for (int L = s - 1; L >= kOzExact; --L) {          // small levels, FP32 in TMEM
+            const double scale = ldexp(1.0, -7 * (L + 2));
+#pragma unroll
+            for (int g = 0; g < kOzN / 2 / 8; ++g) {
+                uint32_t v[8];
+                tmem_ld8(lane_base + (uint32_t)(L * kOzN + colhalf * (kOzN / 2) + g * 8), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[g * 8 + c] = fma((double)__uint_as_float(v[c]), scale, acc[g * 8 + c]);
+            }
+        }
+#pragma unroll
+        for (int L = kOzExact - 1; L >= 0; --L) {
+            if (L >= s) continue;
+            const double scale = ldexp(1.0, -7 * (L + 2));
+#pragma unroll
+            for (int c = 0; c < kOzN / 2; ++c) acc[c] = fma((double)exact[L][c], scale, acc[c]);
+        }
+        if (row < Mrows) {
+#pragma unroll
+            for (int c = 0; c < kOzN / 2; ++c) {
+                const int cc = col0 + colhalf * (kOzN / 2) + c;    // real column of W'
+                const int j = cc >> 1;
+                if (j < ncols_complex) {
+                    double* dst = reinterpret_cast<double*>(Wt + row + (int64_t)j * ldw) + (cc & 1);
+                    *dst = sgm * tau[j] * acc[c];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// digit slices
+// ---------------------------------------------------------------------------
+// sigma_i = 2^e with max_k |A'_ik| < 2^e (1 for a zero row), one thread per row.
+__global__ void row_scale_kernel(int64_t n, const double2* __restrict__ A, double* __restrict__ sigma,
+                                 int64_t Mrows_pad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Mrows_pad) return;
+    double mx = 0.0;
+    if (i < n)
+        for (int64_t k = 0; k < n; ++k) {
+            double2 a = A[i + k * n];
+            mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+        }
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+    sigma[i] = (mx > 0.0) ? ldexp(1.0, e) : 1.0;
+}
+
+// s base-128 digits of r (|r| < 1), truncated toward zero; exact in FP64.
+__device__ __forceinline__ void digits(double r, int s, float* d) {
+    for (int p = 0; p < s; ++p) {
+        r *= 128.0;
+        const double t = trunc(r);
+        d[p] = (float)t;
+        r -= t;
+    }
+}
+
+// A' slices [slice][Mpad][Kp] (bf16): K index k -> Re A[i,k], n + k -> Im A[i,k].
+// Block 32 x 8 handles 32 rows x 32 complex columns through shared memory.
+__global__ void split_rows_kernel(int64_t n, int s, const double2* __restrict__ A,
+                                  const double* __restrict__ sigma, __nv_bfloat16* __restrict__ out,
+                                  int64_t slice_stride, int64_t Kp) {
+    __shared__ float tile[kOzMaxSlices][2][32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+    const int64_t i = i0 + tx;
+    const double inv = (i < n) ? 1.0 / sigma[i] : 0.0;     // exact: sigma is a power of 2
+    for (int kk = ty; kk < 32; kk += 8) {
+        const int64_t k = k0 + kk;
+        double2 a = make_double2(0.0, 0.0);
+        if (i < n && k < n) a = A[i + k * n];
+        float dr[kOzMaxSlices], di[kOzMaxSlices];
+        digits(a.x * inv, s, dr);
+        digits(a.y * inv, s, di);
+        for (int p = 0; p < s; ++p) { tile[p][0][tx][kk] = dr[p]; tile[p][1][tx][kk] = di[p]; }
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t row = i0 + rr;
+        const int64_t k = k0 + tx;
+        if (k >= n) continue;
+        for (int p = 0; p < s; ++p) {
+            __nv_bfloat16* o = out + p * slice_stride + row * Kp;
+            o[k] = __float2bfloat16_rn(tile[p][0][rr][tx]);
+            o[n + k] = __float2bfloat16_rn(tile[p][1][rr][tx]);
+        }
+    }
+}
+
+// Q' slices for complex column j (rows 2j, 2j+1 of [slice][Npad][Kp]) and tau_j.
+__global__ void split_cols_kernel(int64_t n, int s, const double2* __restrict__ Q,
+                                  double* __restrict__ tau, __nv_bfloat16* __restrict__ out,
+                                  int64_t slice_stride, int64_t Kp) {
+    __shared__ double red[32];
+    const int j = blockIdx.x;
+    const double2* q = Q + (int64_t)j * n;
+    double mx = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+        mx = fmax(mx, fmax(fabs(q[k].x), fabs(q[k].y)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+        int e = 0;
+        if (t > 0.0) frexp(t, &e);
+        red[0] = (t > 0.0) ? ldexp(1.0, e) : 1.0;
+        tau[j] = red[0];
+    }
+    __syncthreads();
+    const double inv = 1.0 / red[0];
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        float dr[kOzMaxSlices], di[kOzMaxSlices];
+        digits(q[k].x * inv, s, dr);
+        digits(q[k].y * inv, s, di);
+        for (int p = 0; p < s; ++p) {
+            __nv_bfloat16* r0 = out + p * slice_stride + (int64_t)(2 * j) * Kp;
+            __nv_bfloat16* r1 = r0 + Kp;
+            r0[k] = __float2bfloat16_rn(dr[p]);
+            r0[n + k] = __float2bfloat16_rn(-di[p]);
+            r1[k] = __float2bfloat16_rn(di[p]);
+            r1[n + k] = __float2bfloat16_rn(dr[p]);
+        }
+    }
+}
+
+}  // namespace
+
+OzakiLayout ozaki_layout(int64_t n, int m, int s) {
+    OzakiLayout L;
+    L.s = s;
+    L.Mpad = (n + kOzM - 1) / kOzM * kOzM;
+    L.Kp = (2 * n + kOzBK - 1) / kOzBK * kOzBK;
+    L.Npad = (2 * (int64_t)m + kOzN - 1) / kOzN * kOzN;
+    L.a_slice = L.Mpad * L.Kp;             // elements
+    L.a_term = L.a_slice * s;
+    L.b_slice = L.Npad * L.Kp;
+    return L;
+}
+
+bool ozaki_supported(int64_t n, int s) {
+    // int32 running sums of the exact levels: 3 pairs * 2n * 127^2 < 2^31
+    return s >= 1 && s <= kOzMaxSlices && 3.0 * 2.0 * n * 127.0 * 127.0 < 2147483647.0;
+}
+
+size_t ozaki_elem_bytes() { return sizeof(__nv_bfloat16); }
+
+cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, double* sigma,
+                          void* slices, const OzakiLayout& L) {
+    cudaError_t e = cudaMemsetAsync(slices, 0, (size_t)L.a_term * sizeof(__nv_bfloat16), st);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    row_scale_kernel<<<(unsigned)((L.Mpad + 127) / 128), 128, 0, st>>>(n, A, sigma, L.Mpad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    note_launch();
+    split_rows_kernel<<<g, dim3(32, 8), 0, st>>>(n, s, A, sigma,
+                                                  static_cast<__nv_bfloat16*>(slices), L.a_slice,
+                                                  L.Kp);
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double2* Q, double* tau,
+                          void* slices, const OzakiLayout& L) {
+    note_launch();
+    split_cols_kernel<<<m, 256, 0, st>>>(n, s, Q, tau, static_cast<__nv_bfloat16*>(slices),
+                                         L.b_slice, L.Kp);
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, int nterms,
+                       const void* Aslices, const double* sigma, const void* Qslices,
+                       const double* tau, double2* W, const int* term_slot, int* err) {
+    static bool attr_done = false;
+    const int s = L.s;
+    const int smem = 2 * s * (kOzM + kOzN) * kOzBK * 2;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(ozaki_bf16_gemm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             2 * kOzMaxSlices * (kOzM + kOzN) * kOzBK * 2);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)(L.Mpad / kOzM), (unsigned)(L.Npad / kOzN), (unsigned)nterms);
+    note_launch();
+    ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
+        s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,
+        sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * m,
+        term_slot, m, err);
+    return cudaGetLastError();
+}
+
+}  // namespace fnl

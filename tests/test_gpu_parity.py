@@ -68,7 +68,7 @@ def test_node_solve_matches_oracle(lib, prec, n):
 
 
 # ------------------------------------------------------------------ Step 4 and Step 1 pieces
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
 def test_filter_apply_matches_oracle(lib, prec):
     n, m = 170, 9
     p = random_pep(n, 2, seed=5)
@@ -85,15 +85,16 @@ def test_filter_apply_matches_oracle(lib, prec):
     ref = O.filter_update(lus, z, w, X, lam, R)
     got = s.filter_apply(X, lam)
     kappa = max(np.linalg.cond(O.assemble(p, zj)) for zj in z)
-    tol = 1e-12 * kappa if prec == "fp64" else 2e-6 * kappa
+    tol = 1e-12 * kappa if prec == "fp64" else 2e-6 * kappa    # FP32 node solves otherwise
     assert _relerr(got, ref) < tol
     s.close()
 
 
-def test_project_matches_oracle(lib):
-    n, m = 190, 12
+@pytest.mark.parametrize("prec,n,m", [("fp64", 190, 12), ("fp32_i8", 190, 12),
+                                      ("fp32_i8", 300, 40), ("fp32_i8", 1, 1)])
+def test_project_matches_oracle(lib, prec, n, m):
     p = random_pep(n, 3, seed=8)
-    s = lib.FeastNL(p, "fp64")
+    s = lib.FeastNL(p, prec)
     Q = O.orthonormalize(start_block(n, m, 3))
     got = s.project(Q, 3)
     ref = O.projected_coefficients(p, Q)
@@ -103,7 +104,7 @@ def test_project_matches_oracle(lib):
 
 
 # ------------------------------------------------------------------ whole solve
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
 def test_solve_example1_table1(lib, prec):
     rows = load_table1(os.path.join(GOLD, "e1_table1.txt"))
     p = mass_spring(1000, 0.6202, 0.4807)
@@ -124,7 +125,7 @@ def test_solve_example1_table1(lib, prec):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
 def test_solve_plain_qep_matches_oracle(lib, prec):
     with open(os.path.join(GOLD, "contours.json")) as f:
         w = json.load(f)["qep_plain_n256"]
@@ -146,7 +147,7 @@ def test_solve_plain_qep_matches_oracle(lib, prec):
     s.close()
 
 
-@pytest.mark.parametrize("k,prec", [(3, "fp64"), (3, "fp32"), (1, "fp32")])
+@pytest.mark.parametrize("k,prec", [(3, "fp64"), (3, "fp32"), (1, "fp32"), (3, "fp32_i8")])
 def test_solve_random_pep_matches_bruteforce(lib, k, prec):
     n = 130 if k > 1 else 150
     p = random_pep(n, k, seed=20 + k) if k > 1 else linear_problem(n, seed=4)
