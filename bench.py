@@ -9,7 +9,8 @@ its eigenvalue is within 1e-10 (relative) of the stored reference eigenvalues.
 
 Default workload (qep_mixed_n4096): T(l) = l^2 M + l C + K, n = 4096, complex128
 inputs, 16 Gauss-Legendre nodes on the stored circle holding 64 eigenvalues,
-m0 = 96; node LUs and solves in FP32, everything else FP64-accurate.
+m0 = 96; node LUs and solves in FP32, A_t Q products as exact digit-split BF16
+tensor-core GEMMs, everything else FP64 (FP64-accurate results).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -168,12 +169,20 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------- roofline
+DIGIT_SLICES = 7      # FEAST_NL_FP32_I8: digit slices per operand of A_t Q
+
+
 def phase_work(name, spec, c, iters, nterms_dense):
-    """Algorithmic real flops of one phase over one solve (4M complex counting)."""
+    """Flops of one phase over one solve: algorithmic (4M complex counting), except
+    the digit-split A_t Q, which counts the BF16 tensor-core flops it executes
+    (s(s+1)/2 slice products of the real-embedded n x 2n x 2 m0 GEMM per term)."""
     n, m0, nc = spec["n"], c["m0"], c["nc"]
     if name == "lu":
         return nc * (8.0 / 3.0) * n ** 3
     if name == "apply":
+        if spec["precision"] == "fp32_i8":
+            pairs = DIGIT_SLICES * (DIGIT_SLICES + 1) // 2
+            return iters * nterms_dense * pairs * 2.0 * n * (2 * n) * (2 * m0)
         return iters * nterms_dense * 8.0 * n * n * m0
     if name == "solve":
         return (iters - 1) * nc * 8.0 * n * n * m0
@@ -184,8 +193,12 @@ def phase_work(name, spec, c, iters, nterms_dense):
 
 def phase_peak(name, precision, pk, sm_mhz):
     clk = (sm_mhz or 2070.0) / 2070.0
-    if name in ("lu", "solve") and precision == "fp32":
-        return FP32_SIMT_TFLOPS_AT_MAX * clk, "alu", "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x SM clock"
+    if name in ("lu", "solve") and precision in ("fp32", "fp32_i8"):
+        return (FP32_SIMT_TFLOPS_AT_MAX * clk, "alu",
+                "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x SM clock")
+    if name == "apply" and precision == "fp32_i8":
+        return (pk["bf16_tflops_sustained"], "tensor",
+                f"BF16 dense, {pk['source']} (sustained figure: timed inside a long step)")
     return FP64_NOMINAL_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s"
 
 
@@ -282,7 +295,7 @@ def run_gpu(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64 LU + f64",
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64 LU + bf16-split f64 products + f64",
            "data": "synthetic (seeded generator, no dataset)",
            "config": {"workload": args.workload, "n": n, "degree": 2, "nc": c["nc"],
                       "m0": m0, "count_inside": c["count"], "lu_precision": spec["precision"],

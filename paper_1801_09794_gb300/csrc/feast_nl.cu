@@ -143,6 +143,8 @@ struct feast_nl_handle {
     void* dF = nullptr;             // nc x n x n in LU precision
     int* dpiv = nullptr;
     int* dinfo = nullptr;
+    int2* dGather = nullptr;        // per node and panel: row interchanges as a gather list
+    int* dGcount = nullptr;
     double ms_factor = 0.0;
     // subspace workspace (sized for mcap columns)
     int mcap = 0;
@@ -382,8 +384,8 @@ int filter_step(feast_nl_handle* h, int m) {
             Phase ph(h, FEAST_NL_PH_SOLVE);
             CK(broadcast_rhs<double2>(h->st, n, m, h->dR, h->nc, Y, n * m));
             CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
-                                         static_cast<const double2*>(h->dF), n * n, h->dpiv,
-                                         h->nc, Y, n * m, m));
+                                         static_cast<const double2*>(h->dF), n * n, h->dGather,
+                                         h->dGcount, h->nc, Y, n * m, m));
         }
         Phase ph(h, FEAST_NL_PH_ACCUM);
         CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
@@ -396,8 +398,8 @@ int filter_step(feast_nl_handle* h, int m) {
             Phase ph(h, FEAST_NL_PH_SOLVE);
             CK(broadcast_rhs<float2>(h->st, n, m, h->dR, h->nc, Y, n * m));
             CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
-                                        static_cast<const float2*>(h->dF), n * n, h->dpiv, h->nc,
-                                        Y, n * m, m));
+                                        static_cast<const float2*>(h->dF), n * n, h->dGather,
+                                        h->dGcount, h->nc, Y, n * m, m));
         }
         Phase ph(h, FEAST_NL_PH_ACCUM);
         CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
@@ -482,6 +484,8 @@ void feast_nl_destroy(feast_nl_handle* h) {
     if (h->dF) cudaFree(h->dF);
     dfree(h->dpiv);
     dfree(h->dinfo);
+    dfree(h->dGather);
+    dfree(h->dGcount);
     dfree(h->dStatus);
     if (h->hStatus) cudaFreeHost(h->hStatus);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
@@ -692,12 +696,19 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     if (h->dF) cudaFree(h->dF);
     h->dF = nullptr;
     dfree(h->dpiv); dfree(h->dinfo); dfree(h->dz); dfree(h->dw);
+    dfree(h->dGather); dfree(h->dGcount);
     h->have_contour = false;
     h->have_result = false;
     release_workspace(h);
     double2 *dcoef = nullptr, *ddiag = nullptr;
     CK(cudaMalloc(&h->dF, (size_t)nc * n * n * h->lu_elem()));
     CK(dalloc(&h->dpiv, (size_t)nc * n));
+    {
+        const int nb = h->precision == FEAST_NL_FP64 ? lu_block_size<double2>() : lu_block_size<float2>();
+        const int gs = lu_gather_stride(n, nb);
+        CK(dalloc(&h->dGather, (size_t)nc * gs));
+        CK(dalloc(&h->dGcount, (size_t)nc * (gs / 128)));
+    }
     CK(dalloc(&h->dinfo, (size_t)nc));
     CK(dalloc(&h->dz, (size_t)nc));
     CK(dalloc(&h->dw, (size_t)nc));
@@ -725,7 +736,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
         }
         Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<double2>(h->st, n, lu_block_size<double2>(), F, n * n, h->dpiv, nc,
-                                      h->dinfo));
+                                      h->dinfo, h->dGather, h->dGcount));
     } else {
         float2* F = static_cast<float2*>(h->dF);
         {
@@ -734,7 +745,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
         }
         Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<float2>(h->st, n, lu_block_size<float2>(), F, n * n, h->dpiv, nc,
-                                     h->dinfo));
+                                     h->dinfo, h->dGather, h->dGcount));
     }
     CK(cudaEventRecord(h->ev1, h->st));
     std::vector<int> info(nc);
@@ -889,16 +900,20 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
     if (h->precision == FEAST_NL_FP64) {
         double2* Yb = static_cast<double2*>(h->dY);
         CK(broadcast_rhs<double2>(h->st, n, m, h->dR, 1, Yb, n * m));
+        const int gs = lu_gather_stride(n, lu_block_size<double2>());
         CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
                                      static_cast<const double2*>(h->dF) + (int64_t)j * n * n, n * n,
-                                     h->dpiv + (int64_t)j * n, 1, Yb, n * m, m));
+                                     h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
+                                     1, Yb, n * m, m));
         CK(to_double<double2>(h->st, n * m, Yb, h->dX));
     } else {
         float2* Yb = static_cast<float2*>(h->dY);
         CK(broadcast_rhs<float2>(h->st, n, m, h->dR, 1, Yb, n * m));
+        const int gs = lu_gather_stride(n, lu_block_size<float2>());
         CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
                                     static_cast<const float2*>(h->dF) + (int64_t)j * n * n, n * n,
-                                    h->dpiv + (int64_t)j * n, 1, Yb, n * m, m));
+                                    h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
+                                    1, Yb, n * m, m));
         CK(to_double<float2>(h->st, n * m, Yb, h->dX));
     }
     h->have_result = false;

@@ -199,12 +199,17 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, 
                        const double* tau, double2* W, const int* term_slot, int* err);
 
 // ------------------------------------------------------------------ LU (k_lu.cu)
+// The factorisation also writes, per node and panel, the panel's row interchanges
+// as a gather list (gather: nc x lu_gather_stride int2, gcount: nc x panels ints),
+// which the solves apply to the right-hand sides.
+int lu_gather_stride(int64_t n, int nb);
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
-                              int* piv, int nc, int* info);
+                              int* piv, int nc, int* info, int2* gather, int* gcount);
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
-                             const int* piv, int nc, T* Y, int64_t strideY, int m);
+                             const int2* gather, const int* gcount, int nc, T* Y,
+                             int64_t strideY, int m);
 template <typename T> int lu_block_size();
 
 // ------------------------------------------------------------------ reduced problem (k_reduced.cu)

@@ -3,10 +3,15 @@
 //
 // Right-looking blocked LU, one panel of nb columns at a time, all nodes of the
 // contour in one launch (grid dimension = node):
-//   1. panel:  factor F[k0:n, k0:k0+jb] column by column; pivot = first row of
-//              maximal |Re|+|Im| (LAPACK's cabs1); swap, scale, rank-1 update;
-//   2. swap + trsm: apply the panel's interchanges to the columns right of the
-//              panel, then U12 = L11^{-1} A12;
+//   1. panel:  factor F[k0:n, k0:k0+jb]; pivot = first row of maximal |Re|+|Im|
+//              (LAPACK's cabs1).  The panel is processed in mini-panels of 4
+//              columns held in registers (each of the 1024 threads owns up to 4
+//              rows), so the in-panel rank-1 updates never touch memory; after a
+//              mini-panel its interchanges, triangular solve and rank-4 update are
+//              applied to the rest of the panel in one pass.  The panel's
+//              interchanges are also emitted as a gather list (dst <- src rows).
+//   2. swap + trsm: the gather list applied to the columns right of the panel,
+//              then U12 = L11^{-1} A12 (one warp per column);
 //   3. update: A22 -= L21 U12 (complex GEMM).
 // Interchanges are never applied to the columns LEFT of a panel: every L block
 // stays in the row order it had when it was formed, and the forward solve
@@ -19,12 +24,242 @@
 namespace fnl {
 namespace {
 
-constexpr int kTrsmCols = 64;   // right-hand-side columns per CTA in the triangular kernels
+constexpr int kPanelThreads = 1024;
+constexpr int kMini = 4;           // columns per register-resident mini-panel
+// diagonal-block tile of the triangular kernels (jb <= nb: 64 complex64 / 32 complex128)
+template <typename T> struct TriMax;
+template <> struct TriMax<float2> { static constexpr int value = 64; };
+template <> struct TriMax<double2> { static constexpr int value = 32; };
+constexpr int kWarpsPerCta = 8;    // triangular kernels: one warp per column
 
+// ---------------------------------------------------------------------------
+// block-wide argmax of (value, row): larger value wins, lower row on ties
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void argmax_warp(R& v, int& i) {
+    for (int o = 16; o > 0; o >>= 1) {
+        R ov = __shfl_down_sync(0xffffffffu, v, o);
+        int oi = __shfl_down_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+}
+
+// Gather list of a panel's interchanges: the sequential swaps (c, piv[c]),
+// c = k0..k0+jb-1, permute the rows of the set {k0..k0+jb-1} U {piv[c]}; after
+// them row dst[e] holds what row src[e] held before.  One thread, <= 2 jb rows.
+__device__ void panel_gather_list(int k0, int jb, const int* ip, int2* list, int* count) {
+    int rows[128], src[128];
+    int cnt = 0;
+    for (int c = 0; c < jb; ++c) { rows[cnt] = k0 + c; src[cnt] = k0 + c; ++cnt; }
+    for (int c = 0; c < jb; ++c) {
+        const int a = k0 + c, b = ip[k0 + c];
+        if (a == b) continue;
+        int ia = a - k0, ib = -1;
+        if (b < k0 + jb) ib = b - k0;
+        else {
+            for (int e = jb; e < cnt; ++e)
+                if (rows[e] == b) { ib = e; break; }
+            if (ib < 0) { rows[cnt] = b; src[cnt] = b; ib = cnt++; }
+        }
+        int t = src[ia]; src[ia] = src[ib]; src[ib] = t;
+    }
+    int out = 0;
+    for (int e = 0; e < cnt; ++e)
+        if (rows[e] != src[e]) list[out++] = make_int2(rows[e], src[e]);
+    *count = out;
+}
+
+// ---------------------------------------------------------------------------
+// Panel factorisation, register-resident mini-panels.  ROWS = rows per thread.
+// ---------------------------------------------------------------------------
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
+    int64_t n, int k0, int jb, T* F, int64_t ld, int64_t strideF, int* piv, int* info,
+    int2* gather, int* gcount, int panel_index, int gstride) {
+    typedef typename cplx_real<T>::type R;
+    T* A = F + blockIdx.x * strideF;
+    int* ip = piv + (int64_t)blockIdx.x * n;
+    __shared__ R s_v[32];
+    __shared__ int s_i[32];
+    __shared__ int s_p;
+    __shared__ T s_prow[kMini];     // pivot row of the mini-panel
+    __shared__ T s_crow[kMini];     // row being replaced by the pivot row
+    __shared__ T s_L11[kMini][kMini];
+    __shared__ T s_U[kMini][64];    // U12 rows of the mini-panel (rest of the panel)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int pend = k0 + jb;
+    T v[ROWS][kMini];
+
+    for (int mb0 = k0; mb0 < pend; mb0 += kMini) {
+        const int w = min(kMini, pend - mb0);
+        // load the mini-panel rows owned by this thread: row k0 + tid + i * 1024
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+#pragma unroll
+            for (int c = 0; c < kMini; ++c)
+                v[i][c] = (r < n && c < w) ? A[r + (int64_t)(mb0 + c) * ld] : cmake<T>(0.0, 0.0);
+        }
+        for (int c = 0; c < w; ++c) {
+            const int col = mb0 + c;
+            // pivot search among rows >= col
+            R best = (R)-1;
+            int bi = INT_MAX;
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+                T x = v[i][0];
+#pragma unroll
+                for (int cc = 1; cc < kMini; ++cc) if (cc == c) x = v[i][cc];
+                if (r >= col && r < n) {
+                    R a = cabs1(x);
+                    if (a > best) { best = a; bi = (int)r; }
+                }
+            }
+            argmax_warp(best, bi);
+            if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
+            __syncthreads();
+            if (warp == 0) {
+                best = s_v[lane];
+                bi = s_i[lane];
+                argmax_warp(best, bi);
+                if (lane == 0) {
+                    if (bi == INT_MAX || bi < col || bi >= n) bi = col;
+                    if (!(best > (R)0) && info[blockIdx.x] == 0) info[blockIdx.x] = col + 1;
+                    s_p = bi;
+                    ip[col] = bi;
+                }
+            }
+            __syncthreads();
+            const int p = s_p;
+            const int owner_p = (p - k0) % kPanelThreads, slot_p = (p - k0) / kPanelThreads;
+            const int owner_c = (col - k0) % kPanelThreads, slot_c = (col - k0) / kPanelThreads;
+            if (tid == owner_p) {
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i)
+                    if (i == slot_p)
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) s_prow[cc] = v[i][cc];
+            }
+            if (tid == owner_c && p != col) {
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i)
+                    if (i == slot_c)
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) s_crow[cc] = v[i][cc];
+            }
+            __syncthreads();
+            if (p != col) {
+                if (tid == owner_c) {
+#pragma unroll
+                    for (int i = 0; i < ROWS; ++i)
+                        if (i == slot_c)
+#pragma unroll
+                            for (int cc = 0; cc < kMini; ++cc) v[i][cc] = s_prow[cc];
+                }
+                if (tid == owner_p) {
+#pragma unroll
+                    for (int i = 0; i < ROWS; ++i)
+                        if (i == slot_p)
+#pragma unroll
+                            for (int cc = 0; cc < kMini; ++cc) v[i][cc] = s_crow[cc];
+                }
+            }
+            // scale and rank-1 update inside the mini-panel (rows > col)
+            T piv_v = s_prow[0];
+#pragma unroll
+            for (int cc = 1; cc < kMini; ++cc) if (cc == c) piv_v = s_prow[cc];
+            const T inv = crcp(piv_v);
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+                if (r > col && r < n) {
+                    T l = cmake<T>(0.0, 0.0);
+#pragma unroll
+                    for (int cc = 0; cc < kMini; ++cc) if (cc == c) { l = v[i][cc] * inv; v[i][cc] = l; }
+#pragma unroll
+                    for (int cc = 0; cc < kMini; ++cc)
+                        if (cc > c && cc < w) v[i][cc] = cfms(l, s_prow[cc], v[i][cc]);
+                }
+            }
+            __syncthreads();   // s_prow / s_crow reuse
+        }
+        // write the factored mini-panel back; keep its L11 block in smem
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+            if (r < n)
+#pragma unroll
+                for (int c = 0; c < kMini; ++c)
+                    if (c < w) A[r + (int64_t)(mb0 + c) * ld] = v[i][c];
+            if (r >= mb0 && r < mb0 + w)
+#pragma unroll
+                for (int c = 0; c < kMini; ++c) s_L11[r - mb0][c] = v[i][c];
+        }
+        const int rest0 = mb0 + w, nrest = pend - rest0;   // remaining panel columns
+        const int nleft = mb0 - k0;                        // factored panel columns
+        __syncthreads();
+        // this mini-panel's interchanges on the panel's factored columns, so that the
+        // whole panel ends in the row order of all its interchanges
+        if (tid >= 64 && tid - 64 < nleft) {
+            T* colp = A + (int64_t)(k0 + tid - 64) * ld;
+            for (int c = 0; c < w; ++c) {
+                const int a = mb0 + c, b = ip[a];
+                if (a != b) { T t0 = colp[a]; colp[a] = colp[b]; colp[b] = t0; }
+            }
+        }
+        if (nrest > 0) {
+            // interchanges of this mini-panel on the remaining panel columns, then
+            // U12 = L11^{-1} A12: one thread per remaining column
+            if (tid < nrest) {
+                T* colp = A + (int64_t)(rest0 + tid) * ld;
+                for (int c = 0; c < w; ++c) {
+                    const int a = mb0 + c, b = ip[a];
+                    if (a != b) { T t0 = colp[a]; colp[a] = colp[b]; colp[b] = t0; }
+                }
+                T u[kMini];
+#pragma unroll
+                for (int c = 0; c < kMini; ++c) u[c] = (c < w) ? colp[mb0 + c] : cmake<T>(0.0, 0.0);
+#pragma unroll
+                for (int c = 0; c < kMini; ++c)
+#pragma unroll
+                    for (int r2 = c + 1; r2 < kMini; ++r2)
+                        if (r2 < w) u[r2] = cfms(s_L11[r2][c], u[c], u[r2]);
+#pragma unroll
+                for (int c = 0; c < kMini; ++c) {
+                    if (c < w) colp[mb0 + c] = u[c];
+                    s_U[c][tid] = u[c];
+                }
+            }
+            __syncthreads();
+            // rank-w update of rows below the mini-panel, remaining panel columns
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+                if (r >= rest0 && r < n) {
+                    for (int j = 0; j < nrest; ++j) {
+                        T* ap = A + r + (int64_t)(rest0 + j) * ld;
+                        T a = *ap;
+#pragma unroll
+                        for (int c = 0; c < kMini; ++c)
+                            if (c < w) a = cfms(v[i][c], s_U[c][j], a);
+                        *ap = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && gather != nullptr)
+        panel_gather_list(k0, jb, ip, gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64,
+                          gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
+}
+
+// Column-at-a-time panel in global memory (any n; used above 8192 rows).
 template <typename T>
-__global__ void __launch_bounds__(1024) lu_panel_kernel(int64_t n, int k0, int jb, T* F,
-                                                        int64_t ld, int64_t strideF, int* piv,
-                                                        int* info) {
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(
+    int64_t n, int k0, int jb, T* F, int64_t ld, int64_t strideF, int* piv, int* info,
+    int2* gather, int* gcount, int panel_index, int gstride) {
     typedef typename cplx_real<T>::type R;
     T* A = F + blockIdx.x * strideF;
     int* ip = piv + (int64_t)blockIdx.x * n;
@@ -33,30 +268,20 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(int64_t n, int k0, int j
     __shared__ int s_p;
     __shared__ T s_u[128];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = (nt + 31) >> 5;
     for (int c = k0; c < k0 + jb; ++c) {
-        // --- pivot search in column c, rows c..n-1 (first index among equal maxima)
         R best = (R)-1;
         int bi = INT_MAX;
         for (int64_t r = c + tid; r < n; r += nt) {
             R v = cabs1(A[r + c * ld]);
             if (v > best) { best = v; bi = (int)r; }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            R ov = __shfl_down_sync(0xffffffffu, best, o);
-            int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
+        argmax_warp(best, bi);
         if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
         __syncthreads();
         if (warp == 0) {
-            best = lane < nwarps ? s_v[lane] : (R)-1;
-            bi = lane < nwarps ? s_i[lane] : INT_MAX;
-            for (int o = 16; o > 0; o >>= 1) {
-                R ov = __shfl_down_sync(0xffffffffu, best, o);
-                int oi = __shfl_down_sync(0xffffffffu, bi, o);
-                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-            }
+            best = s_v[lane];
+            bi = s_i[lane];
+            argmax_warp(best, bi);
             if (lane == 0) {
                 if (bi == INT_MAX || bi < c || bi >= n) bi = c;
                 if (!(best > (R)0) && info[blockIdx.x] == 0) info[blockIdx.x] = c + 1;
@@ -66,7 +291,6 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(int64_t n, int k0, int j
         }
         __syncthreads();
         const int p = s_p;
-        // --- interchange rows c and p inside the panel
         if (p != c) {
             for (int cc = k0 + tid; cc < k0 + jb; cc += nt) {
                 T a = A[c + cc * ld], b = A[p + cc * ld];
@@ -77,7 +301,6 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(int64_t n, int k0, int j
         __syncthreads();
         for (int cc = c + tid; cc < k0 + jb; cc += nt) s_u[cc - k0] = A[c + cc * ld];
         __syncthreads();
-        // --- scale the column below the pivot and update the rest of the panel
         const T inv = crcp(s_u[c - k0]);
         for (int64_t r = c + 1 + tid; r < n; r += nt) {
             T l = A[r + c * ld] * inv;
@@ -87,102 +310,120 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(int64_t n, int k0, int j
         }
         __syncthreads();
     }
+    if (tid == 0 && gather != nullptr)
+        panel_gather_list(k0, jb, ip, gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64,
+                          gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
 }
 
-// Columns [col_begin, col_begin+ncols) of B: interchanges of rows k0..k0+jb-1,
-// then B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F).
+// ---------------------------------------------------------------------------
+// Triangular kernels, one warp per right-hand-side column; the jb rows of the
+// diagonal block are spread over the lanes (lane l holds rows l and l + 32).
+// ---------------------------------------------------------------------------
+// Columns [col_begin, col_begin+ncols) of B: the panel's gather list, then
+// B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F).
 template <typename T>
-__global__ void __launch_bounds__(kTrsmCols) swap_trsm_lower_kernel(
+__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
     int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF,
-    const int* __restrict__ piv, T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols) {
-    extern __shared__ unsigned char smem_raw[];
-    T* sL = reinterpret_cast<T*>(smem_raw);          // jb x (jb+1), row-major sL[r*(jb+1)+c]
-    T* sX = sL + jb * (jb + 1);                       // jb x kTrsmCols
+    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
+    T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols) {
+    __shared__ T sL[TriMax<T>::value][TriMax<T>::value + 1];
     const int node = blockIdx.y;
     F += node * strideF;
     B += node * strideB;
-    const int* ip = piv + (int64_t)node * n;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < jb * jb; e += blockDim.x) {
         int r = e % jb, c = e / jb;
-        sL[r * (jb + 1) + c] = F[(k0 + r) + (int64_t)(k0 + c) * ld];
-    }
-    const int cl = blockIdx.x * kTrsmCols + tid;
-    const bool active = cl < ncols;
-    T* col = B + (int64_t)(col_begin + (active ? cl : 0)) * ldb;
-    if (active) {
-        for (int c = k0; c < k0 + jb; ++c) {
-            int p = ip[c];
-            if (p != c) {
-                T a = col[c], b = col[p];
-                col[c] = b;
-                col[p] = a;
-            }
-        }
-        for (int i = 0; i < jb; ++i) sX[i * kTrsmCols + tid] = col[k0 + i];
+        sL[r][c] = F[(k0 + r) + (int64_t)(k0 + c) * ld];
     }
     __syncthreads();
-    if (!active) return;
-    for (int i = 0; i < jb; ++i) {
-        T xi = sX[i * kTrsmCols + tid];
-        for (int r = i + 1; r < jb; ++r)
-            sX[r * kTrsmCols + tid] = cfms(sL[r * (jb + 1) + i], xi, sX[r * kTrsmCols + tid]);
+    const int cl = blockIdx.x * kWarpsPerCta + warp;
+    if (cl >= ncols) return;
+    T* col = B + (int64_t)(col_begin + cl) * ldb;
+    // interchanges: every src read before any dst written
+    const int2* gl = gather + (int64_t)node * gstride + panel_index * 2 * 64;
+    const int cnt = gcount[(int64_t)node * (gstride / 128) + panel_index];
+    T g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        if (e < cnt) g[q] = col[gl[e].y];
     }
-    for (int i = 0; i < jb; ++i) col[k0 + i] = sX[i * kTrsmCols + tid];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        if (e < cnt) col[gl[e].x] = g[q];
+    }
+    __syncwarp();
+    T x0 = (lane < jb) ? col[k0 + lane] : cmake<T>(0.0, 0.0);
+    T x1 = (lane + 32 < jb) ? col[k0 + lane + 32] : cmake<T>(0.0, 0.0);
+    for (int i = 0; i < jb; ++i) {
+        T src = (i < 32) ? x0 : x1;
+        T xi;
+        xi.x = __shfl_sync(0xffffffffu, src.x, i & 31);
+        xi.y = __shfl_sync(0xffffffffu, src.y, i & 31);
+        if (lane > i) x0 = cfms(sL[lane][i], xi, x0);
+        if (lane + 32 > i && lane + 32 < jb) x1 = cfms(sL[lane + 32][i], xi, x1);
+    }
+    if (lane < jb) col[k0 + lane] = x0;
+    if (lane + 32 < jb) col[k0 + lane + 32] = x1;
 }
 
 // B[k0:k0+jb, col] <- U11^{-1} B[k0:k0+jb, col] (U11 upper with its diagonal, from F).
 template <typename T>
-__global__ void __launch_bounds__(kTrsmCols) trsm_upper_kernel(
+__global__ void __launch_bounds__(32 * kWarpsPerCta) trsm_upper_kernel(
     int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF, T* B,
     int64_t ldb, int64_t strideB, int ncols) {
-    extern __shared__ unsigned char smem_raw[];
-    T* sU = reinterpret_cast<T*>(smem_raw);
-    T* sX = sU + jb * (jb + 1);
+    __shared__ T sU[TriMax<T>::value][TriMax<T>::value + 1];
     const int node = blockIdx.y;
     F += node * strideF;
     B += node * strideB;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < jb * jb; e += blockDim.x) {
         int r = e % jb, c = e / jb;
         T v = F[(k0 + r) + (int64_t)(k0 + c) * ld];
-        sU[r * (jb + 1) + c] = (r == c) ? crcp(v) : v;   // diagonal stored inverted
+        sU[r][c] = (r == c) ? crcp(v) : v;          // diagonal stored inverted
     }
-    const int cl = blockIdx.x * kTrsmCols + tid;
-    const bool active = cl < ncols;
-    T* col = B + (int64_t)(active ? cl : 0) * ldb;
-    if (active)
-        for (int i = 0; i < jb; ++i) sX[i * kTrsmCols + tid] = col[k0 + i];
     __syncthreads();
-    if (!active) return;
+    const int cl = blockIdx.x * kWarpsPerCta + warp;
+    if (cl >= ncols) return;
+    T* col = B + (int64_t)cl * ldb;
+    T x0 = (lane < jb) ? col[k0 + lane] : cmake<T>(0.0, 0.0);
+    T x1 = (lane + 32 < jb) ? col[k0 + lane + 32] : cmake<T>(0.0, 0.0);
     for (int i = jb - 1; i >= 0; --i) {
-        T xi = sX[i * kTrsmCols + tid] * sU[i * (jb + 1) + i];
-        sX[i * kTrsmCols + tid] = xi;
-        for (int r = 0; r < i; ++r)
-            sX[r * kTrsmCols + tid] = cfms(sU[r * (jb + 1) + i], xi, sX[r * kTrsmCols + tid]);
+        // x_i <- x_i / U_ii (owner lane), broadcast, eliminate from rows < i
+        if (i < 32) { if (lane == i) x0 = x0 * sU[i][i]; }
+        else        { if (lane == i - 32) x1 = x1 * sU[i][i]; }
+        T src = (i < 32) ? x0 : x1;
+        T xi;
+        xi.x = __shfl_sync(0xffffffffu, src.x, i & 31);
+        xi.y = __shfl_sync(0xffffffffu, src.y, i & 31);
+        if (lane < i) x0 = cfms(sU[lane][i], xi, x0);
+        if (lane + 32 < i) x1 = cfms(sU[lane + 32][i], xi, x1);
     }
-    for (int i = 0; i < jb; ++i) col[k0 + i] = sX[i * kTrsmCols + tid];
+    if (lane < jb) col[k0 + lane] = x0;
+    if (lane + 32 < jb) col[k0 + lane + 32] = x1;
 }
 
 template <typename T>
-size_t tri_smem(int jb) {
-    return sizeof(T) * ((size_t)jb * (jb + 1) + (size_t)jb * kTrsmCols);
-}
-
-template <typename T>
-cudaError_t ensure_attrs() {
-    static bool done = false;   // per process; the attribute is per function
-    if (done) return cudaSuccess;
-    int nb = lu_block_size<T>();
-    int bytes = (int)tri_smem<T>(nb);
-    cudaError_t e = cudaFuncSetAttribute(swap_trsm_lower_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(trsm_upper_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             bytes);
-    if (e != cudaSuccess) return e;
-    done = true;
-    return cudaSuccess;
+cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_t strideF,
+                         int* piv, int nc, int* info, int2* gather, int* gcount, int panel,
+                         int gstride) {
+    const int64_t rows = n - k0;
+    note_launch();
+    if (rows <= kPanelThreads)
+        lu_panel_reg_kernel<T, 1><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
+                                                                gather, gcount, panel, gstride);
+    else if (rows <= kPanelThreads * 2)
+        lu_panel_reg_kernel<T, 2><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
+                                                                gather, gcount, panel, gstride);
+    else if (rows <= kPanelThreads * 4 && sizeof(T) == 8)   // complex128 would spill at 4 rows
+        lu_panel_reg_kernel<T, 4><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
+                                                                gather, gcount, panel, gstride);
+    else
+        lu_panel_kernel<T><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
+                                                         gather, gcount, panel, gstride);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -190,22 +431,29 @@ cudaError_t ensure_attrs() {
 template <> int lu_block_size<double2>() { return 32; }
 template <> int lu_block_size<float2>() { return 64; }
 
+int lu_gather_stride(int64_t n, int nb) {
+    // per node: one 128-entry slot (2 * 64 rows max) per panel
+    return (int)(((n + nb - 1) / nb) * 128);
+}
+
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
-                              int* piv, int nc, int* info) {
-    cudaError_t e = ensure_attrs<T>();
-    if (e != cudaSuccess) return e;
+                              int* piv, int nc, int* info, int2* gather, int* gcount) {
     const T minus1 = cmake<T>(-1.0, 0.0), one = cmake<T>(1.0, 0.0);
-    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    const int gstride = lu_gather_stride(n, nb);
+    cudaError_t e;
+    for (int64_t k0 = 0, panel = 0; k0 < n; k0 += nb, ++panel) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
-        note_launch();
-        lu_panel_kernel<T><<<nc, 1024, 0, st>>>(n, (int)k0, jb, F, n, strideF, piv, info);
+        if ((e = launch_panel<T>(st, n, (int)k0, jb, F, strideF, piv, nc, info, gather, gcount,
+                                 (int)panel, gstride)) != cudaSuccess)
+            return e;
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
-            dim3 g((unsigned)((rest + kTrsmCols - 1) / kTrsmCols), nc);
+            dim3 g((unsigned)((rest + kWarpsPerCta - 1) / kWarpsPerCta), nc);
             note_launch();
-            swap_trsm_lower_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(
-                n, (int)k0, jb, F, n, strideF, piv, F, n, strideF, (int)(k0 + jb), (int)rest);
+            swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
+                n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, F, n, strideF,
+                (int)(k0 + jb), (int)rest);
             e = gemm<T>(st, 0, (int)rest, (int)rest, jb, minus1, F + (k0 + jb) + k0 * n, n,
                         strideF, F + k0 + (k0 + jb) * n, n, strideF, one,
                         F + (k0 + jb) + (k0 + jb) * n, n, strideF, nc);
@@ -217,16 +465,17 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
 
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
-                             const int* piv, int nc, T* Y, int64_t strideY, int m) {
-    cudaError_t e = ensure_attrs<T>();
-    if (e != cudaSuccess) return e;
+                             const int2* gather, const int* gcount, int nc, T* Y, int64_t strideY,
+                             int m) {
     const T minus1 = cmake<T>(-1.0, 0.0), one = cmake<T>(1.0, 0.0);
-    dim3 g((unsigned)((m + kTrsmCols - 1) / kTrsmCols), nc);
-    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    const int gstride = lu_gather_stride(n, nb);
+    cudaError_t e;
+    dim3 g((unsigned)((m + kWarpsPerCta - 1) / kWarpsPerCta), nc);
+    for (int64_t k0 = 0, panel = 0; k0 < n; k0 += nb, ++panel) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
         note_launch();
-        swap_trsm_lower_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(
-            n, (int)k0, jb, F, n, strideF, piv, Y, n, strideY, 0, m);
+        swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
+            n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, 0, m);
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
             e = gemm<T>(st, 0, (int)rest, m, jb, minus1, F + (k0 + jb) + k0 * n, n, strideF,
@@ -238,8 +487,8 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
         note_launch();
-        trsm_upper_kernel<T><<<g, kTrsmCols, tri_smem<T>(jb), st>>>(n, (int)k0, jb, F, n, strideF,
-                                                                    Y, n, strideY, m);
+        trsm_upper_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(n, (int)k0, jb, F, n, strideF, Y, n,
+                                                              strideY, m);
         if (k0 > 0) {
             e = gemm<T>(st, 0, (int)k0, m, jb, minus1, F + k0 * n, n, strideF, Y + k0, n, strideY,
                         one, Y, n, strideY, nc);
@@ -250,12 +499,13 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
 }
 
 template cudaError_t lu_factor_batched<double2>(cudaStream_t, int64_t, int, double2*, int64_t,
-                                                int*, int, int*);
+                                                int*, int, int*, int2*, int*);
 template cudaError_t lu_factor_batched<float2>(cudaStream_t, int64_t, int, float2*, int64_t, int*,
-                                               int, int*);
+                                               int, int*, int2*, int*);
 template cudaError_t lu_solve_batched<double2>(cudaStream_t, int64_t, int, const double2*,
-                                               int64_t, const int*, int, double2*, int64_t, int);
+                                               int64_t, const int2*, const int*, int, double2*,
+                                               int64_t, int);
 template cudaError_t lu_solve_batched<float2>(cudaStream_t, int64_t, int, const float2*, int64_t,
-                                              const int*, int, float2*, int64_t, int);
+                                              const int2*, const int*, int, float2*, int64_t, int);
 
 }  // namespace fnl
