@@ -385,7 +385,7 @@ int filter_step(feast_nl_handle* h, int m) {
             CK(broadcast_rhs<double2>(h->st, n, m, h->dR, h->nc, Y, n * m));
             CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
                                          static_cast<const double2*>(h->dF), n * n, h->dGather,
-                                         h->dGcount, h->nc, Y, n * m, m));
+                                         h->dGcount, h->nc, Y, n * m, m, &h->dStatus->flags));
         }
         Phase ph(h, FEAST_NL_PH_ACCUM);
         CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
@@ -399,7 +399,7 @@ int filter_step(feast_nl_handle* h, int m) {
             CK(broadcast_rhs<float2>(h->st, n, m, h->dR, h->nc, Y, n * m));
             CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
                                         static_cast<const float2*>(h->dF), n * n, h->dGather,
-                                        h->dGcount, h->nc, Y, n * m, m));
+                                        h->dGcount, h->nc, Y, n * m, m, &h->dStatus->flags));
         }
         Phase ph(h, FEAST_NL_PH_ACCUM);
         CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
@@ -727,6 +727,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     CK(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(ddiag, diagc.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemsetAsync(h->dinfo, 0, sizeof(int) * nc, h->st));
+    CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
     CK(cudaEventRecord(h->ev0, h->st));
     if (h->precision == FEAST_NL_FP64) {
         double2* F = static_cast<double2*>(h->dF);
@@ -736,7 +737,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
         }
         Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<double2>(h->st, n, lu_block_size<double2>(), F, n * n, h->dpiv, nc,
-                                      h->dinfo, h->dGather, h->dGcount));
+                                      h->dinfo, h->dGather, h->dGcount, &h->dStatus->flags));
     } else {
         float2* F = static_cast<float2*>(h->dF);
         {
@@ -745,11 +746,12 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
         }
         Phase ph(h, FEAST_NL_PH_LU);
         CK(lu_factor_batched<float2>(h->st, n, lu_block_size<float2>(), F, n * n, h->dpiv, nc,
-                                     h->dinfo, h->dGather, h->dGcount));
+                                     h->dinfo, h->dGather, h->dGcount, &h->dStatus->flags));
     }
     CK(cudaEventRecord(h->ev1, h->st));
     std::vector<int> info(nc);
     CK(cudaMemcpyAsync(info.data(), h->dinfo, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -757,6 +759,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     prof_flush(h);
     dfree(dcoef);
     dfree(ddiag);
+    if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node LU");
     for (int j = 0; j < nc; ++j)
         if (info[j] != 0)
             return fail(FEAST_NL_ESINGULAR_NODE,
@@ -820,6 +823,7 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     int status = converged ? FEAST_NL_OK : FEAST_NL_ENOT_CONVERGED;
     if (stt.n_inside >= m) status = FEAST_NL_ETOO_MANY;
     if (stt.flags & 2) status = FEAST_NL_ESINGULAR_NODE;
+    if (stt.flags & 16) status = FEAST_NL_EDEVICE;
     if (info) {
         info->iters = std::min(it, maxit);
         info->n_inside = stt.n_inside;
@@ -897,6 +901,7 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
     CKS(ensure_workspace(h, std::max(m, h->mcap)));
     const int64_t n = h->n;
     CKS(load_block(h, R, m, h->dR));
+    CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
     if (h->precision == FEAST_NL_FP64) {
         double2* Yb = static_cast<double2*>(h->dY);
         CK(broadcast_rhs<double2>(h->st, n, m, h->dR, 1, Yb, n * m));
@@ -904,7 +909,7 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
         CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
                                      static_cast<const double2*>(h->dF) + (int64_t)j * n * n, n * n,
                                      h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
-                                     1, Yb, n * m, m));
+                                     1, Yb, n * m, m, &h->dStatus->flags));
         CK(to_double<double2>(h->st, n * m, Yb, h->dX));
     } else {
         float2* Yb = static_cast<float2*>(h->dY);
@@ -913,10 +918,13 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
         CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
                                     static_cast<const float2*>(h->dF) + (int64_t)j * n * n, n * n,
                                     h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
-                                    1, Yb, n * m, m));
+                                    1, Yb, n * m, m, &h->dStatus->flags));
         CK(to_double<float2>(h->st, n * m, Yb, h->dX));
     }
     h->have_result = false;
+    CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
     return store_block(h, h->dX, m, Y, m);
 }
 
@@ -946,6 +954,7 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const do
     CKS(filter_step(h, m));
     CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
     if (h->hStatus->flags & 2) return fail(FEAST_NL_ESINGULAR_NODE, "a lambda equals a node");
     return store_block(h, h->dQ, m, Q, m);
 }

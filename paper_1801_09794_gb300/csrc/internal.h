@@ -91,7 +91,8 @@ struct IterStatus {
     int n_inside;
     int n_conv;
     int flags;         // bit 0: reduced QR hit its limit; bit 1: Ritz value on a node;
-                       // bit 2: Cholesky breakdown; bit 3: Newton fallback used
+                       // bit 2: Cholesky breakdown; bit 3: Newton fallback used;
+                       // bit 4: a tensor-core pipeline wait timed out
     int qr_sweeps;     // QR sweeps of the last reduced eigenvalue computation
     double max_relres;
 };
@@ -203,13 +204,23 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, 
 // as a gather list (gather: nc x lu_gather_stride int2, gcount: nc x panels ints),
 // which the solves apply to the right-hand sides.
 int lu_gather_stride(int64_t n, int nb);
+// complex64 factors use the tensor-core update below; a failed internal wait
+// sets bit 4 of *err.
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
-                              int* piv, int nc, int* info, int2* gather, int* gcount);
+                              int* piv, int nc, int* info, int2* gather, int* gcount, int* err);
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y,
-                             int64_t strideY, int m);
+                             int64_t strideY, int m, int* err);
+
+// ------------------------------------------------------------------ k_cgemm_tc.cu
+// C -= A B (complex64, column-major, batch z advances A, B, C by sA, sB, sC) on
+// the TF32 tensor cores with FP32-level accuracy (three TF32 products of the
+// split operands); a failed internal wait sets bit 4 of *err.
+cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda,
+                             int64_t sA, const float2* B, int64_t ldb, int64_t sB, float2* C,
+                             int64_t ldc, int64_t sC, int batch, int* err);
 template <typename T> int lu_block_size();
 
 // ------------------------------------------------------------------ reduced problem (k_reduced.cu)

@@ -12,7 +12,8 @@
 //              interchanges are also emitted as a gather list (dst <- src rows).
 //   2. swap + trsm: the gather list applied to the columns right of the panel,
 //              then U12 = L11^{-1} A12 (one warp per column);
-//   3. update: A22 -= L21 U12 (complex GEMM).
+//   3. update: A22 -= L21 U12 (complex64: TF32 tensor cores on split operands,
+//              FP32-accurate; complex128: FP64 SIMT GEMM).
 // Interchanges are never applied to the columns LEFT of a panel: every L block
 // stays in the row order it had when it was formed, and the forward solve
 // applies each panel's interchanges to the right-hand side just before that
@@ -426,6 +427,19 @@ cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64
     return cudaGetLastError();
 }
 
+// C -= A B: FP64 SIMT for complex128, tensor cores for complex64.
+cudaError_t update(cudaStream_t st, int m, int n, int k, const double2* A, int64_t lda, int64_t sA,
+                   const double2* B, int64_t ldb, int64_t sB, double2* C, int64_t ldc, int64_t sC,
+                   int batch, int*) {
+    return gemm<double2>(st, 0, m, n, k, make_double2(-1.0, 0.0), A, lda, sA, B, ldb, sB,
+                         make_double2(1.0, 0.0), C, ldc, sC, batch);
+}
+cudaError_t update(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda, int64_t sA,
+                   const float2* B, int64_t ldb, int64_t sB, float2* C, int64_t ldc, int64_t sC,
+                   int batch, int* err) {
+    return cgemm_sub_tf32x3(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+}
+
 }  // namespace
 
 template <> int lu_block_size<double2>() { return 32; }
@@ -438,8 +452,7 @@ int lu_gather_stride(int64_t n, int nb) {
 
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
-                              int* piv, int nc, int* info, int2* gather, int* gcount) {
-    const T minus1 = cmake<T>(-1.0, 0.0), one = cmake<T>(1.0, 0.0);
+                              int* piv, int nc, int* info, int2* gather, int* gcount, int* err) {
     const int gstride = lu_gather_stride(n, nb);
     cudaError_t e;
     for (int64_t k0 = 0, panel = 0; k0 < n; k0 += nb, ++panel) {
@@ -454,9 +467,9 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
             swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
                 n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, F, n, strideF,
                 (int)(k0 + jb), (int)rest);
-            e = gemm<T>(st, 0, (int)rest, (int)rest, jb, minus1, F + (k0 + jb) + k0 * n, n,
-                        strideF, F + k0 + (k0 + jb) * n, n, strideF, one,
-                        F + (k0 + jb) + (k0 + jb) * n, n, strideF, nc);
+            e = update(st, (int)rest, (int)rest, jb, F + (k0 + jb) + k0 * n, n, strideF,
+                       F + k0 + (k0 + jb) * n, n, strideF, F + (k0 + jb) + (k0 + jb) * n, n,
+                       strideF, nc, err);
             if (e != cudaSuccess) return e;
         }
     }
@@ -466,8 +479,7 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y, int64_t strideY,
-                             int m) {
-    const T minus1 = cmake<T>(-1.0, 0.0), one = cmake<T>(1.0, 0.0);
+                             int m, int* err) {
     const int gstride = lu_gather_stride(n, nb);
     cudaError_t e;
     dim3 g((unsigned)((m + kWarpsPerCta - 1) / kWarpsPerCta), nc);
@@ -478,8 +490,8 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
             n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, 0, m);
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
-            e = gemm<T>(st, 0, (int)rest, m, jb, minus1, F + (k0 + jb) + k0 * n, n, strideF,
-                        Y + k0, n, strideY, one, Y + k0 + jb, n, strideY, nc);
+            e = update(st, (int)rest, m, jb, F + (k0 + jb) + k0 * n, n, strideF, Y + k0, n,
+                       strideY, Y + k0 + jb, n, strideY, nc, err);
             if (e != cudaSuccess) return e;
         }
     }
@@ -490,8 +502,8 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
         trsm_upper_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(n, (int)k0, jb, F, n, strideF, Y, n,
                                                               strideY, m);
         if (k0 > 0) {
-            e = gemm<T>(st, 0, (int)k0, m, jb, minus1, F + k0 * n, n, strideF, Y + k0, n, strideY,
-                        one, Y, n, strideY, nc);
+            e = update(st, (int)k0, m, jb, F + k0 * n, n, strideF, Y + k0, n, strideY, Y, n,
+                       strideY, nc, err);
             if (e != cudaSuccess) return e;
         }
     }
@@ -499,13 +511,14 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
 }
 
 template cudaError_t lu_factor_batched<double2>(cudaStream_t, int64_t, int, double2*, int64_t,
-                                                int*, int, int*, int2*, int*);
+                                                int*, int, int*, int2*, int*, int*);
 template cudaError_t lu_factor_batched<float2>(cudaStream_t, int64_t, int, float2*, int64_t, int*,
-                                               int, int*, int2*, int*);
+                                               int, int*, int2*, int*, int*);
 template cudaError_t lu_solve_batched<double2>(cudaStream_t, int64_t, int, const double2*,
                                                int64_t, const int2*, const int*, int, double2*,
-                                               int64_t, int);
+                                               int64_t, int, int*);
 template cudaError_t lu_solve_batched<float2>(cudaStream_t, int64_t, int, const float2*, int64_t,
-                                              const int2*, const int*, int, float2*, int64_t, int);
+                                              const int2*, const int*, int, float2*, int64_t, int,
+                                              int*);
 
 }  // namespace fnl

@@ -190,11 +190,15 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
     if (stage == 2 && !(*redflag & kNeed64)) return;
     extern __shared__ unsigned char smem_raw[];
     CT* sv = reinterpret_cast<CT*>(smem_raw);   // N
+    CT* wp = sv + N;                              // G x N partial products
     __shared__ R red[32];
     __shared__ CT s_alpha;
     __shared__ R s_beta;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = nt >> 5;
+    const int G = (N <= nt) ? nt / N : 1;         // column groups of the right update
+    const int g = (N <= nt) ? tid / N : 0;
+    const int r0 = (N <= nt) ? tid % N : tid, rstep = (N <= nt) ? N : nt;
     for (int j = 0; j + 2 < N; ++j) {
         const int len = N - j - 1;
         CT* xcol = C + (int64_t)j * N + (j + 1);
@@ -244,11 +248,22 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
         if (tid == 0) xcol[0] = s_alpha;
         for (int r = 1 + tid; r < len; r += nt) xcol[r] = czero<CT>();
         __syncthreads();
-        for (int r = tid; r < N; r += nt) {
+        // right update C[:, j+1:] -= beta (C[:, j+1:] v) v^H: the columns are
+        // dealt round G thread groups (every warp busy even when N is small),
+        // the partial products meet in shared memory
+        for (int r = r0; r < N; r += rstep) {
             CT w = czero<CT>();
-            for (int c = 0; c < len; ++c) w = cfma(C[r + (int64_t)(j + 1 + c) * N], sv[c], w);
+            if (g < G)
+                for (int c = g; c < len; c += G) w = cfma(C[r + (int64_t)(j + 1 + c) * N], sv[c], w);
+            if (g < G) wp[g * N + r] = w;
+        }
+        __syncthreads();
+        for (int r = r0; r < N; r += rstep) {
+            if (g >= G) break;
+            CT w = czero<CT>();
+            for (int q = 0; q < G; ++q) w = w + wp[q * N + r];
             w = cscale(beta, w);
-            for (int c = 0; c < len; ++c) {
+            for (int c = g; c < len; c += G) {
                 CT* p = C + r + (int64_t)(j + 1 + c) * N;
                 *p = cfms(w, cconj(sv[c]), *p);
             }
@@ -526,9 +541,14 @@ __device__ void newton_lu(int m, double2* T, int* piv, int* s_p) {
     }
 }
 
-__device__ void newton_solve(int m, const double2* T, const int* piv, double2* b) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+// Solves T y = b in place with the LU held in T; warp 0 takes b0 and warp 1
+// takes b1 (when given), so the two right-hand sides of a Newton step proceed
+// side by side.
+__device__ void newton_solve(int m, const double2* T, const int* piv, double2* b0, double2* b1) {
+    const int w = threadIdx.x >> 5;
+    double2* b = (w == 0) ? b0 : b1;
+    if (w < 2 && b != nullptr) {
+        const int lane = threadIdx.x & 31;
         if (lane == 0)
             for (int c = 0; c < m; ++c) {
                 int p = piv[c];
@@ -589,7 +609,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     newton_lu(m, T, piv, &s_p);
     for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = make_double2(1.0, 0.0);
     __syncthreads();
-    newton_solve(m, T, piv, x);
+    newton_solve(m, T, piv, x, nullptr);
     {
         double s = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(x[r]);
@@ -606,6 +626,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     // the steps are still large.
     bool ok = true;
     int refreshes = 0;
+    double prev = INFINITY;
     for (int it = 0; it < kNewtonMax; ++it) {
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
             double2 v = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
@@ -620,8 +641,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
             u[r] = dv;
         }
         __syncthreads();
-        newton_solve(m, T, piv, a);
-        newton_solve(m, T, piv, u);
+        newton_solve(m, T, piv, a, u);
         double are = 0.0, aim = 0.0, ure = 0.0, uim = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
             double2 ta = cconj(x[r]) * a[r], tu = cconj(x[r]) * u[r];
@@ -647,7 +667,9 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         __syncthreads();
         l = l + dl;
         const double rel = cabs(dl) / fmax(cabs(l), 1e-300);
-        if (rel <= 4.0 * DBL_EPSILON) break;
+        // converged, or stalled at the FP64 rounding level of the residual
+        if (rel <= 64.0 * DBL_EPSILON || (rel < 1e-12 && rel > 0.25 * prev)) break;
+        prev = rel;
         if (rel > 1e-9 && refreshes < 2 && (it == 1 || it == 4)) {
             newton_build(m, kmax, Ahat, l, T);
             __syncthreads();
@@ -727,17 +749,21 @@ __global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2*
         }
         __syncthreads();
     }
+    // column c of R^{-1} by back substitution in thread c; X holds it row-major
+    // (entry (r, c) at X[c + r m]) so that a warp's threads touch adjacent words
     for (int c = tid; c < m; c += nt) {
-        float2* x = X + c * m;
-        for (int i = 0; i < m; ++i) x[i] = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
+        for (int i = 0; i < m; ++i) X[c + i * m] = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
         for (int i = c; i >= 0; --i) {
-            float2 xi = x[i] * crcp(R[i + i * m]);
-            x[i] = xi;
-            for (int r = 0; r < i; ++r) x[r] = cfms(R[r + i * m], xi, x[r]);
+            float2 xi = X[c + i * m] * crcp(R[i + i * m]);
+            X[c + i * m] = xi;
+            for (int r = 0; r < i; ++r) X[c + r * m] = cfms(R[r + i * m], xi, X[c + r * m]);
         }
     }
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) Rinv[e] = make_double2(X[e].x, X[e].y);
+    for (int e = tid; e < m * m; e += nt) {
+        const float2 v = X[e / m + (e % m) * m];
+        Rinv[e] = make_double2(v.x, v.y);
+    }
 }
 
 size_t packed_elems(int N) { return (size_t)N * (N + 5) / 2 + 4; }
@@ -784,7 +810,8 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     note_launch();
-    hessenberg_kernel<R><<<1, kRedThreads, sizeof(CT) * N, st>>>(N, C, flag, stage);
+    const size_t hsm = sizeof(CT) * ((size_t)N + (size_t)max(N, kRedThreads));
+    hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, flag, stage);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     size_t hbytes = packed_elems(N) * sizeof(CT);
     int use_smem = (hbytes + sizeof(CT) * N) <= (size_t)kMaxSmemPacked;

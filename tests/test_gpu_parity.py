@@ -48,7 +48,7 @@ def test_nodes_match_oracle(lib, rule, nc):
 
 # ------------------------------------------------------------------ node LU + solve
 @pytest.mark.parametrize("prec,n", [("fp64", 150), ("fp32", 150), ("fp64", 33), ("fp32", 200),
-                                    ("fp64", 1), ("fp32", 65)])
+                                    ("fp64", 1), ("fp32", 65), ("fp32", 1), ("fp32", 700)])
 def test_node_solve_matches_oracle(lib, prec, n):
     p = random_pep(n, 2, seed=3)
     c, ra = 0.05 + 0.1j, 0.6
@@ -56,7 +56,8 @@ def test_node_solve_matches_oracle(lib, prec, n):
     s.set_contour(c, ra, ra, 6, "gl")
     z, _ = O.quadrature(c, ra, ra, 6, "gl")
     rng = np.random.default_rng(7)
-    R = rng.standard_normal((n, 5)) + 1j * rng.standard_normal((n, 5))
+    nrhs = 96 if n >= 500 else 5        # 96: several row tiles and two column tiles
+    R = rng.standard_normal((n, nrhs)) + 1j * rng.standard_normal((n, nrhs))
     for j in range(6):
         T = O.assemble(p, z[j])
         ref = np.linalg.solve(T, R)
