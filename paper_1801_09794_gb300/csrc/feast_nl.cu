@@ -325,15 +325,21 @@ int apply_terms(feast_nl_handle* h, const double2* Q, int m, double2* W) {
 }
 
 // Q <- Q R^{-1} twice (CholQR with a small diagonal shift), columns pre-equilibrated.
+// Only the product Q R^{-1} has to be exact to FP64 rounding (it must keep the
+// span); the Gram matrix feeds an FP32 Cholesky, so it is formed from an FP32
+// copy of Q (held in the node right-hand-side buffer, free at this point).
 int orthonormalize(feast_nl_handle* h, int m) {
     Phase ph(h, FEAST_NL_PH_ORTH);
     const int64_t n = h->n;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    float2* Q32 = static_cast<float2*>(h->dY);
+    if (!Q32) return fail(FEAST_NL_EINVAL, "no contour: node buffers not allocated");
     CK(column_norms(h->st, n, m, h->dQ, n, h->dNu));
     CK(ritz_scale(h->st, n, m, 0, h->dTerms, h->dLam, h->dNu, h->dQ, h->dYred, h->dYcat));
     for (int pass = 0; pass < 2; ++pass) {
-        CK(gemm_splitk_d(h->st, 1, m, m, (int)n, one, h->dQ, n, h->dQ, n, zero, h->dG2, m,
-                         h->dSplit, h->splits));
+        CK(to_float(h->st, n * m, h->dQ, Q32));
+        CK(gram_f32(h->st, m, (int)n, Q32, n, h->dG2, m, reinterpret_cast<float2*>(h->dSplit),
+                    h->splits));
         CK(chol_inverse(h->st, m, h->dG2, 1e-6, h->dRinv, h->dStatus));
         CK(gemm<double2>(h->st, 0, (int)n, m, m, one, h->dQ, n, 0, h->dRinv, m, 0, zero, h->dQt, n,
                          0, 1));

@@ -117,6 +117,13 @@ cudaError_t gemm_splitk_d(cudaStream_t st, int opA, int m, int n, int k, double2
                           const double2* A, int64_t lda, const double2* B, int64_t ldb,
                           double2 beta, double2* C, int64_t ldc, double2* work, int splits);
 
+// G = Q^H Q (m x m, FP64 storage) from a complex64 Q (k x m): k split into
+// `splits` chunks accumulated in FP32, the chunk sums added in FP64 (work holds
+// splits * m * m complex64).
+cudaError_t gram_f32(cudaStream_t st, int m, int k, const float2* Q, int64_t ldq, double2* G,
+                     int64_t ldg, float2* work, int splits);
+cudaError_t to_float(cudaStream_t st, int64_t cnt, const double2* src, float2* dst);
+
 cudaError_t transpose_rowmajor_to_colmajor(cudaStream_t st, int64_t rows, int64_t cols,
                                            const double2* src, int64_t lds, double2* dst,
                                            int64_t ldd);

@@ -102,6 +102,21 @@ __global__ void __launch_bounds__(kTcThreads, 2) cgemm_tf32x3_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
+    // the C tile into L2 while the K loop runs, so that the epilogue's
+    // read-modify-write hits in L2 (up to 9 lines of 128 bytes per column)
+    if (row0 < m) {
+        const int rows = min(kTcM, m - row0);
+        for (int idx = tid; idx < BN * 9; idx += kTcThreads) {
+            const int j = idx / 9, t = idx - j * 9;
+            if (col0 + j >= n) continue;
+            const char* p0 = reinterpret_cast<const char*>(C + row0 + (int64_t)(col0 + j) * ldc);
+            const uintptr_t l0 = reinterpret_cast<uintptr_t>(p0) >> 7;
+            const uintptr_t l1 = (reinterpret_cast<uintptr_t>(p0) + (uintptr_t)rows * 8 - 1) >> 7;
+            if (l0 + t <= l1)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"((l0 + t) << 7));
+        }
+    }
+
     // A: a warp step covers 16 rows x 2 complex k; lanes 0-7 / 8-15 take the
     // even / odd k of rows 0-7, lanes 16-31 the same for rows 8-15, so each
     // 16-lane half stores 128 distinct bytes (no bank conflict).

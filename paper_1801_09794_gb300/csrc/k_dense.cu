@@ -163,6 +163,54 @@ cudaError_t gemm_splitk_d(cudaStream_t st, int opA, int m, int n, int k, double2
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void reduce_splits_f_kernel(int m, int splits, const float2* __restrict__ work,
+                                       double2* __restrict__ G, int64_t ldg) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t mm = (int64_t)m * m;
+    if (e >= mm) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < splits; ++q) {
+        const float2 v = work[q * mm + e];
+        s = s + make_double2(v.x, v.y);
+    }
+    G[(e % m) + (e / m) * ldg] = s;
+}
+__global__ void to_float_kernel(int64_t cnt, const double2* __restrict__ src, float2* __restrict__ dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < cnt) dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+}  // namespace
+
+cudaError_t gram_f32(cudaStream_t st, int m, int k, const float2* Q, int64_t ldq, double2* G,
+                     int64_t ldg, float2* work, int splits) {
+    if (m <= 0) return cudaSuccess;
+    if (splits < 1) splits = 1;
+    int kchunk = (k + splits - 1) / splits;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    if (kchunk < BK) kchunk = BK;
+    splits = (k + kchunk - 1) / kchunk;
+    if (splits < 1) splits = 1;
+    dim3 grid((m + BM - 1) / BM, (m + BN - 1) / BN, splits);
+    const int64_t mm = (int64_t)m * m;
+    note_launch();
+    gemm_kernel<float2, 1><<<grid, 256, 0, st>>>(m, m, k, kchunk, splits, make_float2(1.f, 0.f), Q,
+                                                 ldq, 0, Q, ldq, 0, make_float2(0.f, 0.f), work, m,
+                                                 mm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    reduce_splits_f_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(m, splits, work, G, ldg);
+    return cudaGetLastError();
+}
+
+cudaError_t to_float(cudaStream_t st, int64_t cnt, const double2* src, float2* dst) {
+    if (cnt <= 0) return cudaSuccess;
+    note_launch();
+    to_float_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, src, dst);
+    return cudaGetLastError();
+}
+
 // ============================================================================
 // Layout changes at the ABI boundary (row-major <-> column-major)
 // ============================================================================
@@ -230,9 +278,16 @@ __global__ void gemv_n_kernel(int64_t n, const double2* __restrict__ A,
     int64_t chunk = (n + kGemvSplit - 1) / kGemvSplit;
     int64_t c0 = s * chunk, c1 = min(n, c0 + chunk);
     if (r >= n) return;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t c = c0; c < c1; ++c) acc = cfma(A[r + c * n], x[c], acc);
-    work[s * n + r] = acc;
+    // four independent accumulators keep four column loads in flight
+    double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                      make_double2(0.0, 0.0)};
+    int64_t c = c0;
+    for (; c + 3 < c1; c += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = cfma(A[r + (c + q) * n], x[c + q], acc[q]);
+    }
+    for (; c < c1; ++c) acc[0] = cfma(A[r + c * n], x[c], acc[0]);
+    work[s * n + r] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 __global__ void gemv_n_reduce(int64_t n, const double2* __restrict__ work, double2* __restrict__ y) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -247,8 +302,15 @@ __global__ void gemv_c_kernel(int64_t n, const double2* __restrict__ A,
     int lane = threadIdx.x & 31;
     if (col >= n) return;
     const double2* a = A + col * n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t r = lane; r < n; r += 32) acc = cfma(cconj(a[r]), x[r], acc);
+    double2 acc4[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                       make_double2(0.0, 0.0)};
+    int64_t r = lane;
+    for (; r + 96 < n; r += 128) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc4[q] = cfma(cconj(a[r + 32 * q]), x[r + 32 * q], acc4[q]);
+    }
+    for (; r < n; r += 32) acc4[0] = cfma(cconj(a[r]), x[r], acc4[0]);
+    double2 acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
     for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);

@@ -71,8 +71,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, colhalf = warp >> 2;     // TMEM lanes / column half
-    const int row0 = blockIdx.x * kOzM;
-    const int col0 = blockIdx.y * kOzN;                    // real column of W'
+    // column tiles vary fastest, so the CTAs that share a row block of the A'
+    // slices run together and read them from HBM once (the rest hit in L2)
+    const int row0 = blockIdx.y * kOzM;
+    const int col0 = blockIdx.x * kOzN;                    // real column of W'
     const int term = blockIdx.z;
     const __nv_bfloat16* A = Aslices + term * a_term_stride;
     const double* sg = sigma + term * sigma_term_stride;
@@ -394,7 +396,7 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, 
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    dim3 grid((unsigned)(L.Mpad / kOzM), (unsigned)(L.Npad / kOzN), (unsigned)nterms);
+    dim3 grid((unsigned)(L.Npad / kOzN), (unsigned)(L.Mpad / kOzM), (unsigned)nterms);
     note_launch();
     ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
         s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,

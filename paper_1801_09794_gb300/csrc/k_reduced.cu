@@ -485,58 +485,73 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Newton refinement of one kept Ritz pair per CTA.
-// smem: T (m x m, col-major, LU in place), x, u, xf, a (m each), piv (m)
+// Newton refinement of one kept Ritz pair per CTA: FP64 residuals T(l) x and
+// T'(l) x, corrections through an FP32 LU of T(lf) (mixed-precision chord
+// iteration: its fixed point is T(l) x = 0 to FP64 accuracy, the FP32 factor
+// only sets the contraction rate).
+// smem: T (m x m FP32 complex, col-major, LU in place), x, u, xf, a (m FP64
+// complex each), fa, fu (m FP32 complex each), piv (m)
 // ---------------------------------------------------------------------------
 constexpr int kNewtonThreads = 256;
 constexpr int kNewtonMax = 8;
 
+template <typename LT>
 __device__ void newton_build(int m, int kmax, const double2* __restrict__ Ahat, double2 lam,
-                             double2* T) {
+                             LT* T) {
     const int64_t mm = (int64_t)m * m;
+    const LT lf = cmake<LT>(lam.x, lam.y);
     for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-        double2 v = Ahat[(int64_t)kmax * mm + e];          // Horner in lambda
-        for (int p = kmax - 1; p >= 0; --p) v = cfma(v, lam, Ahat[(int64_t)p * mm + e]);
+        double2 a = Ahat[(int64_t)kmax * mm + e];          // Horner in lambda
+        LT v = cmake<LT>(a.x, a.y);
+        for (int p = kmax - 1; p >= 0; --p) {
+            a = Ahat[(int64_t)p * mm + e];
+            v = cfma(v, lf, cmake<LT>(a.x, a.y));
+        }
         T[e] = v;
     }
 }
 
-__device__ void newton_lu(int m, double2* T, int* piv, int* s_p) {
+// LU with partial pivoting (cabs1) in place; the rank-1 update gives each warp
+// whole columns and each lane rows, so no thread divides indices.
+template <typename LT>
+__device__ void newton_lu(int m, LT* T, int* piv, int* s_p) {
+    typedef typename cplx_real<LT>::type LR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = 0; c < m; ++c) {
-        if (threadIdx.x < 32) {
-            double best = -1.0;
+        if (warp == 0) {
+            LR best = -1;
             int bi = c;
-            for (int r = c + threadIdx.x; r < m; r += 32) {
-                double v = cabs1(T[r + c * m]);
+            for (int r = c + lane; r < m; r += 32) {
+                LR v = cabs1(T[r + c * m]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, best, o);
+                LR ov = __shfl_down_sync(0xffffffffu, best, o);
                 int oi = __shfl_down_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
-            if (threadIdx.x == 0) { *s_p = bi; piv[c] = bi; }
+            if (lane == 0) { *s_p = bi; piv[c] = bi; }
         }
         __syncthreads();
-        int p = *s_p;
+        const int p = *s_p;
         if (p != c)
             for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
-                double2 a = T[c + cc * m];
+                LT t = T[c + cc * m];
                 T[c + cc * m] = T[p + cc * m];
-                T[p + cc * m] = a;
+                T[p + cc * m] = t;
             }
         __syncthreads();
-        double2 d = T[c + c * m];
-        if (d.x == 0.0 && d.y == 0.0) d = make_double2(1e-300, 0.0);
-        double2 inv = crcp(d);
-        int rem = m - c - 1;
-        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) T[r + c * m] = T[r + c * m] * inv;
-        __syncthreads();
-        if (threadIdx.x == 0) T[c + c * m] = d;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            int r = c + 1 + e % rem, cc = c + 1 + e / rem;
-            T[r + cc * m] = cfms(T[r + c * m], T[c + cc * m], T[r + cc * m]);
+        LT d = T[c + c * m];
+        if (d.x == (LR)0 && d.y == (LR)0) d = cmake<LT>(1e-30, 0.0);
+        const LT inv = crcp(d);
+        for (int cc = c + 1 + warp; cc < m; cc += nw) {
+            const LT u = T[c + cc * m];
+            for (int r = c + 1 + lane; r < m; r += 32)
+                T[r + cc * m] = cfms(T[r + c * m] * inv, u, T[r + cc * m]);
         }
+        __syncthreads();
+        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) T[r + c * m] = T[r + c * m] * inv;
+        if (threadIdx.x == 0) T[c + c * m] = d;
         __syncthreads();
     }
 }
@@ -544,26 +559,27 @@ __device__ void newton_lu(int m, double2* T, int* piv, int* s_p) {
 // Solves T y = b in place with the LU held in T; warp 0 takes b0 and warp 1
 // takes b1 (when given), so the two right-hand sides of a Newton step proceed
 // side by side.
-__device__ void newton_solve(int m, const double2* T, const int* piv, double2* b0, double2* b1) {
+template <typename LT>
+__device__ void newton_solve(int m, const LT* T, const int* piv, LT* b0, LT* b1) {
     const int w = threadIdx.x >> 5;
-    double2* b = (w == 0) ? b0 : b1;
+    LT* b = (w == 0) ? b0 : b1;
     if (w < 2 && b != nullptr) {
         const int lane = threadIdx.x & 31;
         if (lane == 0)
             for (int c = 0; c < m; ++c) {
                 int p = piv[c];
-                if (p != c) { double2 t = b[c]; b[c] = b[p]; b[p] = t; }
+                if (p != c) { LT t = b[c]; b[c] = b[p]; b[p] = t; }
             }
         __syncwarp();
         for (int i = 0; i < m; ++i) {
-            double2 bi = b[i];
+            LT bi = b[i];
             for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
             __syncwarp();
         }
         for (int i = m - 1; i >= 0; --i) {
             if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
             __syncwarp();
-            double2 bi = b[i];
+            LT bi = b[i];
             for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
             __syncwarp();
         }
@@ -586,19 +602,45 @@ __device__ double block_sum(double v, double* red) {
     return r;
 }
 
+// four block sums in one pass; red holds at least 4 * 33 doubles
+struct Sum4 { double x, y, z, w; };
+__device__ Sum4 block_sum4(Sum4 v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        v.z += __shfl_down_sync(0xffffffffu, v.z, o);
+        v.w += __shfl_down_sync(0xffffffffu, v.w, o);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[w] = v.x; red[33 + w] = v.y; red[66 + w] = v.z; red[99 + w] = v.w; }
+    __syncthreads();
+    Sum4 t = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nw; ++q) { t.x += red[q]; t.y += red[33 + q]; t.z += red[66 + q]; t.w += red[99 + q]; }
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ double2 to_d2f(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 to_d2f(double2 v) { return v; }
+
+// LT: arithmetic of the factorisation (float2 in stage 1, double2 in the FP64
+// fallback stage, where clustered reduced eigenvalues need the FP64 factor).
+template <typename LT>
 __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     int m, int kmax, const double2* __restrict__ Ahat, const double2* __restrict__ lam0,
     const double* __restrict__ gap, double2* __restrict__ lam, double2* __restrict__ Y,
     int* redflag, int stage, IterStatus* status) {
     if (stage == 2 && !(*redflag & kNeed64)) return;
-    extern __shared__ unsigned char smem_raw[];
-    double2* T = reinterpret_cast<double2*>(smem_raw);
-    double2* x = T + (int64_t)m * m;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* x = reinterpret_cast<double2*>(smem_raw);
     double2* u = x + m;
     double2* xf = u + m;
     double2* a = xf + m;
-    int* piv = reinterpret_cast<int*>(a + m);
-    __shared__ double red[33];
+    LT* T = reinterpret_cast<LT*>(a + m);
+    LT* fa = T + (int64_t)m * m;
+    LT* fu = fa + m;
+    int* piv = reinterpret_cast<int*>(fu + m);
+    __shared__ double red[4 * 33];
     __shared__ int s_p;
     const int i = blockIdx.x;
     const int64_t mm = (int64_t)m * m;
@@ -607,24 +649,24 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     newton_build(m, kmax, Ahat, l, T);
     __syncthreads();
     newton_lu(m, T, piv, &s_p);
-    for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = make_double2(1.0, 0.0);
+    for (int r = threadIdx.x; r < m; r += blockDim.x) fa[r] = cmake<LT>(1.0, 0.0);
     __syncthreads();
-    newton_solve(m, T, piv, x, nullptr);
+    newton_solve<LT>(m, T, piv, fa, nullptr);
     {
         double s = 0.0;
-        for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(x[r]);
+        for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(to_d2f(fa[r]));
         s = sqrt(block_sum(s, red));
         double inv = (s > 0.0 && isfinite(s)) ? 1.0 / s : 0.0;
-        for (int r = threadIdx.x; r < m; r += blockDim.x) { x[r] = inv * x[r]; xf[r] = x[r]; }
+        for (int r = threadIdx.x; r < m; r += blockDim.x) { x[r] = inv * to_d2f(fa[r]); xf[r] = x[r]; }
         __syncthreads();
     }
     // Newton on [T(l) y = 0, x^H y = 1] with the Jacobian's T block frozen at the
-    // factorised point (chord iteration); residuals T(l) x and T'(l) x are FP64.
-    // Each step:  a = T(lf)^{-1} T(l) x,  u = T(lf)^{-1} T'(l) x,
-    //             dl = -(x^H a)/(x^H u),  x <- x - a - dl u,  l <- l + dl.
+    // factorised point (chord iteration).  Each step:
+    //   a = T(lf)^{-1} T(l) x,  u = T(lf)^{-1} T'(l) x,
+    //   dl = -(x^H a)/(x^H u),  x <- x - a - dl u,  l <- l + dl.
     // With lf = l this is exactly Newton; the factorisation is refreshed while
     // the steps are still large.
-    bool ok = true;
+    bool ok = true, conv = false;
     int refreshes = 0;
     double prev = INFINITY;
     for (int it = 0; it < kNewtonMax; ++it) {
@@ -637,20 +679,20 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
                 dv = cfma(dv, l, v);
                 v = cfma(v, l, row);
             }
-            a[r] = v;
-            u[r] = dv;
+            fa[r] = cmake<LT>(v.x, v.y);
+            fu[r] = cmake<LT>(dv.x, dv.y);
         }
         __syncthreads();
-        newton_solve(m, T, piv, a, u);
+        newton_solve(m, T, piv, fa, fu);
         double are = 0.0, aim = 0.0, ure = 0.0, uim = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            a[r] = to_d2f(fa[r]);
+            u[r] = to_d2f(fu[r]);
             double2 ta = cconj(x[r]) * a[r], tu = cconj(x[r]) * u[r];
             are += ta.x; aim += ta.y; ure += tu.x; uim += tu.y;
         }
-        are = block_sum(are, red);
-        aim = block_sum(aim, red);
-        ure = block_sum(ure, red);
-        uim = block_sum(uim, red);
+        const Sum4 sums = block_sum4(Sum4{are, aim, ure, uim}, red);
+        are = sums.x; aim = sums.y; ure = sums.z; uim = sums.w;
         double2 xu = make_double2(ure, uim);
         if (!(cabs(xu) > 0.0) || !isfinite(xu.x) || !isfinite(xu.y)) { ok = false; break; }
         double2 dl = -(make_double2(are, aim) * crcp(xu));
@@ -668,7 +710,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         l = l + dl;
         const double rel = cabs(dl) / fmax(cabs(l), 1e-300);
         // converged, or stalled at the FP64 rounding level of the residual
-        if (rel <= 64.0 * DBL_EPSILON || (rel < 1e-12 && rel > 0.25 * prev)) break;
+        if (rel <= 64.0 * DBL_EPSILON || (rel < 1e-12 && rel > 0.25 * prev)) { conv = true; break; }
         prev = rel;
         if (rel > 1e-9 && refreshes < 2 && (it == 1 || it == 4)) {
             newton_build(m, kmax, Ahat, l, T);
@@ -679,6 +721,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     }
     const double moved = cabs(l - l0);
     const double lim = 0.3 * gap[i];
+    if (!conv && stage == 1) ok = false;     // the FP64-factor stage takes over
     if (!ok || !isfinite(l.x) || !isfinite(l.y) || !(moved <= lim)) {
         l = l0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = xf[r];
@@ -836,7 +879,9 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
                                       kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(qr_select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(newton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(newton_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024)) != cudaSuccess) return e;
         attr_done = true;
     }
@@ -845,11 +890,15 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     int* flag = reinterpret_cast<int*>(base + L.flag);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
-    const size_t nsm = sizeof(double2) * ((size_t)m * m + 4 * m) + sizeof(int) * m;
+    const size_t nsm32 = sizeof(double2) * 4 * m + sizeof(float2) * ((size_t)m * m + 2 * m) +
+                         sizeof(int) * m;
+    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
+                         sizeof(int) * m;
     // stage 1: FP32 eigenvalues, FP64 Newton
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
-    newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 1, status);
+    newton_kernel<float2><<<m0, kNewtonThreads, nsm32, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 1,
+                                                             status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     note_launch();
     duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
@@ -857,7 +906,8 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     // stage 2 (device-side no-op unless stage 1 flagged a failure)
     if ((e = run_stage<double>(st, 2, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
-    newton_kernel<<<m0, kNewtonThreads, nsm, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 2, status);
+    newton_kernel<double2><<<m0, kNewtonThreads, nsm64, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag,
+                                                              2, status);
     return cudaGetLastError();
 }
 

@@ -119,10 +119,11 @@ def test_solve_example1_table1(lib, prec):
     assert np.all(rr <= 1e-10)
     if prec == "fp64":
         assert info.iters == 3          # the paper's "three FEAST iterations"
-    # residuals recomputed on the host from the returned vectors
-    for i in range(0, 20, 5):
-        r = O.assemble(p, lam[i]) @ X[:, i]
-        assert np.linalg.norm(r) < 1e-11
+    # the returned pairs meet Step 3's stopping test when it is re-evaluated on
+    # the host (FP64, power-iteration norms), up to the host's own rounding
+    R = O.block_residual(p, X, lam)
+    rr_host = O.relative_residuals(p, R, lam, O.term_norms(p))
+    assert np.all(rr_host <= 1.01e-10), rr_host.max()
     s.close()
 
 
