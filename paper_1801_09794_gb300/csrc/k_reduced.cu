@@ -73,7 +73,6 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 
 constexpr int kRedThreads = 1024;
 constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (window <= 32)
-constexpr int kMaxCompanion = 1024; // largest companion order (degree * m0)
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
@@ -272,14 +271,111 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
     }
 }
 
-// packed Hessenberg storage with one bulge row: column j holds rows 0..j+2
+// Packed Hessenberg storage with one bulge row: column j holds rows 0..j+2.
+#define PK(i, j) ((((j) * ((j) + 5)) >> 1) + (i))
+
+constexpr int kQrThreads = 256;
+constexpr int kSmallMax = 32;      // active blocks up to this order go to one warp
+constexpr int kSmallLd = 33;       // leading dimension of that dense copy (bank spread)
+
+// G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0)
+template <typename R>
+__device__ __forceinline__ void givens(typename cx<R>::type x, typename cx<R>::type y, R& c,
+                                       typename cx<R>::type& s) {
+    const R nx = cnorm2(x), ny = cnorm2(y);
+    if (ny == (R)0) { c = 1; s.x = 0; s.y = 0; }
+    else if (nx == (R)0) { const R iy = rsqrt(ny); c = 0; s.x = y.x * iy; s.y = -y.y * iy; }
+    else {
+        const R irho = rsqrt(nx + ny), ix = rsqrt(nx);
+        c = nx * ix * irho;                        // |x| / rho
+        s = cscale(ix * irho, x * cconj(y));       // (x/|x|) conj(y) / rho
+    }
+}
+
+// Eigenvalues of the ns x ns (ns <= 32) Hessenberg matrix S (column-major, ld
+// kSmallLd, overwritten) by single-shift complex QR, one warp: lane j owns
+// column j in the row rotations and row j in the column rotations.  Returns the
+// number of sweeps, negated when the iteration cap was reached.
+template <typename R>
+__device__ int small_hess_eig(typename cx<R>::type* S, int ns, typename cx<R>::type* ev) {
+    typedef typename cx<R>::type CT;
+    const int lane = threadIdx.x & 31;
+    const R eps = cx<R>::eps(), tiny = cx<R>::tiny();
+#define SS(i, j) S[(i) + (j) * kSmallLd]
+    int hi = ns - 1, its = 0, total = 0;
+    while (hi >= 0) {
+        if (hi == 0) { if (lane == 0) ev[0] = SS(0, 0); __syncwarp(); break; }
+        bool neg = false;
+        if (lane >= 1 && lane <= hi) {
+            const R h = cabs1(SS(lane, lane - 1));
+            const R sd = cabs1(SS(lane - 1, lane - 1)) + cabs1(SS(lane, lane));
+            neg = (h <= eps * sd) || (h <= tiny);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, neg);
+        const int l = bal ? 31 - __clz(bal) : 0;
+        __syncwarp();
+        if (l > 0 && lane == 0) SS(l, l - 1) = czero<CT>();
+        __syncwarp();
+        if (l == hi) { if (lane == 0) ev[hi] = SS(hi, hi); __syncwarp(); --hi; its = 0; continue; }
+        if (l == hi - 1) {
+            CT e1, e2;
+            eig2x2<R>(SS(hi - 1, hi - 1), SS(hi - 1, hi), SS(hi, hi - 1), SS(hi, hi), &e1, &e2);
+            if (lane == 0) { ev[hi - 1] = e1; ev[hi] = e2; }
+            __syncwarp();
+            hi -= 2; its = 0;
+            continue;
+        }
+        ++its;
+        if (++total > 30 * ns) {       // iteration cap: report, keep the diagonal
+            for (int i = lane; i <= hi; i += 32) ev[i] = SS(i, i);
+            __syncwarp();
+            return -total;
+        }
+        CT mu;
+        const CT d = SS(hi, hi);
+        if (its % 11 == 10) { mu = d; mu.x += (R)0.75 * cabs(SS(hi, hi - 1)); }
+        else {
+            CT e1, e2;
+            eig2x2<R>(SS(hi - 1, hi - 1), SS(hi - 1, hi), SS(hi, hi - 1), d, &e1, &e2);
+            mu = (cabs1(e1 - d) <= cabs1(e2 - d)) ? e1 : e2;
+        }
+        for (int k = l; k < hi; ++k) {
+            CT x, y;
+            if (k == l) { x = SS(l, l) - mu; y = SS(l + 1, l); }
+            else        { x = SS(k, k - 1); y = SS(k + 1, k - 1); }
+            R c;
+            CT s;
+            givens<R>(x, y, c, s);
+            __syncwarp();
+            if (lane >= max(l, k - 1) && lane <= hi) {
+                const CT h1 = SS(k, lane), h2 = SS(k + 1, lane);
+                SS(k, lane) = cscale(c, h1) + s * h2;
+                SS(k + 1, lane) = (lane == k - 1) ? czero<CT>() : cscale(c, h2) - cconj(s) * h1;
+            }
+            __syncwarp();
+            if (lane >= l && lane <= min(k + 2, hi)) {
+                const CT h1 = SS(lane, k), h2 = SS(lane, k + 1);
+                SS(lane, k) = cscale(c, h1) + cconj(s) * h2;
+                SS(lane, k + 1) = cscale(c, h2) - s * h1;
+            }
+            __syncwarp();
+        }
+    }
+#undef SS
+    return total;
+}
 
 // ---------------------------------------------------------------------------
 // Eigenvalues of the Hessenberg matrix by the implicit single-shift complex QR
-// algorithm (one warp chases the bulge), then Step 2's selection.
+// algorithm, then Step 2's selection.  Large active blocks: one warp chases
+// the bulge through windows of kQrChunk rotations, the CTA applies each
+// window's rotations to the rest of the block.  Blocks of order <= kSmallMax:
+// one warp on a dense copy.  (A multishift variant with chains of bulges was
+// measured: it needs ~2.5x the shifts on these companion matrices, and its
+// FP32 eigenvalues come out too coarse for clustered reduced spectra.)
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) qr_select_kernel(
+__global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
     int N, int m0, const typename cx<R>::type* __restrict__ C, typename cx<R>::type* Hglobal,
     int use_smem, double c_re, double c_im, double ra, double rb, double2* __restrict__ lam0,
     double* __restrict__ gap, const int* redflag, int stage, IterStatus* status) {
@@ -287,30 +383,21 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
     if (stage == 2 && !(*redflag & kNeed64)) return;
     extern __shared__ unsigned char smem_raw[];
     CT* ev = reinterpret_cast<CT*>(smem_raw);   // N
-    CT* H = use_smem ? ev + N : Hglobal;
+    CT* Ssm = ev + N;                            // kSmallLd x kSmallMax
+    CT* H = use_smem ? Ssm + kSmallLd * kSmallMax : Hglobal;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-    __shared__ int coff[kMaxCompanion + 1];   // start of packed column j
-    for (int j = tid; j <= N; j += nt) coff[j] = j * (j + 5) / 2;
-    __syncthreads();
-#define HH(i, j) H[coff[(j)] + (i)]
+#define HH(i, j) H[PK(i, j)]
     for (int j = tid; j < N; j += nt)
         for (int i = 0; i <= j + 2; ++i)
             HH(i, j) = (i < N && i <= j + 1) ? C[i + (int64_t)j * N] : czero<CT>();
     __syncthreads();
-    // Every thread runs the same control flow (deflation tests and shifts are
-    // computed redundantly from shared memory).  Each sweep chases the bulge in
-    // chunks of kQrChunk rotations: warp 0 applies them inside a small window
-    // (the only entries the next rotations read), then the whole CTA applies the
-    // chunk's rotations to the columns right of the window and the rows above
-    // it, each column / row independently.
     __shared__ R s_c[kQrChunk];
     __shared__ CT s_s[kQrChunk];
     __shared__ R s_red[32];
     const int warp = tid >> 5;
     const R eps = cx<R>::eps();
     // deflation: a subdiagonal is negligible below eps times its diagonal
-    // neighbours or below eps ||H||_F (a backward-stable perturbation of H; the
-    // kept values are polished in FP64 afterwards)
+    // neighbours or below eps^2 ||H||_F (the kept values are polished in FP64)
     R hn = 0;
     for (int j = tid; j < N; j += nt)
         for (int i = 0; i <= j + 1 && i < N; ++i) hn += cnorm2(HH(i, j));
@@ -319,8 +406,6 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
     __syncthreads();
     hn = 0;
     for (int w = 0; w < (nt >> 5); ++w) hn += s_red[w];
-    // (a floor of eps ||H||_F was tried: it roughly halves nothing -- sweeps are
-    //  already ~1.2 per eigenvalue -- and costs FP32 accuracy, so only a tiny floor)
     const R tiny = fmax(cx<R>::tiny(), eps * eps * sqrt(hn));
     int hi = N - 1, its = 0, total = 0;
     bool failed = false;
@@ -360,6 +445,29 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
         }
         ++its; ++total;
         if (total > 40 * N) { failed = true; break; }
+        if (hi - l < kSmallMax) {
+            // ---- the whole active block (order <= kSmallMax) by one warp in a
+            // dense copy: same single-shift QR, no CTA-wide barriers
+            const int ns = hi - l + 1;
+            if (warp == 0) {
+                for (int j = lane; j < ns; j += 32)
+                    for (int i = 0; i < ns; ++i)
+                        Ssm[i + j * kSmallLd] = (i <= j + 1) ? HH(l + i, l + j) : czero<CT>();
+                __syncwarp();
+                const int sw = small_hess_eig<R>(Ssm, ns, ev + l);
+                if (lane == 0) {
+                    if (sw < 0) atomicOr(&status->flags, 1);
+                    s_red[0] = (R)(sw < 0 ? -sw : sw);
+                }
+            }
+            __syncthreads();
+            total += (int)s_red[0];
+            hi = l - 1;
+            its = 0;
+            __syncthreads();
+            continue;
+        }
+        // ---- single-shift sweep
         CT mu;
         {
             CT d = HH(hi, hi);
@@ -383,34 +491,27 @@ __global__ void __launch_bounds__(256) qr_select_kernel(
                 for (int r = 0; r < kb; ++r) {
                     const int kk = k + r;
                     CT x, y;
-                    if (kk == l) { x = H[coff[l] + l] - mu; y = H[coff[l] + l + 1]; }
-                    else         { x = H[coff[kk - 1] + kk]; y = H[coff[kk - 1] + kk + 1]; }
-                    // G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0)
-                    const R nx = cnorm2(x), ny = cnorm2(y);
+                    if (kk == l) { x = HH(l, l) - mu; y = HH(l + 1, l); }
+                    else         { x = HH(kk, kk - 1); y = HH(kk + 1, kk - 1); }
                     R c;
                     CT s;
-                    if (ny == (R)0) { c = 1; s = czero<CT>(); }
-                    else if (nx == (R)0) { R iy = rsqrt(ny); c = 0; s.x = y.x * iy; s.y = -y.y * iy; }
-                    else {
-                        const R irho = rsqrt(nx + ny), ix = rsqrt(nx);
-                        c = nx * ix * irho;                       // |x| / rho
-                        s = cscale(ix * irho, x * cconj(y));       // (x/|x|) conj(y) / rho
-                    }
+                    givens<R>(x, y, c, s);
                     if (lane == 0) { s_c[r] = c; s_s[r] = s; }
                     const int j = ((kk == l) ? l : kk - 1) + lane;
                     if (j <= w1) {
-                        const int o = coff[j];
-                        CT h1 = H[o + kk], h2 = H[o + kk + 1];
-                        H[o + kk] = cscale(c, h1) + s * h2;
-                        H[o + kk + 1] = (j == kk - 1) ? czero<CT>() : cscale(c, h2) - cconj(s) * h1;
+                        CT* h = H + PK(kk, j);
+                        const CT h1 = h[0], h2 = h[1];
+                        h[0] = cscale(c, h1) + s * h2;
+                        h[1] = (j == kk - 1) ? czero<CT>() : cscale(c, h2) - cconj(s) * h1;
                     }
                     __syncwarp();
                     const int i = w0 + lane;
                     if (i <= min(kk + 2, hi)) {
-                        const int o0 = coff[kk], o1 = coff[kk + 1];
-                        CT h1 = H[o0 + i], h2 = H[o1 + i];
-                        H[o0 + i] = cscale(c, h1) + cconj(s) * h2;
-                        H[o1 + i] = cscale(c, h2) - s * h1;
+                        CT* c0 = H + PK(i, kk);
+                        CT* c1 = H + PK(i, kk + 1);
+                        const CT h1 = *c0, h2 = *c1;
+                        *c0 = cscale(c, h1) + cconj(s) * h2;
+                        *c1 = cscale(c, h2) - s * h1;
                     }
                     __syncwarp();
                 }
@@ -857,10 +958,11 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, flag, stage);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     size_t hbytes = packed_elems(N) * sizeof(CT);
-    int use_smem = (hbytes + sizeof(CT) * N) <= (size_t)kMaxSmemPacked;
-    size_t smem = sizeof(CT) * N + (use_smem ? hbytes : 0);
+    const size_t fixed = sizeof(CT) * ((size_t)N + kSmallLd * kSmallMax);   // ev, dense block
+    int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
+    size_t smem = fixed + (use_smem ? hbytes : 0);
     note_launch();
-    qr_select_kernel<R><<<1, 256, smem, st>>>(N, m0, C, Hg, use_smem, c_re, c_im, ra, rb, lam0,
+    qr_select_kernel<R><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, use_smem, c_re, c_im, ra, rb, lam0,
                                               gap, flag, stage, status);
     return cudaGetLastError();
 }
