@@ -29,13 +29,18 @@
 // accurate to ~1e-14 relative to |A'| |Q'|.
 //
 // Kernel: one CTA (256 threads) per 128 x 48 tile of W'.  K advances in
-// 32-element stages (double-buffered cp.async); thread 0 issues
-// tcgen05.mma.kind::f16 (M = 128, N = 48, K = 16) for every slice pair into
-// its level's TMEM columns and commits each stage to an mbarrier.  Warps w and
-// w + 4 read TMEM lanes 32 (w mod 4) .. and split the 48 columns.  Operand
+// 16-element stages through a 5-slot cp.async ring (four stages in flight);
+// thread 0 issues tcgen05.mma.kind::f16 (M = 128, K = 16) once per A slice p
+// against the B slices q = 0 .. s-1-p side by side (N = 48 per slice, at most
+// five per instruction), with D placed so that slice q's columns fall on
+// level p + q's TMEM region (nine MMAs per K step instead of 28, which cuts
+// the shared-memory reads of A that bound the small-N products), and commits
+// each stage to the slot's mbarrier, which releases the slot for the stage
+// four ahead.  Warps w
+// and w + 4 read TMEM lanes 32 (w mod 4) .. and split the 48 columns.  Operand
 // tiles use the canonical K-major layout without swizzle: 8-row x 16-byte core
-// matrices (128 bytes), the four K chunks of a row group side by side
-// (LBO = 128 B along K, SBO = 512 B between row groups).
+// matrices (128 bytes), the two K chunks of a row group side by side
+// (LBO = 128 B along K, SBO = 256 B between row groups).
 #include "internal.h"
 #include "tc_common.cuh"
 
@@ -47,11 +52,13 @@ using namespace tc;
 
 constexpr int kOzM = 128;          // rows of W' per CTA (TMEM lanes)
 constexpr int kOzN = 48;           // columns of W' per CTA
-constexpr int kOzBK = 32;          // K elements (64 bytes) per stage
+constexpr int kOzBK = 16;          // K elements (32 bytes) per stage
+constexpr int kOzStages = 5;       // shared-memory ring depth
+constexpr int kOzGroup = 5;        // B slices per MMA (N = 5 x 48 <= 256)
 constexpr int kOzThreads = 256;
 constexpr int kOzMaxSlices = 8;
 constexpr int kOzExact = 3;        // levels drained exactly (L = 2..4)
-constexpr int kOzChunkStages = 8;  // 8 x 32 = 256 K elements between drains
+constexpr int kOzChunkStages = 16; // 16 x 16 = 256 K elements between drains
 constexpr uint32_t kTmemCols = 512;
 
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major.
@@ -67,7 +74,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, const int* __restrict__ term_slot,
     int ncols_complex, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[kOzStages];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, colhalf = warp >> 2;     // TMEM lanes / column half
@@ -79,14 +86,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     const __nv_bfloat16* A = Aslices + term * a_term_stride;
     const double* sg = sigma + term * sigma_term_stride;
     double2* Wt = W + (int64_t)term_slot[term] * w_term_stride;
-    const int a_tile = kOzM * kOzBK * 2;                   // bytes per A slice tile (8 KB)
-    const int b_tile = kOzN * kOzBK * 2;                   // 3 KB
+    const int a_tile = kOzM * kOzBK * 2;                   // bytes per A slice tile (4 KB)
+    const int b_tile = kOzN * kOzBK * 2;                   // 1.5 KB
     const int stage_bytes = s * (a_tile + b_tile);
-    unsigned char* stage[2] = {smem, smem + stage_bytes};
 
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int q = 0; q < kOzStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -108,20 +113,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     for (int L = 0; L < kOzExact; ++L)
 #pragma unroll
         for (int c = 0; c < kOzN / 2; ++c) exact[L][c] = 0;
-    bool ok = true;
-    uint32_t level_init = 0;                               // bit L: level L holds data
-    for (int t = 0; t < nk && ok; ++t) {
-        const int b = t & 1;
-        if (t >= 2) ok = mbar_wait(smem_u32(&mbar[b]), ((t - 2) >> 1) & 1);
-        ok = __syncthreads_and(ok);                          // uniform exit on a timeout
-        if (!ok) break;
-        // ---- load stage t: s A tiles (128 x 32 bf16) and s B tiles (48 x 32 bf16)
+    // stage t (16 K elements of every slice) into ring slot t % kOzStages; each
+    // row's 32 bytes are two 16-byte core-matrix rows (LBO 128 B, SBO 256 B)
+    auto load = [&](int t) {
         const int64_t k0 = (int64_t)t * kOzBK;
-        unsigned char* sa = stage[b];
-        unsigned char* sb = stage[b] + s * a_tile;
-        for (int idx = tid; idx < s * (kOzM + kOzN) * 4; idx += kOzThreads) {
-            const int chunk = idx & 3;                     // 16-byte K chunk (8 elements)
-            const int r = idx >> 2;
+        unsigned char* sa = smem + (t % kOzStages) * stage_bytes;
+        unsigned char* sb = sa + s * a_tile;
+        for (int idx = tid; idx < s * (kOzM + kOzN) * 2; idx += kOzThreads) {
+            const int chunk = idx & 1;                     // 16-byte K chunk (8 elements)
+            const int r = idx >> 1;
             int p, rr;
             const __nv_bfloat16* src;
             unsigned char* dst;
@@ -137,41 +137,60 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
                 src = Bslices + p * b_slice_stride + (int64_t)(col0 + rr) * Kp + k0 + chunk * 8;
                 dst = sb + p * b_tile;
             }
-            dst += ((rr >> 3) * 4 + chunk) * 128 + (rr & 7) * 16;
+            dst += ((rr >> 3) * 2 + chunk) * 128 + (rr & 7) * 16;
             cp_async16(smem_u32(dst), src);
         }
+    };
+    bool ok = true;
+    int issued = 0;                                        // stages committed to MMA
+    // prologue: kOzStages - 1 stages in flight (one commit group each)
+    for (int t = 0; t < kOzStages - 1; ++t) {
+        if (t < nk) load(t);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    for (int t = 0; t < nk && ok; ++t) {
+        const int slot = t % kOzStages;
+        asm volatile("cp.async.wait_group %0;" ::"n"(kOzStages - 2) : "memory");   // stage t landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        const bool chunk_start = (t % kOzChunkStages) == 0;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (chunk_start) level_init &= ~((1u << kOzExact) - 1u);   // exact levels restart
+            const uint32_t sa = smem_u32(smem + slot * stage_bytes);
+            const uint32_t sb = sa + s * a_tile;
+            // one MMA per A slice p against B slices q0.. side by side (N up to
+            // 5 x 48): column block q of D lands on level p + q's TMEM region,
+            // so each A slice is read once per K step.  The first step
+            // initialises every level (p = 0 covers them all); the exact levels
+            // are cleared again after each drain.
             for (int p = 0; p < s; ++p) {
-                for (int q = 0; p + q <= s - 1; ++q) {
-                    const int L = p + q;
-                    const uint32_t dcol = tmem + (uint32_t)(L * kOzN);
-                    for (int kk = 0; kk < kOzBK / 16; ++kk) {
-                        const uint64_t ad = smem_desc(smem_u32(sa + p * a_tile) + kk * 256, 128, 512);
-                        const uint64_t bd = smem_desc(smem_u32(sb + q * b_tile) + kk * 256, 128, 512);
-                        const uint32_t acc = (level_init >> L) & 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(dcol),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                        level_init |= 1u << L;
-                    }
+                for (int q0 = 0; q0 < s - p; q0 += kOzGroup) {
+                    const int cnt = min(kOzGroup, s - p - q0);
+                    const uint32_t dcol = tmem + (uint32_t)((p + q0) * kOzN);
+                    const uint64_t ad = smem_desc(sa + p * a_tile, 128, 256);
+                    const uint64_t bd = smem_desc(sb + q0 * b_tile, 128, 256);
+                    const uint32_t acc = (t == 0 && p == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(bf16_idesc(kOzM, cnt * kOzN)), "r"(acc));
                 }
             }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar[b]))
+                    smem_u32(&mbar[slot]))
                 : "memory");
         }
+        ++issued;
+        // refill the slot of stage t - 1 with stage t + kOzStages - 1 once the
+        // MMAs of stage t - 1 are done (those of stage t are already queued)
+        if (t >= 1) ok = mbar_wait(smem_u32(&mbar[(t - 1) % kOzStages]), ((t - 1) / kOzStages) & 1);
+        ok = __syncthreads_and(ok);                          // uniform exit on a timeout
+        if (!ok) break;
+        if (t + kOzStages - 1 < nk) load(t + kOzStages - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
         // ---- end of a 256-element chunk (or of K): drain the exact levels
         if ((t % kOzChunkStages) == kOzChunkStages - 1 || t == nk - 1) {
-            ok = mbar_wait(smem_u32(&mbar[b]), (t >> 1) & 1);
+            ok = mbar_wait(smem_u32(&mbar[slot]), (t / kOzStages) & 1);
             ok = __syncthreads_and(ok);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (ok) {
@@ -186,12 +205,26 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
                             exact[L][g * 8 + c] += __float2int_rn(__uint_as_float(v[c]));
+                        const uint32_t z = 0u;
+                        asm volatile(
+                            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+                                lane_base + (uint32_t)(L * kOzN + colhalf * (kOzN / 2) + g * 8)),
+                            "r"(z)
+                            : "memory");
                     }
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
+    }
+    // copies still in flight (a timeout exit) land before the CTA ends
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok && issued > 0) {
+        // let the queued MMAs finish (bounded) before TMEM is released
+        const int last = issued - 1;
+        (void)mbar_wait(smem_u32(&mbar[last % kOzStages]), (last / kOzStages) & 1);
     }
     if (!ok && tid == 0) atomicOr(err, 16);
     __syncthreads();
@@ -388,11 +421,11 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, 
                        const double* tau, double2* W, const int* term_slot, int* err) {
     static bool attr_done = false;
     const int s = L.s;
-    const int smem = 2 * s * (kOzM + kOzN) * kOzBK * 2;
+    const int smem = kOzStages * s * (kOzM + kOzN) * kOzBK * 2;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(ozaki_bf16_gemm_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             2 * kOzMaxSlices * (kOzM + kOzN) * kOzBK * 2);
+                                             kOzStages * kOzMaxSlices * (kOzM + kOzN) * kOzBK * 2);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
