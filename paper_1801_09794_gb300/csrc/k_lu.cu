@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
     __shared__ T s_U[kMini][64];    // U12 rows of the mini-panel (rest of the panel)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pend = k0 + jb;
+    // panel columns per batch in the in-panel update (as many as the registers
+    // left next to the mini-panel allow at 1024 threads)
+    constexpr int kUpd = (sizeof(T) == 8) ? (ROWS == 4 ? 4 : 8) : (ROWS == 1 ? 4 : 2);
     T v[ROWS][kMini];
 
     for (int mb0 = k0; mb0 < pend; mb0 += kMini) {
@@ -233,18 +236,27 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
                 }
             }
             __syncthreads();
-            // rank-w update of rows below the mini-panel, remaining panel columns
+            // rank-w update of rows below the mini-panel, remaining panel columns;
+            // kUpd columns at a time so that kUpd loads per row are in flight
 #pragma unroll
             for (int i = 0; i < ROWS; ++i) {
                 const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
                 if (r >= rest0 && r < n) {
-                    for (int j = 0; j < nrest; ++j) {
-                        T* ap = A + r + (int64_t)(rest0 + j) * ld;
-                        T a = *ap;
+                    T* ar = A + r + (int64_t)rest0 * ld;
+                    for (int j0 = 0; j0 < nrest; j0 += kUpd) {
+                        T a[kUpd];
 #pragma unroll
-                        for (int c = 0; c < kMini; ++c)
-                            if (c < w) a = cfms(v[i][c], s_U[c][j], a);
-                        *ap = a;
+                        for (int q = 0; q < kUpd; ++q)
+                            if (j0 + q < nrest) a[q] = ar[(int64_t)(j0 + q) * ld];
+#pragma unroll
+                        for (int q = 0; q < kUpd; ++q) {
+                            if (j0 + q < nrest) {
+#pragma unroll
+                                for (int c = 0; c < kMini; ++c)
+                                    if (c < w) a[q] = cfms(v[i][c], s_U[c][j0 + q], a[q]);
+                                ar[(int64_t)(j0 + q) * ld] = a[q];
+                            }
+                        }
                     }
                 }
             }
@@ -418,10 +430,15 @@ cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64
     else if (rows <= kPanelThreads * 2)
         lu_panel_reg_kernel<T, 2><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
                                                                 gather, gcount, panel, gstride);
-    else if (rows <= kPanelThreads * 4 && sizeof(T) == 8)   // complex128 would spill at 4 rows
-        lu_panel_reg_kernel<T, 4><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
-                                                                gather, gcount, panel, gstride);
-    else
+    else if constexpr (sizeof(T) == 8) {                     // complex128 would spill at 4 rows
+        if (rows <= kPanelThreads * 4)
+            lu_panel_reg_kernel<T, 4><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv,
+                                                                    info, gather, gcount, panel,
+                                                                    gstride);
+        else
+            lu_panel_kernel<T><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
+                                                             gather, gcount, panel, gstride);
+    } else
         lu_panel_kernel<T><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
                                                          gather, gcount, panel, gstride);
     return cudaGetLastError();
