@@ -35,6 +35,11 @@ METRIC = "eigenpairs/s at 1e-10 rel. residual"
 UNIT = "eigenpairs/s"
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (vector and tensor), nominal
 FP32_SIMT_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 lanes x FMA x 2.07 GHz
+ONE_SM_FP32_TFLOPS_AT_MAX = 128 * 2 * 2.070e9 / 1e12        # one SM
+# DRAM bytes per step of the dominant phase's kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by phase; the summary
+# and its command are under profiles/.  Absent: not captured for this code.
+ROOF_TRAFFIC = {"reduced": 6 * 2017536}   # 6 iterations per step; n-independent kernels
 TF32_OVER_BF16 = 1.1 / 2.25
 
 WORKLOADS = {
@@ -175,7 +180,10 @@ DIGIT_SLICES = 7      # FEAST_NL_FP32_I8: digit slices per operand of A_t Q
 def phase_work(name, spec, c, iters, nterms_dense):
     """Flops of one phase over one solve: algorithmic (4M complex counting), except
     the digit-split A_t Q, which counts the BF16 tensor-core flops it executes
-    (s(s+1)/2 slice products of the real-embedded n x 2n x 2 m0 GEMM per term)."""
+    (s(s+1)/2 slice products of the real-embedded n x 2n x 2 m0 GEMM per term),
+    and the reduced eigenvalue stage, counted as a dense Hessenberg reduction
+    plus an eigenvalues-only complex QR of the k m0 companion matrix:
+    (40/3 + 10) N^3 real flops per iteration."""
     n, m0, nc = spec["n"], c["m0"], c["nc"]
     if name == "lu":
         return nc * (8.0 / 3.0) * n ** 3
@@ -188,17 +196,25 @@ def phase_work(name, spec, c, iters, nterms_dense):
         return (iters - 1) * nc * 8.0 * n * n * m0
     if name == "project":
         return iters * 8.0 * n * m0 * (3 * m0)
+    if name == "reduced":
+        N = 2 * m0
+        return iters * (40.0 / 3.0 + 10.0) * N ** 3
     return None
 
 
 def phase_peak(name, precision, pk, sm_mhz):
     clk = (sm_mhz or 2070.0) / 2070.0
     if name in ("lu", "solve") and precision in ("fp32", "fp32_i8"):
-        return (FP32_SIMT_TFLOPS_AT_MAX * clk, "alu",
-                "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x SM clock")
+        # trailing updates / block substitutions: three TF32 products per FP32
+        # product; TF32 dense = half the BF16 rate (nominal 1.1 vs 2.25 PF/s)
+        return (pk["bf16_tflops"] * 0.5 / 3.0, "tensor",
+                f"TF32 dense = 0.5 x BF16 ({pk['source']}), / 3 for the split products")
     if name == "apply" and precision == "fp32_i8":
         return (pk["bf16_tflops_sustained"], "tensor",
                 f"BF16 dense, {pk['source']} (sustained figure: timed inside a long step)")
+    if name == "reduced":
+        return (ONE_SM_FP32_TFLOPS_AT_MAX * clk, "alu",
+                "FP32 lanes of the one SM the stage runs on (single CTA): 128 x 2 flop x SM clock")
     return FP64_NOMINAL_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s"
 
 
@@ -282,11 +298,11 @@ def run_gpu(args):
         peak, bound, why = phase_peak(dom, spec["precision"], pk, clk.get("sm_mhz"))
         roof = {"kernel": f"phase '{dom}' (all its launches)", "bound": bound,
                 "achieved": d["tflops"], "peak": peak, "unit": "TFLOP/s", "frac": d["frac"],
-                "traffic": None, "peak_source": why,
+                "traffic": ROOF_TRAFFIC.get(dom), "peak_source": why,
                 "launches_per_step": d["launches_per_step"],
                 "avg_launch_ms": d["ms_per_step"] / max(d["launches_per_step"], 1)}
     else:
-        roof = {"kernel": f"phase '{dom}'", "bound": "latency", "achieved": None, "peak": None,
+        roof = {"kernel": f"phase '{dom}'", "bound": "alu", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
     lu = phases.get("lu", {})
 
@@ -295,7 +311,7 @@ def run_gpu(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64 LU + bf16-split f64 products + f64",
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64",
            "data": "synthetic (seeded generator, no dataset)",
            "config": {"workload": args.workload, "n": n, "degree": 2, "nc": c["nc"],
                       "m0": m0, "count_inside": c["count"], "lu_precision": spec["precision"],
