@@ -34,6 +34,15 @@ Readings of points the paper leaves open (each is also listed in the design doc):
   the first companion form (Sec. 2, the k = 2 pencil there, generalised to
   degree k) and solved by QZ; the Ritz vector is the last block of the pencil
   eigenvector.
+* Step 1 for non-polynomial T (the paper names no reduced solver): the
+  projected problem That(z) = sum_t scale_t f_t(z) Q^H A_t Q is solved by the
+  first two contour moments of That^{-1} (Beyn's method, which the paper
+  cites among the contour methods; here it is only the m0 x m0 reduced
+  solver): trapezoid rule with 256 nodes on the contour scaled by 1.5 about
+  its centre, an m0 x m0 seeded complex-normal probe, rank by
+  sigma > 1e-12 sigma_1; then at most 5 Newton steps (inverse iteration for
+  nonlinear problems) per pair.  Slots the moments leave empty are filled with
+  lambda = c + 1.5 ra (outside C, never tested) and unit coordinate vectors.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -44,7 +53,8 @@ __all__ = [
     "normalized_radius", "select", "ritz_vectors", "block_residual",
     "relative_residuals", "filter_update", "orthonormalize", "factor_nodes",
     "nlfeast", "brute_force_eigs", "winding_count", "shift_invert_nearest",
-    "SingularNode",
+    "SingularNode", "f_derivative", "projected_terms", "reduced_matrix", "beyn_nodes",
+    "reduced_beyn", "newton_reduced", "reduced_solve_general",
 ]
 
 
@@ -104,6 +114,19 @@ def f_value(term, z):
         v = z ** term["p"]
     elif term["kind"] == "exp":
         v = np.exp(-term["tau"] * z)
+    else:
+        raise ValueError(term["kind"])
+    return term["scale"] * v
+
+
+def f_derivative(term, z):
+    """d/dz of f_value: scale * p z^(p-1), or scale * (-tau) exp(-tau z)."""
+    z = np.asarray(z, dtype=np.complex128)
+    if term["kind"] == "pow":
+        p = term["p"]
+        v = p * z ** (p - 1) if p > 0 else np.zeros_like(z)
+    elif term["kind"] == "exp":
+        v = -term["tau"] * np.exp(-term["tau"] * z)
     else:
         raise ValueError(term["kind"])
     return term["scale"] * v
@@ -192,6 +215,114 @@ def reduced_eig(Ahat):
     return lam, Z[-m:, :]
 
 
+# --------------------------------------------------------------------------
+# Step 1 for non-polynomial T (reading in the module docstring)
+# --------------------------------------------------------------------------
+def projected_terms(problem, Q):
+    """G_t = Q^H A_t Q for every term (A_t None: Q^H Q), so that the projected
+    problem is That(z) = sum_t scale_t f_t(z) G_t (Step 1 for any T)."""
+    out = []
+    for t in problem["terms"]:
+        AQ = Q if t["A"] is None else t["A"] @ Q
+        out.append(Q.conj().T @ AQ)
+    return out
+
+
+def reduced_matrix(problem, G, z, derivative=False):
+    """That(z) (or That'(z)) = sum_t scale_t f_t(z) G_t."""
+    f = f_derivative if derivative else f_value
+    M = np.zeros_like(G[0])
+    for t, Gt in zip(problem["terms"], G):
+        M = M + complex(f(t, z)) * Gt
+    return M
+
+
+def beyn_nodes(center, ra, rb, nq=256, scale=1.5):
+    """Trapezoid nodes on the ellipse scaled by `scale` about `center`, with the
+    1/(2 pi i) and dz/dtheta folded into the weights: sum_k w_k g(z_k)
+    approximates (1/(2 pi i)) closed-integral g(z) dz."""
+    theta = 2.0 * np.pi * (np.arange(nq) + 0.5) / nq
+    a, b = scale * ra, scale * rb
+    z = center + a * np.cos(theta) + 1j * b * np.sin(theta)
+    dz = -a * np.sin(theta) + 1j * b * np.cos(theta)
+    w = dz * (2.0 * np.pi / nq) / (2j * np.pi)
+    return z, w
+
+
+def reduced_beyn(problem, G, center, ra, rb, probe, nq=256, scale=1.5, rank_tol=1e-12):
+    """Beyn's moments A0 = sum_k w_k That(z_k)^{-1} V, A1 = sum_k w_k z_k That(z_k)^{-1} V;
+    A0 = U S W^H, rank r by S > rank_tol S_1; B = U_r^H A1 W_r S_r^{-1}; the
+    eigenvalues of B are the eigenvalues of That inside the scaled contour, with
+    vectors U_r s (unit)."""
+    z, w = beyn_nodes(center, ra, rb, nq, scale)
+    m = G[0].shape[0]
+    A0 = np.zeros((m, probe.shape[1]), dtype=np.complex128)
+    A1 = np.zeros_like(A0)
+    for zk, wk in zip(z, w):
+        Y = np.linalg.solve(reduced_matrix(problem, G, zk), probe)
+        A0 += wk * Y
+        A1 += (wk * zk) * Y
+    U, S, Wh = np.linalg.svd(A0, full_matrices=False)
+    r = int(np.sum(S > rank_tol * S[0])) if S.size and S[0] > 0 else 0
+    if r == 0:
+        return np.zeros(0, dtype=np.complex128), np.zeros((m, 0), dtype=np.complex128)
+    Ur, Sr, Wr = U[:, :r], S[:r], Wh[:r, :].conj().T
+    B = (Ur.conj().T @ A1 @ Wr) / Sr[None, :]
+    lam, Sv = np.linalg.eig(B)
+    Y = Ur @ Sv
+    return lam, Y / np.linalg.norm(Y, axis=0)[None, :]
+
+
+def newton_reduced(problem, G, lam, y, steps=5):
+    """Newton's method on [That(l) y = 0, y^H y = 1] (inverse iteration for
+    nonlinear problems): u = That(l)^{-1} That'(l) y, l <- l - 1/(y^H u),
+    y <- u / |u|; at most `steps` steps, stopping at FP64 rounding."""
+    y = y / np.linalg.norm(y)
+    for _ in range(steps):
+        try:
+            u = np.linalg.solve(reduced_matrix(problem, G, lam),
+                                reduced_matrix(problem, G, lam, derivative=True) @ y)
+        except np.linalg.LinAlgError:     # an exact eigenvalue already
+            break
+        yu = np.vdot(y, u)
+        if yu == 0 or not np.isfinite(yu):
+            break
+        dl = -1.0 / yu
+        lam = lam + dl
+        y = u / np.linalg.norm(u)
+        if abs(dl) <= 4.0 * np.finfo(float).eps * max(abs(lam), 1.0):
+            break
+    return lam, y
+
+
+def reduced_solve_general(problem, G, center, ra, rb, m0, probe):
+    """Steps 1-2 for any T: Beyn's eigenpairs of That inside the 1.5x contour,
+    polished by Newton, ranked by (rho, Re, Im); at most m0 kept; the empty
+    slots get lambda = c + 1.5 ra (outside C) and unit coordinate vectors."""
+    lam_b, Y_b = reduced_beyn(problem, G, center, ra, rb, probe)
+    m = G[0].shape[0]
+    lam = []
+    Y = []
+    for i in range(lam_b.size):
+        l, y = newton_reduced(problem, G, lam_b[i], Y_b[:, i])
+        lam.append(l)
+        Y.append(y)
+    lam = np.array(lam, dtype=np.complex128)
+    Y = np.array(Y, dtype=np.complex128).T.reshape(m, -1)
+    if lam.size:
+        order = select(lam, center, ra, rb, min(m0, lam.size))
+        lam, Y = lam[order], Y[:, order]
+    nf = m0 - lam.size
+    if nf > 0:
+        fill_l = np.full(nf, center + 1.5 * ra, dtype=np.complex128)
+        fill_y = np.zeros((m, nf), dtype=np.complex128)
+        for q in range(nf):
+            fill_y[(lam.size + q) % m, q] = 1.0
+        lam = np.concatenate([lam, fill_l])
+        Y = np.concatenate([Y, fill_y], axis=1)
+    return lam, Y
+
+
 def normalized_radius(lam, center, ra, rb):
     """rho(lambda) of the Step 2 reading; rho < 1 means inside C."""
     lam = np.asarray(lam, dtype=np.complex128)
@@ -268,8 +399,10 @@ def orthonormalize(Q):
 # --------------------------------------------------------------------------
 # Algorithm 1
 # --------------------------------------------------------------------------
-def nlfeast(problem, contour, m0, X0, tol=1e-10, maxit=50, lus=None, norms=None):
-    """Algorithm 1 (NLFEAST for T(lambda)x = 0), polynomial T.
+def nlfeast(problem, contour, m0, X0, tol=1e-10, maxit=50, lus=None, norms=None, probe_seed=12345):
+    """Algorithm 1 (NLFEAST for T(lambda)x = 0); polynomial T through the
+    companion linearisation, any other T through the Beyn reduced solver
+    (probe drawn from `probe_seed`).
 
     contour: {"center": complex, "ra": float, "rb": float, "nc": int, "rule": str}.
     Returns a dict with the m0 selected Ritz values ``lam`` and unit vectors ``X``,
@@ -287,12 +420,22 @@ def nlfeast(problem, contour, m0, X0, tol=1e-10, maxit=50, lus=None, norms=None)
     history = []
     converged = False
     it = 0
+    polynomial = all(t["kind"] == "pow" for t in problem["terms"])
+    probe = None
+    if not polynomial:
+        rng = np.random.default_rng(probe_seed)
+        probe = (rng.standard_normal((m0, m0)) + 1j * rng.standard_normal((m0, m0))) / np.sqrt(2.0)
     for it in range(1, maxit + 1):
-        Ahat = projected_coefficients(problem, Q)                      # Step 1
-        lam_all, Y_all = reduced_eig(Ahat)
-        sel = select(lam_all, c, ra, rb, m0)                           # Step 2
-        lam = lam_all[sel]
-        X = ritz_vectors(Q, Y_all[:, sel])
+        if polynomial:
+            Ahat = projected_coefficients(problem, Q)                  # Step 1
+            lam_all, Y_all = reduced_eig(Ahat)
+            sel = select(lam_all, c, ra, rb, m0)                       # Step 2
+            lam = lam_all[sel]
+            X = ritz_vectors(Q, Y_all[:, sel])
+        else:
+            G = projected_terms(problem, Q)                            # Steps 1-2
+            lam, Y = reduced_solve_general(problem, G, c, ra, rb, m0, probe)
+            X = ritz_vectors(Q, Y)
         R = block_residual(problem, X, lam)                            # Step 3
         rr = relative_residuals(problem, R, lam, norms)
         ins = normalized_radius(lam, c, ra, rb) < 1.0

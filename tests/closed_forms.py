@@ -78,3 +78,17 @@ def load_table1(path):
             i, lam, res = line.split()
             rows.append((int(i), float(lam), float(res)))
     return rows
+
+
+def delay_family_eigs(n, c, d, a, tau, branches=range(-3, 4)):
+    """Eigenvalues of -lambda I + (c0 I + d0 S) + (c1 I + d1 S) e^{-tau lambda}:
+    for each eigenvalue s of S, alpha = c0 + d0 s, beta = c1 + d1 s, the roots of
+    -lambda + alpha + beta e^{-tau lambda} = 0 are
+    lambda = alpha + W_l(tau beta e^{-tau alpha}) / tau over the Lambert-W branches l."""
+    from scipy.special import lambertw
+    out = []
+    for s in tridiag_eigs(n, a):
+        al, be = c[0] + d[0] * s, c[1] + d[1] * s
+        for l in branches:
+            out.append(al + lambertw(tau * be * np.exp(-tau * al), l) / tau)
+    return np.array(out, dtype=np.complex128)

@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "tridiag", "sym_gauss", "complex_gauss", "start_block",
     "mass_spring", "closed_form_family", "config1_qep", "config2_qep",
-    "random_pep", "linear_problem", "delay_problem", "cubic_pep",
+    "random_pep", "linear_problem", "delay_problem", "cubic_pep", "delay_family",
 ]
 
 
@@ -147,3 +147,16 @@ def delay_problem(n, seed, tau=1.0):
              {"kind": "pow", "p": 0, "scale": 1.0 + 0j, "A": A0},
              {"kind": "exp", "tau": float(tau), "scale": 1.0 + 0j, "A": A1}]
     return {"n": n, "terms": terms, "name": f"delay_n{n}"}
+
+
+def delay_family(n, c, d, a, tau=1.0):
+    """T(lambda) = -lambda I + (c0 I + d0 S) + (c1 I + d1 S) exp(-tau lambda),
+    S = tridiag(-1, a, -1): every eigenvalue is alpha + W_l(tau beta e^{-tau alpha})/tau
+    for an eigenvalue s of S (alpha = c0 + d0 s, beta = c1 + d1 s) and a branch l
+    of the Lambert W function."""
+    S = tridiag(n, a, -1.0)
+    I = np.eye(n, dtype=np.complex128)
+    terms = [{"kind": "pow", "p": 1, "scale": -1.0 + 0j, "A": None},
+             {"kind": "pow", "p": 0, "scale": 1.0 + 0j, "A": c[0] * I + d[0] * S},
+             {"kind": "exp", "tau": float(tau), "scale": 1.0 + 0j, "A": c[1] * I + d[1] * S}]
+    return {"n": n, "terms": terms, "name": f"delay_family_n{n}"}
