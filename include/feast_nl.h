@@ -141,7 +141,14 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
  *   X0   : n x m0 complex128 row-major start block (host or device), or NULL to
  *          draw one on the device from `seed` (complex normal, counter-based).
  *   info : optional out summary.
- * Polynomial T only (kind POW); EXP terms return EUNSUPPORTED.
+ * Step 1-2 for polynomial T (POW terms only): the first companion
+ * linearisation of the projected polynomial (Sec. 2).  With any EXP term
+ * (e.g. the delay problem T = -lambda I + A0 + A1 e^{-tau lambda}), the paper
+ * names no reduced solver: the projected problem is solved by the first two
+ * contour moments of its inverse (Beyn's method) on the contour scaled by 1.5
+ * (256 trapezoid nodes, FP64), then Newton per pair; slots the moments leave
+ * empty hold lambda = c + 1.5 ra (outside C) and are never tested.  There
+ * m0 <= 64.
  * Returns OK, ENOT_CONVERGED, ETOO_MANY, ESINGULAR_NODE, EINVAL, ENOMEM,
  * EDEVICE.  After OK, ENOT_CONVERGED or ETOO_MANY the last iterate is
  * readable with feast_nl_get_eigpairs. */

@@ -124,6 +124,12 @@ struct HostTerm {
 
 }  // namespace
 
+namespace {
+// seed of the probe block of the reduced solver for non-polynomial T (the
+// result does not depend on it once the probe spans the wanted eigenvectors)
+constexpr uint64_t kBeynProbeSeed = 0x6265796e2d70726full;
+}  // namespace
+
 struct feast_nl_handle {
     int64_t n = 0;
     int nterms = 0, nA = 0, kmax = 0, precision = 0;
@@ -154,6 +160,7 @@ struct feast_nl_handle {
     double2 *dG2 = nullptr, *dRinv = nullptr, *dLam = nullptr, *dCoef = nullptr, *dFsum = nullptr;
     double *dNu = nullptr, *dRnorm = nullptr, *dRelres = nullptr;
     unsigned char* dRed = nullptr;  // reduced-problem workspace (bytes)
+    unsigned char* dBeyn = nullptr; // reduced solver for non-polynomial T (bytes)
     double2* dStage = nullptr;      // n x mcap staging for layout changes
     IterStatus* dStatus = nullptr;
     IterStatus* hStatus = nullptr;  // pinned
@@ -228,7 +235,7 @@ void release_workspace(feast_nl_handle* h) {
     h->dY = nullptr;
     dfree(h->dG); dfree(h->dSplit); dfree(h->dAhat); dfree(h->dYred); dfree(h->dYcat);
     dfree(h->dG2); dfree(h->dRinv); dfree(h->dLam); dfree(h->dCoef); dfree(h->dFsum);
-    dfree(h->dNu); dfree(h->dRnorm); dfree(h->dRelres); dfree(h->dRed); dfree(h->dStage);
+    dfree(h->dNu); dfree(h->dRnorm); dfree(h->dRelres); dfree(h->dRed); dfree(h->dBeyn); dfree(h->dStage);
     dfree(h->dQsl); dfree(h->dTau);
     h->mcap = 0;
     h->have_result = false;
@@ -263,6 +270,7 @@ int ensure_workspace(feast_nl_handle* h, int m) {
     CK(dalloc(&h->dRnorm, (size_t)m));
     CK(dalloc(&h->dRelres, (size_t)m));
     CK(dalloc(&h->dRed, reduced_work_bytes(m, std::max(h->kmax, 1))));
+    if (h->has_exp && m <= beyn_max_m()) CK(dalloc(&h->dBeyn, beyn_work_bytes(m)));
     CK(dalloc(&h->dStage, (size_t)n * m));
     if (h->oz_s > 0) {
         h->oz = ozaki_layout(n, m, h->oz_s);
@@ -361,12 +369,16 @@ int ritz_and_residual(feast_nl_handle* h, int m, double tol) {
         Phase ph(h, FEAST_NL_PH_PROJECT);
         CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, h->dQ, n, h->dW, n, zero, h->dG, m,
                          h->dSplit, h->splits));
-        CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
+        if (!h->has_exp) CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
     }
     {
         Phase ph(h, FEAST_NL_PH_REDUCED);
-        CK(reduced_solve(h->st, m, h->kmax, h->dAhat, m, h->c_re, h->c_im, h->ra, h->rb, h->dRed,
-                         h->dLam, h->dYred, h->dStatus));
+        if (h->has_exp)
+            CK(reduced_solve_general(h->st, m, T, h->dTerms, h->dG, h->c_re, h->c_im, h->ra, h->rb,
+                                     kBeynProbeSeed, h->dBeyn, h->dLam, h->dYred, h->dStatus));
+        else
+            CK(reduced_solve(h->st, m, h->kmax, h->dAhat, m, h->c_re, h->c_im, h->ra, h->rb,
+                             h->dRed, h->dLam, h->dYred, h->dStatus));
     }
     Phase ph(h, FEAST_NL_PH_RITZ);
     CK(gemm<double2>(h->st, 0, (int)n, m, m, one, h->dQ, n, 0, h->dYred, m, 0, zero, h->dX, n, 0,
@@ -780,8 +792,9 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     CKS(validate_handle(h));
     if (info) std::memset(info, 0, sizeof(*info));
     if (!h->have_contour) return fail(FEAST_NL_EINVAL, "set_contour must succeed before solve");
-    if (h->has_exp) return fail(FEAST_NL_EUNSUPPORTED, "non-polynomial T: solve not implemented");
     if (m0 < 1 || m0 > kMaxM0 || m0 > h->n) return fail(FEAST_NL_EINVAL, "m0 must be in [1, min(n, 112)]");
+    if (h->has_exp && m0 > beyn_max_m())
+        return fail(FEAST_NL_EINVAL, "non-polynomial T: m0 must be <= " + std::to_string(beyn_max_m()));
     if (h->kmax * m0 > 1024) return fail(FEAST_NL_EINVAL, "degree * m0 must be <= 1024");
     if (maxit < 1) return fail(FEAST_NL_EINVAL, "maxit must be >= 1");
     if (!(tol > 0.0)) return fail(FEAST_NL_EINVAL, "tol must be > 0");

@@ -239,6 +239,18 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
                           double c_re, double c_im, double ra, double rb, void* work,
                           double2* lam, double2* Yred, IterStatus* status);
 size_t reduced_work_bytes(int m, int kmax);
+// Steps 1-2 for general T (any term kinds): G = [G_0 | .. | G_{T-1}] (m x T m,
+// G_t = Q^H A_t Q, scales applied through `terms`).  Eigenvalues of
+// That(z) = sum_t f_t(z) G_t inside the contour scaled by 1.5 from the first two
+// contour moments (FP64, 256 trapezoid nodes, probe drawn from probe_seed), ranked
+// by Step 2's rule, refined by Newton; slots beyond the moments' rank get
+// lambda = c + 1.5 ra and unit vectors.  m <= beyn_max_m().
+size_t beyn_work_bytes(int m);
+int beyn_max_m();
+cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const TermDev* terms,
+                                  const double2* G, double c_re, double c_im, double ra,
+                                  double rb, uint64_t probe_seed, void* work, double2* lam,
+                                  double2* Yred, IterStatus* status);
 // Cholesky G = R^H R (with diagonal shift), returns R^{-1} (upper) in Rinv.
 cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_rel,
                          double2* Rinv, IterStatus* status);

@@ -76,6 +76,18 @@ constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (win
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
+// The reduced problem seen by the refinement: the projected matrix polynomial
+// (kmax >= 0: Ahat holds the kmax + 1 coefficients, stacked m x m), or general
+// terms (kmax < 0): That(l) = sum_t f_t(l) G_t, G_t = Q^H A_t Q stacked m x m,
+// f_t with the term's scale.
+struct RedProblem {
+    int kmax;
+    const double2* Ahat;
+    int nterms;
+    const TermDev* terms;
+    const double2* G;
+};
+
 // ---------------------------------------------------------------------------
 // companion matrix: LU of Ahat_k, solve for the top block row (precision R).
 // ---------------------------------------------------------------------------
@@ -596,20 +608,73 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
 constexpr int kNewtonThreads = 256;
 constexpr int kNewtonMax = 8;
 
-template <typename LT>
-__device__ void newton_build(int m, int kmax, const double2* __restrict__ Ahat, double2 lam,
-                             LT* T) {
-    const int64_t mm = (int64_t)m * m;
-    const LT lf = cmake<LT>(lam.x, lam.y);
-    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-        double2 a = Ahat[(int64_t)kmax * mm + e];          // Horner in lambda
-        LT v = cmake<LT>(a.x, a.y);
-        for (int p = kmax - 1; p >= 0; --p) {
-            a = Ahat[(int64_t)p * mm + e];
-            v = cfma(v, lf, cmake<LT>(a.x, a.y));
-        }
-        T[e] = v;
+// f_t(l) (scale included) or its derivative, for the general reduced problem
+__device__ __forceinline__ double2 rp_term(const TermDev& t, double2 l, bool deriv) {
+    double2 v;
+    if (t.kind == 0) {
+        const int p = deriv ? t.p - 1 : t.p;
+        if (p < 0) return make_double2(0.0, 0.0);
+        v = make_double2(1.0, 0.0);
+        for (int q = 0; q < p; ++q) v = v * l;
+        if (deriv) v = (double)t.p * v;
+    } else {
+        const double er = exp(-t.tau * l.x);
+        double sn, cs;
+        sincos(-t.tau * l.y, &sn, &cs);
+        v = make_double2(er * cs, er * sn);
+        if (deriv) v = (-t.tau) * v;
     }
+    return t.scale * v;
+}
+
+template <typename LT>
+__device__ void newton_build(int m, const RedProblem& P, double2 lam, LT* T) {
+    const int64_t mm = (int64_t)m * m;
+    if (P.kmax >= 0) {
+        const LT lf = cmake<LT>(lam.x, lam.y);
+        for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
+            double2 a = P.Ahat[(int64_t)P.kmax * mm + e];      // Horner in lambda
+            LT v = cmake<LT>(a.x, a.y);
+            for (int p = P.kmax - 1; p >= 0; --p) {
+                a = P.Ahat[(int64_t)p * mm + e];
+                v = cfma(v, lf, cmake<LT>(a.x, a.y));
+            }
+            T[e] = v;
+        }
+    } else {
+        for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int t = 0; t < P.nterms; ++t)
+                v = cfma(rp_term(P.terms[t], lam, false), P.G[(int64_t)t * mm + e], v);
+            T[e] = cmake<LT>(v.x, v.y);
+        }
+    }
+}
+
+// Row r of T(l) x and T'(l) x, in FP64.
+__device__ void newton_apply(int m, const RedProblem& P, double2 l, const double2* x, int r,
+                             double2* v_out, double2* dv_out) {
+    const int64_t mm = (int64_t)m * m;
+    double2 v = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
+    if (P.kmax >= 0) {
+        for (int p = P.kmax; p >= 0; --p) {                 // Horner for T(l)x and T'(l)x
+            double2 row = make_double2(0.0, 0.0);
+            const double2* Ap = P.Ahat + (int64_t)p * mm;
+            for (int c = 0; c < m; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
+            dv = cfma(dv, l, v);
+            v = cfma(v, l, row);
+        }
+    } else {
+        for (int t = 0; t < P.nterms; ++t) {
+            double2 row = make_double2(0.0, 0.0);
+            const double2* Gt = P.G + (int64_t)t * mm;
+            for (int c = 0; c < m; ++c) row = cfma(Gt[r + (int64_t)c * m], x[c], row);
+            v = cfma(rp_term(P.terms[t], l, false), row, v);
+            dv = cfma(rp_term(P.terms[t], l, true), row, dv);
+        }
+    }
+    *v_out = v;
+    *dv_out = dv;
 }
 
 // LU with partial pivoting (cabs1) in place; the rank-1 update gives each warp
@@ -728,10 +793,18 @@ __device__ __forceinline__ double2 to_d2f(double2 v) { return v; }
 // fallback stage, where clustered reduced eigenvalues need the FP64 factor).
 template <typename LT>
 __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
-    int m, int kmax, const double2* __restrict__ Ahat, const double2* __restrict__ lam0,
+    int m, RedProblem P, const double2* __restrict__ lam0,
     const double* __restrict__ gap, double2* __restrict__ lam, double2* __restrict__ Y,
-    int* redflag, int stage, IterStatus* status) {
+    int* redflag, int stage, IterStatus* status, const int* __restrict__ nkeep,
+    double2 filler) {
     if (stage == 2 && !(*redflag & kNeed64)) return;
+    if (nkeep != nullptr && (int)blockIdx.x >= *nkeep) {
+        // a slot the reduced solver left empty: lambda outside C, unit vector
+        if (threadIdx.x == 0) lam[blockIdx.x] = filler;
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            Y[r + (int64_t)blockIdx.x * m] = make_double2(r == (int)(blockIdx.x % m) ? 1.0 : 0.0, 0.0);
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* x = reinterpret_cast<double2*>(smem_raw);
     double2* u = x + m;
@@ -747,7 +820,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     const int64_t mm = (int64_t)m * m;
     const double2 l0 = lam0[i];
     double2 l = l0;
-    newton_build(m, kmax, Ahat, l, T);
+    newton_build(m, P, l, T);
     __syncthreads();
     newton_lu(m, T, piv, &s_p);
     for (int r = threadIdx.x; r < m; r += blockDim.x) fa[r] = cmake<LT>(1.0, 0.0);
@@ -772,14 +845,8 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     double prev = INFINITY;
     for (int it = 0; it < kNewtonMax; ++it) {
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
-            double2 v = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
-            for (int p = kmax; p >= 0; --p) {             // Horner for T(l)x and T'(l)x
-                double2 row = make_double2(0.0, 0.0);
-                const double2* Ap = Ahat + (int64_t)p * mm;
-                for (int c = 0; c < m; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
-                dv = cfma(dv, l, v);
-                v = cfma(v, l, row);
-            }
+            double2 v, dv;
+            newton_apply(m, P, l, x, r, &v, &dv);
             fa[r] = cmake<LT>(v.x, v.y);
             fu[r] = cmake<LT>(dv.x, dv.y);
         }
@@ -814,7 +881,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         if (rel <= 64.0 * DBL_EPSILON || (rel < 1e-12 && rel > 0.25 * prev)) { conv = true; break; }
         prev = rel;
         if (rel > 1e-9 && refreshes < 2 && (it == 1 || it == 4)) {
-            newton_build(m, kmax, Ahat, l, T);
+            newton_build(m, P, l, T);
             __syncthreads();
             newton_lu(m, T, piv, &s_p);
             ++refreshes;
@@ -999,8 +1066,9 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     // stage 1: FP32 eigenvalues, FP64 Newton
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
-    newton_kernel<float2><<<m0, kNewtonThreads, nsm32, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag, 1,
-                                                             status);
+    const RedProblem P{kmax, Ahat, 0, nullptr, nullptr};
+    newton_kernel<float2><<<m0, kNewtonThreads, nsm32, st>>>(m, P, lam0, gap, lam, Yred, flag, 1,
+                                                             status, nullptr, make_double2(0.0, 0.0));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     note_launch();
     duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
@@ -1008,8 +1076,317 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     // stage 2 (device-side no-op unless stage 1 flagged a failure)
     if ((e = run_stage<double>(st, 2, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
-    newton_kernel<double2><<<m0, kNewtonThreads, nsm64, st>>>(m, kmax, Ahat, lam0, gap, lam, Yred, flag,
-                                                              2, status);
+    newton_kernel<double2><<<m0, kNewtonThreads, nsm64, st>>>(m, P, lam0, gap, lam, Yred, flag,
+                                                              2, status, nullptr, make_double2(0.0, 0.0));
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Reduced solver for general T (reading: Beyn's first two contour moments of
+// That^{-1} on the contour scaled by 1.5, 256 trapezoid nodes, an m x m probe,
+// rank by sigma > 1e-12 sigma_1, then Newton per pair; empty slots filled with
+// lambda = c + 1.5 ra and unit vectors)
+// ===========================================================================
+namespace {
+constexpr int kBeynNodes = 256;
+constexpr double kBeynScale = 1.5;
+constexpr double kBeynRankTol = 1e-12;
+constexpr int kBeynThreads = 256;
+constexpr int kSvdThreads = 512;
+constexpr int kSvdMaxSweeps = 40;
+
+__device__ __forceinline__ void beyn_node(int k, double c_re, double c_im, double ra, double rb,
+                                          double2* z, double2* w) {
+    const double th = 2.0 * M_PI * (k + 0.5) / kBeynNodes;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double a = kBeynScale * ra, b = kBeynScale * rb;
+    *z = make_double2(c_re + a * cs, c_im + b * sn);
+    const double2 dz = make_double2(-a * sn, b * cs);
+    // w = dz * (2 pi / nodes) / (2 pi i) = dz * (-i) / nodes
+    *w = make_double2(dz.y / kBeynNodes, -dz.x / kBeynNodes);
+}
+
+// one warp solves L U y = P b in place (LU and pivots of newton_lu)
+__device__ void lu_solve_warp(int m, const double2* T, const int* piv, double2* b) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int c = 0; c < m; ++c) {
+            const int p = piv[c];
+            if (p != c) { double2 t = b[c]; b[c] = b[p]; b[p] = t; }
+        }
+    __syncwarp();
+    for (int i = 0; i < m; ++i) {
+        const double2 bi = b[i];
+        for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
+        __syncwarp();
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
+        __syncwarp();
+        const double2 bi = b[i];
+        for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
+        __syncwarp();
+    }
+}
+
+// CTA k: That(z_k)^{-1} V (FP64 LU), written as w_k Y and w_k z_k Y.
+__global__ void __launch_bounds__(kBeynThreads) beyn_solve_kernel(
+    int m, RedProblem P, double c_re, double c_im, double ra, double rb,
+    const double2* __restrict__ V, double2* __restrict__ P0, double2* __restrict__ P1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* T = reinterpret_cast<double2*>(smem_raw);
+    double2* Y = T + (int64_t)m * m;
+    int* piv = reinterpret_cast<int*>(Y + (int64_t)m * m);
+    __shared__ int s_p;
+    const int k = blockIdx.x;
+    double2 z, w;
+    beyn_node(k, c_re, c_im, ra, rb, &z, &w);
+    newton_build(m, P, z, T);
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) Y[e] = V[e];
+    __syncthreads();
+    newton_lu(m, T, piv, &s_p);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int col = warp; col < m; col += nw) lu_solve_warp(m, T, piv, Y + (int64_t)col * m);
+    __syncthreads();
+    const double2 wz = w * z;
+    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
+        P0[(int64_t)k * mm + e] = w * Y[e];
+        P1[(int64_t)k * mm + e] = wz * Y[e];
+    }
+}
+
+// A0 = sum_k P0[k], A1 = sum_k P1[k] in node order (deterministic)
+__global__ void beyn_reduce_kernel(int64_t mm, const double2* __restrict__ P0,
+                                   const double2* __restrict__ P1, double2* __restrict__ A0,
+                                   double2* __restrict__ A1) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= mm) return;
+    double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
+    for (int k = 0; k < kBeynNodes; ++k) {
+        s0 = s0 + P0[(int64_t)k * mm + e];
+        s1 = s1 + P1[(int64_t)k * mm + e];
+    }
+    A0[e] = s0;
+    A1[e] = s1;
+}
+
+// One CTA: one-sided Jacobi SVD of A0 (m x m, m even after padding by the
+// caller's choice of m), A0 = U diag(sigma) W^H; then the rank r (sigma >
+// 1e-12 sigma_max), B = U_K^H A1 W_K diag(1/sigma_K) for the kept columns K,
+// written into the top-left r x r of Bfull (m x m); the rest of Bfull is a
+// diagonal far outside the contour (sorted last by Step 2's ranking).
+__global__ void __launch_bounds__(kSvdThreads) beyn_svd_kernel(
+    int m, const double2* __restrict__ A0, const double2* __restrict__ A1, double c_re,
+    double c_im, double ra, double2* __restrict__ Bfull, int* __restrict__ rank,
+    IterStatus* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* M = reinterpret_cast<double2*>(smem_raw);          // m x m, becomes U diag(sigma)
+    double2* W = M + (int64_t)m * m;                              // m x m
+    double* sig = reinterpret_cast<double*>(W + (int64_t)m * m);  // m
+    int* keep = reinterpret_cast<int*>(sig + m);                  // m
+    __shared__ double s_off;
+    __shared__ int s_r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t mm = (int64_t)m * m;
+    for (int64_t e = tid; e < mm; e += blockDim.x) {
+        M[e] = A0[e];
+        W[e] = make_double2((e % m) == (e / m) ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    const int me = (m + 1) & ~1;          // players (a phantom column when m is odd)
+    for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
+        if (tid == 0) s_off = 0.0;
+        __syncthreads();
+        double off = 0.0;
+        for (int round = 0; round < me - 1; ++round) {
+            for (int pr = warp; pr < me / 2; pr += nw) {
+                auto idx = [&](int j) { return j == 0 ? 0 : 1 + (j - 1 + round) % (me - 1); };
+                int p = idx(pr), q = idx(me - 1 - pr);
+                if (p > q) { int t = p; p = q; q = t; }
+                if (q >= m) continue;                                  // phantom
+                double2* ap = M + (int64_t)p * m;
+                double2* aq = M + (int64_t)q * m;
+                double al = 0.0, be = 0.0;
+                double2 ga = make_double2(0.0, 0.0);
+                for (int r = lane; r < m; r += 32) {
+                    al += cnorm2(ap[r]);
+                    be += cnorm2(aq[r]);
+                    ga = cfma(cconj(ap[r]), aq[r], ga);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+                    ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+                }
+                const double g = cabs(ga);
+                const double nrm = sqrt(al * be);
+                if (!(g > 1e-15 * nrm) || !(nrm > 0.0)) continue;
+                off = fmax(off, g / nrm);
+                const double2 e = make_double2(ga.x / g, ga.y / g);   // phase of gamma
+                const double zeta = (be - al) / (2.0 * g);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                // [a_p, a_q] <- [a_p, a_q] diag(1, conj(e)) [[c, s], [-s, c]]
+                double2* wp = W + (int64_t)p * m;
+                double2* wq = W + (int64_t)q * m;
+                for (int r = lane; r < m; r += 32) {
+                    const double2 x = ap[r], y = cconj(e) * aq[r];
+                    ap[r] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+                    aq[r] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+                    const double2 u = wp[r], v = cconj(e) * wq[r];
+                    wp[r] = make_double2(c * u.x - s * v.x, c * u.y - s * v.y);
+                    wq[r] = make_double2(s * u.x + c * v.x, s * u.y + c * v.y);
+                }
+            }
+            __syncthreads();
+        }
+        if (lane == 0 && off > 0.0) atomicMax(reinterpret_cast<unsigned long long*>(&s_off),
+                                              (unsigned long long)__double_as_longlong(off));
+        __syncthreads();
+        if (s_off < 1e-14) break;
+        __syncthreads();
+        if (sweep == kSvdMaxSweeps - 1 && tid == 0) atomicOr(&status->flags, 1);
+    }
+    // singular values, rank, U columns (M / sigma)
+    for (int j = warp; j < m; j += nw) {
+        double sj = 0.0;
+        for (int r = lane; r < m; r += 32) sj += cnorm2(M[r + (int64_t)j * m]);
+        for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+        if (lane == 0) sig[j] = sqrt(sj);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double smax = 0.0;
+        for (int j = 0; j < m; ++j) smax = fmax(smax, sig[j]);
+        int r = 0;
+        for (int j = 0; j < m; ++j)
+            if (smax > 0.0 && sig[j] > kBeynRankTol * smax) keep[r++] = j;
+        s_r = r;
+        *rank = r;
+    }
+    __syncthreads();
+    const int r = s_r;
+    // T1 = A1 W_K (m x r), then B(i, j) = U_K_i^H T1_j / sigma_K_j with U = M / sigma
+    double2* T1 = reinterpret_cast<double2*>(
+        (reinterpret_cast<uintptr_t>(keep + m) + 15) & ~static_cast<uintptr_t>(15));
+    for (int e = tid; e < m * r; e += blockDim.x) {
+        const int a = e % m, j = e / m;
+        const double2* wj = W + (int64_t)keep[j] * m;
+        double2 t = make_double2(0.0, 0.0);
+        for (int b = 0; b < m; ++b) t = cfma(A1[a + (int64_t)b * m], wj[b], t);
+        T1[e] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < r && j < r) {
+            const int ki = keep[i], kj = keep[j];
+            const double2* ui = M + (int64_t)ki * m;
+            const double2* tj = T1 + (int64_t)j * m;
+            for (int a = 0; a < m; ++a) v = cfma(cconj(ui[a]), tj[a], v);
+            v = (1.0 / (sig[ki] * sig[kj])) * v;
+        } else if (i == j) {
+            v = make_double2(c_re + 10.0 * ra * (1.0 + i), c_im);
+        }
+        Bfull[e] = v;
+    }
+}
+
+struct BeynLayout { size_t V, P0, P1, A0, A1, B, Hg, lam0, gap, flag, rank, total; };
+BeynLayout beyn_layout(int m) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t mm = (size_t)m * m * sizeof(double2);
+    BeynLayout L;
+    size_t o = 0;
+    L.V = o;    o = al(o + mm);
+    L.P0 = o;   o = al(o + mm * kBeynNodes);
+    L.P1 = o;   o = al(o + mm * kBeynNodes);
+    L.A0 = o;   o = al(o + mm);
+    L.A1 = o;   o = al(o + mm);
+    L.B = o;    o = al(o + mm);
+    L.Hg = o;   o = al(o + packed_elems(m) * sizeof(double2));
+    L.lam0 = o; o = al(o + (size_t)m * sizeof(double2));
+    L.gap = o;  o = al(o + (size_t)m * sizeof(double));
+    L.flag = o; o = al(o + 16);
+    L.rank = o; o = al(o + 16);
+    L.total = o;
+    return L;
+}
+}  // namespace
+
+size_t beyn_work_bytes(int m) { return beyn_layout(m).total; }
+int beyn_max_m() { return 64; }
+
+cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const TermDev* terms,
+                                  const double2* G, double c_re, double c_im, double ra,
+                                  double rb, uint64_t probe_seed, void* work, double2* lam,
+                                  double2* Yred, IterStatus* status) {
+    if (m < 1 || m > beyn_max_m()) return cudaErrorInvalidValue;
+    cudaError_t e;
+    static bool attr_done = false;
+    const size_t solve_smem = 2 * sizeof(double2) * (size_t)m * m + sizeof(int) * m;
+    const size_t svd_smem = 3 * sizeof(double2) * (size_t)m * m + (sizeof(double) + sizeof(int)) * m + 16;
+    if (!attr_done) {
+        const int cap = 3 * 16 * 64 * 64 + 16 * 64 + 64;
+        if ((e = cudaFuncSetAttribute(beyn_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      cap)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(beyn_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      cap)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(qr_select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024)) != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const BeynLayout L = beyn_layout(m);
+    unsigned char* base = static_cast<unsigned char*>(work);
+    double2* V = reinterpret_cast<double2*>(base + L.V);
+    double2* P0 = reinterpret_cast<double2*>(base + L.P0);
+    double2* P1 = reinterpret_cast<double2*>(base + L.P1);
+    double2* A0 = reinterpret_cast<double2*>(base + L.A0);
+    double2* A1 = reinterpret_cast<double2*>(base + L.A1);
+    double2* B = reinterpret_cast<double2*>(base + L.B);
+    double2* Hg = reinterpret_cast<double2*>(base + L.Hg);
+    double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
+    double* gap = reinterpret_cast<double*>(base + L.gap);
+    int* flag = reinterpret_cast<int*>(base + L.flag);
+    int* rank = reinterpret_cast<int*>(base + L.rank);
+    const RedProblem P{-1, nullptr, nterms, terms, G};
+    if ((e = random_block(st, m, m, probe_seed, V)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return e;
+    note_launch();
+    beyn_solve_kernel<<<kBeynNodes, kBeynThreads, solve_smem, st>>>(m, P, c_re, c_im, ra, rb, V, P0, P1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t mm = (int64_t)m * m;
+    note_launch();
+    beyn_reduce_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(mm, P0, P1, A0, A1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    beyn_svd_kernel<<<1, kSvdThreads, svd_smem, st>>>(m, A0, A1, c_re, c_im, ra, B, rank, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // eigenvalues of B (FP64 Hessenberg + QR), ranked by Step 2's rule
+    const size_t hsm = sizeof(double2) * ((size_t)m + (size_t)max(m, kRedThreads));
+    note_launch();
+    hessenberg_kernel<double><<<1, kRedThreads, hsm, st>>>(m, B, flag, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t hbytes = packed_elems(m) * sizeof(double2);
+    const size_t fixed = sizeof(double2) * ((size_t)m + kSmallLd * kSmallMax);
+    const int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
+    const size_t qsm = fixed + (use_smem ? hbytes : 0);
+    note_launch();
+    qr_select_kernel<double><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, use_smem, c_re, c_im, ra, rb,
+                                                         lam0, gap, flag, 1, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Newton per kept pair (FP64 factor), fillers for the slots beyond the rank
+    note_launch();
+    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
+                         sizeof(int) * m;
+    newton_kernel<double2><<<m, kNewtonThreads, nsm64, st>>>(
+        m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
     return cudaGetLastError();
 }
 
