@@ -1082,15 +1082,17 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
 }
 
 // ===========================================================================
-// Reduced solver for general T (reading: Beyn's first two contour moments of
-// That^{-1} on the contour scaled by 1.5, 256 trapezoid nodes, an m x m probe,
-// rank by sigma > 1e-12 sigma_1, then Newton per pair; empty slots filled with
-// lambda = c + 1.5 ra and unit vectors)
+// Reduced solver for general T: the first two contour moments of That^{-1}
+// (Beyn's method) on the contour scaled by 1.5, 256 trapezoid nodes, an m x m
+// probe; the moments' pipeline runs in FP32 (node solves, SVD, the small
+// eigenproblem) with the rank cut at the FP32 noise level, and every kept
+// value is then refined by the Newton kernel (FP64 residuals).  Empty slots:
+// lambda = c + 1.5 ra and unit vectors.
 // ===========================================================================
 namespace {
 constexpr int kBeynNodes = 256;
 constexpr double kBeynScale = 1.5;
-constexpr double kBeynRankTol = 1e-12;
+constexpr float kBeynRankTol = 1e-5f;   // FP32 moments: noise near 1e-7 sigma_1
 constexpr int kBeynThreads = 256;
 constexpr int kSvdThreads = 512;
 constexpr int kSvdMaxSweeps = 40;
@@ -1108,35 +1110,37 @@ __device__ __forceinline__ void beyn_node(int k, double c_re, double c_im, doubl
 }
 
 // one warp solves L U y = P b in place (LU and pivots of newton_lu)
-__device__ void lu_solve_warp(int m, const double2* T, const int* piv, double2* b) {
+template <typename LT>
+__device__ void lu_solve_warp(int m, const LT* T, const int* piv, LT* b) {
     const int lane = threadIdx.x & 31;
     if (lane == 0)
         for (int c = 0; c < m; ++c) {
             const int p = piv[c];
-            if (p != c) { double2 t = b[c]; b[c] = b[p]; b[p] = t; }
+            if (p != c) { LT t = b[c]; b[c] = b[p]; b[p] = t; }
         }
     __syncwarp();
     for (int i = 0; i < m; ++i) {
-        const double2 bi = b[i];
+        const LT bi = b[i];
         for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
         __syncwarp();
     }
     for (int i = m - 1; i >= 0; --i) {
         if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
         __syncwarp();
-        const double2 bi = b[i];
+        const LT bi = b[i];
         for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
         __syncwarp();
     }
 }
 
-// CTA k: That(z_k)^{-1} V (FP64 LU), written as w_k Y and w_k z_k Y.
+// CTA k: Y = That(z_k)^{-1} V (FP32 LU: the nodes lie away from the
+// eigenvalues), written as w_k Y and w_k z_k Y.
 __global__ void __launch_bounds__(kBeynThreads) beyn_solve_kernel(
     int m, RedProblem P, double c_re, double c_im, double ra, double rb,
-    const double2* __restrict__ V, double2* __restrict__ P0, double2* __restrict__ P1) {
+    const double2* __restrict__ V, float2* __restrict__ P0, float2* __restrict__ P1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* T = reinterpret_cast<double2*>(smem_raw);
-    double2* Y = T + (int64_t)m * m;
+    float2* T = reinterpret_cast<float2*>(smem_raw);
+    float2* Y = T + (int64_t)m * m;
     int* piv = reinterpret_cast<int*>(Y + (int64_t)m * m);
     __shared__ int s_p;
     const int k = blockIdx.x;
@@ -1144,72 +1148,88 @@ __global__ void __launch_bounds__(kBeynThreads) beyn_solve_kernel(
     beyn_node(k, c_re, c_im, ra, rb, &z, &w);
     newton_build(m, P, z, T);
     const int64_t mm = (int64_t)m * m;
-    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) Y[e] = V[e];
+    for (int64_t e = threadIdx.x; e < mm; e += blockDim.x)
+        Y[e] = make_float2((float)V[e].x, (float)V[e].y);
     __syncthreads();
     newton_lu(m, T, piv, &s_p);
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int col = warp; col < m; col += nw) lu_solve_warp(m, T, piv, Y + (int64_t)col * m);
     __syncthreads();
+    const float2 wf = make_float2((float)w.x, (float)w.y);
     const double2 wz = w * z;
+    const float2 wzf = make_float2((float)wz.x, (float)wz.y);
     for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-        P0[(int64_t)k * mm + e] = w * Y[e];
-        P1[(int64_t)k * mm + e] = wz * Y[e];
+        P0[(int64_t)k * mm + e] = wf * Y[e];
+        P1[(int64_t)k * mm + e] = wzf * Y[e];
     }
 }
 
-// A0 = sum_k P0[k], A1 = sum_k P1[k] in node order (deterministic)
-__global__ void beyn_reduce_kernel(int64_t mm, const double2* __restrict__ P0,
-                                   const double2* __restrict__ P1, double2* __restrict__ A0,
-                                   double2* __restrict__ A1) {
+// A0 = sum_k P0[k], A1 = sum_k P1[k] in node order (deterministic), summed in FP64
+__global__ void beyn_reduce_kernel(int64_t mm, const float2* __restrict__ P0,
+                                   const float2* __restrict__ P1, float2* __restrict__ A0,
+                                   float2* __restrict__ A1) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= mm) return;
     double2 s0 = make_double2(0.0, 0.0), s1 = make_double2(0.0, 0.0);
     for (int k = 0; k < kBeynNodes; ++k) {
-        s0 = s0 + P0[(int64_t)k * mm + e];
-        s1 = s1 + P1[(int64_t)k * mm + e];
+        const float2 a = P0[(int64_t)k * mm + e], b = P1[(int64_t)k * mm + e];
+        s0 = s0 + make_double2(a.x, a.y);
+        s1 = s1 + make_double2(b.x, b.y);
     }
-    A0[e] = s0;
-    A1[e] = s1;
+    A0[e] = make_float2((float)s0.x, (float)s0.y);
+    A1[e] = make_float2((float)s1.x, (float)s1.y);
 }
 
-// One CTA: one-sided Jacobi SVD of A0 (m x m, m even after padding by the
-// caller's choice of m), A0 = U diag(sigma) W^H; then the rank r (sigma >
-// 1e-12 sigma_max), B = U_K^H A1 W_K diag(1/sigma_K) for the kept columns K,
-// written into the top-left r x r of Bfull (m x m); the rest of Bfull is a
-// diagonal far outside the contour (sorted last by Step 2's ranking).
+// One CTA, FP32: one-sided Jacobi SVD A0 = U diag(sigma) W^H (round-robin pair
+// ordering, one warp per pair); rank r (sigma > kBeynRankTol sigma_max); the
+// small matrix B = U_K^H A1 W_K diag(1/sigma_K) of the kept columns K in the
+// top-left r x r of Bfull (m x m); the rest of Bfull is a diagonal far outside
+// the contour, which Step 2's ranking puts last.
 __global__ void __launch_bounds__(kSvdThreads) beyn_svd_kernel(
-    int m, const double2* __restrict__ A0, const double2* __restrict__ A1, double c_re,
-    double c_im, double ra, double2* __restrict__ Bfull, int* __restrict__ rank,
+    int m, const float2* __restrict__ A0, const float2* __restrict__ A1, double c_re,
+    double c_im, double ra, float2* __restrict__ Bfull, int* __restrict__ rank,
     IterStatus* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* M = reinterpret_cast<double2*>(smem_raw);          // m x m, becomes U diag(sigma)
-    double2* W = M + (int64_t)m * m;                              // m x m
-    double* sig = reinterpret_cast<double*>(W + (int64_t)m * m);  // m
+    float2* M = reinterpret_cast<float2*>(smem_raw);             // m x m, becomes U diag(sigma)
+    float2* W = M + (int64_t)m * m;                               // m x m
+    float2* T1 = W + (int64_t)m * m;                              // m x r
+    float* sig = reinterpret_cast<float*>(T1 + (int64_t)m * m);  // m
     int* keep = reinterpret_cast<int*>(sig + m);                  // m
-    __shared__ double s_off;
+    __shared__ float s_off, s_nmax;
     __shared__ int s_r;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int64_t mm = (int64_t)m * m;
     for (int64_t e = tid; e < mm; e += blockDim.x) {
         M[e] = A0[e];
-        W[e] = make_double2((e % m) == (e / m) ? 1.0 : 0.0, 0.0);
+        W[e] = make_float2((e % m) == (e / m) ? 1.0f : 0.0f, 0.0f);
     }
     __syncthreads();
     const int me = (m + 1) & ~1;          // players (a phantom column when m is odd)
     for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
-        if (tid == 0) s_off = 0.0;
+        // largest squared column norm: a column far below it (under the rank
+        // cut) only carries the rounding of the others' updates, so pairs with
+        // such a column are left alone (they would never settle)
+        if (tid == 0) { s_off = 0.0f; s_nmax = 0.0f; }
         __syncthreads();
-        double off = 0.0;
+        for (int j = warp; j < m; j += nw) {
+            float sj = 0.0f;
+            for (int r = lane; r < m; r += 32) sj += cnorm2(M[r + (int64_t)j * m]);
+            for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+            if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&s_nmax), __float_as_uint(sj));
+        }
+        __syncthreads();
+        const float negl = 1e-12f * s_nmax;
+        float off = 0.0f;
         for (int round = 0; round < me - 1; ++round) {
             for (int pr = warp; pr < me / 2; pr += nw) {
                 auto idx = [&](int j) { return j == 0 ? 0 : 1 + (j - 1 + round) % (me - 1); };
                 int p = idx(pr), q = idx(me - 1 - pr);
                 if (p > q) { int t = p; p = q; q = t; }
                 if (q >= m) continue;                                  // phantom
-                double2* ap = M + (int64_t)p * m;
-                double2* aq = M + (int64_t)q * m;
-                double al = 0.0, be = 0.0;
-                double2 ga = make_double2(0.0, 0.0);
+                float2* ap = M + (int64_t)p * m;
+                float2* aq = M + (int64_t)q * m;
+                float al = 0.0f, be = 0.0f;
+                float2 ga = make_float2(0.0f, 0.0f);
                 for (int r = lane; r < m; r += 32) {
                     al += cnorm2(ap[r]);
                     be += cnorm2(aq[r]);
@@ -1221,76 +1241,73 @@ __global__ void __launch_bounds__(kSvdThreads) beyn_svd_kernel(
                     ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
                     ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
                 }
-                const double g = cabs(ga);
-                const double nrm = sqrt(al * be);
-                if (!(g > 1e-15 * nrm) || !(nrm > 0.0)) continue;
-                off = fmax(off, g / nrm);
-                const double2 e = make_double2(ga.x / g, ga.y / g);   // phase of gamma
-                const double zeta = (be - al) / (2.0 * g);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                const float g = cabs(ga);
+                const float nrm = sqrtf(al * be);
+                if (!(g > 1e-7f * nrm) || !(nrm > 0.0f) || fminf(al, be) <= negl) continue;
+                off = fmaxf(off, g / nrm);
+                const float2 e = make_float2(ga.x / g, ga.y / g);       // phase of gamma
+                const float zeta = (be - al) / (2.0f * g);
+                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                const float c = 1.0f / sqrtf(1.0f + t * t), s = c * t;
                 // [a_p, a_q] <- [a_p, a_q] diag(1, conj(e)) [[c, s], [-s, c]]
-                double2* wp = W + (int64_t)p * m;
-                double2* wq = W + (int64_t)q * m;
+                float2* wp = W + (int64_t)p * m;
+                float2* wq = W + (int64_t)q * m;
                 for (int r = lane; r < m; r += 32) {
-                    const double2 x = ap[r], y = cconj(e) * aq[r];
-                    ap[r] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-                    aq[r] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-                    const double2 u = wp[r], v = cconj(e) * wq[r];
-                    wp[r] = make_double2(c * u.x - s * v.x, c * u.y - s * v.y);
-                    wq[r] = make_double2(s * u.x + c * v.x, s * u.y + c * v.y);
+                    const float2 x = ap[r], y = cconj(e) * aq[r];
+                    ap[r] = make_float2(c * x.x - s * y.x, c * x.y - s * y.y);
+                    aq[r] = make_float2(s * x.x + c * y.x, s * x.y + c * y.y);
+                    const float2 u = wp[r], v = cconj(e) * wq[r];
+                    wp[r] = make_float2(c * u.x - s * v.x, c * u.y - s * v.y);
+                    wq[r] = make_float2(s * u.x + c * v.x, s * u.y + c * v.y);
                 }
             }
             __syncthreads();
         }
-        if (lane == 0 && off > 0.0) atomicMax(reinterpret_cast<unsigned long long*>(&s_off),
-                                              (unsigned long long)__double_as_longlong(off));
+        if (lane == 0 && off > 0.0f) atomicMax(reinterpret_cast<unsigned int*>(&s_off), __float_as_uint(off));
         __syncthreads();
-        if (s_off < 1e-14) break;
-        __syncthreads();
+        if (s_off < 2e-7f) break;
         if (sweep == kSvdMaxSweeps - 1 && tid == 0) atomicOr(&status->flags, 1);
+        __syncthreads();
     }
-    // singular values, rank, U columns (M / sigma)
+    // singular values, rank
     for (int j = warp; j < m; j += nw) {
-        double sj = 0.0;
+        float sj = 0.0f;
         for (int r = lane; r < m; r += 32) sj += cnorm2(M[r + (int64_t)j * m]);
         for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
-        if (lane == 0) sig[j] = sqrt(sj);
+        if (lane == 0) sig[j] = sqrtf(sj);
     }
     __syncthreads();
     if (tid == 0) {
-        double smax = 0.0;
-        for (int j = 0; j < m; ++j) smax = fmax(smax, sig[j]);
+        float smax = 0.0f;
+        for (int j = 0; j < m; ++j) smax = fmaxf(smax, sig[j]);
         int r = 0;
         for (int j = 0; j < m; ++j)
-            if (smax > 0.0 && sig[j] > kBeynRankTol * smax) keep[r++] = j;
+            if (smax > 0.0f && sig[j] > kBeynRankTol * smax) keep[r++] = j;
         s_r = r;
         *rank = r;
     }
     __syncthreads();
     const int r = s_r;
     // T1 = A1 W_K (m x r), then B(i, j) = U_K_i^H T1_j / sigma_K_j with U = M / sigma
-    double2* T1 = reinterpret_cast<double2*>(
-        (reinterpret_cast<uintptr_t>(keep + m) + 15) & ~static_cast<uintptr_t>(15));
     for (int e = tid; e < m * r; e += blockDim.x) {
         const int a = e % m, j = e / m;
-        const double2* wj = W + (int64_t)keep[j] * m;
-        double2 t = make_double2(0.0, 0.0);
+        const float2* wj = W + (int64_t)keep[j] * m;
+        float2 t = make_float2(0.0f, 0.0f);
         for (int b = 0; b < m; ++b) t = cfma(A1[a + (int64_t)b * m], wj[b], t);
         T1[e] = t;
     }
     __syncthreads();
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e % m, j = e / m;
-        double2 v = make_double2(0.0, 0.0);
+        float2 v = make_float2(0.0f, 0.0f);
         if (i < r && j < r) {
             const int ki = keep[i], kj = keep[j];
-            const double2* ui = M + (int64_t)ki * m;
-            const double2* tj = T1 + (int64_t)j * m;
+            const float2* ui = M + (int64_t)ki * m;
+            const float2* tj = T1 + (int64_t)j * m;
             for (int a = 0; a < m; ++a) v = cfma(cconj(ui[a]), tj[a], v);
-            v = (1.0 / (sig[ki] * sig[kj])) * v;
+            v = (1.0f / (sig[ki] * sig[kj])) * v;
         } else if (i == j) {
-            v = make_double2(c_re + 10.0 * ra * (1.0 + i), c_im);
+            v = make_float2((float)(c_re + 10.0 * ra * (1.0 + i)), (float)c_im);
         }
         Bfull[e] = v;
     }
@@ -1299,16 +1316,16 @@ __global__ void __launch_bounds__(kSvdThreads) beyn_svd_kernel(
 struct BeynLayout { size_t V, P0, P1, A0, A1, B, Hg, lam0, gap, flag, rank, total; };
 BeynLayout beyn_layout(int m) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t mm = (size_t)m * m * sizeof(double2);
+    const size_t mm = (size_t)m * m;
     BeynLayout L;
     size_t o = 0;
-    L.V = o;    o = al(o + mm);
-    L.P0 = o;   o = al(o + mm * kBeynNodes);
-    L.P1 = o;   o = al(o + mm * kBeynNodes);
-    L.A0 = o;   o = al(o + mm);
-    L.A1 = o;   o = al(o + mm);
-    L.B = o;    o = al(o + mm);
-    L.Hg = o;   o = al(o + packed_elems(m) * sizeof(double2));
+    L.V = o;    o = al(o + mm * sizeof(double2));
+    L.P0 = o;   o = al(o + mm * sizeof(float2) * kBeynNodes);
+    L.P1 = o;   o = al(o + mm * sizeof(float2) * kBeynNodes);
+    L.A0 = o;   o = al(o + mm * sizeof(float2));
+    L.A1 = o;   o = al(o + mm * sizeof(float2));
+    L.B = o;    o = al(o + mm * sizeof(float2));
+    L.Hg = o;   o = al(o + packed_elems(m) * sizeof(float2));
     L.lam0 = o; o = al(o + (size_t)m * sizeof(double2));
     L.gap = o;  o = al(o + (size_t)m * sizeof(double));
     L.flag = o; o = al(o + 16);
@@ -1328,29 +1345,29 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     if (m < 1 || m > beyn_max_m()) return cudaErrorInvalidValue;
     cudaError_t e;
     static bool attr_done = false;
-    const size_t solve_smem = 2 * sizeof(double2) * (size_t)m * m + sizeof(int) * m;
-    const size_t svd_smem = 3 * sizeof(double2) * (size_t)m * m + (sizeof(double) + sizeof(int)) * m + 16;
+    const size_t solve_smem = 2 * sizeof(float2) * (size_t)m * m + sizeof(int) * m;
+    const size_t svd_smem = 3 * sizeof(float2) * (size_t)m * m + (sizeof(float) + sizeof(int)) * m;
     if (!attr_done) {
-        const int cap = 3 * 16 * 64 * 64 + 16 * 64 + 64;
+        const int cap = 3 * 8 * 64 * 64 + 8 * 64 + 64;
         if ((e = cudaFuncSetAttribute(beyn_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       cap)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(beyn_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       cap)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(qr_select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(qr_select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(newton_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024)) != cudaSuccess) return e;
         attr_done = true;
     }
     const BeynLayout L = beyn_layout(m);
     unsigned char* base = static_cast<unsigned char*>(work);
     double2* V = reinterpret_cast<double2*>(base + L.V);
-    double2* P0 = reinterpret_cast<double2*>(base + L.P0);
-    double2* P1 = reinterpret_cast<double2*>(base + L.P1);
-    double2* A0 = reinterpret_cast<double2*>(base + L.A0);
-    double2* A1 = reinterpret_cast<double2*>(base + L.A1);
-    double2* B = reinterpret_cast<double2*>(base + L.B);
-    double2* Hg = reinterpret_cast<double2*>(base + L.Hg);
+    float2* P0 = reinterpret_cast<float2*>(base + L.P0);
+    float2* P1 = reinterpret_cast<float2*>(base + L.P1);
+    float2* A0 = reinterpret_cast<float2*>(base + L.A0);
+    float2* A1 = reinterpret_cast<float2*>(base + L.A1);
+    float2* B = reinterpret_cast<float2*>(base + L.B);
+    float2* Hg = reinterpret_cast<float2*>(base + L.Hg);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
     int* flag = reinterpret_cast<int*>(base + L.flag);
@@ -1368,24 +1385,24 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     note_launch();
     beyn_svd_kernel<<<1, kSvdThreads, svd_smem, st>>>(m, A0, A1, c_re, c_im, ra, B, rank, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // eigenvalues of B (FP64 Hessenberg + QR), ranked by Step 2's rule
-    const size_t hsm = sizeof(double2) * ((size_t)m + (size_t)max(m, kRedThreads));
+    // eigenvalues of B (FP32 Hessenberg + QR), ranked by Step 2's rule
+    const size_t hsm = sizeof(float2) * ((size_t)m + (size_t)max(m, kRedThreads));
     note_launch();
-    hessenberg_kernel<double><<<1, kRedThreads, hsm, st>>>(m, B, flag, 1);
+    hessenberg_kernel<float><<<1, kRedThreads, hsm, st>>>(m, B, flag, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t hbytes = packed_elems(m) * sizeof(double2);
-    const size_t fixed = sizeof(double2) * ((size_t)m + kSmallLd * kSmallMax);
+    const size_t hbytes = packed_elems(m) * sizeof(float2);
+    const size_t fixed = sizeof(float2) * ((size_t)m + kSmallLd * kSmallMax);
     const int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
     const size_t qsm = fixed + (use_smem ? hbytes : 0);
     note_launch();
-    qr_select_kernel<double><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, use_smem, c_re, c_im, ra, rb,
-                                                         lam0, gap, flag, 1, status);
+    qr_select_kernel<float><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, use_smem, c_re, c_im, ra, rb,
+                                                        lam0, gap, flag, 1, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // Newton per kept pair (FP64 factor), fillers for the slots beyond the rank
-    note_launch();
-    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
+    // Newton per kept value (FP32 factor, FP64 residuals), fillers beyond the rank
+    const size_t nsm32 = sizeof(double2) * 4 * m + sizeof(float2) * ((size_t)m * m + 2 * m) +
                          sizeof(int) * m;
-    newton_kernel<double2><<<m, kNewtonThreads, nsm64, st>>>(
+    note_launch();
+    newton_kernel<float2><<<m, kNewtonThreads, nsm32, st>>>(
         m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
     return cudaGetLastError();
 }

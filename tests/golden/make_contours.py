@@ -1,8 +1,10 @@
 """Writes tests/golden/contours.json: the contour of each benchmark workload and
-the eigenvalues it encloses, computed ONLY with the oracle's brute-force tools
-(QZ on the companion pencil for n = 256, shift-invert Arnoldi for n = 4096).
+the eigenvalues it encloses, computed ONLY with the oracle (QZ on the companion
+pencil for n = 256, shift-invert Arnoldi for n = 4096, an oracle solve plus an
+argument-principle count for the n = 2048 delay problem).
 
 Run from the repository root:  python tests/golden/make_contours.py
+(`python tests/golden/make_contours.py delay_n2048` refreshes that entry only.)
 """
 import json
 import os
@@ -13,8 +15,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-from oracle import brute_force_eigs, shift_invert_nearest, winding_count  # noqa: E402
-from workloads import config1_qep, config2_qep  # noqa: E402
+from oracle import (assemble, brute_force_eigs, nlfeast, normalized_radius,  # noqa: E402
+                    shift_invert_nearest, winding_count)
+from workloads import config1_qep, config2_qep, delay_problem, start_block  # noqa: E402
 
 
 def circle_around(lam, target, count):
@@ -29,7 +32,57 @@ def circle_around(lam, target, count):
     return center, float(r), float(gap), inside
 
 
+def adaptive_winding(problem, center, ra, rb, nsamp=512, tol=np.pi / 4, depth=10):
+    """Argument-principle count with the samples refined (bisection in theta)
+    wherever arg det T changes by more than `tol` between neighbours."""
+    def phase(th):
+        z = center + ra * np.cos(th) + 1j * rb * np.sin(th)
+        sign, _ = np.linalg.slogdet(assemble(problem, z))
+        return np.angle(sign)
+
+    def span(ta, pa, tb, pb, d):
+        dp = np.angle(np.exp(1j * (pb - pa)))
+        if abs(dp) <= tol or d == 0:
+            return dp
+        tm = 0.5 * (ta + tb)
+        pm = phase(tm)
+        return span(ta, pa, tm, pm, d - 1) + span(tm, pm, tb, pb, d - 1)
+
+    th = 2.0 * np.pi * np.arange(nsamp + 1) / nsamp
+    ph = [phase(t) for t in th[:-1]]
+    ph.append(ph[0])
+    total = sum(span(th[i], ph[i], th[i + 1], ph[i + 1], depth) for i in range(nsamp))
+    return int(round(total / (2.0 * np.pi)))
+
+
+def delay_contour():
+    """C3: n = 2048 delay problem, ellipse with axes 2:1 at -0.9 (the rightmost
+    cluster), semi-axis chosen at a gap of the normalised radii of the
+    eigenvalues an oracle solve finds on a larger ellipse."""
+    n = 2048
+    p = delay_problem(n, 0)
+    c = -0.9 + 0j
+    big = nlfeast(p, {"center": c, "ra": 0.2, "rb": 0.1, "nc": 24, "rule": "gl"}, 72,
+                  start_block(n, 72, 0), tol=1e-11, maxit=40)
+    assert big["converged"]
+    lam = big["lam"][big["inside"]]
+    rho = 0.2 * normalized_radius(lam, c, 0.2, 0.1)       # in units of ra
+    rs = np.sort(rho)
+    count = 29                                             # largest relative gap near 32
+    ra = 0.5 * (rs[count - 1] + rs[count])
+    gap = (rs[count] - rs[count - 1]) / ra
+    inside = lam[rho < ra]
+    assert len(inside) == count
+    w = adaptive_winding(p, c, ra, ra / 2)
+    assert w == count, (w, count)
+    return p, c, float(ra), float(gap), inside, w
+
+
 def main():
+    path = os.path.join(ROOT, "tests", "golden", "contours.json")
+    if sys.argv[1:] == ["delay_n2048"]:          # refresh that entry only
+        main_delay_only(path)
+        return
     out = {}
     p1 = config1_qep(256, 0)
     lam1 = brute_force_eigs(p1)
@@ -60,7 +113,24 @@ def main():
         "eigs_inside": [[x.real, x.imag] for x in sorted(in2, key=lambda v: (v.real, v.imag))],
         "method": "shift-invert Arnoldi (110 nearest) on the 8192 first companion pencil"}
     print("C2", c2, r2, g2)
-    with open(os.path.join(ROOT, "tests", "golden", "contours.json"), "w") as f:
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    main_delay_only(path)
+
+
+def main_delay_only(path):
+    with open(path) as f:
+        out = json.load(f)
+    _, c3, r3, g3, in3, w3 = delay_contour()
+    out["delay_n2048"] = {
+        "generator": "delay_problem(n=2048, seed=0, tau=1)", "center": [c3.real, c3.imag],
+        "ra": r3, "rb": r3 / 2, "nc": 24, "rule": "gl", "m0": 48, "count": len(in3),
+        "relative_gap": g3, "winding_count": w3,
+        "eigs_inside": [[x.real, x.imag] for x in sorted(in3, key=lambda v: (v.real, v.imag))],
+        "method": "oracle solve on the ellipse (0.2, 0.1) with m0 = 72 to 1e-11; "
+                  "count checked by the argument principle with adaptive sampling"}
+    print("C3", c3, r3, g3, w3)
+    with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
 

@@ -72,3 +72,22 @@ def test_delay_m0_limit(lib):
         s.solve(65, tol=1e-10, maxit=2)
     assert e.value.status == lib.FEAST_NL_EINVAL
     s.close()
+
+
+def test_delay_n2048_matches_stored_reference(lib):
+    """The full-size delay workload: every eigenvalue the stored oracle solve found
+    inside the ellipse (29, argument-principle count 29), to 1e-10."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "contours.json")) as f:
+        w = json.load(f)["delay_n2048"]
+    gold = np.array([complex(*x) for x in w["eigs_inside"]])
+    p = delay_problem(2048, 0)
+    s = lib.FeastNL(p, "fp32_i8")
+    s.set_contour(complex(*w["center"]), w["ra"], w["rb"], w["nc"], w["rule"])
+    st, info = s.solve(w["m0"], tol=1e-10, maxit=40, seed=0)
+    lam, X, rr = s.get_eigpairs(inside_only=True, vectors=False)
+    assert len(lam) == len(gold) == w["winding_count"]
+    assert match_sets(lam, gold) < 1e-10
+    assert np.all(rr <= 1e-10)
+    s.close()
