@@ -189,6 +189,52 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X,
 int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat,
                      int32_t* kmax_out);
 
+/* ---- serving: continuous batching of independent requests ------------------ */
+/* No counterpart in the paper (its parallelism is over nodes and regions on
+ * CPUs).  A request is one whole run of Algorithm 1 (create + set_contour +
+ * solve) on its own handle and stream.  The server keeps up to max_active
+ * requests in flight, admitting them in submission order while the summed
+ * device-memory footprint (feast_nl_request_footprint) stays within
+ * hbm_budget bytes (a request larger than the budget runs when nothing else
+ * does).  Requests in flight overlap on the GPU; each one's arithmetic is the
+ * same as when it runs alone.  The caller keeps the term buffers of a request
+ * alive until the request is done.  All calls are thread-safe. */
+typedef struct feast_nl_server feast_nl_server;
+typedef struct {
+    int64_t n;
+    int32_t nterms;
+    const feast_nl_term* terms;   /* as for feast_nl_create */
+    int32_t precision;
+    double c_re, c_im, ra, rb;    /* contour, as for feast_nl_set_contour */
+    int32_t nc, rule;
+    int32_t m0;                   /* as for feast_nl_solve (start block drawn from seed) */
+    double tol;
+    int32_t maxit;
+    uint64_t seed;
+} feast_nl_request;
+
+/* Estimated device bytes of one request (coefficients, node factors, digit
+ * slices, subspace blocks); host-only; -1 for an invalid request. */
+int64_t feast_nl_request_footprint(const feast_nl_request* r);
+/* 1 <= max_active <= 64 worker threads; hbm_budget > 0 bytes. */
+int feast_nl_server_create(feast_nl_server** s, int32_t max_active, int64_t hbm_budget);
+/* Queues a request; *ticket identifies it.  Errors: EINVAL. */
+int feast_nl_server_submit(feast_nl_server* s, const feast_nl_request* r, uint64_t* ticket);
+/* *state: 0 queued, 1 running, 2 done.  Errors: EINVAL (unknown ticket). */
+int feast_nl_server_poll(feast_nl_server* s, uint64_t ticket, int32_t* state);
+/* Blocks until the request is done; returns the status of its run (as
+ * feast_nl_solve), fills info and the time from submission to completion. */
+int feast_nl_server_wait(feast_nl_server* s, uint64_t ticket, feast_nl_info* info,
+                         double* latency_ms);
+/* Copies the kept Ritz pairs of a done request into host buffers (layouts as
+ * feast_nl_get_eigpairs) and releases the ticket; returns the run's status. */
+int feast_nl_server_fetch(feast_nl_server* s, uint64_t ticket, int32_t capacity, int32_t* m_out,
+                          double* lambda, void* X, double* relres, int32_t inside_only);
+/* Largest number of requests seen in flight at once, requests completed. */
+int feast_nl_server_stats(feast_nl_server* s, int32_t* max_concurrent, int64_t* completed);
+/* Finishes every submitted request, then stops the workers. */
+void feast_nl_server_destroy(feast_nl_server* s);
+
 /* ---- measurement ------------------------------------------------------------ */
 /* Phases of the path, for feast_nl_get_profile. */
 enum feast_nl_phase {

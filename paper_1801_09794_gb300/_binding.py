@@ -32,7 +32,9 @@ EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_n
            "feast_nl_get_nodes", "feast_nl_node_solve", "feast_nl_filter_apply",
            "feast_nl_project", "feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
            "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count",
-           "feast_nl_gram_noalloc"]
+           "feast_nl_gram_noalloc", "feast_nl_request_footprint", "feast_nl_server_create",
+           "feast_nl_server_submit", "feast_nl_server_poll", "feast_nl_server_wait",
+           "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy"]
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
 
@@ -48,6 +50,15 @@ class feast_nl_info(ctypes.Structure):
                 ("n_converged", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("max_relres", ctypes.c_double), ("ms_factor", ctypes.c_double),
                 ("ms_iterate", ctypes.c_double)]
+
+
+class feast_nl_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nterms", ctypes.c_int32),
+                ("terms", ctypes.POINTER(feast_nl_term)), ("precision", ctypes.c_int32),
+                ("c_re", ctypes.c_double), ("c_im", ctypes.c_double), ("ra", ctypes.c_double),
+                ("rb", ctypes.c_double), ("nc", ctypes.c_int32), ("rule", ctypes.c_int32),
+                ("m0", ctypes.c_int32), ("tol", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class FeastError(RuntimeError):
@@ -88,9 +99,20 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_launch_count.argtypes = []
     lib.feast_nl_launch_count.restype = ctypes.c_int64
     lib.feast_nl_gram_noalloc.argtypes = [I64, I32, P, I64, P, P]
+    lib.feast_nl_request_footprint.argtypes = [ctypes.POINTER(feast_nl_request)]
+    lib.feast_nl_request_footprint.restype = I64
+    lib.feast_nl_server_create.argtypes = [ctypes.POINTER(P), I32, I64]
+    lib.feast_nl_server_submit.argtypes = [P, ctypes.POINTER(feast_nl_request), ctypes.POINTER(U64)]
+    lib.feast_nl_server_poll.argtypes = [P, U64, ctypes.POINTER(I32)]
+    lib.feast_nl_server_wait.argtypes = [P, U64, ctypes.POINTER(feast_nl_info), ctypes.POINTER(D)]
+    lib.feast_nl_server_fetch.argtypes = [P, U64, I32, ctypes.POINTER(I32), P, P, P, I32]
+    lib.feast_nl_server_stats.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I64)]
+    lib.feast_nl_server_destroy.argtypes = [P]
+    lib.feast_nl_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
-                        "feast_nl_launch_count"):
+                        "feast_nl_launch_count", "feast_nl_request_footprint",
+                        "feast_nl_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -250,3 +272,107 @@ class FeastNL:
         _check(self.lib.feast_nl_project(self.h, m, Q.ctypes.data, out.ctypes.data, ctypes.byref(k)),
                "feast_nl_project")
         return out[: k.value + 1]
+
+
+def _host_terms(problem, keep):
+    """feast_nl_term array for host-resident coefficients (references kept in `keep`)."""
+    n = int(problem["n"])
+    terms = (feast_nl_term * len(problem["terms"]))()
+    for t, src in zip(terms, problem["terms"]):
+        t.kind = FEAST_NL_POW if src["kind"] == "pow" else FEAST_NL_EXP
+        t.p = int(src.get("p", 0))
+        t.tau = float(src.get("tau", 0.0))
+        sc = complex(src.get("scale", 1.0))
+        t.scale_re, t.scale_im = sc.real, sc.imag
+        t.lda = n
+        t.on_device = 0
+        if src["A"] is None:
+            t.A = None
+        else:
+            A = np.ascontiguousarray(src["A"], dtype=np.complex128)
+            keep.append(A)
+            t.A = A.ctypes.data
+    keep.append(terms)
+    return terms
+
+
+def make_request(problem, center, ra, rb, nc, m0, precision="fp32", rule="gl", tol=1e-10,
+                 maxit=50, seed=0, keep=None):
+    keep = [] if keep is None else keep
+    terms = _host_terms(problem, keep)
+    r = feast_nl_request(n=int(problem["n"]), nterms=len(problem["terms"]), terms=terms,
+                         precision=PRECISIONS[precision], c_re=complex(center).real,
+                         c_im=complex(center).imag, ra=float(ra), rb=float(rb), nc=int(nc),
+                         rule=RULES[rule], m0=int(m0), tol=float(tol), maxit=int(maxit),
+                         seed=int(seed))
+    keep.append(r)
+    return r, keep
+
+
+def request_footprint(problem, nc, m0, precision="fp32"):
+    r, _ = make_request(problem, 0.0, 1.0, 1.0, nc, m0, precision)
+    return int(load_library().feast_nl_request_footprint(ctypes.byref(r)))
+
+
+class Server:
+    """Serving loop of the library: requests run concurrently on their own handles."""
+
+    def __init__(self, max_active=4, hbm_budget=64 << 30):
+        self.lib = load_library()
+        s = ctypes.c_void_p()
+        _check(self.lib.feast_nl_server_create(ctypes.byref(s), int(max_active), int(hbm_budget)),
+               "feast_nl_server_create")
+        self.s = s
+        self._keep = {}
+        self._meta = {}
+
+    def submit(self, problem, center, ra, rb, nc, m0, precision="fp32", rule="gl", tol=1e-10,
+               maxit=50, seed=0):
+        r, keep = make_request(problem, center, ra, rb, nc, m0, precision, rule, tol, maxit, seed)
+        t = ctypes.c_uint64()
+        _check(self.lib.feast_nl_server_submit(self.s, ctypes.byref(r), ctypes.byref(t)),
+               "feast_nl_server_submit")
+        self._keep[t.value] = keep
+        self._meta[t.value] = (int(problem["n"]), int(m0))
+        return t.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int32()
+        _check(self.lib.feast_nl_server_poll(self.s, ticket, ctypes.byref(st)), "feast_nl_server_poll")
+        return st.value
+
+    def wait(self, ticket, allow=(FEAST_NL_OK, FEAST_NL_ENOT_CONVERGED, FEAST_NL_ETOO_MANY)):
+        info = feast_nl_info()
+        lat = ctypes.c_double()
+        st = self.lib.feast_nl_server_wait(self.s, ticket, ctypes.byref(info), ctypes.byref(lat))
+        self._keep.pop(ticket, None)          # the request has run: its inputs may go
+        _check(st, "feast_nl_server_wait", ok=allow)
+        return st, info, lat.value
+
+    def fetch(self, ticket, inside_only=False, vectors=True):
+        n, cap = self._meta.pop(ticket)
+        lam = np.zeros(2 * cap)
+        rr = np.zeros(cap)
+        X = np.zeros((n, cap), dtype=np.complex128) if vectors else None
+        mo = ctypes.c_int32()
+        self.lib.feast_nl_server_fetch(self.s, ticket, cap, ctypes.byref(mo), lam.ctypes.data,
+                                       X.ctypes.data if vectors else None, rr.ctypes.data,
+                                       int(inside_only))
+        m = mo.value
+        return lam[0:2 * m:2] + 1j * lam[1:2 * m:2], (X[:, :m] if vectors else None), rr[:m]
+
+    def stats(self):
+        mc = ctypes.c_int32()
+        done = ctypes.c_int64()
+        _check(self.lib.feast_nl_server_stats(self.s, ctypes.byref(mc), ctypes.byref(done)),
+               "feast_nl_server_stats")
+        return {"max_concurrent": mc.value, "completed": done.value}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.feast_nl_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()

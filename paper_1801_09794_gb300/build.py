@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["k_dense.cu", "k_lu.cu", "k_reduced.cu", "k_ozaki.cu", "k_cgemm_tc.cu", "feast_nl.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "server.cpp"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_common.cuh"), os.path.join(ROOT, "include", "feast_nl.h")]
 LIB = os.path.join(HERE, "libfeast_nl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,7 +44,7 @@ def build(force=False, verbose=False, extra_flags=()):
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(objdir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
 
     def compile_one(pair):
         src, obj = pair
@@ -61,7 +61,7 @@ def build(force=False, verbose=False, extra_flags=()):
             if msg:
                 print(msg)
     if force or _stale(LIB, objs):
-        cmd = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        cmd = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 // ---------------------------------------------------------------------------
 // complex arithmetic on double2 / float2
 // ---------------------------------------------------------------------------

@@ -265,7 +265,7 @@ cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_
                    const float2* B, int64_t ldb, int64_t sB, float2* C, int64_t ldc, int64_t sC,
                    int batch, int* err) {
     constexpr int smem = stage_smem<BN>();
-    static bool attr_set[64] = {};
+    static std::atomic<bool> attr_set[64] = {};   // idempotent setup; atomic for concurrent handles
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

@@ -419,7 +419,7 @@ cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double
 cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, int nterms,
                        const void* Aslices, const double* sigma, const void* Qslices,
                        const double* tau, double2* W, const int* term_slot, int* err) {
-    static bool attr_done = false;
+    static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     const int s = L.s;
     const int smem = kOzStages * s * (kOzM + kOzN) * kOzBK * 2;
     if (!attr_done) {

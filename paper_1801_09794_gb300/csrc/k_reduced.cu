@@ -1041,7 +1041,7 @@ size_t reduced_work_bytes(int m, int kmax) { return red_layout(m, kmax).total; }
 cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat, int m0,
                           double c_re, double c_im, double ra, double rb, void* work,
                           double2* lam, double2* Yred, IterStatus* status) {
-    static bool attr_done = false;
+    static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     cudaError_t e;
     if (!attr_done) {
         if ((e = cudaFuncSetAttribute(qr_select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1344,7 +1344,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                                   double2* Yred, IterStatus* status) {
     if (m < 1 || m > beyn_max_m()) return cudaErrorInvalidValue;
     cudaError_t e;
-    static bool attr_done = false;
+    static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     const size_t solve_smem = 2 * sizeof(float2) * (size_t)m * m + sizeof(int) * m;
     const size_t svd_smem = 3 * sizeof(float2) * (size_t)m * m + (sizeof(float) + sizeof(int)) * m;
     if (!attr_done) {
@@ -1409,7 +1409,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
 
 cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_rel,
                          double2* Rinv, IterStatus* status) {
-    static bool attr_done = false;
+    static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(chol_inverse_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
