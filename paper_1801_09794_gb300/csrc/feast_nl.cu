@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -53,15 +54,38 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream, from the device's default pool): no allocation or release
+// synchronises the device, so handles on different streams (the serving loop)
+// never stall one another.  Every entry point that allocates sets the stream.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+struct AllocScope {
+    cudaStream_t prev;
+    explicit AllocScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~AllocScope() { g_alloc_stream = prev; }
+};
+void keep_pool_memory() {
+    // freed blocks stay in the pool for the next handle instead of going back
+    // to the driver at every synchronisation
+    static std::atomic<bool> done{false};
+    if (done.exchange(true)) return;
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = (uint64_t)32 << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+}
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc((void**)p, count * sizeof(T));
+    return cudaMallocAsync((void**)p, count * sizeof(T), g_alloc_stream);
 }
 template <typename T>
 void dfree(T*& p) {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, g_alloc_stream);
     p = nullptr;
 }
 
@@ -163,7 +187,8 @@ struct feast_nl_handle {
     unsigned char* dBeyn = nullptr; // reduced solver for non-polynomial T (bytes)
     double2* dStage = nullptr;      // n x mcap staging for layout changes
     IterStatus* dStatus = nullptr;
-    IterStatus* hStatus = nullptr;  // pinned
+    // pageable: freeing pinned memory would synchronise the whole device
+    std::unique_ptr<IterStatus> hStatus{new IterStatus()};
     int splits = 1;
     // digit-split products on the tensor cores (precision FEAST_NL_FP32_I8)
     int oz_s = 0;
@@ -231,8 +256,7 @@ void prof_flush(feast_nl_handle* h) {
 
 void release_workspace(feast_nl_handle* h) {
     dfree(h->dQ); dfree(h->dQt); dfree(h->dX); dfree(h->dR); dfree(h->dW);
-    if (h->dY) cudaFree(h->dY);
-    h->dY = nullptr;
+    dfree(h->dY);
     dfree(h->dG); dfree(h->dSplit); dfree(h->dAhat); dfree(h->dYred); dfree(h->dYcat);
     dfree(h->dG2); dfree(h->dRinv); dfree(h->dLam); dfree(h->dCoef); dfree(h->dFsum);
     dfree(h->dNu); dfree(h->dRnorm); dfree(h->dRelres); dfree(h->dRed); dfree(h->dBeyn); dfree(h->dStage);
@@ -252,7 +276,11 @@ int ensure_workspace(feast_nl_handle* h, int m) {
     CK(dalloc(&h->dX, (size_t)n * m));
     CK(dalloc(&h->dR, (size_t)n * m));
     CK(dalloc(&h->dW, (size_t)n * m * T));
-    CK(cudaMalloc(&h->dY, (size_t)nc * n * m * h->lu_elem()));
+    {
+        unsigned char* y = nullptr;
+        CK(dalloc(&y, (size_t)nc * n * m * h->lu_elem()));
+        h->dY = y;
+    }
     // split-K so that the m x (T m) products fill the GPU
     int tiles = ((m + 63) / 64) * ((T * m + 63) / 64);
     h->splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, std::min<int64_t>(n / 64, 304 / tiles)));
@@ -490,6 +518,7 @@ int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_
 
 void feast_nl_destroy(feast_nl_handle* h) {
     if (!h) return;
+    AllocScope as(h->st);
     if (h->st) cudaStreamSynchronize(h->st);
     release_workspace(h);
     dfree(h->dA);
@@ -499,13 +528,12 @@ void feast_nl_destroy(feast_nl_handle* h) {
     dfree(h->dTerms);
     dfree(h->dz);
     dfree(h->dw);
-    if (h->dF) cudaFree(h->dF);
+    dfree(h->dF);
     dfree(h->dpiv);
     dfree(h->dinfo);
     dfree(h->dGather);
     dfree(h->dGcount);
     dfree(h->dStatus);
-    if (h->hStatus) cudaFreeHost(h->hStatus);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -566,12 +594,13 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         if (e != cudaSuccess) return cleanup(fail_cuda(e, "cudaStreamCreate", __LINE__));
         h->own_stream = true;
     }
+    keep_pool_memory();
+    AllocScope as(h->st);
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess)
         return cleanup(fail_cuda(e, "cudaEventCreate", __LINE__));
     if ((e = dalloc(&h->dA, (size_t)h->nA * n * n)) != cudaSuccess ||
         (e = dalloc(&h->dTerms, (size_t)nterms)) != cudaSuccess ||
-        (e = dalloc(&h->dStatus, 1)) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&h->hStatus, sizeof(IterStatus))) != cudaSuccess)
+        (e = dalloc(&h->dStatus, 1)) != cudaSuccess)
         return cleanup(fail_cuda(e, "allocation", __LINE__));
     if (precision == FEAST_NL_FP32_I8 && h->nA > 0 && ozaki_supported(n, kOzakiSlices)) {
         h->oz_s = kOzakiSlices;
@@ -582,8 +611,9 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         if ((e = dalloc(&h->dAsl, (size_t)(L.a_term * h->nA) * ozaki_elem_bytes())) != cudaSuccess ||
             (e = dalloc(&h->dSigma, (size_t)(L.Mpad * h->nA))) != cudaSuccess ||
             (e = dalloc(&h->dSlot, slot.size())) != cudaSuccess ||
-            (e = cudaMemcpy(h->dSlot, slot.data(), sizeof(int) * slot.size(),
-                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            (e = cudaMemcpyAsync(h->dSlot, slot.data(), sizeof(int) * slot.size(),
+                                 cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->st)) != cudaSuccess)
             return cleanup(fail_cuda(e, "allocation of digit slices", __LINE__));
     }
     // copy the coefficients in, transposed to column-major
@@ -666,6 +696,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
                          int32_t nc, int32_t rule) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (!(ra > 0.0) || !(rb > 0.0) || !std::isfinite(c_re) || !std::isfinite(c_im))
         return fail(FEAST_NL_EINVAL, "contour needs finite center and ra, rb > 0");
     if (nc < 1 || nc > 1024) return fail(FEAST_NL_EINVAL, "nc must be in [1, 1024]");
@@ -711,15 +742,18 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
         diagc[j] = make_double2(dsum.real(), dsum.imag());
     }
     // (re)allocate node storage
-    if (h->dF) cudaFree(h->dF);
-    h->dF = nullptr;
+    dfree(h->dF);
     dfree(h->dpiv); dfree(h->dinfo); dfree(h->dz); dfree(h->dw);
     dfree(h->dGather); dfree(h->dGcount);
     h->have_contour = false;
     h->have_result = false;
     release_workspace(h);
     double2 *dcoef = nullptr, *ddiag = nullptr;
-    CK(cudaMalloc(&h->dF, (size_t)nc * n * n * h->lu_elem()));
+    {
+        unsigned char* f = nullptr;
+        CK(dalloc(&f, (size_t)nc * n * n * h->lu_elem()));
+        h->dF = f;
+    }
     CK(dalloc(&h->dpiv, (size_t)nc * n));
     {
         const int nb = h->precision == FEAST_NL_FP64 ? lu_block_size<double2>() : lu_block_size<float2>();
@@ -769,7 +803,7 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     CK(cudaEventRecord(h->ev1, h->st));
     std::vector<int> info(nc);
     CK(cudaMemcpyAsync(info.data(), h->dinfo, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -790,6 +824,7 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
                    const void* X0, feast_nl_info* info) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (info) std::memset(info, 0, sizeof(*info));
     if (!h->have_contour) return fail(FEAST_NL_EINVAL, "set_contour must succeed before solve");
     if (m0 < 1 || m0 > kMaxM0 || m0 > h->n) return fail(FEAST_NL_EINVAL, "m0 must be in [1, min(n, 112)]");
@@ -814,14 +849,15 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     IterStatus stt{};
     for (it = 1; it <= maxit; ++it) {
         CKS(ritz_and_residual(h, m, tol));                      // Steps 1-3
-        CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         stt = *h->hStatus;
         if (trace_enabled()) {
             std::vector<double2> lam(m);
             std::vector<double> rr(m);
-            cudaMemcpy(lam.data(), h->dLam, sizeof(double2) * m, cudaMemcpyDeviceToHost);
-            cudaMemcpy(rr.data(), h->dRelres, sizeof(double) * m, cudaMemcpyDeviceToHost);
+            cudaMemcpyAsync(lam.data(), h->dLam, sizeof(double2) * m, cudaMemcpyDeviceToHost, h->st);
+            cudaMemcpyAsync(rr.data(), h->dRelres, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st);
+            cudaStreamSynchronize(h->st);
             fprintf(stderr, "[feast_nl] it %d inside %d conv %d max_relres %.3e flags %d qr_sweeps %d\n",
                     it, stt.n_inside, stt.n_conv, stt.max_relres, stt.flags, stt.qr_sweeps);
             for (int i = 0; i < m; ++i)
@@ -862,6 +898,7 @@ int feast_nl_get_eigpairs(feast_nl_handle* h, int32_t capacity, int32_t* m_out, 
                           void* X, double* relres, int32_t inside_only) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (!h->have_result) return fail(FEAST_NL_EINVAL, "no solve result");
     if (capacity < 0 || !m_out) return fail(FEAST_NL_EINVAL, "bad capacity or m_out");
     const int m = h->m_last;
@@ -915,6 +952,7 @@ int feast_nl_get_nodes(feast_nl_handle* h, double* z, double* omega) {
 int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R, void* Y) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (!h->have_contour) return fail(FEAST_NL_EINVAL, "no contour");
     if (j < 0 || j >= h->nc || m < 1 || m > kMaxM0 || !R || !Y) return fail(FEAST_NL_EINVAL, "bad node, m or pointer");
     CKS(ensure_workspace(h, std::max(m, h->mcap)));
@@ -941,7 +979,7 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
         CK(to_double<float2>(h->st, n * m, Yb, h->dX));
     }
     h->have_result = false;
-    CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
     return store_block(h, h->dX, m, Y, m);
@@ -951,6 +989,7 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const do
                           void* Q) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (!h->have_contour) return fail(FEAST_NL_EINVAL, "no contour");
     if (m < 1 || m > kMaxM0 || m > h->n || !X || !lambda || !Q) return fail(FEAST_NL_EINVAL, "bad m or pointer");
     CKS(ensure_workspace(h, std::max(m, h->mcap)));
@@ -971,7 +1010,7 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const do
     CK(gemm<double2>(h->st, 0, (int)n, m, T * m, one, h->dW, n, 0, h->dYcat, (int64_t)T * m, 0,
                      zero, h->dR, n, 0, 1));
     CKS(filter_step(h, m));
-    CK(cudaMemcpyAsync(h->hStatus, h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
     if (h->hStatus->flags & 2) return fail(FEAST_NL_ESINGULAR_NODE, "a lambda equals a node");
@@ -981,6 +1020,7 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const do
 int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat, int32_t* kmax_out) {
     g_last_error.clear();
     CKS(validate_handle(h));
+    AllocScope as(h->st);
     if (h->has_exp) return fail(FEAST_NL_EUNSUPPORTED, "projection by powers needs polynomial T");
     if (m < 1 || m > kMaxM0 || m > h->n || !Q || !Ahat) return fail(FEAST_NL_EINVAL, "bad m or pointer");
     CKS(ensure_workspace(h, std::max(m, h->mcap)));
