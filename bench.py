@@ -36,10 +36,11 @@ UNIT = "eigenpairs/s"
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (vector and tensor), nominal
 FP32_SIMT_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 lanes x FMA x 2.07 GHz
 ONE_SM_FP32_TFLOPS_AT_MAX = 128 * 2 * 2.070e9 / 1e12        # one SM
+BEYN_NODES = 256                    # trapezoid nodes of the projected delay problem's moments
 # DRAM bytes per step of the dominant phase's kernels from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by phase; the summary
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, phase); the summary
 # and its command are under profiles/.  Absent: not captured for this code.
-ROOF_TRAFFIC = {"reduced": 6 * 2017536}   # 6 iterations per step; n-independent kernels
+ROOF_TRAFFIC = {("qep_mixed_n4096", "reduced"): 6 * 2017536}   # 6 iterations per step
 TF32_OVER_BF16 = 1.1 / 2.25
 
 WORKLOADS = {
@@ -211,13 +212,15 @@ def phase_work(name, spec, c, iters, nterms_dense):
         return iters * 8.0 * n * m0 * (3 * m0)
     if name == "reduced":
         if spec["gen"] == "delay_problem":
-            return None        # contour-moment solver: latency-bound small solves
+            # contour moments of the projected problem: one m0 x m0 complex LU
+            # plus solves against the m0-column probe at each of the 256 nodes
+            return iters * BEYN_NODES * (8.0 / 3.0 + 8.0) * m0 ** 3
         N = 2 * m0
         return iters * (40.0 / 3.0 + 10.0) * N ** 3
     return None
 
 
-def phase_peak(name, precision, pk, sm_mhz):
+def phase_peak(name, precision, pk, sm_mhz, delay=False):
     clk = (sm_mhz or 2070.0) / 2070.0
     if name in ("lu", "solve") and precision in ("fp32", "fp32_i8"):
         # trailing updates / block substitutions: three TF32 products per FP32
@@ -227,6 +230,9 @@ def phase_peak(name, precision, pk, sm_mhz):
     if name == "apply" and precision == "fp32_i8":
         return (pk["bf16_tflops_sustained"], "tensor",
                 f"BF16 dense, {pk['source']} (sustained figure: timed inside a long step)")
+    if name == "reduced" and delay:
+        return (FP32_SIMT_TFLOPS_AT_MAX * clk, "alu",
+                "FP32 lanes of all 152 SMs (the node solves of the moments span the GPU)")
     if name == "reduced":
         return (ONE_SM_FP32_TFLOPS_AT_MAX * clk, "alu",
                 "FP32 lanes of the one SM the stage runs on (single CTA): 128 x 2 flop x SM clock")
@@ -304,16 +310,16 @@ def run_gpu(args):
         ent = {"ms_per_step": pms / args.steps, "launches_per_step": pl / args.steps}
         if w is not None:
             tf = w / (pms / args.steps / 1e3) / 1e12
-            peak, bound, why = phase_peak(name, spec["precision"], pk, clk.get("sm_mhz"))
+            peak, bound, why = phase_peak(name, spec["precision"], pk, clk.get("sm_mhz"), spec["gen"] == "delay_problem")
             ent.update(tflops=tf, peak_tflops=peak, frac=tf / peak, bound=bound)
         phases[name] = ent
     dom = max(phases, key=lambda k: phases[k]["ms_per_step"])
     d = phases[dom]
     if "tflops" in d:
-        peak, bound, why = phase_peak(dom, spec["precision"], pk, clk.get("sm_mhz"))
+        peak, bound, why = phase_peak(dom, spec["precision"], pk, clk.get("sm_mhz"), spec["gen"] == "delay_problem")
         roof = {"kernel": f"phase '{dom}' (all its launches)", "bound": bound,
                 "achieved": d["tflops"], "peak": peak, "unit": "TFLOP/s", "frac": d["frac"],
-                "traffic": ROOF_TRAFFIC.get(dom), "peak_source": why,
+                "traffic": ROOF_TRAFFIC.get((args.workload, dom)), "peak_source": why,
                 "launches_per_step": d["launches_per_step"],
                 "avg_launch_ms": d["ms_per_step"] / max(d["launches_per_step"], 1)}
     else:
