@@ -51,6 +51,9 @@ WORKLOADS = {
     # non-polynomial T = -lambda I + A0 + A1 exp(-lambda), ellipse 2:1 at -0.9
     "delay_n2048": {"gen": "delay_problem", "n": 2048, "precision": "fp32_i8", "tol": 1e-10,
                     "maxit": 40},
+    # spectrum slicing: random cubic, 64 discs of an 8 x 8 grid, 8 nodes each
+    "slices_n2048": {"gen": "cubic_pep", "n": 2048, "precision": "fp32_i8", "tol": 1e-10,
+                     "maxit": 40, "slices": True},
 }
 
 
@@ -87,7 +90,10 @@ def load_workload(name):
     with open(os.path.join(ROOT, "tests", "golden", "contours.json")) as f:
         c = json.load(f)[name]
     problem = getattr(workloads, spec["gen"])(spec["n"], 0)
-    gold = np.array([complex(*x) for x in c["eigs_inside"]])
+    if spec.get("slices"):
+        gold = [np.array([complex(*x) for x in e]) for e in c["eigs_inside"]]
+    else:
+        gold = np.array([complex(*x) for x in c["eigs_inside"]])
     return spec, c, problem, gold
 
 
@@ -452,6 +458,207 @@ def run_reference(args):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------- slicing
+def slices_good(sl, centers, r, gold, tol=1e-10):
+    good = 0
+    for d, cen in enumerate(centers):
+        lam, _, rr = sl.get_eigpairs(d, inside_only=True, vectors=False)
+        good += count_good(lam, rr, gold[d], cen, r, r, tol)
+    return good
+
+
+def run_slices(args):
+    """Spectrum slicing (Sec. 1 and Sec. 3): one step = assembly and LU of all
+    64 x 8 node matrices in one batch plus every iteration of all 64 contours
+    (graph-replayed), on one stream; eigenpairs counted over all discs."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1801_09794_gb300 as P
+    spec, c, problem, gold = load_workload(args.workload)
+    n, m0, nc = spec["n"], c["m0"], c["nc"]
+    centers = np.array([complex(*x) for x in c["centers"]])
+    r = c["r"]
+    nd = len(centers)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    pdev = {"n": n, "terms": []}
+    for t in problem["terms"]:
+        A = t["A"]
+        pdev["terms"].append(dict(t, A=None if A is None else torch.from_numpy(A).to(dev)))
+    torch.cuda.synchronize()
+    h = P.FeastNL(pdev, spec["precision"], stream=stream.cuda_stream)
+    nterms_dense = sum(1 for t in problem["terms"] if t["A"] is not None)
+
+    def step():
+        sl = P.Slices(h, centers, r, r, nc, c["rule"], stream=stream.cuda_stream)
+        st, infos = sl.solve(m0, tol=spec["tol"], maxit=spec["maxit"], seed=args.seed,
+                             graph=not args.no_graph, allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        return sl, infos
+
+    for _ in range(args.warmup):
+        sl, _ = step()
+        sl.close()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = P.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    goods, fac_ms, it_ms, iters, gl = [], [], [], [], 0
+    for _ in range(args.steps):
+        sl, infos = step()
+        goods.append(slices_good(sl, centers, r, gold))
+        fac_ms.append(infos[0].ms_factor)
+        it_ms.append(infos[0].ms_iterate)
+        iters.append(max(i.iters for i in infos))
+        gl = sl.graph_launches()
+        sl.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = P.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    h.close()
+    barrier()
+    ms_max = reduce_over_ranks(ms, "max", dev)
+    good_total = reduce_over_ranks(min(goods), "sum", dev)
+    value = good_total / (ms_max / 1e3)
+    pk = peaks()
+    # dominant kernel group: the batched node LU (assembly + 512 factorisations,
+    # CUDA events around it on the set's stream)
+    lu_flops = nd * nc * (8.0 / 3.0) * n ** 3
+    fms = statistics.median(fac_ms)
+    ach = lu_flops / (fms / 1e3) / 1e12
+    peak, bound, why = phase_peak("lu", spec["precision"], pk, clk.get("sm_mhz"))
+    roof = {"kernel": f"node assembly + batched LU of {nd * nc} nodes (one launch sequence)",
+            "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": why, "ms_per_launch_sequence": fms}
+    e2e = run_slices_e2e(args, P, torch, problem, spec, c, centers, gold, dev)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64",
+           "data": "synthetic (seeded generator, no dataset)",
+           "config": {"workload": args.workload, "n": n, "T": describe_terms(problem),
+                      "discs": nd, "nc": nc, "node_lus": nd * nc, "m0": m0,
+                      "count_inside": c["count"], "lu_precision": spec["precision"],
+                      "tol": spec["tol"], "iterations_max_over_discs": max(iters),
+                      "eigenpairs_per_step": min(goods), "graph": not args.no_graph,
+                      "graph_kernels_per_iteration": gl,
+                      "ms_factor": fms, "ms_iterate": statistics.median(it_ms),
+                      "l2": "inputs larger than L2 (A_t %.0f MB, node factors %.1f GB)" % (
+                          nterms_dense * n * n * 16 / 1e6, nd * nc * n * n * 8 / 1e9),
+                      "parallelism": f"replicas x{ws}"},
+           "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                      "reasons": clk["reasons"]},
+           "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+           "node_lu_tflops": ach, "peaks": pk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = slices_cpu_sample(args, problem, spec, c, centers, gold, discs=1)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_slices_e2e(args, P, torch, problem, spec, c, centers, gold, dev):
+    """Host buffers in, every kept pair (with vectors) out, per step: handle
+    creation (H2D of the coefficients), the slicing set, its solve."""
+    pinned = {"n": problem["n"], "terms": []}
+    h2d = 0
+    for t in problem["terms"]:
+        A = t["A"]
+        if A is not None:
+            A = torch.from_numpy(A).pin_memory()
+            h2d += A.numel() * 16
+        pinned["terms"].append(dict(t, A=A))
+    steps = max(1, min(args.steps, 3))
+    times, goods, d2h = [], [], 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = P.FeastNL(pinned, spec["precision"])
+        sl = P.Slices(h, centers, c["r"], c["r"], c["nc"], c["rule"])
+        sl.solve(c["m0"], tol=spec["tol"], maxit=spec["maxit"], seed=args.seed,
+                 allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        good, nb = 0, 0
+        for d, cen in enumerate(centers):
+            lam, X, rr = sl.get_eigpairs(d, inside_only=True, vectors=True)
+            good += count_good(lam, rr, gold[d], cen, c["r"], c["r"])
+            nb += X.nbytes + lam.nbytes + rr.nbytes
+        sl.close()
+        h.close()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if i > 0:
+            times.append(t1 - t0)
+            goods.append(good)
+            d2h = nb
+    t = reduce_over_ranks(statistics.median(times), "max", dev)
+    g = reduce_over_ranks(min(goods), "sum", dev)
+    return {"value": g / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "s_per_step": t, "steps": steps}
+
+
+def slices_cpu_sample(args, problem, spec, c, centers, gold, discs=1, first=0):
+    """The FP64 oracle on `discs` of the 64 contours (each: its 8 node LUs and
+    every iteration), as eigenpairs per second of that sample."""
+    from workloads import start_block
+    import oracle as O
+    t_all, good = 0.0, 0
+    iters = []
+    for d in range(first, first + discs):
+        cen = centers[d]
+        X0 = start_block(problem["n"], c["m0"], args.seed + d)
+        t0 = time.perf_counter()
+        res = O.nlfeast(problem, {"center": cen, "ra": c["r"], "rb": c["r"], "nc": c["nc"],
+                                  "rule": c["rule"]}, c["m0"], X0, tol=spec["tol"],
+                        maxit=spec["maxit"])
+        t_all += time.perf_counter() - t0
+        good += count_good(res["lam"], res["relres"], gold[d], cen, c["r"], c["r"])
+        iters.append(res["iters"])
+    return {"value": good / t_all, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{discs} of the {len(centers)} discs (discs {first}..{first + discs - 1}: "
+                      f"{c['nc']} node LUs and {iters} iterations each) in {t_all:.1f} s; "
+                      f"{good} eigenpairs",
+            "seconds": t_all}
+
+
+def run_slices_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    spec, c, problem, gold = load_workload(args.workload)
+    centers = np.array([complex(*x) for x in c["centers"]])
+    w, k = min(args.warmup, 1), min(args.steps, 3)
+    for i in range(w):
+        slices_cpu_sample(args, problem, spec, c, centers, gold, discs=1, first=i)
+    vals, ts, samples = [], [], []
+    for i in range(k):
+        r = slices_cpu_sample(args, problem, spec, c, centers, gold, discs=1, first=w + i)
+        vals.append(r["value"])
+        ts.append(r["seconds"])
+        samples.append(r["sample"])
+    v = statistics.mean(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": k, "warmup": w, "ms_per_step": statistics.mean(ts) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": problem["n"], "discs": len(centers),
+                   "nc": c["nc"], "m0": c["m0"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "; ".join(samples)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 # ---------------------------------------------------------------------------- serving
 def serving_stream(num, seed, rate=200.0, n_lo=128, n_hi=2048):
     """Seeded request stream: Poisson arrivals (rate per second); n log-uniform;
@@ -556,6 +763,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="qep_mixed_n4096")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="slicing workloads: launch each iteration's kernels one by one")
     args = ap.parse_args()
     if args.workload == "serving":
         if args.impl == "reference":
@@ -563,6 +772,11 @@ def main():
                               "on the GPU arm only (the oracle has no server)"}))
             return
         run_serving(args)
+    elif WORKLOADS[args.workload].get("slices"):
+        if args.impl == "reference":
+            run_slices_reference(args)
+        else:
+            run_slices(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

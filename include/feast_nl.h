@@ -235,6 +235,47 @@ int feast_nl_server_stats(feast_nl_server* s, int32_t* max_concurrent, int64_t* 
 /* Finishes every submitted request, then stops the workers. */
 void feast_nl_server_destroy(feast_nl_server* s);
 
+/* ---- spectrum slicing: many contours of one problem ------------------------- */
+/* Sec. 1 and Sec. 3: disjoint regions of the complex plane are solved
+ * independently of one another.  A slicing set holds ndisc such contours of the
+ * problem of a handle, each with nc nodes of the given rule; it assembles and
+ * factors all ndisc * nc node matrices in one batch (create), then runs
+ * Algorithm 1 for every contour at once (solve): each iteration forms A_t Q for
+ * all contours in one product and solves all node systems in one batch, and
+ * the per-contour steps run side by side.  Every contour keeps its pairs from
+ * the iteration at which it passed Step 3 (or from maxit).  The handle must
+ * outlive the set and is only read by it; the set owns its own stream and
+ * device memory (node factors: ndisc * nc * n * n elements in the handle's LU
+ * precision). */
+typedef struct feast_nl_slices feast_nl_slices;
+/* Contour d: center c_re[d] + i c_im[d], semi-axes ra[d], rb[d] (host arrays of
+ * ndisc doubles).  1 <= ndisc <= 4096, 1 <= nc <= 1024, ndisc * nc <= 65535.
+ * stream: cudaStream_t the set's work is ordered on (its per-contour steps fork
+ * from and join back into it), or NULL for a stream of its own.
+ * Errors: EINVAL, ESINGULAR_NODE (an exact zero pivot), ENOMEM, EDEVICE. */
+int feast_nl_slices_create(feast_nl_slices** s, feast_nl_handle* h, int32_t ndisc,
+                           const double* c_re, const double* c_im, const double* ra,
+                           const double* rb, int32_t nc, int32_t rule, void* stream);
+/* Solve flags. */
+#define FEAST_NL_SLICES_NO_GRAPH 1   /* launch every iteration's kernels one by one */
+/* Algorithm 1 on every contour with m0 columns each (arguments as for
+ * feast_nl_solve; the start blocks of all contours are one n x (ndisc m0)
+ * block drawn from seed, contour d taking columns d m0 .. d m0 + m0 - 1).
+ * Unless flags has FEAST_NL_SLICES_NO_GRAPH, the iteration after the first is
+ * captured once as a CUDA graph and replayed.  infos: host array of ndisc
+ * (may be NULL).  Returns OK when every contour converged, else the status of
+ * the first contour that did not (EDEVICE first). */
+int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t maxit,
+                          uint64_t seed, int32_t flags, feast_nl_info* infos);
+/* Contour d's kept pairs, layouts and ordering as feast_nl_get_eigpairs. */
+int feast_nl_slices_get_eigpairs(feast_nl_slices* s, int32_t disc, int32_t capacity,
+                                 int32_t* m_out, double* lambda, void* X, double* relres,
+                                 int32_t inside_only);
+/* Kernel launches in one replay of the last solve's iteration graph (0 when
+ * it ran without a graph). */
+int64_t feast_nl_slices_graph_launches(feast_nl_slices* s);
+void feast_nl_slices_destroy(feast_nl_slices* s);
+
 /* ---- measurement ------------------------------------------------------------ */
 /* Phases of the path, for feast_nl_get_profile. */
 enum feast_nl_phase {

@@ -484,25 +484,41 @@ def winding_count(problem, center, ra, rb, nsamp=2048):
 
 
 def shift_invert_nearest(problem, sigma, nev):
-    """The nev eigenvalues of a quadratic problem nearest sigma, by shift-invert
-    Arnoldi on the first companion pencil, applying L(sigma)^{-1} through one
-    n x n LU of P(sigma) (no 2n x 2n factorisation)."""
+    """The nev eigenvalues of a polynomial problem nearest sigma, by shift-invert
+    Arnoldi on the first companion pencil L(lambda) = L0 + lambda L1 (`companion`),
+    eigenvalue theta = 1/(sigma - lambda) of (L0 + sigma L1)^{-1} L1.  Block
+    elimination of the companion structure reduces each application to one solve
+    with P(sigma) (one n x n LU, no k n x k n factorisation): for b = L1 v
+    (b_0 = A_k v_0, b_j = v_j) and c_{k-1} = 0, c_j = b_{j+1} + sigma c_{j+1},
+        P(sigma) u_{k-1} = b_0 + sigma A_k c_0 + sum_j A_{k-1-j} c_j,
+        u_j = sigma u_{j+1} - b_{j+1}  (j = k-2 .. 0)."""
     from scipy.sparse.linalg import LinearOperator, eigs
-    A0, A1, A2 = _power_matrices(problem)
+    mats = _power_matrices(problem)
+    k = len(mats) - 1
     n = problem["n"]
-    lu = sla.lu_factor(sigma * sigma * A2 + sigma * A1 + A0)
-    S = sigma * A2 + A1
+    Ps = mats[k].copy()
+    for p in range(k - 1, -1, -1):
+        Ps = sigma * Ps + mats[p]
+    lu = sla.lu_factor(Ps)
 
     def op(v):
-        v = np.asarray(v).reshape(-1)
-        v1 = A2 @ v[:n]          # L1 [u1; u2] = [A2 u1; u2]
-        v2 = v[n:]
-        u2 = sla.lu_solve(lu, v1 + S @ v2)
-        u1 = sigma * u2 - v2
-        return np.concatenate([u1, u2])
+        v = np.asarray(v).reshape(k, n)
+        b = [mats[k] @ v[0]] + [v[j] for j in range(1, k)]
+        c = [None] * k
+        c[k - 1] = np.zeros(n, dtype=np.complex128)
+        for j in range(k - 2, -1, -1):
+            c[j] = b[j + 1] + sigma * c[j + 1]
+        rhs = b[0] + sigma * (mats[k] @ c[0])
+        for j in range(k):
+            rhs = rhs + mats[k - 1 - j] @ c[j]
+        u = [None] * k
+        u[k - 1] = sla.lu_solve(lu, rhs)
+        for j in range(k - 2, -1, -1):
+            u[j] = sigma * u[j + 1] - b[j + 1]
+        return np.concatenate(u)
 
-    L = LinearOperator((2 * n, 2 * n), matvec=op, dtype=np.complex128)
+    L = LinearOperator((k * n, k * n), matvec=op, dtype=np.complex128)
     theta = eigs(L, k=nev, which="LM", return_eigenvectors=False, tol=1e-13,
-                 ncv=min(2 * n, max(2 * nev + 1, 160)))
+                 ncv=min(k * n, max(2 * nev + 1, 160)))
     lam = sigma - 1.0 / theta
     return lam[np.argsort(np.abs(lam - sigma))]

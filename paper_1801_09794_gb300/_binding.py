@@ -34,7 +34,10 @@ EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_n
            "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count",
            "feast_nl_gram_noalloc", "feast_nl_request_footprint", "feast_nl_server_create",
            "feast_nl_server_submit", "feast_nl_server_poll", "feast_nl_server_wait",
-           "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy"]
+           "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy",
+           "feast_nl_slices_create", "feast_nl_slices_solve", "feast_nl_slices_get_eigpairs",
+           "feast_nl_slices_graph_launches", "feast_nl_slices_destroy"]
+FEAST_NL_SLICES_NO_GRAPH = 1
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
 
@@ -109,10 +112,18 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_server_stats.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I64)]
     lib.feast_nl_server_destroy.argtypes = [P]
     lib.feast_nl_server_destroy.restype = None
+    lib.feast_nl_slices_create.argtypes = [ctypes.POINTER(P), P, I32, P, P, P, P, I32, I32, P]
+    lib.feast_nl_slices_solve.argtypes = [P, I32, D, I32, U64, I32, P]
+    lib.feast_nl_slices_get_eigpairs.argtypes = [P, I32, I32, ctypes.POINTER(I32), P, P, P, I32]
+    lib.feast_nl_slices_graph_launches.argtypes = [P]
+    lib.feast_nl_slices_graph_launches.restype = I64
+    lib.feast_nl_slices_destroy.argtypes = [P]
+    lib.feast_nl_slices_destroy.restype = None
     for name in EXPORTS:
         if name not in ("feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
                         "feast_nl_launch_count", "feast_nl_request_footprint",
-                        "feast_nl_server_destroy"):
+                        "feast_nl_server_destroy", "feast_nl_slices_graph_launches",
+                        "feast_nl_slices_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -376,3 +387,64 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+class Slices:
+    """Spectrum slicing: many contours of the problem of ``solver`` (a FeastNL)
+    factored in one batch and iterated together."""
+
+    def __init__(self, solver, centers, ra, rb, nc, rule="gl", stream=None):
+        self.lib = load_library()
+        self.solver = solver                  # keeps the handle alive
+        centers = np.asarray(centers, dtype=np.complex128).reshape(-1)
+        self.nd = centers.size
+        cre = np.ascontiguousarray(centers.real)
+        cim = np.ascontiguousarray(centers.imag)
+        ra = np.ascontiguousarray(np.broadcast_to(np.asarray(ra, dtype=np.float64), (self.nd,)))
+        rb = np.ascontiguousarray(np.broadcast_to(np.asarray(rb, dtype=np.float64), (self.nd,)))
+        self.n = solver.n
+        s = ctypes.c_void_p()
+        _check(self.lib.feast_nl_slices_create(ctypes.byref(s), solver.h, self.nd, cre.ctypes.data,
+                                               cim.ctypes.data, ra.ctypes.data, rb.ctypes.data,
+                                               int(nc), RULES[rule],
+                                               None if stream is None else ctypes.c_void_p(int(stream))),
+               "feast_nl_slices_create")
+        self.s = s
+        self.m0 = 0
+
+    def solve(self, m0, tol=1e-10, maxit=50, seed=0, graph=True, allow=()):
+        infos = (feast_nl_info * self.nd)()
+        flags = 0 if graph else FEAST_NL_SLICES_NO_GRAPH
+        st = self.lib.feast_nl_slices_solve(self.s, int(m0), float(tol), int(maxit), int(seed),
+                                            flags, infos)
+        _check(st, "feast_nl_slices_solve", ok=(FEAST_NL_OK,) + tuple(allow))
+        self.m0 = int(m0)
+        return st, list(infos)
+
+    def get_eigpairs(self, disc, inside_only=False, vectors=True):
+        cap = self.m0
+        lam = np.zeros(2 * cap)
+        rr = np.zeros(cap)
+        X = np.zeros((self.n, cap), dtype=np.complex128) if vectors else None
+        mo = ctypes.c_int32()
+        _check(self.lib.feast_nl_slices_get_eigpairs(self.s, int(disc), cap, ctypes.byref(mo),
+                                                     lam.ctypes.data,
+                                                     X.ctypes.data if vectors else None,
+                                                     rr.ctypes.data, int(inside_only)),
+               "feast_nl_slices_get_eigpairs")
+        m = mo.value
+        return lam[0:2 * m:2] + 1j * lam[1:2 * m:2], (X[:, :m] if vectors else None), rr[:m]
+
+    def graph_launches(self):
+        return int(self.lib.feast_nl_slices_graph_launches(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.feast_nl_slices_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

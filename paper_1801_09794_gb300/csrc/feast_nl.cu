@@ -154,6 +154,66 @@ namespace {
 constexpr uint64_t kBeynProbeSeed = 0x6265796e2d70726full;
 }  // namespace
 
+
+namespace {
+
+// Quadrature nodes of nd contours (nd * nc nodes, contour-major) and the LU
+// factors of T at every node.  A handle holds one contour; a spectrum-slicing
+// set holds many, factored in one batch.
+struct NodeSet {
+    int nd = 0, nc = 0, rule = 0;
+    std::vector<double> c_re, c_im, ra, rb;   // per contour
+    std::vector<zd> z, w;                      // nd * nc
+    double2* dz = nullptr;
+    double2* dw = nullptr;
+    void* dF = nullptr;             // nd * nc factors of n x n, LU precision
+    int* dpiv = nullptr;
+    int* dinfo = nullptr;
+    int2* dGather = nullptr;        // per node and panel: row interchanges as a gather list
+    int* dGcount = nullptr;
+    double ms_factor = 0.0;
+    bool ready = false;
+};
+
+// Subspace workspace of nd contours with m columns each; every per-contour
+// block is contiguous, contour d at offset d * (block size).
+struct Work {
+    int nd = 0, mcap = 0, nc = 0;
+    double2 *Q = nullptr, *Qt = nullptr, *X = nullptr, *R = nullptr;
+    double2* W = nullptr;           // per contour: [A_0 Q | .. | A_{T-1} Q], n x T m
+    void* Y = nullptr;              // per contour: nc node right-hand sides, LU precision
+    double2 *G = nullptr, *Split = nullptr, *Ahat = nullptr, *Yred = nullptr, *Ycat = nullptr;
+    double2 *G2 = nullptr, *Rinv = nullptr, *Lam = nullptr, *Coef = nullptr, *Fsum = nullptr;
+    double *Nu = nullptr, *Rnorm = nullptr, *Relres = nullptr;
+    unsigned char* Red = nullptr;   // reduced-problem workspace (bytes)
+    size_t red_bytes = 0;
+    unsigned char* Beyn = nullptr;  // reduced solver for non-polynomial T (bytes)
+    size_t beyn_bytes = 0;
+    double2* Stage = nullptr;       // n x (nd mcap) staging for layout changes
+    IterStatus* Status = nullptr;   // one per contour
+    int splits = 1;
+    unsigned char* Qsl = nullptr;   // digit slices of Q' (all contours at once)
+    double* Tau = nullptr;          // their column scales
+};
+
+// One contour's view of a NodeSet and a Work, with the stream its per-contour
+// steps run on.
+struct Disc {
+    int d = 0, m = 0, nc = 0;
+    cudaStream_t st = nullptr;
+    bool prof = false;
+    double c_re = 0, c_im = 0, ra = 1, rb = 1;
+    const double2 *z = nullptr, *w = nullptr;
+    double2 *Q, *Qt, *X, *R, *W, *G, *Split, *Ahat, *Yred, *Ycat, *G2, *Rinv, *Lam, *Coef, *Fsum;
+    double *Nu, *Rnorm, *Relres;
+    unsigned char *Red, *Beyn;
+    void* Y;
+    IterStatus* status;
+    int splits;
+};
+
+}  // namespace
+
 struct feast_nl_handle {
     int64_t n = 0;
     int nterms = 0, nA = 0, kmax = 0, precision = 0;
@@ -163,40 +223,15 @@ struct feast_nl_handle {
     std::vector<HostTerm> terms;
     double2* dA = nullptr;          // nA x n x n, column-major
     TermDev* dTerms = nullptr;
-    // contour
-    bool have_contour = false;
-    double c_re = 0, c_im = 0, ra = 1, rb = 1;
-    int nc = 0, rule = 0;
-    std::vector<zd> z, w;
-    double2* dz = nullptr;
-    double2* dw = nullptr;
-    void* dF = nullptr;             // nc x n x n in LU precision
-    int* dpiv = nullptr;
-    int* dinfo = nullptr;
-    int2* dGather = nullptr;        // per node and panel: row interchanges as a gather list
-    int* dGcount = nullptr;
-    double ms_factor = 0.0;
-    // subspace workspace (sized for mcap columns)
-    int mcap = 0;
-    double2 *dQ = nullptr, *dQt = nullptr, *dX = nullptr, *dR = nullptr, *dW = nullptr;
-    void* dY = nullptr;
-    double2 *dG = nullptr, *dSplit = nullptr, *dAhat = nullptr, *dYred = nullptr, *dYcat = nullptr;
-    double2 *dG2 = nullptr, *dRinv = nullptr, *dLam = nullptr, *dCoef = nullptr, *dFsum = nullptr;
-    double *dNu = nullptr, *dRnorm = nullptr, *dRelres = nullptr;
-    unsigned char* dRed = nullptr;  // reduced-problem workspace (bytes)
-    unsigned char* dBeyn = nullptr; // reduced solver for non-polynomial T (bytes)
-    double2* dStage = nullptr;      // n x mcap staging for layout changes
-    IterStatus* dStatus = nullptr;
+    NodeSet ns;                     // the handle's contour
+    Work wk;                        // its subspace workspace
+    IterStatus* dStatus = nullptr;  // status of create / set_contour / stage calls
     // pageable: freeing pinned memory would synchronise the whole device
     std::unique_ptr<IterStatus> hStatus{new IterStatus()};
-    int splits = 1;
     // digit-split products on the tensor cores (precision FEAST_NL_FP32_I8)
     int oz_s = 0;
-    OzakiLayout oz;                 // layout for mcap columns
     unsigned char* dAsl = nullptr;  // nA x s slices of A'
     double* dSigma = nullptr;       // nA x Mpad row scales
-    unsigned char* dQsl = nullptr;  // s slices of Q'
-    double* dTau = nullptr;         // column scales
     int* dSlot = nullptr;           // dense index -> term index
     // results of the last solve
     bool have_result = false;
@@ -214,7 +249,34 @@ struct feast_nl_handle {
     size_t lu_elem() const { return precision == FEAST_NL_FP64 ? sizeof(double2) : sizeof(float2); }
 };
 
+// Spectrum slicing: nd contours of one problem solved together.  All nd * nc
+// node matrices are assembled and factored in one batch; every iteration runs
+// the wide steps (A_t Q for all contours, the node solves of all nodes) as
+// single launches and the per-contour steps on parallel streams, captured
+// once per solve as a CUDA graph and replayed.
+struct feast_nl_slices {
+    feast_nl_handle* h = nullptr;   // the problem (not owned)
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    NodeSet ns;
+    Work wk;
+    IterStatus* dStatus = nullptr;  // factorisation status
+    std::vector<cudaStream_t> side; // one per contour (at most kMaxSide)
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+    // results: each contour's pairs at its convergence (or at maxit)
+    int m_last = 0;
+    double2* dLamRes = nullptr;
+    double* dRelresRes = nullptr;
+    double2* dXRes = nullptr;
+    std::vector<feast_nl_info> info;
+    bool have_result = false;
+    int64_t graph_launches = 0;     // kernels per replay of the iteration graph
+};
+
 namespace {
+
+constexpr int kMaxSide = 128;
 
 cudaEvent_t prof_event(feast_nl_handle* h) {
     if (h->pool_used == h->pool.size()) {
@@ -224,12 +286,13 @@ cudaEvent_t prof_event(feast_nl_handle* h) {
     }
     return h->pool[h->pool_used++];
 }
-// Scoped device-time measurement of one phase (no-op unless profiling is on).
+// Scoped device-time measurement of one phase on the handle's stream (no-op
+// unless profiling is on and the caller asks for it).
 struct Phase {
     feast_nl_handle* h;
     int idx = -1;
-    Phase(feast_nl_handle* hh, int phase) : h(hh) {
-        if (!h->prof) return;
+    Phase(feast_nl_handle* hh, int phase, bool on = true) : h(hh) {
+        if (!on || !h->prof) return;
         cudaEvent_t a = prof_event(h), b = prof_event(h);
         if (!a || !b) return;
         cudaEventRecord(a, h->st);
@@ -254,205 +317,467 @@ void prof_flush(feast_nl_handle* h) {
     h->pool_used = 0;
 }
 
-void release_workspace(feast_nl_handle* h) {
-    dfree(h->dQ); dfree(h->dQt); dfree(h->dX); dfree(h->dR); dfree(h->dW);
-    dfree(h->dY);
-    dfree(h->dG); dfree(h->dSplit); dfree(h->dAhat); dfree(h->dYred); dfree(h->dYcat);
-    dfree(h->dG2); dfree(h->dRinv); dfree(h->dLam); dfree(h->dCoef); dfree(h->dFsum);
-    dfree(h->dNu); dfree(h->dRnorm); dfree(h->dRelres); dfree(h->dRed); dfree(h->dBeyn); dfree(h->dStage);
-    dfree(h->dQsl); dfree(h->dTau);
-    h->mcap = 0;
-    h->have_result = false;
+size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
+
+void free_nodes(NodeSet& ns) {
+    dfree(ns.dF);
+    dfree(ns.dpiv); dfree(ns.dinfo); dfree(ns.dz); dfree(ns.dw);
+    dfree(ns.dGather); dfree(ns.dGcount);
+    ns.ready = false;
+}
+
+void free_work(Work& wk) {
+    dfree(wk.Q); dfree(wk.Qt); dfree(wk.X); dfree(wk.R); dfree(wk.W); dfree(wk.Y);
+    dfree(wk.G); dfree(wk.Split); dfree(wk.Ahat); dfree(wk.Yred); dfree(wk.Ycat);
+    dfree(wk.G2); dfree(wk.Rinv); dfree(wk.Lam); dfree(wk.Coef); dfree(wk.Fsum);
+    dfree(wk.Nu); dfree(wk.Rnorm); dfree(wk.Relres); dfree(wk.Red); dfree(wk.Beyn); dfree(wk.Stage);
+    dfree(wk.Status); dfree(wk.Qsl); dfree(wk.Tau);
+    wk.nd = 0;
+    wk.mcap = 0;
+}
+
+// Workspace for nd contours of m columns and nc nodes each.
+int alloc_work(const feast_nl_handle* h, Work& wk, int nd, int nc, int m) {
+    free_work(wk);
+    const int64_t n = h->n;
+    const int T = h->nterms;
+    nc = std::max(nc, 1);
+    const int64_t M = (int64_t)nd * m;
+    CK(dalloc(&wk.Q, (size_t)(n * M)));
+    CK(dalloc(&wk.Qt, (size_t)(n * M)));
+    CK(dalloc(&wk.X, (size_t)(n * M)));
+    CK(dalloc(&wk.R, (size_t)(n * M)));
+    CK(dalloc(&wk.W, (size_t)(n * M * T)));
+    CK(dalloc(&wk.Stage, (size_t)(n * M)));
+    {
+        unsigned char* y = nullptr;
+        CK(dalloc(&y, (size_t)nc * n * M * h->lu_elem()));
+        wk.Y = y;
+    }
+    // split-K so that the m x (T m) products fill the GPU
+    const int tiles = ((m + 63) / 64) * ((T * m + 63) / 64);
+    wk.splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, std::min<int64_t>(n / 64, 304 / tiles)));
+    const size_t mm = (size_t)m * m;
+    CK(dalloc(&wk.G, nd * mm * T));
+    CK(dalloc(&wk.Split, nd * (wk.splits * mm * T + 16)));
+    CK(dalloc(&wk.Ahat, nd * (h->kmax + 1) * mm));
+    CK(dalloc(&wk.Yred, nd * mm));
+    CK(dalloc(&wk.Ycat, nd * mm * T));
+    CK(dalloc(&wk.G2, nd * mm));
+    CK(dalloc(&wk.Rinv, nd * mm));
+    CK(dalloc(&wk.Lam, (size_t)M));
+    CK(dalloc(&wk.Coef, (size_t)M * nc));
+    CK(dalloc(&wk.Fsum, (size_t)M));
+    CK(dalloc(&wk.Nu, (size_t)M));
+    CK(dalloc(&wk.Rnorm, (size_t)M));
+    CK(dalloc(&wk.Relres, (size_t)M));
+    wk.red_bytes = round_up(reduced_work_bytes(m, std::max(h->kmax, 1)), 256);
+    CK(dalloc(&wk.Red, nd * wk.red_bytes));
+    wk.beyn_bytes = 0;
+    if (h->has_exp && m <= beyn_max_m()) {
+        wk.beyn_bytes = round_up(beyn_work_bytes(m), 256);
+        CK(dalloc(&wk.Beyn, nd * wk.beyn_bytes));
+    }
+    CK(dalloc(&wk.Status, (size_t)nd));
+    if (h->oz_s > 0) {
+        const OzakiLayout L = ozaki_layout(n, (int)M, h->oz_s);
+        const size_t qb = (size_t)(L.b_slice * h->oz_s) * ozaki_elem_bytes();
+        CK(dalloc(&wk.Qsl, qb));
+        CK(cudaMemsetAsync(wk.Qsl, 0, qb, g_alloc_stream));
+        CK(dalloc(&wk.Tau, (size_t)M));
+    }
+    wk.nd = nd;
+    wk.mcap = m;
+    wk.nc = nc;
+    return FEAST_NL_OK;
+}
+
+// Contour d's blocks when every contour has m columns.
+Disc disc_view(const feast_nl_handle* h, const NodeSet& ns, const Work& wk, int d, int m,
+               cudaStream_t st, bool prof) {
+    const int64_t n = h->n;
+    const int T = h->nterms;
+    const size_t mm = (size_t)m * m;
+    Disc D;
+    D.d = d;
+    D.m = m;
+    D.nc = ns.nc;
+    D.st = st;
+    D.prof = prof;
+    if (d < ns.nd) {
+        D.c_re = ns.c_re[d]; D.c_im = ns.c_im[d]; D.ra = ns.ra[d]; D.rb = ns.rb[d];
+        D.z = ns.dz + (int64_t)d * ns.nc;
+        D.w = ns.dw + (int64_t)d * ns.nc;
+    }
+    const int64_t nm = n * m;
+    D.Q = wk.Q + d * nm;
+    D.Qt = wk.Qt + d * nm;
+    D.X = wk.X + d * nm;
+    D.R = wk.R + d * nm;
+    D.W = wk.W + d * nm * T;
+    D.Y = static_cast<unsigned char*>(wk.Y) + (size_t)d * wk.nc * nm * h->lu_elem();
+    D.G = wk.G + d * mm * T;
+    D.Split = wk.Split + d * (wk.splits * mm * T + 16);
+    D.Ahat = wk.Ahat + d * (h->kmax + 1) * mm;
+    D.Yred = wk.Yred + d * mm;
+    D.Ycat = wk.Ycat + d * mm * T;
+    D.G2 = wk.G2 + d * mm;
+    D.Rinv = wk.Rinv + d * mm;
+    D.Lam = wk.Lam + (int64_t)d * m;
+    D.Coef = wk.Coef + (int64_t)d * m * wk.nc;
+    D.Fsum = wk.Fsum + (int64_t)d * m;
+    D.Nu = wk.Nu + (int64_t)d * m;
+    D.Rnorm = wk.Rnorm + (int64_t)d * m;
+    D.Relres = wk.Relres + (int64_t)d * m;
+    D.Red = wk.Red + d * wk.red_bytes;
+    D.Beyn = wk.Beyn ? wk.Beyn + d * wk.beyn_bytes : nullptr;
+    D.status = wk.Status + d;
+    D.splits = wk.splits;
+    return D;
 }
 
 int ensure_workspace(feast_nl_handle* h, int m) {
-    if (m <= h->mcap && (h->dY || h->nc == 0)) return FEAST_NL_OK;
-    release_workspace(h);
-    const int64_t n = h->n;
-    const int T = h->nterms;
-    const int nc = std::max(h->nc, 1);
-    CK(dalloc(&h->dQ, (size_t)n * m));
-    CK(dalloc(&h->dQt, (size_t)n * m));
-    CK(dalloc(&h->dX, (size_t)n * m));
-    CK(dalloc(&h->dR, (size_t)n * m));
-    CK(dalloc(&h->dW, (size_t)n * m * T));
-    {
-        unsigned char* y = nullptr;
-        CK(dalloc(&y, (size_t)nc * n * m * h->lu_elem()));
-        h->dY = y;
-    }
-    // split-K so that the m x (T m) products fill the GPU
-    int tiles = ((m + 63) / 64) * ((T * m + 63) / 64);
-    h->splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, std::min<int64_t>(n / 64, 304 / tiles)));
-    CK(dalloc(&h->dG, (size_t)m * m * T));
-    CK(dalloc(&h->dSplit, (size_t)h->splits * m * m * T + 16));
-    CK(dalloc(&h->dAhat, (size_t)(h->kmax + 1) * m * m));
-    CK(dalloc(&h->dYred, (size_t)m * m));
-    CK(dalloc(&h->dYcat, (size_t)T * m * m));
-    CK(dalloc(&h->dG2, (size_t)m * m));
-    CK(dalloc(&h->dRinv, (size_t)m * m));
-    CK(dalloc(&h->dLam, (size_t)m));
-    CK(dalloc(&h->dCoef, (size_t)nc * m));
-    CK(dalloc(&h->dFsum, (size_t)m));
-    CK(dalloc(&h->dNu, (size_t)m));
-    CK(dalloc(&h->dRnorm, (size_t)m));
-    CK(dalloc(&h->dRelres, (size_t)m));
-    CK(dalloc(&h->dRed, reduced_work_bytes(m, std::max(h->kmax, 1))));
-    if (h->has_exp && m <= beyn_max_m()) CK(dalloc(&h->dBeyn, beyn_work_bytes(m)));
-    CK(dalloc(&h->dStage, (size_t)n * m));
-    if (h->oz_s > 0) {
-        h->oz = ozaki_layout(n, m, h->oz_s);
-        const size_t qb = (size_t)(h->oz.b_slice * h->oz_s) * ozaki_elem_bytes();
-        CK(dalloc(&h->dQsl, qb));
-        CK(cudaMemsetAsync(h->dQsl, 0, qb, h->st));
-        CK(dalloc(&h->dTau, (size_t)m));
-    }
-    h->mcap = m;
-    return FEAST_NL_OK;
+    if (m <= h->wk.mcap && h->wk.nd == 1 && h->wk.nc == std::max(h->ns.nc, 1)) return FEAST_NL_OK;
+    h->have_result = false;
+    return alloc_work(h, h->wk, 1, h->ns.nc, m);
 }
 
 // Copy an n x m complex128 row-major block (host or device) into column-major dst.
-int load_block(feast_nl_handle* h, const void* src, int m, double2* dst) {
+int load_block(const feast_nl_handle* h, cudaStream_t st, double2* stage, const void* src, int m,
+               double2* dst) {
     const size_t bytes = (size_t)h->n * m * sizeof(double2);
     const double2* s = static_cast<const double2*>(src);
     if (!is_device_ptr(src)) {
-        CK(cudaMemcpyAsync(h->dStage, src, bytes, cudaMemcpyHostToDevice, h->st));
-        s = h->dStage;
+        CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
+        s = stage;
     }
-    CK(transpose_rowmajor_to_colmajor(h->st, h->n, m, s, m, dst, h->n));
+    CK(transpose_rowmajor_to_colmajor(st, h->n, m, s, m, dst, h->n));
     return FEAST_NL_OK;
 }
 // Copy column-major src (n x m, ld n) out as row-major with row stride ldd (host or device).
-int store_block(feast_nl_handle* h, const double2* src, int m, void* dst, int64_t ldd) {
+int store_block(const feast_nl_handle* h, cudaStream_t st, double2* stage, const double2* src,
+                int m, void* dst, int64_t ldd) {
     if (is_device_ptr(dst)) {
-        CK(transpose_colmajor_to_rowmajor(h->st, h->n, m, src, h->n,
-                                          static_cast<double2*>(dst), ldd));
-        CK(cudaStreamSynchronize(h->st));
+        CK(transpose_colmajor_to_rowmajor(st, h->n, m, src, h->n, static_cast<double2*>(dst), ldd));
+        CK(cudaStreamSynchronize(st));
         return FEAST_NL_OK;
     }
-    CK(transpose_colmajor_to_rowmajor(h->st, h->n, m, src, h->n, h->dStage, m));
-    CK(cudaMemcpy2DAsync(dst, ldd * sizeof(double2), h->dStage, m * sizeof(double2),
-                         m * sizeof(double2), h->n, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(transpose_colmajor_to_rowmajor(st, h->n, m, src, h->n, stage, m));
+    CK(cudaMemcpy2DAsync(dst, ldd * sizeof(double2), stage, m * sizeof(double2),
+                         m * sizeof(double2), h->n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return FEAST_NL_OK;
 }
 
-// Columns of the stacked product W = [A_0 Q, ..., A_{T-1} Q] (identity terms copy Q).
-int apply_terms(feast_nl_handle* h, const double2* Q, int m, double2* W) {
+// W = [A_0 Q_d, .., A_{T-1} Q_d] for the nd contours' blocks Q_d (n x m each,
+// contiguous) at once: one product over all nd m columns (identity terms copy Q).
+int apply_terms(const feast_nl_handle* h, const Work& wk, int nd, int m, const double2* Q,
+                double2* W, cudaStream_t st, int* err) {
     const int64_t n = h->n;
+    const int T = h->nterms;
+    const int M = nd * m;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     if (h->oz_s > 0 && h->nA > 0) {
-        // all dense terms at once on the INT8 tensor cores
-        const OzakiLayout L = ozaki_layout(n, m, h->oz_s);
-        CK(ozaki_split_Q(h->st, n, m, h->oz_s, Q, h->dTau, h->dQsl, L));
-        CK(ozaki_gemm(h->st, n, m, L, h->nA, h->dAsl, h->dSigma, h->dQsl, h->dTau, W, h->dSlot,
-                      &h->dStatus->flags));
-        CK(copy_identity_terms(h->st, n, m, h->nterms, h->dTerms, Q, W));
+        // all dense terms and all contours at once on the BF16 tensor cores
+        const OzakiLayout L = ozaki_layout(n, M, h->oz_s);
+        CK(ozaki_split_Q(st, n, M, h->oz_s, Q, wk.Tau, wk.Qsl, L));
+        CK(ozaki_gemm(st, n, M, m, T, L, h->nA, h->dAsl, h->dSigma, wk.Qsl, wk.Tau, W, h->dSlot, err));
+        CK(copy_identity_terms(st, n, m, nd, T, h->dTerms, Q, W));
         return FEAST_NL_OK;
     }
-    for (int t = 0; t < h->nterms; ++t) {
+    for (int t = 0; t < T; ++t) {
         const HostTerm& ht = h->terms[t];
         if (ht.aidx < 0) continue;
-        CK(gemm<double2>(h->st, 0, (int)n, m, (int)n, one, h->dA + (int64_t)ht.aidx * n * n, n, 0,
-                         Q, n, 0, zero, W + (int64_t)t * n * m, n, 0, 1));
+        CK(gemm<double2>(st, 0, (int)n, m, (int)n, one, h->dA + (int64_t)ht.aidx * n * n, n, 0, Q, n,
+                         n * m, zero, W + (int64_t)t * n * m, n, (int64_t)T * n * m, nd));
     }
-    CK(copy_identity_terms(h->st, n, m, h->nterms, h->dTerms, Q, W));
+    CK(copy_identity_terms(st, n, m, nd, T, h->dTerms, Q, W));
     return FEAST_NL_OK;
 }
 
 // Q <- Q R^{-1} twice (CholQR with a small diagonal shift), columns pre-equilibrated.
 // Only the product Q R^{-1} has to be exact to FP64 rounding (it must keep the
 // span); the Gram matrix feeds an FP32 Cholesky, so it is formed from an FP32
-// copy of Q (held in the node right-hand-side buffer, free at this point).
-int orthonormalize(feast_nl_handle* h, int m) {
-    Phase ph(h, FEAST_NL_PH_ORTH);
+// copy of Q (held in the contour's node right-hand-side buffer, free at this
+// point).  D is a copy: its Q / Qt swaps stay local, and after the two passes
+// the result is back in the caller's Q.
+int orthonormalize(feast_nl_handle* h, Disc D) {
+    Phase ph(h, FEAST_NL_PH_ORTH, D.prof);
     const int64_t n = h->n;
+    const int m = D.m;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-    float2* Q32 = static_cast<float2*>(h->dY);
-    if (!Q32) return fail(FEAST_NL_EINVAL, "no contour: node buffers not allocated");
-    CK(column_norms(h->st, n, m, h->dQ, n, h->dNu));
-    CK(ritz_scale(h->st, n, m, 0, h->dTerms, h->dLam, h->dNu, h->dQ, h->dYred, h->dYcat));
+    float2* Q32 = static_cast<float2*>(D.Y);
+    CK(column_norms(D.st, n, m, D.Q, n, D.Nu));
+    CK(ritz_scale(D.st, n, m, 0, h->dTerms, D.Lam, D.Nu, D.Q, D.Yred, D.Ycat));
     for (int pass = 0; pass < 2; ++pass) {
-        CK(to_float(h->st, n * m, h->dQ, Q32));
-        CK(gram_f32(h->st, m, (int)n, Q32, n, h->dG2, m, reinterpret_cast<float2*>(h->dSplit),
-                    h->splits));
-        CK(chol_inverse(h->st, m, h->dG2, 1e-6, h->dRinv, h->dStatus));
-        CK(gemm<double2>(h->st, 0, (int)n, m, m, one, h->dQ, n, 0, h->dRinv, m, 0, zero, h->dQt, n,
-                         0, 1));
-        std::swap(h->dQ, h->dQt);
+        CK(to_float(D.st, n * m, D.Q, Q32));
+        CK(gram_f32(D.st, m, (int)n, Q32, n, D.G2, m, reinterpret_cast<float2*>(D.Split), D.splits));
+        CK(chol_inverse(D.st, m, D.G2, 1e-6, D.Rinv, D.status));
+        CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Rinv, m, 0, zero, D.Qt, n, 0, 1));
+        std::swap(D.Q, D.Qt);
     }
     return FEAST_NL_OK;
 }
 
-// Rayleigh-Ritz (Steps 1-2) and the block residual (Step 3) for the current Q.
-int ritz_and_residual(feast_nl_handle* h, int m, double tol) {
+// Rayleigh-Ritz (Steps 1-2) and the block residual (Step 3) for contour D, with
+// W = [A_t Q] already formed.
+int ritz_and_residual(feast_nl_handle* h, const Disc& D, double tol) {
     const int64_t n = h->n;
     const int T = h->nterms;
+    const int m = D.m;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     {
-        Phase ph(h, FEAST_NL_PH_APPLY);
-        CKS(apply_terms(h, h->dQ, m, h->dW));
+        Phase ph(h, FEAST_NL_PH_PROJECT, D.prof);
+        CK(gemm_splitk_d(D.st, 1, m, T * m, (int)n, one, D.Q, n, D.W, n, zero, D.G, m, D.Split,
+                         D.splits));
+        if (!h->has_exp) CK(form_reduced(D.st, m, T, h->kmax, h->dTerms, D.G, D.Ahat));
     }
     {
-        Phase ph(h, FEAST_NL_PH_PROJECT);
-        CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, h->dQ, n, h->dW, n, zero, h->dG, m,
-                         h->dSplit, h->splits));
-        if (!h->has_exp) CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
-    }
-    {
-        Phase ph(h, FEAST_NL_PH_REDUCED);
+        Phase ph(h, FEAST_NL_PH_REDUCED, D.prof);
         if (h->has_exp)
-            CK(reduced_solve_general(h->st, m, T, h->dTerms, h->dG, h->c_re, h->c_im, h->ra, h->rb,
-                                     kBeynProbeSeed, h->dBeyn, h->dLam, h->dYred, h->dStatus));
+            CK(reduced_solve_general(D.st, m, T, h->dTerms, D.G, D.c_re, D.c_im, D.ra, D.rb,
+                                     kBeynProbeSeed, D.Beyn, D.Lam, D.Yred, D.status));
         else
-            CK(reduced_solve(h->st, m, h->kmax, h->dAhat, m, h->c_re, h->c_im, h->ra, h->rb,
-                             h->dRed, h->dLam, h->dYred, h->dStatus));
+            CK(reduced_solve(D.st, m, h->kmax, D.Ahat, m, D.c_re, D.c_im, D.ra, D.rb, D.Red, D.Lam,
+                             D.Yred, D.status));
     }
-    Phase ph(h, FEAST_NL_PH_RITZ);
-    CK(gemm<double2>(h->st, 0, (int)n, m, m, one, h->dQ, n, 0, h->dYred, m, 0, zero, h->dX, n, 0,
-                     1));
-    CK(column_norms(h->st, n, m, h->dX, n, h->dNu));
-    CK(ritz_scale(h->st, n, m, T, h->dTerms, h->dLam, h->dNu, h->dX, h->dYred, h->dYcat));
-    CK(gemm<double2>(h->st, 0, (int)n, m, T * m, one, h->dW, n, 0, h->dYcat, (int64_t)T * m, 0,
-                     zero, h->dR, n, 0, 1));
-    CK(column_norms(h->st, n, m, h->dR, n, h->dRnorm));
-    CK(residual_summary(h->st, m, T, h->dTerms, h->dLam, h->dRnorm, h->c_re, h->c_im, h->ra,
-                        h->rb, tol, h->dRelres, h->dStatus));
+    Phase ph(h, FEAST_NL_PH_RITZ, D.prof);
+    CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Yred, m, 0, zero, D.X, n, 0, 1));
+    CK(column_norms(D.st, n, m, D.X, n, D.Nu));
+    CK(ritz_scale(D.st, n, m, T, h->dTerms, D.Lam, D.Nu, D.X, D.Yred, D.Ycat));
+    CK(gemm<double2>(D.st, 0, (int)n, m, T * m, one, D.W, n, 0, D.Ycat, (int64_t)T * m, 0, zero, D.R,
+                     n, 0, 1));
+    CK(column_norms(D.st, n, m, D.R, n, D.Rnorm));
+    CK(residual_summary(D.st, m, T, h->dTerms, D.Lam, D.Rnorm, D.c_re, D.c_im, D.ra, D.rb, tol,
+                        D.Relres, D.status));
     return FEAST_NL_OK;
 }
 
-// Step 4 for the current (X, Lambda, R): node solves and weighted accumulation into Q.
-int filter_step(feast_nl_handle* h, int m) {
+// Step 4, first half, for every contour at once: each contour's T(X, Lambda)
+// is copied to its nodes and all nd * nc systems are solved as one batch.
+int filter_solve(feast_nl_handle* h, const NodeSet& ns, const Work& wk, int nd, int m,
+                 cudaStream_t st, int* err, bool prof) {
+    Phase ph(h, FEAST_NL_PH_SOLVE, prof);
     const int64_t n = h->n;
+    const int nb = nd * ns.nc;
     if (h->precision == FEAST_NL_FP64) {
-        double2* Y = static_cast<double2*>(h->dY);
-        {
-            Phase ph(h, FEAST_NL_PH_SOLVE);
-            CK(broadcast_rhs<double2>(h->st, n, m, h->dR, h->nc, Y, n * m));
-            CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
-                                         static_cast<const double2*>(h->dF), n * n, h->dGather,
-                                         h->dGcount, h->nc, Y, n * m, m, &h->dStatus->flags));
-        }
-        Phase ph(h, FEAST_NL_PH_ACCUM);
-        CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
-                               h->dStatus));
-        CK(accumulate_filter<double2>(h->st, n, m, h->nc, h->dX, Y, n * m, h->dCoef, h->dFsum,
-                                      h->dQ));
+        double2* Y = static_cast<double2*>(wk.Y);
+        CK(broadcast_rhs<double2>(st, n, m, wk.R, nd, ns.nc, Y, n * m));
+        CK(lu_solve_batched<double2>(st, n, lu_block_size<double2>(),
+                                     static_cast<const double2*>(ns.dF), n * n, ns.dGather,
+                                     ns.dGcount, nb, Y, n * m, m, err));
     } else {
-        float2* Y = static_cast<float2*>(h->dY);
-        {
-            Phase ph(h, FEAST_NL_PH_SOLVE);
-            CK(broadcast_rhs<float2>(h->st, n, m, h->dR, h->nc, Y, n * m));
-            CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
-                                        static_cast<const float2*>(h->dF), n * n, h->dGather,
-                                        h->dGcount, h->nc, Y, n * m, m, &h->dStatus->flags));
-        }
-        Phase ph(h, FEAST_NL_PH_ACCUM);
-        CK(filter_coefficients(h->st, h->nc, m, h->dz, h->dw, h->dLam, h->dCoef, h->dFsum,
-                               h->dStatus));
-        CK(accumulate_filter<float2>(h->st, n, m, h->nc, h->dX, Y, n * m, h->dCoef, h->dFsum,
-                                     h->dQ));
+        float2* Y = static_cast<float2*>(wk.Y);
+        const float2* F = static_cast<const float2*>(ns.dF);
+        // tile width from the autotuner (times the candidates on Y before it is filled)
+        const int bn = lu_solve_pick_bn(st, n, lu_block_size<float2>(), F, n * n, ns.dGather,
+                                        ns.dGcount, nb, Y, n * m, m, err);
+        CK(broadcast_rhs<float2>(st, n, m, wk.R, nd, ns.nc, Y, n * m));
+        CK(lu_solve_batched<float2>(st, n, lu_block_size<float2>(), F, n * n, ns.dGather,
+                                    ns.dGcount, nb, Y, n * m, m, err, bn));
     }
+    return FEAST_NL_OK;
+}
+
+// Step 4, second half, for contour D: quadrature weights and accumulation into Q.
+int filter_accumulate(feast_nl_handle* h, const Disc& D) {
+    Phase ph(h, FEAST_NL_PH_ACCUM, D.prof);
+    const int64_t n = h->n;
+    const int m = D.m;
+    CK(filter_coefficients(D.st, D.nc, m, D.z, D.w, D.Lam, D.Coef, D.Fsum, D.status));
+    if (h->precision == FEAST_NL_FP64)
+        CK(accumulate_filter<double2>(D.st, n, m, D.nc, D.X, static_cast<const double2*>(D.Y), n * m,
+                                      D.Coef, D.Fsum, D.Q));
+    else
+        CK(accumulate_filter<float2>(D.st, n, m, D.nc, D.X, static_cast<const float2*>(D.Y), n * m,
+                                     D.Coef, D.Fsum, D.Q));
+    return FEAST_NL_OK;
+}
+
+// Quadrature nodes of nd contours, assembly of T at all of them and the batched
+// LU factorisation.  Fails with ESINGULAR_NODE on an exact zero pivot.
+int build_nodes(feast_nl_handle* h, NodeSet& ns, int nd, const double* c_re, const double* c_im,
+                const double* ra, const double* rb, int nc, int rule, cudaStream_t st,
+                IterStatus* dstat, bool prof) {
+    for (int d = 0; d < nd; ++d)
+        if (!(ra[d] > 0.0) || !(rb[d] > 0.0) || !std::isfinite(c_re[d]) || !std::isfinite(c_im[d]))
+            return fail(FEAST_NL_EINVAL, "contour needs finite center and ra, rb > 0");
+    if (nc < 1 || nc > 1024) return fail(FEAST_NL_EINVAL, "nc must be in [1, 1024]");
+    if ((int64_t)nd * nc > 65535) return fail(FEAST_NL_EINVAL, "ndisc * nc must be <= 65535");
+    if (rule < FEAST_NL_GL || rule > FEAST_NL_GL_HALVES) return fail(FEAST_NL_EINVAL, "unknown rule");
+    if (rule == FEAST_NL_GL_HALVES && (nc % 2)) return fail(FEAST_NL_EINVAL, "GL_HALVES needs even nc");
+    const int64_t n = h->n;
+    const int nb = nd * nc;
+    // nodes and weights: z(theta) = c + ra cos + i rb sin, omega = w z'(theta)/(2 pi i)
+    std::vector<double> th(nc), wt(nc);
+    if (rule == FEAST_NL_GL) {
+        std::vector<double> x, w;
+        gauss_legendre(nc, x, w);
+        for (int j = 0; j < nc; ++j) { th[j] = M_PI * (x[j] + 1.0); wt[j] = M_PI * w[j]; }
+    } else if (rule == FEAST_NL_TRAPEZOID) {
+        for (int j = 0; j < nc; ++j) { th[j] = 2.0 * M_PI * (j + 0.5) / nc; wt[j] = 2.0 * M_PI / nc; }
+    } else {
+        std::vector<double> x, w;
+        gauss_legendre(nc / 2, x, w);
+        for (int j = 0; j < nc / 2; ++j) {
+            th[j] = 0.5 * M_PI * (x[j] + 1.0);
+            wt[j] = 0.5 * M_PI * w[j];
+            th[j + nc / 2] = th[j] + M_PI;
+            wt[j + nc / 2] = wt[j];
+        }
+    }
+    free_nodes(ns);
+    ns.z.assign(nb, 0.0);
+    ns.w.assign(nb, 0.0);
+    ns.c_re.assign(c_re, c_re + nd);
+    ns.c_im.assign(c_im, c_im + nd);
+    ns.ra.assign(ra, ra + nd);
+    ns.rb.assign(rb, rb + nd);
+    for (int d = 0; d < nd; ++d) {
+        const zd c(c_re[d], c_im[d]);
+        for (int j = 0; j < nc; ++j) {
+            ns.z[d * nc + j] = c + ra[d] * std::cos(th[j]) + zd(0.0, 1.0) * rb[d] * std::sin(th[j]);
+            zd dz(-ra[d] * std::sin(th[j]), rb[d] * std::cos(th[j]));
+            ns.w[d * nc + j] = wt[j] * dz / zd(0.0, 2.0 * M_PI);
+        }
+    }
+    // node-matrix coefficients
+    std::vector<double2> coef((size_t)std::max(h->nA, 1) * nb), diagc(nb);
+    for (int j = 0; j < nb; ++j) {
+        zd dsum = 0.0;
+        for (int t = 0; t < h->nterms; ++t) {
+            const HostTerm& ht = h->terms[t];
+            zd f = term_f_host(ht.kind, ht.p, ht.tau, ht.scale, ns.z[j]);
+            if (ht.aidx < 0) dsum += f;
+            else coef[(size_t)ht.aidx * nb + j] = make_double2(f.real(), f.imag());
+        }
+        diagc[j] = make_double2(dsum.real(), dsum.imag());
+    }
+    double2 *dcoef = nullptr, *ddiag = nullptr;
+    auto free_tmp = [&]() { dfree(dcoef); dfree(ddiag); };
+    int rc = [&]() -> int {
+        {
+            unsigned char* f = nullptr;
+            CK(dalloc(&f, (size_t)nb * n * n * h->lu_elem()));
+            ns.dF = f;
+        }
+        CK(dalloc(&ns.dpiv, (size_t)nb * n));
+        {
+            const int blk = h->precision == FEAST_NL_FP64 ? lu_block_size<double2>() : lu_block_size<float2>();
+            const int gs = lu_gather_stride(n, blk);
+            CK(dalloc(&ns.dGather, (size_t)nb * gs));
+            CK(dalloc(&ns.dGcount, (size_t)nb * (gs / 128)));
+        }
+        CK(dalloc(&ns.dinfo, (size_t)nb));
+        CK(dalloc(&ns.dz, (size_t)nb));
+        CK(dalloc(&ns.dw, (size_t)nb));
+        CK(dalloc(&dcoef, coef.size()));
+        CK(dalloc(&ddiag, (size_t)nb));
+        ns.nd = nd;
+        ns.nc = nc;
+        ns.rule = rule;
+        std::vector<double2> zz(nb), ww(nb);
+        for (int j = 0; j < nb; ++j) {
+            zz[j] = make_double2(ns.z[j].real(), ns.z[j].imag());
+            ww[j] = make_double2(ns.w[j].real(), ns.w[j].imag());
+        }
+        CK(cudaMemcpyAsync(ns.dz, zz.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ns.dw, ww.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ddiag, diagc.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(ns.dinfo, 0, sizeof(int) * nb, st));
+        CK(cudaMemsetAsync(dstat, 0, sizeof(IterStatus), st));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+        if (h->precision == FEAST_NL_FP64) {
+            double2* F = static_cast<double2*>(ns.dF);
+            {
+                Phase ph(h, FEAST_NL_PH_ASSEMBLE, prof);
+                CK(assemble_nodes<double2>(st, n, h->nA, h->dA, dcoef, ddiag, nb, F, n * n));
+            }
+            Phase ph(h, FEAST_NL_PH_LU, prof);
+            CK(lu_factor_batched<double2>(st, n, lu_block_size<double2>(), F, n * n, ns.dpiv, nb,
+                                          ns.dinfo, ns.dGather, ns.dGcount, &dstat->flags));
+        } else {
+            float2* F = static_cast<float2*>(ns.dF);
+            {
+                Phase ph(h, FEAST_NL_PH_ASSEMBLE, prof);
+                CK(assemble_nodes<float2>(st, n, h->nA, h->dA, dcoef, ddiag, nb, F, n * n));
+            }
+            Phase ph(h, FEAST_NL_PH_LU, prof);
+            CK(lu_factor_batched<float2>(st, n, lu_block_size<float2>(), F, n * n, ns.dpiv, nb,
+                                         ns.dinfo, ns.dGather, ns.dGcount, &dstat->flags));
+        }
+        CK(cudaEventRecord(e1, st));
+        std::vector<int> info(nb);
+        IterStatus hs{};
+        CK(cudaMemcpyAsync(info.data(), ns.dinfo, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&hs, dstat, sizeof(IterStatus), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ns.ms_factor = ms;
+        if (prof) prof_flush(h);
+        if (hs.flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node LU");
+        for (int j = 0; j < nb; ++j)
+            if (info[j] != 0)
+                return fail(FEAST_NL_ESINGULAR_NODE,
+                            "zero pivot in T(z_" + std::to_string(j) + ") at column " + std::to_string(info[j] - 1));
+        return FEAST_NL_OK;
+    }();
+    free_tmp();
+    if (rc != FEAST_NL_OK) {
+        free_nodes(ns);
+        ns.nd = 0;
+        return rc;
+    }
+    ns.ready = true;
+    return FEAST_NL_OK;
+}
+
+// Copies the pairs (lam, relres, X: m columns) of one contour out to the
+// caller, in Step 2's order, optionally only those strictly inside.
+int copy_pairs(const feast_nl_handle* h, cudaStream_t st, double2* gather, double2* stage, int m,
+               const double2* dlam, const double* drr, const double2* dX, double c_re, double c_im,
+               double ra, double rb, int capacity, int32_t* m_out, double* lambda, void* X,
+               double* relres, int inside_only) {
+    std::vector<double2> lam(m);
+    std::vector<double> rr(m);
+    CK(cudaMemcpyAsync(lam.data(), dlam, sizeof(double2) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rr.data(), drr, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> idx;
+    for (int i = 0; i < m; ++i) {
+        double dx = (lam[i].x - c_re) / ra, dy = (lam[i].y - c_im) / rb;
+        bool ins = std::sqrt(dx * dx + dy * dy) < 1.0;
+        if (!inside_only || ins) idx.push_back(i);
+    }
+    const int cnt = std::min<int>((int)idx.size(), capacity);
+    *m_out = cnt;
+    if (cnt == 0) return FEAST_NL_OK;
+    std::vector<double2> lo(cnt);
+    std::vector<double> ro(cnt);
+    for (int q = 0; q < cnt; ++q) { lo[q] = lam[idx[q]]; ro[q] = rr[idx[q]]; }
+    if (lambda) {
+        if (is_device_ptr(lambda)) CK(cudaMemcpyAsync(lambda, lo.data(), sizeof(double2) * cnt, cudaMemcpyHostToDevice, st));
+        else std::memcpy(lambda, lo.data(), sizeof(double2) * cnt);
+    }
+    if (relres) {
+        if (is_device_ptr(relres)) CK(cudaMemcpyAsync(relres, ro.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+        else std::memcpy(relres, ro.data(), sizeof(double) * cnt);
+    }
+    if (X) {
+        // gather the chosen columns (column-major), then store
+        for (int q = 0; q < cnt; ++q)
+            CK(cudaMemcpyAsync(gather + (int64_t)q * h->n, dX + (int64_t)idx[q] * h->n,
+                               sizeof(double2) * h->n, cudaMemcpyDeviceToDevice, st));
+        CKS(store_block(h, st, stage, gather, cnt, X, capacity));
+    }
+    CK(cudaStreamSynchronize(st));
     return FEAST_NL_OK;
 }
 
@@ -469,6 +794,25 @@ bool trace_enabled() {
 int validate_handle(feast_nl_handle* h) {
     if (!h) return fail(FEAST_NL_EINVAL, "null handle");
     return FEAST_NL_OK;
+}
+
+int check_solve_args(const feast_nl_handle* h, int m0, double tol, int maxit) {
+    if (m0 < 1 || m0 > kMaxM0 || m0 > h->n) return fail(FEAST_NL_EINVAL, "m0 must be in [1, min(n, 112)]");
+    if (h->has_exp && m0 > beyn_max_m())
+        return fail(FEAST_NL_EINVAL, "non-polynomial T: m0 must be <= " + std::to_string(beyn_max_m()));
+    if (h->kmax * m0 > 1024) return fail(FEAST_NL_EINVAL, "degree * m0 must be <= 1024");
+    if (maxit < 1) return fail(FEAST_NL_EINVAL, "maxit must be >= 1");
+    if (!(tol > 0.0)) return fail(FEAST_NL_EINVAL, "tol must be > 0");
+    return FEAST_NL_OK;
+}
+
+// Final status of one contour from its last iteration's summary.
+int contour_status(const IterStatus& s, bool converged, int m) {
+    int status = converged ? FEAST_NL_OK : FEAST_NL_ENOT_CONVERGED;
+    if (s.n_inside >= m) status = FEAST_NL_ETOO_MANY;
+    if (s.flags & 2) status = FEAST_NL_ESINGULAR_NODE;
+    if (s.flags & 16) status = FEAST_NL_EDEVICE;
+    return status;
 }
 
 }  // namespace
@@ -520,24 +864,21 @@ void feast_nl_destroy(feast_nl_handle* h) {
     if (!h) return;
     AllocScope as(h->st);
     if (h->st) cudaStreamSynchronize(h->st);
-    release_workspace(h);
+    free_work(h->wk);
+    free_nodes(h->ns);
     dfree(h->dA);
     dfree(h->dAsl);
     dfree(h->dSigma);
     dfree(h->dSlot);
     dfree(h->dTerms);
-    dfree(h->dz);
-    dfree(h->dw);
-    dfree(h->dF);
-    dfree(h->dpiv);
-    dfree(h->dinfo);
-    dfree(h->dGather);
-    dfree(h->dGcount);
     dfree(h->dStatus);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
-    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    if (h->own_stream && h->st) {
+        cudaStreamSynchronize(h->st);
+        cudaStreamDestroy(h->st);
+    }
     delete h;
 }
 
@@ -697,127 +1038,9 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     g_last_error.clear();
     CKS(validate_handle(h));
     AllocScope as(h->st);
-    if (!(ra > 0.0) || !(rb > 0.0) || !std::isfinite(c_re) || !std::isfinite(c_im))
-        return fail(FEAST_NL_EINVAL, "contour needs finite center and ra, rb > 0");
-    if (nc < 1 || nc > 1024) return fail(FEAST_NL_EINVAL, "nc must be in [1, 1024]");
-    if (rule < FEAST_NL_GL || rule > FEAST_NL_GL_HALVES) return fail(FEAST_NL_EINVAL, "unknown rule");
-    if (rule == FEAST_NL_GL_HALVES && (nc % 2)) return fail(FEAST_NL_EINVAL, "GL_HALVES needs even nc");
-    const int64_t n = h->n;
-    // nodes and weights: z(theta) = c + ra cos + i rb sin, omega = w z'(theta)/(2 pi i)
-    std::vector<double> th(nc), wt(nc);
-    if (rule == FEAST_NL_GL) {
-        std::vector<double> x, w;
-        gauss_legendre(nc, x, w);
-        for (int j = 0; j < nc; ++j) { th[j] = M_PI * (x[j] + 1.0); wt[j] = M_PI * w[j]; }
-    } else if (rule == FEAST_NL_TRAPEZOID) {
-        for (int j = 0; j < nc; ++j) { th[j] = 2.0 * M_PI * (j + 0.5) / nc; wt[j] = 2.0 * M_PI / nc; }
-    } else {
-        std::vector<double> x, w;
-        gauss_legendre(nc / 2, x, w);
-        for (int j = 0; j < nc / 2; ++j) {
-            th[j] = 0.5 * M_PI * (x[j] + 1.0);
-            wt[j] = 0.5 * M_PI * w[j];
-            th[j + nc / 2] = th[j] + M_PI;
-            wt[j + nc / 2] = wt[j];
-        }
-    }
-    h->z.assign(nc, 0.0);
-    h->w.assign(nc, 0.0);
-    const zd c(c_re, c_im);
-    for (int j = 0; j < nc; ++j) {
-        h->z[j] = c + ra * std::cos(th[j]) + zd(0.0, 1.0) * rb * std::sin(th[j]);
-        zd dz(-ra * std::sin(th[j]), rb * std::cos(th[j]));
-        h->w[j] = wt[j] * dz / zd(0.0, 2.0 * M_PI);
-    }
-    // node-matrix coefficients
-    std::vector<double2> coef((size_t)std::max(h->nA, 1) * nc), diagc(nc);
-    for (int j = 0; j < nc; ++j) {
-        zd dsum = 0.0;
-        for (int t = 0; t < h->nterms; ++t) {
-            const HostTerm& ht = h->terms[t];
-            zd f = term_f_host(ht.kind, ht.p, ht.tau, ht.scale, h->z[j]);
-            if (ht.aidx < 0) dsum += f;
-            else coef[(size_t)ht.aidx * nc + j] = make_double2(f.real(), f.imag());
-        }
-        diagc[j] = make_double2(dsum.real(), dsum.imag());
-    }
-    // (re)allocate node storage
-    dfree(h->dF);
-    dfree(h->dpiv); dfree(h->dinfo); dfree(h->dz); dfree(h->dw);
-    dfree(h->dGather); dfree(h->dGcount);
-    h->have_contour = false;
     h->have_result = false;
-    release_workspace(h);
-    double2 *dcoef = nullptr, *ddiag = nullptr;
-    {
-        unsigned char* f = nullptr;
-        CK(dalloc(&f, (size_t)nc * n * n * h->lu_elem()));
-        h->dF = f;
-    }
-    CK(dalloc(&h->dpiv, (size_t)nc * n));
-    {
-        const int nb = h->precision == FEAST_NL_FP64 ? lu_block_size<double2>() : lu_block_size<float2>();
-        const int gs = lu_gather_stride(n, nb);
-        CK(dalloc(&h->dGather, (size_t)nc * gs));
-        CK(dalloc(&h->dGcount, (size_t)nc * (gs / 128)));
-    }
-    CK(dalloc(&h->dinfo, (size_t)nc));
-    CK(dalloc(&h->dz, (size_t)nc));
-    CK(dalloc(&h->dw, (size_t)nc));
-    CK(dalloc(&dcoef, coef.size()));
-    CK(dalloc(&ddiag, (size_t)nc));
-    h->nc = nc;
-    h->rule = rule;
-    h->c_re = c_re; h->c_im = c_im; h->ra = ra; h->rb = rb;
-    std::vector<double2> zz(nc), ww(nc);
-    for (int j = 0; j < nc; ++j) {
-        zz[j] = make_double2(h->z[j].real(), h->z[j].imag());
-        ww[j] = make_double2(h->w[j].real(), h->w[j].imag());
-    }
-    CK(cudaMemcpyAsync(h->dz, zz.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->dw, ww.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(ddiag, diagc.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemsetAsync(h->dinfo, 0, sizeof(int) * nc, h->st));
-    CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
-    CK(cudaEventRecord(h->ev0, h->st));
-    if (h->precision == FEAST_NL_FP64) {
-        double2* F = static_cast<double2*>(h->dF);
-        {
-            Phase ph(h, FEAST_NL_PH_ASSEMBLE);
-            CK(assemble_nodes<double2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
-        }
-        Phase ph(h, FEAST_NL_PH_LU);
-        CK(lu_factor_batched<double2>(h->st, n, lu_block_size<double2>(), F, n * n, h->dpiv, nc,
-                                      h->dinfo, h->dGather, h->dGcount, &h->dStatus->flags));
-    } else {
-        float2* F = static_cast<float2*>(h->dF);
-        {
-            Phase ph(h, FEAST_NL_PH_ASSEMBLE);
-            CK(assemble_nodes<float2>(h->st, n, h->nA, h->dA, dcoef, ddiag, nc, F, n * n));
-        }
-        Phase ph(h, FEAST_NL_PH_LU);
-        CK(lu_factor_batched<float2>(h->st, n, lu_block_size<float2>(), F, n * n, h->dpiv, nc,
-                                     h->dinfo, h->dGather, h->dGcount, &h->dStatus->flags));
-    }
-    CK(cudaEventRecord(h->ev1, h->st));
-    std::vector<int> info(nc);
-    CK(cudaMemcpyAsync(info.data(), h->dinfo, sizeof(int) * nc, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    h->ms_factor = ms;
-    prof_flush(h);
-    dfree(dcoef);
-    dfree(ddiag);
-    if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node LU");
-    for (int j = 0; j < nc; ++j)
-        if (info[j] != 0)
-            return fail(FEAST_NL_ESINGULAR_NODE,
-                        "zero pivot in T(z_" + std::to_string(j) + ") at column " + std::to_string(info[j] - 1));
-    h->have_contour = true;
-    return FEAST_NL_OK;
+    free_work(h->wk);
+    return build_nodes(h, h->ns, 1, &c_re, &c_im, &ra, &rb, nc, rule, h->st, h->dStatus, true);
 }
 
 int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, uint64_t seed,
@@ -826,37 +1049,37 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     CKS(validate_handle(h));
     AllocScope as(h->st);
     if (info) std::memset(info, 0, sizeof(*info));
-    if (!h->have_contour) return fail(FEAST_NL_EINVAL, "set_contour must succeed before solve");
-    if (m0 < 1 || m0 > kMaxM0 || m0 > h->n) return fail(FEAST_NL_EINVAL, "m0 must be in [1, min(n, 112)]");
-    if (h->has_exp && m0 > beyn_max_m())
-        return fail(FEAST_NL_EINVAL, "non-polynomial T: m0 must be <= " + std::to_string(beyn_max_m()));
-    if (h->kmax * m0 > 1024) return fail(FEAST_NL_EINVAL, "degree * m0 must be <= 1024");
-    if (maxit < 1) return fail(FEAST_NL_EINVAL, "maxit must be >= 1");
-    if (!(tol > 0.0)) return fail(FEAST_NL_EINVAL, "tol must be > 0");
+    if (!h->ns.ready) return fail(FEAST_NL_EINVAL, "set_contour must succeed before solve");
+    CKS(check_solve_args(h, m0, tol, maxit));
     CKS(ensure_workspace(h, m0));
     h->have_result = false;
     const int m = m0;
-    CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
+    const Disc D = disc_view(h, h->ns, h->wk, 0, m, h->st, true);
+    CK(cudaMemsetAsync(D.status, 0, sizeof(IterStatus), h->st));
     CK(cudaEventRecord(h->ev0, h->st));
     {
         Phase ph(h, FEAST_NL_PH_IO);
-        if (X0) CKS(load_block(h, X0, m, h->dQ));
-        else CK(random_block(h->st, h->n, m, seed, h->dQ));
+        if (X0) CKS(load_block(h, h->st, h->wk.Stage, X0, m, D.Q));
+        else CK(random_block(h->st, h->n, m, seed, D.Q));
     }
-    CKS(orthonormalize(h, m));                                  // Step 0
+    CKS(orthonormalize(h, D));                                  // Step 0
     int it = 0;
     bool converged = false;
     IterStatus stt{};
     for (it = 1; it <= maxit; ++it) {
-        CKS(ritz_and_residual(h, m, tol));                      // Steps 1-3
-        CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+        {
+            Phase ph(h, FEAST_NL_PH_APPLY);
+            CKS(apply_terms(h, h->wk, 1, m, D.Q, D.W, h->st, &D.status->flags));
+        }
+        CKS(ritz_and_residual(h, D, tol));                      // Steps 1-3
+        CK(cudaMemcpyAsync(h->hStatus.get(), D.status, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         stt = *h->hStatus;
         if (trace_enabled()) {
             std::vector<double2> lam(m);
             std::vector<double> rr(m);
-            cudaMemcpyAsync(lam.data(), h->dLam, sizeof(double2) * m, cudaMemcpyDeviceToHost, h->st);
-            cudaMemcpyAsync(rr.data(), h->dRelres, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st);
+            cudaMemcpyAsync(lam.data(), D.Lam, sizeof(double2) * m, cudaMemcpyDeviceToHost, h->st);
+            cudaMemcpyAsync(rr.data(), D.Relres, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st);
             cudaStreamSynchronize(h->st);
             fprintf(stderr, "[feast_nl] it %d inside %d conv %d max_relres %.3e flags %d qr_sweeps %d\n",
                     it, stt.n_inside, stt.n_conv, stt.max_relres, stt.flags, stt.qr_sweeps);
@@ -865,8 +1088,9 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
         }
         if (it > 1 && stt.n_conv == stt.n_inside) { converged = true; break; }
         if (it == maxit) break;
-        CKS(filter_step(h, m));                                 // Step 4
-        CKS(orthonormalize(h, m));                              // Step 5
+        CKS(filter_solve(h, h->ns, h->wk, 1, m, h->st, &D.status->flags, true));   // Step 4
+        CKS(filter_accumulate(h, D));
+        CKS(orthonormalize(h, D));                              // Step 5
     }
     CK(cudaEventRecord(h->ev1, h->st));
     CK(cudaEventSynchronize(h->ev1));
@@ -875,17 +1099,14 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     prof_flush(h);
     h->have_result = true;
     h->m_last = m;
-    int status = converged ? FEAST_NL_OK : FEAST_NL_ENOT_CONVERGED;
-    if (stt.n_inside >= m) status = FEAST_NL_ETOO_MANY;
-    if (stt.flags & 2) status = FEAST_NL_ESINGULAR_NODE;
-    if (stt.flags & 16) status = FEAST_NL_EDEVICE;
+    const int status = contour_status(stt, converged, m);
     if (info) {
         info->iters = std::min(it, maxit);
         info->n_inside = stt.n_inside;
         info->n_converged = stt.n_conv;
         info->status = status;
         info->max_relres = stt.max_relres;
-        info->ms_factor = h->ms_factor;
+        info->ms_factor = h->ns.ms_factor;
         info->ms_iterate = ms;
     }
     if (status == FEAST_NL_ENOT_CONVERGED) g_last_error = "maxit reached";
@@ -901,50 +1122,18 @@ int feast_nl_get_eigpairs(feast_nl_handle* h, int32_t capacity, int32_t* m_out, 
     AllocScope as(h->st);
     if (!h->have_result) return fail(FEAST_NL_EINVAL, "no solve result");
     if (capacity < 0 || !m_out) return fail(FEAST_NL_EINVAL, "bad capacity or m_out");
-    const int m = h->m_last;
-    std::vector<double2> lam(m);
-    std::vector<double> rr(m);
-    CK(cudaMemcpyAsync(lam.data(), h->dLam, sizeof(double2) * m, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(rr.data(), h->dRelres, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    std::vector<int> idx;
-    for (int i = 0; i < m; ++i) {
-        double dx = (lam[i].x - h->c_re) / h->ra, dy = (lam[i].y - h->c_im) / h->rb;
-        bool ins = std::sqrt(dx * dx + dy * dy) < 1.0;
-        if (!inside_only || ins) idx.push_back(i);
-    }
-    const int cnt = std::min<int>((int)idx.size(), capacity);
-    *m_out = cnt;
-    if (cnt == 0) return FEAST_NL_OK;
-    std::vector<double2> lo(cnt);
-    std::vector<double> ro(cnt);
-    for (int q = 0; q < cnt; ++q) { lo[q] = lam[idx[q]]; ro[q] = rr[idx[q]]; }
-    if (lambda) {
-        if (is_device_ptr(lambda)) CK(cudaMemcpyAsync(lambda, lo.data(), sizeof(double2) * cnt, cudaMemcpyHostToDevice, h->st));
-        else std::memcpy(lambda, lo.data(), sizeof(double2) * cnt);
-    }
-    if (relres) {
-        if (is_device_ptr(relres)) CK(cudaMemcpyAsync(relres, ro.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, h->st));
-        else std::memcpy(relres, ro.data(), sizeof(double) * cnt);
-    }
-    if (X) {
-        // gather the chosen columns into the staging buffer (column-major), then store
-        for (int q = 0; q < cnt; ++q)
-            CK(cudaMemcpyAsync(h->dQt + (int64_t)q * h->n, h->dX + (int64_t)idx[q] * h->n,
-                               sizeof(double2) * h->n, cudaMemcpyDeviceToDevice, h->st));
-        CKS(store_block(h, h->dQt, cnt, X, capacity));
-    }
-    CK(cudaStreamSynchronize(h->st));
-    return FEAST_NL_OK;
+    const Disc D = disc_view(h, h->ns, h->wk, 0, h->m_last, h->st, false);
+    return copy_pairs(h, h->st, h->wk.Qt, h->wk.Stage, h->m_last, D.Lam, D.Relres, D.X, D.c_re,
+                      D.c_im, D.ra, D.rb, capacity, m_out, lambda, X, relres, inside_only);
 }
 
 int feast_nl_get_nodes(feast_nl_handle* h, double* z, double* omega) {
     g_last_error.clear();
     CKS(validate_handle(h));
-    if (!h->have_contour) return fail(FEAST_NL_EINVAL, "no contour");
-    for (int j = 0; j < h->nc; ++j) {
-        if (z) { z[2 * j] = h->z[j].real(); z[2 * j + 1] = h->z[j].imag(); }
-        if (omega) { omega[2 * j] = h->w[j].real(); omega[2 * j + 1] = h->w[j].imag(); }
+    if (!h->ns.ready) return fail(FEAST_NL_EINVAL, "no contour");
+    for (int j = 0; j < h->ns.nc; ++j) {
+        if (z) { z[2 * j] = h->ns.z[j].real(); z[2 * j + 1] = h->ns.z[j].imag(); }
+        if (omega) { omega[2 * j] = h->ns.w[j].real(); omega[2 * j + 1] = h->ns.w[j].imag(); }
     }
     return FEAST_NL_OK;
 }
@@ -953,36 +1142,38 @@ int feast_nl_node_solve(feast_nl_handle* h, int32_t j, int32_t m, const void* R,
     g_last_error.clear();
     CKS(validate_handle(h));
     AllocScope as(h->st);
-    if (!h->have_contour) return fail(FEAST_NL_EINVAL, "no contour");
-    if (j < 0 || j >= h->nc || m < 1 || m > kMaxM0 || !R || !Y) return fail(FEAST_NL_EINVAL, "bad node, m or pointer");
-    CKS(ensure_workspace(h, std::max(m, h->mcap)));
+    if (!h->ns.ready) return fail(FEAST_NL_EINVAL, "no contour");
+    if (j < 0 || j >= h->ns.nc || m < 1 || m > kMaxM0 || !R || !Y) return fail(FEAST_NL_EINVAL, "bad node, m or pointer");
+    CKS(ensure_workspace(h, std::max(m, h->wk.mcap)));
+    h->have_result = false;
     const int64_t n = h->n;
-    CKS(load_block(h, R, m, h->dR));
+    const Work& wk = h->wk;
+    CKS(load_block(h, h->st, wk.Stage, R, m, wk.R));
     CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
+    const NodeSet& ns = h->ns;
     if (h->precision == FEAST_NL_FP64) {
-        double2* Yb = static_cast<double2*>(h->dY);
-        CK(broadcast_rhs<double2>(h->st, n, m, h->dR, 1, Yb, n * m));
+        double2* Yb = static_cast<double2*>(wk.Y);
+        CK(broadcast_rhs<double2>(h->st, n, m, wk.R, 1, 1, Yb, n * m));
         const int gs = lu_gather_stride(n, lu_block_size<double2>());
         CK(lu_solve_batched<double2>(h->st, n, lu_block_size<double2>(),
-                                     static_cast<const double2*>(h->dF) + (int64_t)j * n * n, n * n,
-                                     h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
+                                     static_cast<const double2*>(ns.dF) + (int64_t)j * n * n, n * n,
+                                     ns.dGather + (int64_t)j * gs, ns.dGcount + (int64_t)j * (gs / 128),
                                      1, Yb, n * m, m, &h->dStatus->flags));
-        CK(to_double<double2>(h->st, n * m, Yb, h->dX));
+        CK(to_double<double2>(h->st, n * m, Yb, wk.X));
     } else {
-        float2* Yb = static_cast<float2*>(h->dY);
-        CK(broadcast_rhs<float2>(h->st, n, m, h->dR, 1, Yb, n * m));
+        float2* Yb = static_cast<float2*>(wk.Y);
+        CK(broadcast_rhs<float2>(h->st, n, m, wk.R, 1, 1, Yb, n * m));
         const int gs = lu_gather_stride(n, lu_block_size<float2>());
         CK(lu_solve_batched<float2>(h->st, n, lu_block_size<float2>(),
-                                    static_cast<const float2*>(h->dF) + (int64_t)j * n * n, n * n,
-                                    h->dGather + (int64_t)j * gs, h->dGcount + (int64_t)j * (gs / 128),
+                                    static_cast<const float2*>(ns.dF) + (int64_t)j * n * n, n * n,
+                                    ns.dGather + (int64_t)j * gs, ns.dGcount + (int64_t)j * (gs / 128),
                                     1, Yb, n * m, m, &h->dStatus->flags));
-        CK(to_double<float2>(h->st, n * m, Yb, h->dX));
+        CK(to_double<float2>(h->st, n * m, Yb, wk.X));
     }
-    h->have_result = false;
     CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
-    return store_block(h, h->dX, m, Y, m);
+    return store_block(h, h->st, wk.Stage, wk.X, m, Y, m);
 }
 
 int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const double* lambda,
@@ -990,31 +1181,33 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X, const do
     g_last_error.clear();
     CKS(validate_handle(h));
     AllocScope as(h->st);
-    if (!h->have_contour) return fail(FEAST_NL_EINVAL, "no contour");
+    if (!h->ns.ready) return fail(FEAST_NL_EINVAL, "no contour");
     if (m < 1 || m > kMaxM0 || m > h->n || !X || !lambda || !Q) return fail(FEAST_NL_EINVAL, "bad m or pointer");
-    CKS(ensure_workspace(h, std::max(m, h->mcap)));
+    CKS(ensure_workspace(h, std::max(m, h->wk.mcap)));
     const int64_t n = h->n;
     const int T = h->nterms;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     h->have_result = false;
-    CKS(load_block(h, X, m, h->dX));
+    const Disc D = disc_view(h, h->ns, h->wk, 0, m, h->st, false);
+    CKS(load_block(h, h->st, h->wk.Stage, X, m, D.X));
     if (is_device_ptr(lambda))
-        CK(cudaMemcpyAsync(h->dLam, lambda, sizeof(double2) * m, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(D.Lam, lambda, sizeof(double2) * m, cudaMemcpyDeviceToDevice, h->st));
     else
-        CK(cudaMemcpyAsync(h->dLam, lambda, sizeof(double2) * m, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemsetAsync(h->dStatus, 0, sizeof(IterStatus), h->st));
+        CK(cudaMemcpyAsync(D.Lam, lambda, sizeof(double2) * m, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(D.status, 0, sizeof(IterStatus), h->st));
     // R = sum_t A_t X diag(scale_t f_t(lambda))
-    CKS(apply_terms(h, h->dX, m, h->dW));
-    CK(set_identity(h->st, m, h->dYred, h->dNu));
-    CK(ritz_scale(h->st, n, m, T, h->dTerms, h->dLam, h->dNu, h->dX, h->dYred, h->dYcat));
-    CK(gemm<double2>(h->st, 0, (int)n, m, T * m, one, h->dW, n, 0, h->dYcat, (int64_t)T * m, 0,
-                     zero, h->dR, n, 0, 1));
-    CKS(filter_step(h, m));
-    CK(cudaMemcpyAsync(h->hStatus.get(), h->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
+    CKS(apply_terms(h, h->wk, 1, m, D.X, D.W, h->st, &D.status->flags));
+    CK(set_identity(h->st, m, D.Yred, D.Nu));
+    CK(ritz_scale(h->st, n, m, T, h->dTerms, D.Lam, D.Nu, D.X, D.Yred, D.Ycat));
+    CK(gemm<double2>(h->st, 0, (int)n, m, T * m, one, D.W, n, 0, D.Ycat, (int64_t)T * m, 0, zero,
+                     D.R, n, 0, 1));
+    CKS(filter_solve(h, h->ns, h->wk, 1, m, h->st, &D.status->flags, false));
+    CKS(filter_accumulate(h, D));
+    CK(cudaMemcpyAsync(h->hStatus.get(), D.status, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->hStatus->flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node solve");
     if (h->hStatus->flags & 2) return fail(FEAST_NL_ESINGULAR_NODE, "a lambda equals a node");
-    return store_block(h, h->dQ, m, Q, m);
+    return store_block(h, h->st, h->wk.Stage, D.Q, m, Q, m);
 }
 
 int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat, int32_t* kmax_out) {
@@ -1023,24 +1216,25 @@ int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat, i
     AllocScope as(h->st);
     if (h->has_exp) return fail(FEAST_NL_EUNSUPPORTED, "projection by powers needs polynomial T");
     if (m < 1 || m > kMaxM0 || m > h->n || !Q || !Ahat) return fail(FEAST_NL_EINVAL, "bad m or pointer");
-    CKS(ensure_workspace(h, std::max(m, h->mcap)));
+    CKS(ensure_workspace(h, std::max(m, h->wk.mcap)));
     const int64_t n = h->n;
     const int T = h->nterms;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     h->have_result = false;
-    CKS(load_block(h, Q, m, h->dQ));
-    CKS(apply_terms(h, h->dQ, m, h->dW));
-    CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, h->dQ, n, h->dW, n, zero, h->dG, m,
-                     h->dSplit, h->splits));
-    CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, h->dG, h->dAhat));
+    const Disc D = disc_view(h, h->ns, h->wk, 0, m, h->st, false);
+    CKS(load_block(h, h->st, h->wk.Stage, Q, m, D.Q));
+    CKS(apply_terms(h, h->wk, 1, m, D.Q, D.W, h->st, &h->dStatus->flags));
+    CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, D.Q, n, D.W, n, zero, D.G, m, D.Split,
+                     D.splits));
+    CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, D.G, D.Ahat));
     const bool dev = is_device_ptr(Ahat);
     for (int p = 0; p <= h->kmax; ++p) {
         double2* dst = static_cast<double2*>(Ahat) + (int64_t)p * m * m;
         if (dev) {
-            CK(transpose_colmajor_to_rowmajor(h->st, m, m, h->dAhat + (int64_t)p * m * m, m, dst, m));
+            CK(transpose_colmajor_to_rowmajor(h->st, m, m, D.Ahat + (int64_t)p * m * m, m, dst, m));
         } else {
-            CK(transpose_colmajor_to_rowmajor(h->st, m, m, h->dAhat + (int64_t)p * m * m, m, h->dStage, m));
-            CK(cudaMemcpyAsync(dst, h->dStage, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, h->st));
+            CK(transpose_colmajor_to_rowmajor(h->st, m, m, D.Ahat + (int64_t)p * m * m, m, h->wk.Stage, m));
+            CK(cudaMemcpyAsync(dst, h->wk.Stage, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, h->st));
             CK(cudaStreamSynchronize(h->st));
         }
     }
@@ -1048,5 +1242,273 @@ int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat, i
     if (kmax_out) *kmax_out = h->kmax;
     return FEAST_NL_OK;
 }
+
+// ---------------------------------------------------------------- spectrum slicing
+
+void feast_nl_slices_destroy(feast_nl_slices* s) {
+    if (!s) return;
+    AllocScope as(s->st);
+    if (s->st) cudaStreamSynchronize(s->st);
+    free_work(s->wk);
+    free_nodes(s->ns);
+    dfree(s->dStatus);
+    dfree(s->dLamRes);
+    dfree(s->dRelresRes);
+    dfree(s->dXRes);
+    for (cudaEvent_t e : s->join) cudaEventDestroy(e);
+    for (cudaStream_t t : s->side) cudaStreamDestroy(t);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+}
+
+int feast_nl_slices_create(feast_nl_slices** out, feast_nl_handle* h, int32_t ndisc,
+                           const double* c_re, const double* c_im, const double* ra,
+                           const double* rb, int32_t nc, int32_t rule, void* stream) {
+    g_last_error.clear();
+    if (!out) return fail(FEAST_NL_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    CKS(validate_handle(h));
+    if (ndisc < 1 || ndisc > 4096) return fail(FEAST_NL_EINVAL, "ndisc must be in [1, 4096]");
+    if (!c_re || !c_im || !ra || !rb) return fail(FEAST_NL_EINVAL, "contour arrays are NULL");
+    feast_nl_slices* s = new (std::nothrow) feast_nl_slices();
+    if (!s) return fail(FEAST_NL_ENOMEM, "host allocation failed");
+    s->h = h;
+    auto cleanup = [&](int st) { feast_nl_slices_destroy(s); return st; };
+    cudaError_t e;
+    if (stream) {
+        s->st = static_cast<cudaStream_t>(stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking)) != cudaSuccess)
+            return cleanup(fail_cuda(e, "cudaStreamCreate", __LINE__));
+        s->own_stream = true;
+    }
+    AllocScope as(s->st);
+    // the problem's device data may still be in flight on the handle's stream
+    if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return cleanup(fail_cuda(e, "sync", __LINE__));
+    const int nside = std::min<int>(ndisc, kMaxSide);
+    for (int i = 0; i < nside; ++i) {
+        cudaStream_t t = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking)) != cudaSuccess)
+            return cleanup(fail_cuda(e, "cudaStreamCreate", __LINE__));
+        s->side.push_back(t);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cleanup(fail_cuda(e, "cudaEventCreate", __LINE__));
+        s->join.push_back(ev);
+    }
+    if ((e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreate(&s->ev0)) != cudaSuccess || (e = cudaEventCreate(&s->ev1)) != cudaSuccess)
+        return cleanup(fail_cuda(e, "cudaEventCreate", __LINE__));
+    if ((e = dalloc(&s->dStatus, 1)) != cudaSuccess) return cleanup(fail_cuda(e, "allocation", __LINE__));
+    const int rc = build_nodes(h, s->ns, ndisc, c_re, c_im, ra, rb, nc, rule, s->st, s->dStatus, false);
+    if (rc != FEAST_NL_OK) return cleanup(rc);
+    *out = s;
+    return FEAST_NL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Runs f(Disc) for every contour, each on its own side stream, between a fork
+// from and a join back into the set's stream (a fan-out in a captured graph).
+template <class F>
+int per_disc(feast_nl_slices* s, int m, F&& f) {
+    const int nd = s->ns.nd;
+    const int nside = (int)s->side.size();
+    CK(cudaEventRecord(s->fork, s->st));
+    for (int i = 0; i < nside; ++i) CK(cudaStreamWaitEvent(s->side[i], s->fork, 0));
+    for (int d = 0; d < nd; ++d)
+        CKS(f(disc_view(s->h, s->ns, s->wk, d, m, s->side[d % nside], false)));
+    for (int i = 0; i < nside; ++i) {
+        CK(cudaEventRecord(s->join[i], s->side[i]));
+        CK(cudaStreamWaitEvent(s->st, s->join[i], 0));
+    }
+    return FEAST_NL_OK;
+}
+
+// Steps 1-3 for every contour: one product A_t Q over all contours, then each
+// contour's Rayleigh-Ritz and residual test in parallel.
+int slices_ritz(feast_nl_slices* s, int m, double tol) {
+    feast_nl_handle* h = s->h;
+    CKS(apply_terms(h, s->wk, s->ns.nd, m, s->wk.Q, s->wk.W, s->st, &s->dStatus->flags));
+    return per_disc(s, m, [&](const Disc& D) { return ritz_and_residual(h, D, tol); });
+}
+
+// Steps 4-5 for every contour: all node solves in one batch, then each
+// contour's accumulation and orthonormalisation in parallel.
+int slices_filter(feast_nl_slices* s, int m) {
+    feast_nl_handle* h = s->h;
+    CKS(filter_solve(h, s->ns, s->wk, s->ns.nd, m, s->st, &s->dStatus->flags, false));
+    return per_disc(s, m, [&](const Disc& D) {
+        CKS(filter_accumulate(h, D));
+        return orthonormalize(h, D);
+    });
+}
+
+// Keeps contour d's current pairs as its result.
+int slices_keep(feast_nl_slices* s, int d, int m) {
+    const int64_t n = s->h->n;
+    const Disc D = disc_view(s->h, s->ns, s->wk, d, m, s->st, false);
+    CK(cudaMemcpyAsync(s->dLamRes + (int64_t)d * m, D.Lam, sizeof(double2) * m, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(s->dRelresRes + (int64_t)d * m, D.Relres, sizeof(double) * m, cudaMemcpyDeviceToDevice, s->st));
+    CK(cudaMemcpyAsync(s->dXRes + (int64_t)d * n * m, D.X, sizeof(double2) * n * m, cudaMemcpyDeviceToDevice, s->st));
+    return FEAST_NL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t maxit,
+                          uint64_t seed, int32_t flags, feast_nl_info* infos) {
+    g_last_error.clear();
+    if (!s) return fail(FEAST_NL_EINVAL, "null slices");
+    feast_nl_handle* h = s->h;
+    AllocScope as(s->st);
+    const int nd = s->ns.nd;
+    if (infos) std::memset(infos, 0, sizeof(feast_nl_info) * nd);
+    CKS(check_solve_args(h, m0, tol, maxit));
+    const int m = m0;
+    const int64_t n = h->n;
+    s->have_result = false;
+    if (s->wk.mcap != m || s->wk.nd != nd) {
+        CKS(alloc_work(h, s->wk, nd, s->ns.nc, m));
+        dfree(s->dLamRes);
+        dfree(s->dRelresRes);
+        dfree(s->dXRes);
+        CK(dalloc(&s->dLamRes, (size_t)nd * m));
+        CK(dalloc(&s->dRelresRes, (size_t)nd * m));
+        CK(dalloc(&s->dXRes, (size_t)nd * n * m));
+    }
+    const bool use_graph = (flags & FEAST_NL_SLICES_NO_GRAPH) == 0;
+    CK(cudaMemsetAsync(s->wk.Status, 0, sizeof(IterStatus) * nd, s->st));
+    CK(cudaMemsetAsync(s->dStatus, 0, sizeof(IterStatus), s->st));   // the batched steps' flags
+    CK(cudaEventRecord(s->ev0, s->st));
+    CK(random_block(s->st, n, nd * m, seed, s->wk.Q));
+    CKS(per_disc(s, m, [&](const Disc& D) { return orthonormalize(h, D); }));   // Step 0
+    CKS(slices_ritz(s, m, tol));                                                 // Steps 1-3
+    if (h->precision != FEAST_NL_FP64)           // tune the node solves before any capture
+        lu_solve_pick_bn(s->st, n, lu_block_size<float2>(), static_cast<const float2*>(s->ns.dF),
+                         n * n, s->ns.dGather, s->ns.dGcount, nd * s->ns.nc,
+                         static_cast<float2*>(s->wk.Y), n * m, m, &s->dStatus->flags);
+    // the rest of every iteration (Steps 4, 5, 1-3) as one graph
+    cudaGraphExec_t exec = nullptr;
+    int64_t per_iter = 0;
+    if (use_graph) {
+        cudaGraph_t graph = nullptr;
+        const uint64_t l0 = launch_count();
+        CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+        int rc = slices_filter(s, m);
+        if (rc == FEAST_NL_OK) rc = slices_ritz(s, m, tol);
+        const cudaError_t ec = cudaStreamEndCapture(s->st, &graph);
+        if (rc != FEAST_NL_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        CK(ec);
+        per_iter = (int64_t)(launch_count() - l0);
+        note_launch(-(int)per_iter);          // captured, not launched: counted at each replay
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+    }
+    auto run_iteration = [&]() -> int {
+        if (exec) {
+            CK(cudaGraphLaunch(exec, s->st));
+            // the graph's kernels count as launches of this library
+            note_launch((int)per_iter);
+            return FEAST_NL_OK;
+        }
+        CKS(slices_filter(s, m));
+        return slices_ritz(s, m, tol);
+    };
+    std::vector<IterStatus> stt(nd), kept(nd);
+    std::vector<char> done(nd, 0), conv_at(nd, 0);
+    IterStatus wide{};
+    int remaining = nd, it = 1;
+    int rc = FEAST_NL_OK;
+    for (it = 1; it <= maxit; ++it) {
+        if (it > 1) {
+            rc = run_iteration();
+            if (rc != FEAST_NL_OK) break;
+        }
+        cudaError_t e = cudaMemcpyAsync(stt.data(), s->wk.Status, sizeof(IterStatus) * nd,
+                                        cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&wide, s->dStatus, sizeof(IterStatus), cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) {
+            rc = fail_cuda(e, "status read", __LINE__);
+            break;
+        }
+        if (wide.flags & 16) {
+            rc = fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in a batched step");
+            break;
+        }
+        for (int d = 0; d < nd; ++d) {
+            if (done[d]) continue;
+            const bool conv = it > 1 && stt[d].n_conv == stt[d].n_inside;
+            const bool fatal = (stt[d].flags & (2 | 16)) != 0;
+            if (conv || fatal || it == maxit) {
+                rc = slices_keep(s, d, m);
+                if (rc != FEAST_NL_OK) break;
+                done[d] = 1;
+                conv_at[d] = conv;
+                kept[d] = stt[d];
+                --remaining;
+                if (infos) {
+                    infos[d].iters = it;
+                    infos[d].n_inside = stt[d].n_inside;
+                    infos[d].n_converged = stt[d].n_conv;
+                    infos[d].status = contour_status(stt[d], conv, m);
+                    infos[d].max_relres = stt[d].max_relres;
+                }
+            }
+        }
+        if (rc != FEAST_NL_OK || remaining == 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    CKS(rc);
+    CK(cudaEventRecord(s->ev1, s->st));
+    CK(cudaEventSynchronize(s->ev1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+    int worst = FEAST_NL_OK;
+    for (int d = 0; d < nd; ++d) {
+        if (infos) {
+            infos[d].ms_factor = s->ns.ms_factor;
+            infos[d].ms_iterate = ms;
+        }
+        const int sd = contour_status(kept[d], conv_at[d] != 0, m);
+        if (sd == FEAST_NL_EDEVICE) worst = sd;
+        else if (worst == FEAST_NL_OK && sd != FEAST_NL_OK) worst = sd;
+    }
+    s->m_last = m;
+    s->have_result = true;
+    s->graph_launches = per_iter;
+    if (worst != FEAST_NL_OK) g_last_error = "some contours did not converge (see their infos)";
+    return worst;
+}
+
+int feast_nl_slices_get_eigpairs(feast_nl_slices* s, int32_t disc, int32_t capacity,
+                                 int32_t* m_out, double* lambda, void* X, double* relres,
+                                 int32_t inside_only) {
+    g_last_error.clear();
+    if (!s) return fail(FEAST_NL_EINVAL, "null slices");
+    AllocScope as(s->st);
+    if (!s->have_result) return fail(FEAST_NL_EINVAL, "no solve result");
+    if (disc < 0 || disc >= s->ns.nd) return fail(FEAST_NL_EINVAL, "disc out of range");
+    if (capacity < 0 || !m_out) return fail(FEAST_NL_EINVAL, "bad capacity or m_out");
+    const int m = s->m_last;
+    const int64_t n = s->h->n;
+    return copy_pairs(s->h, s->st, s->wk.Qt, s->wk.Stage, m, s->dLamRes + (int64_t)disc * m,
+                      s->dRelresRes + (int64_t)disc * m, s->dXRes + (int64_t)disc * n * m,
+                      s->ns.c_re[disc], s->ns.c_im[disc], s->ns.ra[disc], s->ns.rb[disc], capacity,
+                      m_out, lambda, X, relres, inside_only);
+}
+
+int64_t feast_nl_slices_graph_launches(feast_nl_slices* s) { return s ? s->graph_launches : -1; }
 
 }  // extern "C"

@@ -149,10 +149,10 @@ cudaError_t assemble_nodes(cudaStream_t st, int64_t n, int nA, const double2* A,
 
 // complex normal start block (counter-based: splitmix64 + Box-Muller), n x m col-major
 cudaError_t random_block(cudaStream_t st, int64_t n, int m, uint64_t seed, double2* X);
-// Y_j <- convert(R) for every node
+// Y_b <- convert(R_{b / nc}) for the nd * nc nodes b (R: nd blocks of n x m)
 template <typename T>
-cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nc, T* Y,
-                          int64_t strideY);
+cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nd, int nc,
+                          T* Y, int64_t strideY);
 cudaError_t filter_coefficients(cudaStream_t st, int nc, int m, const double2* z,
                                 const double2* w, const double2* lam, double2* coef,
                                 double2* fsum, IterStatus* status);
@@ -179,7 +179,9 @@ template <typename T>
 cudaError_t to_double(cudaStream_t st, int64_t cnt, const T* src, double2* dst);
 // Y = I (m x m), ones[0..m) = 1
 cudaError_t set_identity(cudaStream_t st, int m, double2* Y, double* ones);
-cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nterms,
+// identity terms of W (layout of ozaki_gemm, nd blocks of m columns): slot t of
+// block b <- Q_b
+cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nd, int nterms,
                                 const TermDev* terms, const double2* Q, double2* W);
 
 // ------------------------------------------------------------------ digit-split products (k_ozaki.cu)
@@ -202,10 +204,12 @@ cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, d
 // tau (m doubles) and the s digit slices of the real embedding of Q (n x m col-major)
 cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double2* Q, double* tau,
                           void* slices, const OzakiLayout& L);
-// W + term_slot[t] * n * m  <-  A_t Q for t < nterms (complex128, col-major, ld n);
-// a failed internal wait sets bit 4 of *err.
-cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, int nterms,
-                       const void* Aslices, const double* sigma, const void* Qslices,
+// A_t Q for the dense terms t < nterms, Q = n x m (complex128, col-major, ld n)
+// made of m / mb blocks of mb columns (one block per contour); W holds per block
+// `wterms` n x mb slots and A_t Q_b goes to slot term_slot[t] of block b:
+// W + (b * wterms + term_slot[t]) * n * mb.  A failed internal wait sets bit 4 of *err.
+cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, const OzakiLayout& L,
+                       int nterms, const void* Aslices, const double* sigma, const void* Qslices,
                        const double* tau, double2* W, const int* term_slot, int* err);
 
 // ------------------------------------------------------------------ LU (k_lu.cu)
@@ -218,18 +222,29 @@ int lu_gather_stride(int64_t n, int nb);
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
                               int* piv, int nc, int* info, int2* gather, int* gcount, int* err);
+// bn: tile width of the complex64 tensor-core updates (0 = cgemm_default_bn)
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y,
-                             int64_t strideY, int m, int* err);
+                             int64_t strideY, int m, int* err, int bn = 0);
+// Autotuner of the complex64 solves: the tile width for nc systems of order n
+// with m right-hand sides, chosen once per (n, m, nc) in the process by timing
+// lu_solve_batched with every width on the given factors and on Y (which it
+// overwrites: pass a scratch or not-yet-filled block), then cached.  During a
+// stream capture, or when timing fails, the cached or default width is returned.
+int lu_solve_pick_bn(cudaStream_t st, int64_t n, int nb, const float2* F, int64_t strideF,
+                     const int2* gather, const int* gcount, int nc, float2* Y, int64_t strideY,
+                     int m, int* err);
 
 // ------------------------------------------------------------------ k_cgemm_tc.cu
 // C -= A B (complex64, column-major, batch z advances A, B, C by sA, sB, sC) on
 // the TF32 tensor cores with FP32-level accuracy (three TF32 products of the
-// split operands); a failed internal wait sets bit 4 of *err.
+// split operands); a failed internal wait sets bit 4 of *err.  bn: complex
+// columns per CTA tile (16, 32, 48 or 64; 0 = the widest with the least waste).
 cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda,
                              int64_t sA, const float2* B, int64_t ldb, int64_t sB, float2* C,
-                             int64_t ldc, int64_t sC, int batch, int* err);
+                             int64_t ldc, int64_t sC, int batch, int* err, int bn = 0);
+int cgemm_default_bn(int n);
 template <typename T> int lu_block_size();
 
 // ------------------------------------------------------------------ reduced problem (k_reduced.cu)
@@ -244,7 +259,7 @@ size_t reduced_work_bytes(int m, int kmax);
 // Steps 1-2 for general T (any term kinds): G = [G_0 | .. | G_{T-1}] (m x T m,
 // G_t = Q^H A_t Q, scales applied through `terms`).  Eigenvalues of
 // That(z) = sum_t f_t(z) G_t inside the contour scaled by 1.5 from the first two
-// contour moments (FP64, 256 trapezoid nodes, probe drawn from probe_seed), ranked
+// contour moments (FP32, 256 trapezoid nodes, probe drawn from probe_seed), ranked
 // by Step 2's rule, refined by Newton; slots beyond the moments' rank get
 // lambda = c + 1.5 ra and unit vectors.  m <= beyn_max_m().
 size_t beyn_work_bytes(int m);

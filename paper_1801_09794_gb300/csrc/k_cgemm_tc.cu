@@ -283,16 +283,29 @@ cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_
 }
 }  // namespace
 
+int cgemm_default_bn(int n) {
+    // the widest tile that wastes the fewest columns (e.g. 48 for 96 right-hand sides)
+    int best = 64, waste = ((n + 63) / 64) * 64 - n;
+    for (int bn : {48, 32, 16}) {
+        const int w = ((n + bn - 1) / bn) * bn - n;
+        if (w < waste) { best = bn; waste = w; }
+    }
+    return best;
+}
+
 cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda,
                              int64_t sA, const float2* B, int64_t ldb, int64_t sB, float2* C,
-                             int64_t ldc, int64_t sC, int batch, int* err) {
+                             int64_t ldc, int64_t sC, int batch, int* err, int bn) {
     if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return cudaSuccess;
     if (batch > 65535) return cudaErrorInvalidValue;
-    // the narrower tile when it wastes fewer columns (e.g. 96 right-hand sides)
-    const int waste64 = ((n + 63) / 64) * 64 - n, waste48 = ((n + 47) / 48) * 48 - n;
-    if (waste48 < waste64)
-        return launch<48>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
-    return launch<64>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+    if (bn == 0) bn = cgemm_default_bn(n);
+    switch (bn) {
+        case 16: return launch<16>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+        case 32: return launch<32>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+        case 48: return launch<48>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+        case 64: return launch<64>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace fnl

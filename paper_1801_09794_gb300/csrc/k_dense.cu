@@ -451,8 +451,10 @@ __global__ void broadcast_rhs_kernel(int64_t nm, const double2* __restrict__ R, 
                                      T* __restrict__ Y, int64_t strideY) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nm) return;
-    T v = from_d2<T>(R[e]);
-    for (int j = 0; j < nc; ++j) Y[j * strideY + e] = v;
+    const int d = blockIdx.y;                      // contour: nodes d*nc .. d*nc+nc-1
+    T v = from_d2<T>(R[d * nm + e]);
+    T* Yd = Y + (int64_t)d * nc * strideY;
+    for (int j = 0; j < nc; ++j) Yd[j * strideY + e] = v;
 }
 __global__ void filter_coef_kernel(int nc, int m, const double2* __restrict__ z,
                                    const double2* __restrict__ w,
@@ -496,16 +498,17 @@ cudaError_t random_block(cudaStream_t st, int64_t n, int m, uint64_t seed, doubl
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nc, T* Y,
-                          int64_t strideY) {
+cudaError_t broadcast_rhs(cudaStream_t st, int64_t n, int m, const double2* R, int nd, int nc,
+                          T* Y, int64_t strideY) {
     int64_t nm = n * m;
     note_launch();
-    broadcast_rhs_kernel<T><<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, R, nc, Y, strideY);
+    dim3 g((unsigned)((nm + 255) / 256), (unsigned)nd);
+    broadcast_rhs_kernel<T><<<g, 256, 0, st>>>(nm, R, nc, Y, strideY);
     return cudaGetLastError();
 }
-template cudaError_t broadcast_rhs<double2>(cudaStream_t, int64_t, int, const double2*, int,
+template cudaError_t broadcast_rhs<double2>(cudaStream_t, int64_t, int, const double2*, int, int,
                                             double2*, int64_t);
-template cudaError_t broadcast_rhs<float2>(cudaStream_t, int64_t, int, const double2*, int,
+template cudaError_t broadcast_rhs<float2>(cudaStream_t, int64_t, int, const double2*, int, int,
                                            float2*, int64_t);
 cudaError_t filter_coefficients(cudaStream_t st, int nc, int m, const double2* z,
                                 const double2* w, const double2* lam, double2* coef,
@@ -633,9 +636,11 @@ __global__ void copy_identity_kernel(int64_t nm, int nterms, const TermDev* __re
                                      const double2* __restrict__ Q, double2* __restrict__ W) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nm) return;
-    double2 q = Q[e];
+    const int d = blockIdx.y;                      // contour block
+    double2 q = Q[d * nm + e];
+    double2* Wd = W + (int64_t)d * nterms * nm;
     for (int t = 0; t < nterms; ++t)
-        if (terms[t].aidx < 0) W[t * nm + e] = q;
+        if (terms[t].aidx < 0) Wd[t * nm + e] = q;
 }
 }  // namespace
 
@@ -678,11 +683,12 @@ cudaError_t form_reduced(cudaStream_t st, int m, int nterms, int kmax, const Ter
                                                                       Ahat);
     return cudaGetLastError();
 }
-cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nterms,
+cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nd, int nterms,
                                 const TermDev* terms, const double2* Q, double2* W) {
     int64_t nm = n * m;
     note_launch();
-    copy_identity_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, nterms, terms, Q, W);
+    dim3 g((unsigned)((nm + 255) / 256), (unsigned)nd);
+    copy_identity_kernel<<<g, 256, 0, st>>>(nm, nterms, terms, Q, W);
     return cudaGetLastError();
 }
 

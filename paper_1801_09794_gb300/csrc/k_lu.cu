@@ -20,6 +20,10 @@
 // panel's elimination (the order Gaussian elimination itself uses), which is
 // equivalent to P T = L U and saves the strided row traffic on L.
 #include "internal.h"
+
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <climits>
 
 namespace fnl {
@@ -447,14 +451,14 @@ cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64
 // C -= A B: FP64 SIMT for complex128, tensor cores for complex64.
 cudaError_t update(cudaStream_t st, int m, int n, int k, const double2* A, int64_t lda, int64_t sA,
                    const double2* B, int64_t ldb, int64_t sB, double2* C, int64_t ldc, int64_t sC,
-                   int batch, int*) {
+                   int batch, int*, int) {
     return gemm<double2>(st, 0, m, n, k, make_double2(-1.0, 0.0), A, lda, sA, B, ldb, sB,
                          make_double2(1.0, 0.0), C, ldc, sC, batch);
 }
 cudaError_t update(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda, int64_t sA,
                    const float2* B, int64_t ldb, int64_t sB, float2* C, int64_t ldc, int64_t sC,
-                   int batch, int* err) {
-    return cgemm_sub_tf32x3(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+                   int batch, int* err, int bn) {
+    return cgemm_sub_tf32x3(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, bn);
 }
 
 }  // namespace
@@ -486,7 +490,7 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
                 (int)(k0 + jb), (int)rest);
             e = update(st, (int)rest, (int)rest, jb, F + (k0 + jb) + k0 * n, n, strideF,
                        F + k0 + (k0 + jb) * n, n, strideF, F + (k0 + jb) + (k0 + jb) * n, n,
-                       strideF, nc, err);
+                       strideF, nc, err, 0);
             if (e != cudaSuccess) return e;
         }
     }
@@ -496,7 +500,7 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y, int64_t strideY,
-                             int m, int* err) {
+                             int m, int* err, int bn) {
     const int gstride = lu_gather_stride(n, nb);
     cudaError_t e;
     dim3 g((unsigned)((m + kWarpsPerCta - 1) / kWarpsPerCta), nc);
@@ -508,7 +512,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
             e = update(st, (int)rest, m, jb, F + (k0 + jb) + k0 * n, n, strideF, Y + k0, n,
-                       strideY, Y + k0 + jb, n, strideY, nc, err);
+                       strideY, Y + k0 + jb, n, strideY, nc, err, bn);
             if (e != cudaSuccess) return e;
         }
     }
@@ -520,7 +524,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
                                                               strideY, m);
         if (k0 > 0) {
             e = update(st, (int)k0, m, jb, F + k0 * n, n, strideF, Y + k0, n, strideY, Y, n,
-                       strideY, nc, err);
+                       strideY, nc, err, bn);
             if (e != cudaSuccess) return e;
         }
     }
@@ -533,9 +537,62 @@ template cudaError_t lu_factor_batched<float2>(cudaStream_t, int64_t, int, float
                                                int, int*, int2*, int*, int*);
 template cudaError_t lu_solve_batched<double2>(cudaStream_t, int64_t, int, const double2*,
                                                int64_t, const int2*, const int*, int, double2*,
-                                               int64_t, int, int*);
+                                               int64_t, int, int*, int);
 template cudaError_t lu_solve_batched<float2>(cudaStream_t, int64_t, int, const float2*, int64_t,
                                               const int2*, const int*, int, float2*, int64_t, int,
-                                              int*);
+                                              int*, int);
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int, int>, int> g_tuned_bn;   // (n, m, nc) -> tile width
+}  // namespace
+
+int lu_solve_pick_bn(cudaStream_t st, int64_t n, int nb, const float2* F, int64_t strideF,
+                     const int2* gather, const int* gcount, int nc, float2* Y, int64_t strideY,
+                     int m, int* err) {
+    const auto key = std::make_tuple(n, m, nc);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned_bn.find(key);
+        if (it != g_tuned_bn.end()) return it->second;
+    }
+    const int fallback = cgemm_default_bn(m);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return fallback;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return fallback;
+    }
+    int best = fallback;
+    float best_ms = 0.0f;
+    bool ok = true;
+    for (int bn : {16, 32, 48, 64}) {
+        if (bn >= 2 * m + 16 && bn != fallback) continue;   // mostly empty tiles
+        float ms_min = 0.0f;
+        for (int rep = 0; rep < 3 && ok; ++rep) {           // first run warms the kernel
+            ok = cudaEventRecord(e0, st) == cudaSuccess &&
+                 lu_solve_batched<float2>(st, n, nb, F, strideF, gather, gcount, nc, Y, strideY, m,
+                                          err, bn) == cudaSuccess &&
+                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.0f;
+            if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (rep == 1 || (rep > 1 && ms < ms_min)) ms_min = ms;
+        }
+        if (!ok) break;
+        if (best_ms == 0.0f || ms_min < best_ms) { best_ms = ms_min; best = bn; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) {
+        cudaGetLastError();
+        return fallback;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_bn[key] = best;
+    return best;
+}
 
 }  // namespace fnl

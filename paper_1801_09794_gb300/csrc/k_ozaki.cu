@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     int s, int Mrows, int Kp, const __nv_bfloat16* __restrict__ Aslices, int64_t a_slice_stride,
     int64_t a_term_stride, const double* __restrict__ sigma, int64_t sigma_term_stride,
     const __nv_bfloat16* __restrict__ Bslices, int64_t b_slice_stride, const double* __restrict__ tau,
-    double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, const int* __restrict__ term_slot,
-    int ncols_complex, int* __restrict__ err) {
+    double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, int mb, int64_t w_block_stride,
+    const int* __restrict__ term_slot, int ncols_complex, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kOzStages];
     __shared__ uint32_t s_tmem;
@@ -259,7 +259,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
                 const int cc = col0 + colhalf * (kOzN / 2) + c;    // real column of W'
                 const int j = cc >> 1;
                 if (j < ncols_complex) {
-                    double* dst = reinterpret_cast<double*>(Wt + row + (int64_t)j * ldw) + (cc & 1);
+                    // column j belongs to block j / mb (one subspace block per contour)
+                    const int blk = j / mb, jj = j - blk * mb;
+                    double* dst = reinterpret_cast<double*>(Wt + blk * w_block_stride + row +
+                                                            (int64_t)jj * ldw) + (cc & 1);
                     *dst = sgm * tau[j] * acc[c];
                 }
             }
@@ -416,8 +419,8 @@ cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double
     return cudaGetLastError();
 }
 
-cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, int nterms,
-                       const void* Aslices, const double* sigma, const void* Qslices,
+cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, const OzakiLayout& L,
+                       int nterms, const void* Aslices, const double* sigma, const void* Qslices,
                        const double* tau, double2* W, const int* term_slot, int* err) {
     static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     const int s = L.s;
@@ -433,8 +436,8 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, const OzakiLayout& L, 
     note_launch();
     ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
         s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,
-        sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * m,
-        term_slot, m, err);
+        sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * mb, mb,
+        (int64_t)wterms * n * mb, term_slot, m, err);
     return cudaGetLastError();
 }
 

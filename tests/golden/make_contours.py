@@ -1,10 +1,12 @@
 """Writes tests/golden/contours.json: the contour of each benchmark workload and
 the eigenvalues it encloses, computed ONLY with the oracle (QZ on the companion
-pencil for n = 256, shift-invert Arnoldi for n = 4096, an oracle solve plus an
-argument-principle count for the n = 2048 delay problem).
+pencil for n = 256, shift-invert Arnoldi for n = 4096 and for the 64 discs of
+the n = 2048 cubic, an oracle solve plus an argument-principle count for the
+n = 2048 delay problem).
 
 Run from the repository root:  python tests/golden/make_contours.py
-(`python tests/golden/make_contours.py delay_n2048` refreshes that entry only.)
+(`python tests/golden/make_contours.py delay_n2048` or `... slices_n2048`
+refreshes that entry only.)
 """
 import json
 import os
@@ -17,7 +19,7 @@ sys.path.insert(0, ROOT)
 
 from oracle import (assemble, brute_force_eigs, nlfeast, normalized_radius,  # noqa: E402
                     shift_invert_nearest, winding_count)
-from workloads import config1_qep, config2_qep, delay_problem, start_block  # noqa: E402
+from workloads import config1_qep, config2_qep, cubic_pep, delay_problem, start_block  # noqa: E402
 
 
 def circle_around(lam, target, count):
@@ -83,6 +85,9 @@ def main():
     if sys.argv[1:] == ["delay_n2048"]:          # refresh that entry only
         main_delay_only(path)
         return
+    if sys.argv[1:] == ["slices_n2048"]:
+        main_slices_only(path)
+        return
     out = {}
     p1 = config1_qep(256, 0)
     lam1 = brute_force_eigs(p1)
@@ -116,6 +121,7 @@ def main():
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     main_delay_only(path)
+    main_slices_only(path)
 
 
 def main_delay_only(path):
@@ -130,6 +136,49 @@ def main_delay_only(path):
         "method": "oracle solve on the ellipse (0.2, 0.1) with m0 = 72 to 1e-11; "
                   "count checked by the argument principle with adaptive sampling"}
     print("C3", c3, r3, g3, w3)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+# spectrum slicing: the square of side 0.8 centred at 0.5 + 0.25i cut into an
+# 8 x 8 grid of cells, one inscribed disc (radius 0.05) per cell
+SLICE_CENTER, SLICE_SIDE, SLICE_GRID = 0.5 + 0.25j, 0.8, 8
+
+
+def slice_discs():
+    step = SLICE_SIDE / SLICE_GRID
+    x0 = SLICE_CENTER.real - SLICE_SIDE / 2 + step / 2
+    y0 = SLICE_CENTER.imag - SLICE_SIDE / 2 + step / 2
+    centers = [complex(x0 + i * step, y0 + j * step)
+               for j in range(SLICE_GRID) for i in range(SLICE_GRID)]
+    return centers, step / 2
+
+
+def main_slices_only(path):
+    """Every eigenvalue in each disc, from the 24 nearest its center (shift-invert
+    Arnoldi on the 6144 x 6144 companion pencil); the 24th must lie outside, so
+    none is missed, and no disc may hold 12 or more."""
+    with open(path) as f:
+        out = json.load(f)
+    p = cubic_pep(2048, 0)
+    centers, r = slice_discs()
+    eigs, margin = [], np.inf
+    for c in centers:
+        near = shift_invert_nearest(p, c, 24)
+        d = np.abs(near - c) / r
+        assert d[-1] > 1.0, (c, d[-1])
+        inside = near[d < 1.0]
+        assert len(inside) < 12, (c, len(inside))
+        margin = min(margin, float(np.min(np.abs(d - 1.0))))
+        eigs.append([[x.real, x.imag] for x in sorted(inside, key=lambda v: (v.real, v.imag))])
+    out["slices_n2048"] = {
+        "generator": "cubic_pep(n=2048, seed=0)",
+        "centers": [[c.real, c.imag] for c in centers], "r": r, "nc": 8, "rule": "gl", "m0": 16,
+        "count": int(sum(len(e) for e in eigs)), "counts": [len(e) for e in eigs],
+        "min_boundary_margin": margin, "eigs_inside": eigs,
+        "method": "shift-invert Arnoldi (24 nearest each disc center) on the first companion "
+                  "pencil through one n x n LU per disc"}
+    print("C4", len(centers), "discs,", out["slices_n2048"]["count"], "eigenvalues, margin", margin)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 

@@ -158,6 +158,20 @@ def test_oracle_matches_qz_random_pep(k):
     assert O.winding_count(p, center, r, r, nsamp=1024) == 6
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_shift_invert_nearest_matches_qz(k):
+    # the structured shift-invert behind the stored n = 4096 and n = 2048 cubic
+    # references, against QZ on the second companion form
+    n = 40
+    p = random_pep(n, k, seed=11 + k)
+    lam_all = second_companion_eigs(problem_mats(p))
+    lam_all = lam_all[np.isfinite(lam_all)]
+    sigma = 0.31 + 0.17j
+    ref = lam_all[np.argsort(np.abs(lam_all - sigma))][:10]
+    got = O.shift_invert_nearest(p, sigma, 10)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12
+
+
 def test_linear_special_case_matches_eigvals():
     n = 50
     p = linear_problem(n, seed=21)               # T = A - lambda I
