@@ -21,6 +21,7 @@
 // equivalent to P T = L U and saves the strided row traffic on L.
 #include "internal.h"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -471,30 +472,101 @@ int lu_gather_stride(int64_t n, int nb) {
     return (int)(((n + nb - 1) / nb) * 128);
 }
 
+// swap + trsm of panel k0 on the columns [c0, c0 + nc_cols), then their update
+// with the panel's L21 (all rows below the panel)
+template <typename T>
+cudaError_t panel_apply(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_t strideF,
+                        int nc, const int2* gather, const int* gcount, int gstride, int panel,
+                        int64_t c0, int64_t ncols, int* err) {
+    if (ncols <= 0) return cudaSuccess;
+    dim3 g((unsigned)((ncols + kWarpsPerCta - 1) / kWarpsPerCta), nc);
+    note_launch();
+    swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
+        n, k0, jb, F, n, strideF, gather, gcount, gstride, panel, F, n, strideF, (int)c0,
+        (int)ncols);
+    const int64_t rows = n - k0 - jb;
+    if (rows <= 0) return cudaGetLastError();
+    return update(st, (int)rows, (int)ncols, jb, F + (k0 + jb) + (int64_t)k0 * n, n, strideF,
+                  F + k0 + c0 * n, n, strideF, F + (k0 + jb) + c0 * n, n, strideF, nc, err, 0);
+}
+
+// Right-looking blocked LU with a look-ahead of one panel: after panel k is
+// factored, a high-priority stream updates only the next panel's columns and
+// factors that panel, while a low-priority stream updates every column beyond
+// it; so each panel factorisation (one CTA per node) overlaps the previous
+// panel's trailing update, and the block scheduler hands freed SMs to the
+// panel first.  Events order the two streams:
+//   high:  panel(k) -> [P] -> wait R(k-1) -> apply k to panel k+1's columns
+//   low:   wait P -> apply k to the columns right of panel k+1 -> [R(k)]
+// (the low stream's update of step k-1 covers panel k+1's columns, hence the
+// wait; panel k itself only needs what the high stream did before it).
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
                               int* piv, int nc, int* info, int2* gather, int* gcount, int* err) {
     const int gstride = lu_gather_stride(n, nb);
+    const int npanel = (int)((n + nb - 1) / nb);
     cudaError_t e;
-    for (int64_t k0 = 0, panel = 0; k0 < n; k0 += nb, ++panel) {
-        int jb = (int)((n - k0) < nb ? (n - k0) : nb);
-        if ((e = launch_panel<T>(st, n, (int)k0, jb, F, strideF, piv, nc, info, gather, gcount,
-                                 (int)panel, gstride)) != cudaSuccess)
-            return e;
-        int64_t rest = n - k0 - jb;
-        if (rest > 0) {
-            dim3 g((unsigned)((rest + kWarpsPerCta - 1) / kWarpsPerCta), nc);
-            note_launch();
-            swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
-                n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, F, n, strideF,
-                (int)(k0 + jb), (int)rest);
-            e = update(st, (int)rest, (int)rest, jb, F + (k0 + jb) + k0 * n, n, strideF,
-                       F + k0 + (k0 + jb) * n, n, strideF, F + (k0 + jb) + (k0 + jb) * n, n,
-                       strideF, nc, err, 0);
-            if (e != cudaSuccess) return e;
+    cudaStream_t hi = nullptr, side = nullptr;
+    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr;
+    auto cleanup = [&](cudaError_t r) {
+        if (evP) cudaEventDestroy(evP);
+        if (evR[0]) cudaEventDestroy(evR[0]);
+        if (evR[1]) cudaEventDestroy(evR[1]);
+        if (evH) cudaEventDestroy(evH);
+        if (side) cudaStreamDestroy(side);   // released once their work completes
+        if (hi) cudaStreamDestroy(hi);
+        return r;
+    };
+    int prio_lo = 0, prio_hi = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evH, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evR[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evR[1], cudaEventDisableTiming)) != cudaSuccess)
+        return cleanup(e);
+    // both streams start after everything already queued on st (the assembly)
+    if ((e = cudaEventRecord(evP, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(hi, evP, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
+        return cleanup(e);
+    int last_r = -1;                              // step whose side update was recorded last
+    for (int k = 0; k < npanel; ++k) {
+        const int k0 = k * nb;
+        const int jb = (int)std::min<int64_t>(nb, n - k0);
+        if ((e = launch_panel<T>(hi, n, k0, jb, F, strideF, piv, nc, info, gather, gcount, k,
+                                 gstride)) != cudaSuccess)
+            return cleanup(e);
+        const int64_t rest = n - k0 - jb;
+        if (rest <= 0) break;
+        const int64_t jn = std::min<int64_t>(nb, rest);     // next panel's columns
+        const int64_t rr = rest - jn;                        // columns beyond it
+        if (rr > 0) {
+            if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
+                return cleanup(e);
+            if ((e = panel_apply<T>(side, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
+                                    k0 + jb + jn, rr, err)) != cudaSuccess)
+                return cleanup(e);
         }
+        if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
+            return cleanup(e);
+        if (rr > 0) {
+            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return cleanup(e);
+            last_r = k;
+        }
+        if ((e = panel_apply<T>(hi, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
+                                k0 + jb, jn, err)) != cudaSuccess)
+            return cleanup(e);
     }
-    return cudaGetLastError();
+    // everything both streams did is ordered before what follows on st
+    if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
+        return cleanup(e);
+    if (last_r >= 0 && (e = cudaStreamWaitEvent(st, evR[last_r & 1], 0)) != cudaSuccess)
+        return cleanup(e);
+    return cleanup(cudaGetLastError());
 }
 
 template <typename T>
