@@ -51,9 +51,11 @@ WORKLOADS = {
     # non-polynomial T = -lambda I + A0 + A1 exp(-lambda), ellipse 2:1 at -0.9
     "delay_n2048": {"gen": "delay_problem", "n": 2048, "precision": "fp32_i8", "tol": 1e-10,
                     "maxit": 40},
-    # spectrum slicing: random cubic, 64 discs of an 8 x 8 grid, 8 nodes each
-    "slices_n2048": {"gen": "cubic_pep", "n": 2048, "precision": "fp32_i8", "tol": 1e-10,
-                     "maxit": 40, "slices": True},
+    # spectrum slicing: random cubic, 64 discs of an 8 x 8 grid, 8 nodes each; its
+    # eigenvalues are non-normal (condition ~5), so relres 1e-10 alone leaves
+    # ~5e-10 eigenvalue error: the solve stops at 1e-12, pairs count at 1e-10
+    "slices_n2048": {"gen": "cubic_pep", "n": 2048, "precision": "fp32_i8", "tol": 1e-12,
+                     "maxit": 60, "slices": True},
 }
 
 

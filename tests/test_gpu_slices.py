@@ -124,7 +124,9 @@ def test_slices_full_size_match_stored_eigenvalues(lib):
     centers = np.array([complex(*c) for c in g["centers"]])
     s = lib.FeastNL(p, "fp32_i8")
     sl = lib.Slices(s, centers, g["r"], g["r"], g["nc"], g["rule"])
-    st, infos = sl.solve(g["m0"], tol=1e-10, maxit=40, seed=0)
+    # stopping at relres 1e-12: these non-normal eigenvalues (condition ~5) need it
+    # for 1e-10 eigenvalue accuracy, as the oracle itself does
+    st, infos = sl.solve(g["m0"], tol=1e-12, maxit=60, seed=0)
     assert st == lib.FEAST_NL_OK, [i.status for i in infos]
     found = 0
     for d, c in enumerate(centers):
