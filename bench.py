@@ -40,7 +40,7 @@ BEYN_NODES = 256                    # trapezoid nodes of the projected delay pro
 # DRAM bytes per step of the dominant phase's kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, phase); the summary
 # and its command are under profiles/.  Absent: not captured for this code.
-ROOF_TRAFFIC = {("qep_mixed_n4096", "reduced"): 6 * 2017536}   # 6 iterations per step
+ROOF_TRAFFIC = {("qep_mixed_n4096", "reduced"): 6 * 2301696}   # 6 iterations per step
 TF32_OVER_BF16 = 1.1 / 2.25
 
 WORKLOADS = {
