@@ -269,6 +269,8 @@ struct feast_nl_slices {
     double2* dLamRes = nullptr;
     double* dRelresRes = nullptr;
     double2* dXRes = nullptr;
+    int* dActive = nullptr;         // per contour: 1 while it still iterates
+    std::vector<int> live;          // contours whose per-contour steps are launched
     std::vector<feast_nl_info> info;
     bool have_result = false;
     int64_t graph_launches = 0;     // kernels per replay of the iteration graph
@@ -472,7 +474,7 @@ int store_block(const feast_nl_handle* h, cudaStream_t st, double2* stage, const
 // W = [A_0 Q_d, .., A_{T-1} Q_d] for the nd contours' blocks Q_d (n x m each,
 // contiguous) at once: one product over all nd m columns (identity terms copy Q).
 int apply_terms(const feast_nl_handle* h, const Work& wk, int nd, int m, const double2* Q,
-                double2* W, cudaStream_t st, int* err) {
+                double2* W, cudaStream_t st, int* err, const int* active = nullptr) {
     const int64_t n = h->n;
     const int T = h->nterms;
     const int M = nd * m;
@@ -481,7 +483,8 @@ int apply_terms(const feast_nl_handle* h, const Work& wk, int nd, int m, const d
         // all dense terms and all contours at once on the BF16 tensor cores
         const OzakiLayout L = ozaki_layout(n, M, h->oz_s);
         CK(ozaki_split_Q(st, n, M, h->oz_s, Q, wk.Tau, wk.Qsl, L));
-        CK(ozaki_gemm(st, n, M, m, T, L, h->nA, h->dAsl, h->dSigma, wk.Qsl, wk.Tau, W, h->dSlot, err));
+        CK(ozaki_gemm(st, n, M, m, T, L, h->nA, h->dAsl, h->dSigma, wk.Qsl, wk.Tau, W, h->dSlot, err,
+                      active));
         CK(copy_identity_terms(st, n, m, nd, T, h->dTerms, Q, W));
         return FEAST_NL_OK;
     }
@@ -556,7 +559,7 @@ int ritz_and_residual(feast_nl_handle* h, const Disc& D, double tol) {
 // Step 4, first half, for every contour at once: each contour's T(X, Lambda)
 // is copied to its nodes and all nd * nc systems are solved as one batch.
 int filter_solve(feast_nl_handle* h, const NodeSet& ns, const Work& wk, int nd, int m,
-                 cudaStream_t st, int* err, bool prof) {
+                 cudaStream_t st, int* err, bool prof, const int* active = nullptr) {
     Phase ph(h, FEAST_NL_PH_SOLVE, prof);
     const int64_t n = h->n;
     const int nb = nd * ns.nc;
@@ -565,7 +568,7 @@ int filter_solve(feast_nl_handle* h, const NodeSet& ns, const Work& wk, int nd, 
         CK(broadcast_rhs<double2>(st, n, m, wk.R, nd, ns.nc, Y, n * m));
         CK(lu_solve_batched<double2>(st, n, lu_block_size<double2>(),
                                      static_cast<const double2*>(ns.dF), n * n, ns.dGather,
-                                     ns.dGcount, nb, Y, n * m, m, err));
+                                     ns.dGcount, nb, Y, n * m, m, err, 0, active, ns.nc));
     } else {
         float2* Y = static_cast<float2*>(wk.Y);
         const float2* F = static_cast<const float2*>(ns.dF);
@@ -574,7 +577,7 @@ int filter_solve(feast_nl_handle* h, const NodeSet& ns, const Work& wk, int nd, 
                                         ns.dGcount, nb, Y, n * m, m, err);
         CK(broadcast_rhs<float2>(st, n, m, wk.R, nd, ns.nc, Y, n * m));
         CK(lu_solve_batched<float2>(st, n, lu_block_size<float2>(), F, n * n, ns.dGather,
-                                    ns.dGcount, nb, Y, n * m, m, err, bn));
+                                    ns.dGcount, nb, Y, n * m, m, err, bn, active, ns.nc));
     }
     return FEAST_NL_OK;
 }
@@ -1255,6 +1258,7 @@ void feast_nl_slices_destroy(feast_nl_slices* s) {
     dfree(s->dLamRes);
     dfree(s->dRelresRes);
     dfree(s->dXRes);
+    dfree(s->dActive);
     for (cudaEvent_t e : s->join) cudaEventDestroy(e);
     for (cudaStream_t t : s->side) cudaStreamDestroy(t);
     if (s->fork) cudaEventDestroy(s->fork);
@@ -1314,15 +1318,15 @@ int feast_nl_slices_create(feast_nl_slices** out, feast_nl_handle* h, int32_t nd
 
 namespace {
 
-// Runs f(Disc) for every contour, each on its own side stream, between a fork
-// from and a join back into the set's stream (a fan-out in a captured graph).
+// Runs f(Disc) for every contour of s->live, each on its own side stream,
+// between a fork from and a join back into the set's stream (a fan-out in a
+// captured graph).
 template <class F>
 int per_disc(feast_nl_slices* s, int m, F&& f) {
-    const int nd = s->ns.nd;
     const int nside = (int)s->side.size();
     CK(cudaEventRecord(s->fork, s->st));
     for (int i = 0; i < nside; ++i) CK(cudaStreamWaitEvent(s->side[i], s->fork, 0));
-    for (int d = 0; d < nd; ++d)
+    for (int d : s->live)
         CKS(f(disc_view(s->h, s->ns, s->wk, d, m, s->side[d % nside], false)));
     for (int i = 0; i < nside; ++i) {
         CK(cudaEventRecord(s->join[i], s->side[i]));
@@ -1335,7 +1339,8 @@ int per_disc(feast_nl_slices* s, int m, F&& f) {
 // contour's Rayleigh-Ritz and residual test in parallel.
 int slices_ritz(feast_nl_slices* s, int m, double tol) {
     feast_nl_handle* h = s->h;
-    CKS(apply_terms(h, s->wk, s->ns.nd, m, s->wk.Q, s->wk.W, s->st, &s->dStatus->flags));
+    CKS(apply_terms(h, s->wk, s->ns.nd, m, s->wk.Q, s->wk.W, s->st, &s->dStatus->flags,
+                    s->dActive));
     return per_disc(s, m, [&](const Disc& D) { return ritz_and_residual(h, D, tol); });
 }
 
@@ -1343,7 +1348,7 @@ int slices_ritz(feast_nl_slices* s, int m, double tol) {
 // contour's accumulation and orthonormalisation in parallel.
 int slices_filter(feast_nl_slices* s, int m) {
     feast_nl_handle* h = s->h;
-    CKS(filter_solve(h, s->ns, s->wk, s->ns.nd, m, s->st, &s->dStatus->flags, false));
+    CKS(filter_solve(h, s->ns, s->wk, s->ns.nd, m, s->st, &s->dStatus->flags, false, s->dActive));
     return per_disc(s, m, [&](const Disc& D) {
         CKS(filter_accumulate(h, D));
         return orthonormalize(h, D);
@@ -1385,6 +1390,13 @@ int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t ma
         CK(dalloc(&s->dRelresRes, (size_t)nd * m));
         CK(dalloc(&s->dXRes, (size_t)nd * n * m));
     }
+    if (!s->dActive) CK(dalloc(&s->dActive, (size_t)nd));
+    // every contour iterates until it passes Step 3; then the batched steps (A_t Q
+    // and the node solves) skip it, its pairs being kept from that iteration
+    std::vector<int> active(nd, 1);
+    CK(cudaMemcpyAsync(s->dActive, active.data(), sizeof(int) * nd, cudaMemcpyHostToDevice, s->st));
+    s->live.resize(nd);
+    for (int d = 0; d < nd; ++d) s->live[d] = d;
     const bool use_graph = (flags & FEAST_NL_SLICES_NO_GRAPH) == 0;
     CK(cudaMemsetAsync(s->wk.Status, 0, sizeof(IterStatus) * nd, s->st));
     CK(cudaMemsetAsync(s->dStatus, 0, sizeof(IterStatus), s->st));   // the batched steps' flags
@@ -1396,24 +1408,32 @@ int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t ma
         lu_solve_pick_bn(s->st, n, lu_block_size<float2>(), static_cast<const float2*>(s->ns.dF),
                          n * n, s->ns.dGather, s->ns.dGcount, nd * s->ns.nc,
                          static_cast<float2*>(s->wk.Y), n * m, m, &s->dStatus->flags);
-    // the rest of every iteration (Steps 4, 5, 1-3) as one graph
+    // the rest of every iteration (Steps 4, 5, 1-3) as one graph over the
+    // contours of s->live, captured again whenever that set has halved
     cudaGraphExec_t exec = nullptr;
-    int64_t per_iter = 0;
-    if (use_graph) {
+    int64_t per_iter = 0, first_graph = 0;
+    auto capture = [&]() -> int {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
         cudaGraph_t graph = nullptr;
         const uint64_t l0 = launch_count();
         CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-        int rc = slices_filter(s, m);
-        if (rc == FEAST_NL_OK) rc = slices_ritz(s, m, tol);
+        int rc2 = slices_filter(s, m);
+        if (rc2 == FEAST_NL_OK) rc2 = slices_ritz(s, m, tol);
         const cudaError_t ec = cudaStreamEndCapture(s->st, &graph);
-        if (rc != FEAST_NL_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (rc2 != FEAST_NL_OK) { if (graph) cudaGraphDestroy(graph); return rc2; }
         CK(ec);
         per_iter = (int64_t)(launch_count() - l0);
         note_launch(-(int)per_iter);          // captured, not launched: counted at each replay
+        if (!first_graph) first_graph = per_iter;
         const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         CK(ei);
-    }
+        return FEAST_NL_OK;
+    };
+    if (use_graph) CKS(capture());
     auto run_iteration = [&]() -> int {
         if (exec) {
             CK(cudaGraphLaunch(exec, s->st));
@@ -1457,6 +1477,7 @@ int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t ma
                 done[d] = 1;
                 conv_at[d] = conv;
                 kept[d] = stt[d];
+                active[d] = 0;
                 --remaining;
                 if (infos) {
                     infos[d].iters = it;
@@ -1468,6 +1489,19 @@ int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t ma
             }
         }
         if (rc != FEAST_NL_OK || remaining == 0) break;
+        if (2 * remaining <= (int)s->live.size()) {
+            // drop the finished contours' per-contour steps (graph and eager alike)
+            s->live.clear();
+            for (int d = 0; d < nd; ++d)
+                if (!done[d]) s->live.push_back(d);
+            if (use_graph && (rc = capture()) != FEAST_NL_OK) break;
+        }
+        // read by the next replay (stream order); the host copy outlives it
+        if (cudaMemcpyAsync(s->dActive, active.data(), sizeof(int) * nd, cudaMemcpyHostToDevice,
+                            s->st) != cudaSuccess) {
+            rc = fail_cuda(cudaGetLastError(), "contour mask", __LINE__);
+            break;
+        }
     }
     if (exec) cudaGraphExecDestroy(exec);
     CKS(rc);
@@ -1487,7 +1521,7 @@ int feast_nl_slices_solve(feast_nl_slices* s, int32_t m0, double tol, int32_t ma
     }
     s->m_last = m;
     s->have_result = true;
-    s->graph_launches = per_iter;
+    s->graph_launches = first_graph;
     if (worst != FEAST_NL_OK) g_last_error = "some contours did not converge (see their infos)";
     return worst;
 }

@@ -208,9 +208,12 @@ cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double
 // made of m / mb blocks of mb columns (one block per contour); W holds per block
 // `wterms` n x mb slots and A_t Q_b goes to slot term_slot[t] of block b:
 // W + (b * wterms + term_slot[t]) * n * mb.  A failed internal wait sets bit 4 of *err.
+// active (device, optional): column tiles whose blocks all have active[b] == 0
+// are skipped (their W blocks are left as they were).
 cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, const OzakiLayout& L,
                        int nterms, const void* Aslices, const double* sigma, const void* Qslices,
-                       const double* tau, double2* W, const int* term_slot, int* err);
+                       const double* tau, double2* W, const int* term_slot, int* err,
+                       const int* active = nullptr);
 
 // ------------------------------------------------------------------ LU (k_lu.cu)
 // The factorisation also writes, per node and panel, the panel's row interchanges
@@ -222,11 +225,14 @@ int lu_gather_stride(int64_t n, int nb);
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
                               int* piv, int nc, int* info, int2* gather, int* gcount, int* err);
-// bn: tile width of the complex64 tensor-core updates (0 = cgemm_default_bn)
+// bn: tile width of the complex64 tensor-core updates (0 = cgemm_default_bn).
+// active (device, optional): the systems of group g = node / group are skipped
+// when active[g] == 0 (a finished contour's nodes; their Y is left as it was).
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y,
-                             int64_t strideY, int m, int* err, int bn = 0);
+                             int64_t strideY, int m, int* err, int bn = 0,
+                             const int* active = nullptr, int group = 1);
 // Autotuner of the complex64 solves: the tile width for nc systems of order n
 // with m right-hand sides, chosen once per (n, m, nc) in the process by timing
 // lu_solve_batched with every width on the given factors and on Y (which it
@@ -241,9 +247,11 @@ int lu_solve_pick_bn(cudaStream_t st, int64_t n, int nb, const float2* F, int64_
 // the TF32 tensor cores with FP32-level accuracy (three TF32 products of the
 // split operands); a failed internal wait sets bit 4 of *err.  bn: complex
 // columns per CTA tile (16, 32, 48 or 64; 0 = the widest with the least waste).
+// active (device, optional): batch entry z is skipped when active[z / group] == 0.
 cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda,
                              int64_t sA, const float2* B, int64_t ldb, int64_t sB, float2* C,
-                             int64_t ldc, int64_t sC, int batch, int* err, int bn = 0);
+                             int64_t ldc, int64_t sC, int batch, int* err, int bn = 0,
+                             const int* active = nullptr, int group = 1);
 int cgemm_default_bn(int n);
 template <typename T> int lu_block_size();
 

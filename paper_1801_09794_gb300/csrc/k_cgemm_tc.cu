@@ -70,13 +70,15 @@ template <int BN>
 __global__ void __launch_bounds__(kTcThreads, 2) cgemm_tf32x3_kernel(
     int m, int n, int k, const float2* __restrict__ A, int64_t lda, int64_t sA,
     const float2* __restrict__ B, int64_t ldb, int64_t sB, float2* __restrict__ C, int64_t ldc,
-    int64_t sC, int* __restrict__ err) {
+    int64_t sC, int* __restrict__ err, const int* __restrict__ active, int group) {
     constexpr int NR = 2 * BN;                   // real columns of the tile
     constexpr int kBtile = NR * 2 * kTcBK * 4;   // bytes of one B part
     constexpr int kStage = 2 * kTcAtile + 2 * kBtile;
     constexpr int kAIt = (kTcM / 16) * (kTcBK / 2) / 4;   // A loads per thread and stage
     constexpr int kBIt = 2 * (BN / 8) / 4;                 // B loads per thread and stage
     static_assert(BN % 16 == 0 && NR <= 256, "tile width");
+    // batch entries of a finished contour (active[z / group] == 0) do nothing
+    if (active && !active[blockIdx.z / group]) return;
 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kTcStages];
@@ -263,7 +265,7 @@ constexpr int stage_smem() {
 template <int BN>
 cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda, int64_t sA,
                    const float2* B, int64_t ldb, int64_t sB, float2* C, int64_t ldc, int64_t sC,
-                   int batch, int* err) {
+                   int batch, int* err, const int* active, int group) {
     constexpr int smem = stage_smem<BN>();
     static std::atomic<bool> attr_set[64] = {};   // idempotent setup; atomic for concurrent handles
     int dev = 0;
@@ -278,7 +280,7 @@ cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_
     dim3 grid((unsigned)((m + kTcM - 1) / kTcM), (unsigned)((n + BN - 1) / BN), (unsigned)batch);
     note_launch();
     cgemm_tf32x3_kernel<BN><<<grid, kTcThreads, smem, st>>>(m, n, k, A, lda, sA, B, ldb, sB, C, ldc,
-                                                           sC, err);
+                                                           sC, err, active, group);
     return cudaGetLastError();
 }
 }  // namespace
@@ -295,15 +297,16 @@ int cgemm_default_bn(int n) {
 
 cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda,
                              int64_t sA, const float2* B, int64_t ldb, int64_t sB, float2* C,
-                             int64_t ldc, int64_t sC, int batch, int* err, int bn) {
+                             int64_t ldc, int64_t sC, int batch, int* err, int bn,
+                             const int* active, int group) {
     if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return cudaSuccess;
     if (batch > 65535) return cudaErrorInvalidValue;
     if (bn == 0) bn = cgemm_default_bn(n);
     switch (bn) {
-        case 16: return launch<16>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
-        case 32: return launch<32>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
-        case 48: return launch<48>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
-        case 64: return launch<64>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err);
+        case 16: return launch<16>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, active, group);
+        case 32: return launch<32>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, active, group);
+        case 48: return launch<48>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, active, group);
+        case 64: return launch<64>(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, active, group);
         default: return cudaErrorInvalidValue;
     }
 }

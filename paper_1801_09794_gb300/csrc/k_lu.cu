@@ -343,9 +343,11 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
     int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF,
     const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
-    T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols) {
+    T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols, const int* __restrict__ active,
+    int group) {
     __shared__ T sL[TriMax<T>::value][TriMax<T>::value + 1];
     const int node = blockIdx.y;
+    if (active && !active[node / group]) return;     // a finished contour's nodes
     F += node * strideF;
     B += node * strideB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -391,9 +393,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
 template <typename T>
 __global__ void __launch_bounds__(32 * kWarpsPerCta) trsm_upper_kernel(
     int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF, T* B,
-    int64_t ldb, int64_t strideB, int ncols) {
+    int64_t ldb, int64_t strideB, int ncols, const int* __restrict__ active, int group) {
     __shared__ T sU[TriMax<T>::value][TriMax<T>::value + 1];
     const int node = blockIdx.y;
+    if (active && !active[node / group]) return;
     F += node * strideF;
     B += node * strideB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -452,14 +455,15 @@ cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64
 // C -= A B: FP64 SIMT for complex128, tensor cores for complex64.
 cudaError_t update(cudaStream_t st, int m, int n, int k, const double2* A, int64_t lda, int64_t sA,
                    const double2* B, int64_t ldb, int64_t sB, double2* C, int64_t ldc, int64_t sC,
-                   int batch, int*, int) {
+                   int batch, int*, int, const int* = nullptr, int = 1) {
     return gemm<double2>(st, 0, m, n, k, make_double2(-1.0, 0.0), A, lda, sA, B, ldb, sB,
                          make_double2(1.0, 0.0), C, ldc, sC, batch);
 }
 cudaError_t update(cudaStream_t st, int m, int n, int k, const float2* A, int64_t lda, int64_t sA,
                    const float2* B, int64_t ldb, int64_t sB, float2* C, int64_t ldc, int64_t sC,
-                   int batch, int* err, int bn) {
-    return cgemm_sub_tf32x3(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, bn);
+                   int batch, int* err, int bn, const int* active = nullptr, int group = 1) {
+    return cgemm_sub_tf32x3(st, m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err, bn, active,
+                            group);
 }
 
 }  // namespace
@@ -483,7 +487,7 @@ cudaError_t panel_apply(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_
     note_launch();
     swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
         n, k0, jb, F, n, strideF, gather, gcount, gstride, panel, F, n, strideF, (int)c0,
-        (int)ncols);
+        (int)ncols, nullptr, 1);
     const int64_t rows = n - k0 - jb;
     if (rows <= 0) return cudaGetLastError();
     return update(st, (int)rows, (int)ncols, jb, F + (k0 + jb) + (int64_t)k0 * n, n, strideF,
@@ -572,7 +576,7 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y, int64_t strideY,
-                             int m, int* err, int bn) {
+                             int m, int* err, int bn, const int* active, int group) {
     const int gstride = lu_gather_stride(n, nb);
     cudaError_t e;
     dim3 g((unsigned)((m + kWarpsPerCta - 1) / kWarpsPerCta), nc);
@@ -580,11 +584,12 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
         note_launch();
         swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
-            n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, 0, m);
+            n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, 0, m,
+            active, group);
         int64_t rest = n - k0 - jb;
         if (rest > 0) {
             e = update(st, (int)rest, m, jb, F + (k0 + jb) + k0 * n, n, strideF, Y + k0, n,
-                       strideY, Y + k0 + jb, n, strideY, nc, err, bn);
+                       strideY, Y + k0 + jb, n, strideY, nc, err, bn, active, group);
             if (e != cudaSuccess) return e;
         }
     }
@@ -593,10 +598,10 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
         int jb = (int)((n - k0) < nb ? (n - k0) : nb);
         note_launch();
         trsm_upper_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(n, (int)k0, jb, F, n, strideF, Y, n,
-                                                              strideY, m);
+                                                              strideY, m, active, group);
         if (k0 > 0) {
             e = update(st, (int)k0, m, jb, F + k0 * n, n, strideF, Y + k0, n, strideY, Y, n,
-                       strideY, nc, err, bn);
+                       strideY, nc, err, bn, active, group);
             if (e != cudaSuccess) return e;
         }
     }
@@ -609,10 +614,10 @@ template cudaError_t lu_factor_batched<float2>(cudaStream_t, int64_t, int, float
                                                int, int*, int2*, int*, int*);
 template cudaError_t lu_solve_batched<double2>(cudaStream_t, int64_t, int, const double2*,
                                                int64_t, const int2*, const int*, int, double2*,
-                                               int64_t, int, int*, int);
+                                               int64_t, int, int*, int, const int*, int);
 template cudaError_t lu_solve_batched<float2>(cudaStream_t, int64_t, int, const float2*, int64_t,
                                               const int2*, const int*, int, float2*, int64_t, int,
-                                              int*, int);
+                                              int*, int, const int*, int);
 
 namespace {
 std::mutex g_tune_mu;

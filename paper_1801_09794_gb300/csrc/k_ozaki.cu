@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     int64_t a_term_stride, const double* __restrict__ sigma, int64_t sigma_term_stride,
     const __nv_bfloat16* __restrict__ Bslices, int64_t b_slice_stride, const double* __restrict__ tau,
     double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, int mb, int64_t w_block_stride,
-    const int* __restrict__ term_slot, int ncols_complex, int* __restrict__ err) {
+    const int* __restrict__ term_slot, int ncols_complex, int* __restrict__ err,
+    const int* __restrict__ active) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kOzStages];
     __shared__ uint32_t s_tmem;
@@ -83,6 +84,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     const int row0 = blockIdx.y * kOzM;
     const int col0 = blockIdx.x * kOzN;                    // real column of W'
     const int term = blockIdx.z;
+    if (active) {
+        // complex columns [c_lo, c_hi] of this tile belong to blocks c / mb
+        const int c_lo = col0 / 2, c_hi = min(ncols_complex, (col0 + kOzN) / 2) - 1;
+        bool any = false;
+        for (int b = c_lo / mb; b <= c_hi / mb; ++b) any = any || active[b] != 0;
+        if (!any) return;
+    }
     const __nv_bfloat16* A = Aslices + term * a_term_stride;
     const double* sg = sigma + term * sigma_term_stride;
     double2* Wt = W + (int64_t)term_slot[term] * w_term_stride;
@@ -421,7 +429,8 @@ cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double
 
 cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, const OzakiLayout& L,
                        int nterms, const void* Aslices, const double* sigma, const void* Qslices,
-                       const double* tau, double2* W, const int* term_slot, int* err) {
+                       const double* tau, double2* W, const int* term_slot, int* err,
+                       const int* active) {
     static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     const int s = L.s;
     const int smem = kOzStages * s * (kOzM + kOzN) * kOzBK * 2;
@@ -437,7 +446,7 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, co
     ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
         s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,
         sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * mb, mb,
-        (int64_t)wterms * n * mb, term_slot, m, err);
+        (int64_t)wterms * n * mb, term_slot, m, err, active);
     return cudaGetLastError();
 }
 
