@@ -399,6 +399,74 @@ __global__ void assemble_kernel(int64_t n, int nA, const double2* __restrict__ A
         }
     }
 }
+// Complex64 node matrices are formed without FP64 arithmetic: the FP64 version
+// above is bound by the FP64 rate (4 DFMA per term, node and element), this one
+// by the HBM writes of the factors.  To keep the result as accurate as the
+// FP64 sum rounded once (the node matrices of the delay problem are
+// ill-conditioned enough for a few extra FP32 roundings to slow the iteration
+// down), every A_t entry and coefficient is split into two FP32 parts (hi + lo,
+// the lo part from the exact FP64 difference, once per element or per block),
+// each real product is formed as hi*hi with its exact FMA error plus the two
+// cross terms, and the terms are summed as an unevaluated FP32 pair (TwoSum);
+// the pair is rounded once to complex64.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_split(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+// s += x * y (x, y, s as FP32 pairs; the lo*lo term is below the FP32 ulp of the sum)
+// (explicitly rounded operations: a contraction into an FMA would break TwoSum)
+__device__ __forceinline__ void ff_madd(FF& s, FF x, FF y, float sign) {
+    const float xh = sign * x.hi, xl = sign * x.lo;
+    const float ph = __fmul_rn(xh, y.hi);
+    const float pe = fmaf(xh, y.hi, -ph);
+    const float pl = fmaf(xh, y.lo, fmaf(xl, y.hi, pe));
+    const float t = __fadd_rn(s.hi, ph);
+    const float bv = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bv)), __fsub_rn(ph, bv));
+    s.hi = t;
+    s.lo += err + pl;
+}
+template <int NA>
+__global__ void assemble_f32_kernel(int64_t n, int nA, const double2* __restrict__ A,
+                                    const double2* __restrict__ coef,
+                                    const double2* __restrict__ diagc, int nc,
+                                    float2* __restrict__ F, int64_t strideF) {
+    extern __shared__ FF s_coef[];              // (re, im) pairs: nA * nc coefficients, then nc diagonal ones
+    const int ncoef = nA * nc;
+    for (int e = threadIdx.x; e < ncoef + nc; e += blockDim.x) {
+        const double2 c = e < ncoef ? coef[e] : diagc[e - ncoef];
+        s_coef[2 * e] = ff_split(c.x);
+        s_coef[2 * e + 1] = ff_split(c.y);
+    }
+    __syncthreads();
+    const FF* s_diag = s_coef + 2 * ncoef;
+    const int64_t nn = n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const bool diag = (e % (n + 1)) == 0;
+        FF ar[NA], ai[NA];
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            const double2 v = A[t * nn + e];
+            ar[t] = ff_split(v.x);
+            ai[t] = ff_split(v.y);
+        }
+        for (int j = 0; j < nc; ++j) {
+            FF re = diag ? s_diag[2 * j] : FF{0.f, 0.f};
+            FF im = diag ? s_diag[2 * j + 1] : FF{0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < NA; ++t) {
+                const FF cr = s_coef[2 * (t * nc + j)], ci = s_coef[2 * (t * nc + j) + 1];
+                ff_madd(re, cr, ar[t], 1.f);
+                ff_madd(re, ci, ai[t], -1.f);
+                ff_madd(im, cr, ai[t], 1.f);
+                ff_madd(im, ci, ar[t], 1.f);
+            }
+            F[j * strideF + e] = make_float2(re.hi + re.lo, im.hi + im.lo);
+        }
+    }
+}
 }  // namespace
 
 template <typename T>
@@ -408,6 +476,19 @@ cudaError_t assemble_nodes(cudaStream_t st, int64_t n, int nA, const double2* A,
     int64_t nn = n * n;
     int64_t want = (nn + 255) / 256;
     int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    if constexpr (sizeof(T) == 8) {
+        const size_t smem = 2 * sizeof(float2) * (size_t)nc * (nA + 1);
+        if (nA >= 1 && nA <= 4 && smem <= 48 * 1024) {
+            note_launch();
+            switch (nA) {
+                case 1: assemble_f32_kernel<1><<<blocks, 256, smem, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+                case 2: assemble_f32_kernel<2><<<blocks, 256, smem, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+                case 3: assemble_f32_kernel<3><<<blocks, 256, smem, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+                default: assemble_f32_kernel<4><<<blocks, 256, smem, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
+            }
+            return cudaGetLastError();
+        }
+    }
     switch (nA) {
         case 1: note_launch(); assemble_kernel<T, 1><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
         case 2: note_launch(); assemble_kernel<T, 2><<<blocks, 256, 0, st>>>(n, nA, A, coef, diagc, nc, F, strideF); break;
