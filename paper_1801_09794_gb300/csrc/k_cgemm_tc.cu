@@ -19,12 +19,14 @@
 //
 // CTA: 128 threads and one 128 x BN complex tile of C, held in TMEM as 128
 // lanes x 2 BN FP32 columns.  K advances 8 complex (16 real) entries per stage
-// through a 3-stage shared-memory ring: the threads load a stage, split it and
+// through a 2-stage shared-memory ring: the threads load a stage, split it and
 // store the four parts (A_hi, A_lo, B_hi, B_lo) in the canonical K-major
 // SWIZZLE_NONE layout (8-row x 16-byte core matrices, the four K core matrices
 // of a row group side by side: LBO 128 B, SBO 512 B); thread 0 issues six
 // MMAs (M = 128, N = 2 BN, K = 8) per stage and commits the stage to its
-// mbarrier, which frees the slot three stages later.  The epilogue reads TMEM
+// mbarrier, which frees the slot two stages later (two stages rather than
+// three: the kernel is latency-bound, and the smaller ring fits three CTAs per
+// SM instead of two).  The epilogue reads TMEM
 // with lane = row of C and updates C column by column (coalesced along rows).
 #include "internal.h"
 #include "tc_common.cuh"
@@ -35,7 +37,7 @@ using namespace tc;
 
 constexpr int kTcM = 128;                      // rows of C per CTA (TMEM lanes)
 constexpr int kTcBK = 8;                       // complex K entries per stage
-constexpr int kTcStages = 3;
+constexpr int kTcStages = 2;
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcTmemCols = 128;
 constexpr int kTcAtile = kTcM * 2 * kTcBK * 4;  // bytes of one A part (8 KB)
@@ -67,7 +69,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kTcThreads, 2) cgemm_tf32x3_kernel(
+__global__ void __launch_bounds__(kTcThreads, 3) cgemm_tf32x3_kernel(
     int m, int n, int k, const float2* __restrict__ A, int64_t lda, int64_t sA,
     const float2* __restrict__ B, int64_t ldb, int64_t sB, float2* __restrict__ C, int64_t ldc,
     int64_t sC, int* __restrict__ err, const int* __restrict__ active, int group) {
