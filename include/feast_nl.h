@@ -189,6 +189,21 @@ int feast_nl_filter_apply(feast_nl_handle* h, int32_t m, const void* X,
 int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat,
                      int32_t* kmax_out);
 
+/* Grouped factorisation: sets the contour of each of count handles (arrays of
+ * count entries, as for feast_nl_set_contour, one rule for all) and factors
+ * the node matrices of all of them, whatever their orders, in one launch
+ * sequence per panel (Sec. 4.2: the nodes' linear systems are the independent
+ * parallel work of the method; here nodes of different problems share each
+ * launch).  Every handle needs complex64 factors (FP32 or FP32_I8) and
+ * n <= 4096; at most 65535 nodes in all.  stream: where the assembly and the
+ * factorisation run (NULL: a temporary stream); the call returns when they are
+ * done, after which each handle solves on its own stream as usual.
+ * Errors: EINVAL, ESINGULAR_NODE (an exact zero pivot), ENOMEM, EDEVICE; after
+ * an error none of the group's handles has a contour. */
+int feast_nl_set_contour_group(int32_t count, feast_nl_handle* const* hs, const double* c_re,
+                               const double* c_im, const double* ra, const double* rb,
+                               const int32_t* nc, int32_t rule, void* stream);
+
 /* ---- serving: continuous batching of independent requests ------------------ */
 /* No counterpart in the paper (its parallelism is over nodes and regions on
  * CPUs).  A request is one whole run of Algorithm 1 (create + set_contour +

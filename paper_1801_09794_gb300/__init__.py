@@ -4,6 +4,7 @@ The compute path is libfeast_nl.so (CUDA, C ABI in include/feast_nl.h); this
 package only builds it and binds it.
 """
 from ._binding import (FeastNL, FeastError, Server, Slices, request_footprint, load_library,  # noqa: F401
+                       set_contour_group,
                        strerror, last_error,
                        EXPORTS, LIB_PATH, feast_nl_term, feast_nl_info, launch_count,
                        PHASES)

@@ -36,7 +36,8 @@ EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_n
            "feast_nl_server_submit", "feast_nl_server_poll", "feast_nl_server_wait",
            "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy",
            "feast_nl_slices_create", "feast_nl_slices_solve", "feast_nl_slices_get_eigpairs",
-           "feast_nl_slices_graph_launches", "feast_nl_slices_destroy"]
+           "feast_nl_slices_graph_launches", "feast_nl_slices_destroy",
+           "feast_nl_set_contour_group"]
 FEAST_NL_SLICES_NO_GRAPH = 1
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
@@ -117,6 +118,7 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_slices_get_eigpairs.argtypes = [P, I32, I32, ctypes.POINTER(I32), P, P, P, I32]
     lib.feast_nl_slices_graph_launches.argtypes = [P]
     lib.feast_nl_slices_graph_launches.restype = I64
+    lib.feast_nl_set_contour_group.argtypes = [I32, P, P, P, P, P, P, I32, P]
     lib.feast_nl_slices_destroy.argtypes = [P]
     lib.feast_nl_slices_destroy.restype = None
     for name in EXPORTS:
@@ -448,3 +450,24 @@ class Slices:
             self.close()
         except Exception:
             pass
+
+
+def set_contour_group(solvers, centers, ra, rb, nc, rule="gl", stream=None):
+    """Sets one contour per FeastNL handle (their orders may differ) and factors
+    the node matrices of all of them together (feast_nl_set_contour_group)."""
+    lib = load_library()
+    k = len(solvers)
+    centers = np.asarray(centers, dtype=np.complex128).reshape(-1)
+    cre = np.ascontiguousarray(centers.real)
+    cim = np.ascontiguousarray(centers.imag)
+    ra = np.ascontiguousarray(np.broadcast_to(np.asarray(ra, dtype=np.float64), (k,)))
+    rb = np.ascontiguousarray(np.broadcast_to(np.asarray(rb, dtype=np.float64), (k,)))
+    ncs = np.ascontiguousarray(np.broadcast_to(np.asarray(nc, dtype=np.int32), (k,)))
+    hs = (ctypes.c_void_p * k)(*[s.h.value for s in solvers])
+    _check(lib.feast_nl_set_contour_group(k, hs, cre.ctypes.data, cim.ctypes.data, ra.ctypes.data,
+                                          rb.ctypes.data, ncs.ctypes.data, RULES[rule],
+                                          None if stream is None else ctypes.c_void_p(int(stream))),
+           "feast_nl_set_contour_group")
+    for s_, n_ in zip(solvers, ncs):
+        s_.nc = int(n_)
+

@@ -601,7 +601,7 @@ int filter_accumulate(feast_nl_handle* h, const Disc& D) {
 // LU factorisation.  Fails with ESINGULAR_NODE on an exact zero pivot.
 int build_nodes(feast_nl_handle* h, NodeSet& ns, int nd, const double* c_re, const double* c_im,
                 const double* ra, const double* rb, int nc, int rule, cudaStream_t st,
-                IterStatus* dstat, bool prof) {
+                IterStatus* dstat, bool prof, bool factor = true) {
     for (int d = 0; d < nd; ++d)
         if (!(ra[d] > 0.0) || !(rb[d] > 0.0) || !std::isfinite(c_re[d]) || !std::isfinite(c_im[d]))
             return fail(FEAST_NL_EINVAL, "contour needs finite center and ra, rb > 0");
@@ -709,9 +709,16 @@ int build_nodes(feast_nl_handle* h, NodeSet& ns, int nd, const double* c_re, con
                 Phase ph(h, FEAST_NL_PH_ASSEMBLE, prof);
                 CK(assemble_nodes<float2>(st, n, h->nA, h->dA, dcoef, ddiag, nb, F, n * n));
             }
-            Phase ph(h, FEAST_NL_PH_LU, prof);
-            CK(lu_factor_batched<float2>(st, n, lu_block_size<float2>(), F, n * n, ns.dpiv, nb,
-                                         ns.dinfo, ns.dGather, ns.dGcount, &dstat->flags));
+            if (factor) {
+                Phase ph(h, FEAST_NL_PH_LU, prof);
+                CK(lu_factor_batched<float2>(st, n, lu_block_size<float2>(), F, n * n, ns.dpiv, nb,
+                                             ns.dinfo, ns.dGather, ns.dGcount, &dstat->flags));
+            }
+        }
+        if (!factor) {                       // assembled only: a grouped factorisation follows
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return FEAST_NL_OK;
         }
         CK(cudaEventRecord(e1, st));
         std::vector<int> info(nb);
@@ -738,7 +745,7 @@ int build_nodes(feast_nl_handle* h, NodeSet& ns, int nd, const double* c_re, con
         ns.nd = 0;
         return rc;
     }
-    ns.ready = true;
+    ns.ready = factor;
     return FEAST_NL_OK;
 }
 
@@ -1044,6 +1051,104 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
     h->have_result = false;
     free_work(h->wk);
     return build_nodes(h, h->ns, 1, &c_re, &c_im, &ra, &rb, nc, rule, h->st, h->dStatus, true);
+}
+
+int feast_nl_set_contour_group(int32_t count, feast_nl_handle* const* hs, const double* c_re,
+                               const double* c_im, const double* ra, const double* rb,
+                               const int32_t* nc, int32_t rule, void* stream) {
+    g_last_error.clear();
+    if (count < 1 || count > 4096 || !hs || !c_re || !c_im || !ra || !rb || !nc)
+        return fail(FEAST_NL_EINVAL, "count in [1, 4096] and non-NULL arrays required");
+    int64_t nodes_total = 0;
+    for (int i = 0; i < count; ++i) {
+        feast_nl_handle* h = hs[i];
+        if (!h) return fail(FEAST_NL_EINVAL, "NULL handle in the group");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return fail(FEAST_NL_EINVAL, "a handle appears twice in the group");
+        if (h->precision == FEAST_NL_FP64)
+            return fail(FEAST_NL_EINVAL, "grouped factorisation needs complex64 factors (FP32 precisions)");
+        if (h->n > 4096) return fail(FEAST_NL_EINVAL, "grouped factorisation needs n <= 4096");
+        if (nc[i] < 1 || nc[i] > 1024) return fail(FEAST_NL_EINVAL, "nc must be in [1, 1024]");
+        nodes_total += nc[i];
+    }
+    if (nodes_total > 65535) return fail(FEAST_NL_EINVAL, "more than 65535 nodes in the group");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool own = false;
+    if (!st) {
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    int rc = [&]() -> int {
+        AllocScope as(st);
+        LuNode* dnodes = nullptr;
+        IterStatus* dstat = nullptr;
+        std::vector<LuNode> nodes;
+        std::vector<int64_t> ns_n;
+        // every handle's earlier work is finished before its buffers are replaced
+        for (int i = 0; i < count; ++i) CK(cudaStreamSynchronize(hs[i]->st));
+        CK(dalloc(&dstat, 1));
+        CK(cudaMemsetAsync(dstat, 0, sizeof(IterStatus), st));
+        for (int i = 0; i < count; ++i) {
+            feast_nl_handle* h = hs[i];
+            h->have_result = false;
+            free_work(h->wk);
+            int r = build_nodes(h, h->ns, 1, &c_re[i], &c_im[i], &ra[i], &rb[i], nc[i], rule, st,
+                                dstat, false, false);
+            if (r != FEAST_NL_OK) { dfree(dstat); return r; }
+            const int gs = lu_gather_stride(h->n, lu_block_size<float2>());
+            for (int j = 0; j < nc[i]; ++j) {
+                LuNode d;
+                d.F = static_cast<float2*>(h->ns.dF) + (int64_t)j * h->n * h->n;
+                d.piv = h->ns.dpiv + (int64_t)j * h->n;
+                d.info = h->ns.dinfo + j;
+                d.gather = h->ns.dGather + (int64_t)j * gs;
+                d.gcount = h->ns.dGcount + (int64_t)j * (gs / 128);
+                d.n = h->n;
+                nodes.push_back(d);
+                ns_n.push_back(h->n);
+            }
+        }
+        const int nb_nodes = (int)nodes.size();
+        CK(dalloc(&dnodes, (size_t)nb_nodes));
+        CK(cudaMemcpyAsync(dnodes, nodes.data(), sizeof(LuNode) * nb_nodes, cudaMemcpyHostToDevice, st));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+        CK(lu_factor_grouped(st, dnodes, ns_n.data(), nb_nodes, lu_block_size<float2>(), &dstat->flags));
+        CK(cudaEventRecord(e1, st));
+        IterStatus hst{};
+        CK(cudaMemcpyAsync(&hst, dstat, sizeof(IterStatus), cudaMemcpyDeviceToHost, st));
+        std::vector<std::vector<int>> infos(count);
+        for (int i = 0; i < count; ++i) {
+            infos[i].resize(nc[i]);
+            CK(cudaMemcpyAsync(infos[i].data(), hs[i]->ns.dinfo, sizeof(int) * nc[i],
+                               cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dfree(dnodes);
+        dfree(dstat);
+        if (hst.flags & 16) return fail(FEAST_NL_EDEVICE, "tensor-core wait timed out in the node LU");
+        for (int i = 0; i < count; ++i)
+            for (int j = 0; j < nc[i]; ++j)
+                if (infos[i][j] != 0)
+                    return fail(FEAST_NL_ESINGULAR_NODE, "zero pivot in node " + std::to_string(j) +
+                                                             " of group member " + std::to_string(i));
+        for (int i = 0; i < count; ++i) {
+            hs[i]->ns.ms_factor = ms;
+            hs[i]->ns.ready = true;
+        }
+        return FEAST_NL_OK;
+    }();
+    if (own) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
 }
 
 int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, uint64_t seed,

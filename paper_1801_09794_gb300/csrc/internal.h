@@ -216,6 +216,37 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, co
                        const int* active = nullptr);
 
 // ------------------------------------------------------------------ LU (k_lu.cu)
+// One node matrix of a grouped factorisation (orders may differ): F is n x n
+// column-major (leading dimension n) in the LU precision; piv (n), info (1),
+// gather / gcount are this node's own slots (lu_gather_stride(n, nb) entries).
+struct LuNode {
+    void* F;
+    int* piv;
+    int* info;
+    int2* gather;
+    int* gcount;
+    int64_t n;
+};
+// Column range of the look-ahead split for a node of order n at panel k0:
+// the panel is jb wide; mode 0 = the next panel's columns, mode 1 = the rest.
+// False when the range is empty (or the node has no panel k0).
+__host__ __device__ __forceinline__ bool lookahead_cols(int64_t n, int k0, int nb, int mode, int* jb,
+                                                        int* c0, int* ncols) {
+    if (k0 >= n) return false;
+    *jb = (int)(n - k0 < nb ? n - k0 : nb);
+    const int64_t rest = n - k0 - *jb;
+    const int64_t jn = rest < nb ? rest : nb;
+    *c0 = (int)(k0 + *jb + (mode == 0 ? 0 : jn));
+    *ncols = (int)(mode == 0 ? jn : rest - jn);
+    return *ncols > 0;
+}
+// Factors nodes of different orders in one launch sequence per panel (grid
+// dimension = node; a node whose order is exhausted skips the rest), complex64
+// only, every order <= 4096; nodes: device array of count descriptors; n_host:
+// their orders.  Same look-ahead as lu_factor_batched.
+cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_t* n_host,
+                              int count, int nb, int* err);
+
 // The factorisation also writes, per node and panel, the panel's row interchanges
 // as a gather list (gather: nc x lu_gather_stride int2, gcount: nc x panels ints),
 // which the solves apply to the right-hand sides.
@@ -253,6 +284,11 @@ cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2*
                              int64_t ldc, int64_t sC, int batch, int* err, int bn = 0,
                              const int* active = nullptr, int group = 1);
 int cgemm_default_bn(int n);
+// The LU's trailing update for grouped nodes (lu_factor_grouped): node z of
+// `nodes`, panel at k0 of width min(nb, n - k0), columns of the look-ahead
+// split `mode`; the grid covers the largest node (max_rows x max_cols).
+cudaError_t cgemm_sub_grouped(cudaStream_t st, const LuNode* nodes, int count, int k0, int nb,
+                              int mode, int64_t max_rows, int64_t max_cols, int* err);
 template <typename T> int lu_block_size();
 
 // ------------------------------------------------------------------ reduced problem (k_reduced.cu)

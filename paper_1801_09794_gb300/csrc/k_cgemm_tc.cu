@@ -68,28 +68,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// One CTA's 128 x BN tile (blockIdx.x, blockIdx.y) of C -= A B for one matrix.
 template <int BN>
-__global__ void __launch_bounds__(kTcThreads, 3) cgemm_tf32x3_kernel(
-    int m, int n, int k, const float2* __restrict__ A, int64_t lda, int64_t sA,
-    const float2* __restrict__ B, int64_t ldb, int64_t sB, float2* __restrict__ C, int64_t ldc,
-    int64_t sC, int* __restrict__ err, const int* __restrict__ active, int group) {
+__device__ __forceinline__ void cgemm_body(int m, int n, int k, const float2* __restrict__ A,
+                                           int64_t lda, const float2* __restrict__ B, int64_t ldb,
+                                           float2* __restrict__ C, int64_t ldc,
+                                           int* __restrict__ err) {
     constexpr int NR = 2 * BN;                   // real columns of the tile
     constexpr int kBtile = NR * 2 * kTcBK * 4;   // bytes of one B part
     constexpr int kStage = 2 * kTcAtile + 2 * kBtile;
     constexpr int kAIt = (kTcM / 16) * (kTcBK / 2) / 4;   // A loads per thread and stage
     constexpr int kBIt = 2 * (BN / 8) / 4;                 // B loads per thread and stage
     static_assert(BN % 16 == 0 && NR <= 256, "tile width");
-    // batch entries of a finished contour (active[z / group] == 0) do nothing
-    if (active && !active[blockIdx.z / group]) return;
 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * kTcM, col0 = blockIdx.y * BN;
-    A += blockIdx.z * sA;
-    B += blockIdx.z * sB;
-    C += blockIdx.z * sC;
 
     if (tid == 0) {
         for (int q = 0; q < kTcStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
@@ -260,6 +256,33 @@ __global__ void __launch_bounds__(kTcThreads, 3) cgemm_tf32x3_kernel(
 }
 
 template <int BN>
+__global__ void __launch_bounds__(kTcThreads, 3) cgemm_tf32x3_kernel(
+    int m, int n, int k, const float2* __restrict__ A, int64_t lda, int64_t sA,
+    const float2* __restrict__ B, int64_t ldb, int64_t sB, float2* __restrict__ C, int64_t ldc,
+    int64_t sC, int* __restrict__ err, const int* __restrict__ active, int group) {
+    // batch entries of a finished contour (active[z / group] == 0) do nothing
+    if (active && !active[blockIdx.z / group]) return;
+    cgemm_body<BN>(m, n, k, A + blockIdx.z * sA, lda, B + blockIdx.z * sB, ldb, C + blockIdx.z * sC,
+                   ldc, err);
+}
+
+// Trailing update of grouped LU nodes (orders may differ): node blockIdx.z;
+// tiles outside that node's update do nothing.
+template <int BN>
+__global__ void __launch_bounds__(kTcThreads, 3) cgemm_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int mode, int* __restrict__ err) {
+    const LuNode d = nodes[blockIdx.z];
+    int jb, c0, ncols;
+    if (!lookahead_cols(d.n, k0, nb, mode, &jb, &c0, &ncols)) return;
+    const int rows = (int)(d.n - k0 - jb);
+    if ((int)blockIdx.x * kTcM >= rows || (int)blockIdx.y * BN >= ncols) return;
+    float2* F = static_cast<float2*>(d.F);
+    const int64_t n = d.n;
+    cgemm_body<BN>(rows, ncols, jb, F + (k0 + jb) + (int64_t)k0 * n, n, F + k0 + (int64_t)c0 * n, n,
+                   F + (k0 + jb) + (int64_t)c0 * n, n, err);
+}
+
+template <int BN>
 constexpr int stage_smem() {
     return kTcStages * (2 * kTcAtile + 2 * (2 * BN) * 2 * kTcBK * 4);
 }
@@ -286,6 +309,29 @@ cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_
     return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t cgemm_sub_grouped(cudaStream_t st, const LuNode* nodes, int count, int k0, int nb,
+                              int mode, int64_t max_rows, int64_t max_cols, int* err) {
+    constexpr int BN = 64;
+    if (count <= 0 || max_rows <= 0 || max_cols <= 0) return cudaSuccess;
+    if (count > 65535) return cudaErrorInvalidValue;
+    constexpr int smem = stage_smem<BN>();
+    static std::atomic<bool> attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(cgemm_grouped_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    dim3 grid((unsigned)((max_rows + kTcM - 1) / kTcM), (unsigned)((max_cols + BN - 1) / BN),
+              (unsigned)count);
+    note_launch();
+    cgemm_grouped_kernel<BN><<<grid, kTcThreads, smem, st>>>(nodes, k0, nb, mode, err);
+    return cudaGetLastError();
+}
 
 int cgemm_default_bn(int n) {
     // the widest tile that wastes the fewest columns (e.g. 48 for 96 right-hand sides)

@@ -38,6 +38,7 @@ template <> struct TriMax<float2> { static constexpr int value = 64; };
 template <> struct TriMax<double2> { static constexpr int value = 32; };
 constexpr int kWarpsPerCta = 8;    // triangular kernels: one warp per column
 
+
 // ---------------------------------------------------------------------------
 // block-wide argmax of (value, row): larger value wins, lower row on ties
 // ---------------------------------------------------------------------------
@@ -78,13 +79,12 @@ __device__ void panel_gather_list(int k0, int jb, const int* ip, int2* list, int
 // ---------------------------------------------------------------------------
 // Panel factorisation, register-resident mini-panels.  ROWS = rows per thread.
 // ---------------------------------------------------------------------------
+// One node's panel: A (n x n, leading dimension ld), its pivot array ip, its
+// info word, and this panel's gather-list slot (gl, gc; gl may be null).
 template <typename T, int ROWS>
-__global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
-    int64_t n, int k0, int jb, T* F, int64_t ld, int64_t strideF, int* piv, int* info,
-    int2* gather, int* gcount, int panel_index, int gstride) {
+__device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, int64_t ld,
+                                               int* ip, int* info1, int2* gl, int* gc) {
     typedef typename cplx_real<T>::type R;
-    T* A = F + blockIdx.x * strideF;
-    int* ip = piv + (int64_t)blockIdx.x * n;
     __shared__ R s_v[32];
     __shared__ int s_i[32];
     __shared__ int s_p;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
                 argmax_warp(best, bi);
                 if (lane == 0) {
                     if (bi == INT_MAX || bi < col || bi >= n) bi = col;
-                    if (!(best > (R)0) && info[blockIdx.x] == 0) info[blockIdx.x] = col + 1;
+                    if (!(best > (R)0) && *info1 == 0) *info1 = col + 1;
                     s_p = bi;
                     ip[col] = bi;
                 }
@@ -268,9 +268,29 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
             __syncthreads();
         }
     }
-    if (tid == 0 && gather != nullptr)
-        panel_gather_list(k0, jb, ip, gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64,
-                          gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
+    if (tid == 0 && gl != nullptr) panel_gather_list(k0, jb, ip, gl, gc);
+}
+
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
+    int64_t n, int k0, int jb, T* F, int64_t ld, int64_t strideF, int* piv, int* info,
+    int2* gather, int* gcount, int panel_index, int gstride) {
+    panel_reg_body<T, ROWS>(n, k0, jb, F + blockIdx.x * strideF, ld, piv + (int64_t)blockIdx.x * n,
+                            info + blockIdx.x,
+                            gather ? gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64 : nullptr,
+                            gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
+}
+
+// Nodes of different orders in one launch: node blockIdx.x from its
+// descriptor; nodes whose order ends before this panel do nothing.
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int panel_index) {
+    const LuNode d = nodes[blockIdx.x];
+    if (k0 >= d.n) return;
+    const int jb = (int)min((int64_t)nb, d.n - k0);
+    panel_reg_body<T, ROWS>(d.n, k0, jb, static_cast<T*>(d.F), d.n, d.piv, d.info,
+                            d.gather + panel_index * 2 * 64, d.gcount + panel_index);
 }
 
 // Column-at-a-time panel in global memory (any n; used above 8192 rows).
@@ -340,16 +360,10 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(
 // Columns [col_begin, col_begin+ncols) of B: the panel's gather list, then
 // B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F).
 template <typename T>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
-    int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF,
-    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
-    T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols, const int* __restrict__ active,
-    int group) {
+__device__ __forceinline__ void swap_trsm_body(int k0, int jb, const T* __restrict__ F, int64_t ld,
+                                               const int2* __restrict__ gl, int cnt, T* B,
+                                               int64_t ldb, int col_begin, int ncols) {
     __shared__ T sL[TriMax<T>::value][TriMax<T>::value + 1];
-    const int node = blockIdx.y;
-    if (active && !active[node / group]) return;     // a finished contour's nodes
-    F += node * strideF;
-    B += node * strideB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < jb * jb; e += blockDim.x) {
         int r = e % jb, c = e / jb;
@@ -360,8 +374,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
     if (cl >= ncols) return;
     T* col = B + (int64_t)(col_begin + cl) * ldb;
     // interchanges: every src read before any dst written
-    const int2* gl = gather + (int64_t)node * gstride + panel_index * 2 * 64;
-    const int cnt = gcount[(int64_t)node * (gstride / 128) + panel_index];
     T g[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -387,6 +399,33 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
     }
     if (lane < jb) col[k0 + lane] = x0;
     if (lane + 32 < jb) col[k0 + lane + 32] = x1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_lower_kernel(
+    int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF,
+    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
+    T* B, int64_t ldb, int64_t strideB, int col_begin, int ncols, const int* __restrict__ active,
+    int group) {
+    const int node = blockIdx.y;
+    if (active && !active[node / group]) return;     // a finished contour's nodes
+    swap_trsm_body<T>(k0, jb, F + node * strideF, ld,
+                      gather + (int64_t)node * gstride + panel_index * 2 * 64,
+                      gcount[(int64_t)node * (gstride / 128) + panel_index], B + node * strideB, ldb,
+                      col_begin, ncols);
+}
+
+// Columns of nodes of different orders, from their descriptors: mode 0 the
+// next panel's columns, mode 1 the columns right of it (the look-ahead split).
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int panel_index, int mode) {
+    const LuNode d = nodes[blockIdx.y];
+    int jb, c0, ncols;
+    if (!lookahead_cols(d.n, k0, nb, mode, &jb, &c0, &ncols)) return;
+    T* F = static_cast<T*>(d.F);
+    swap_trsm_body<T>(k0, jb, F, d.n, d.gather + panel_index * 2 * 64, d.gcount[panel_index], F,
+                      d.n, c0, ncols);
 }
 
 // B[k0:k0+jb, col] <- U11^{-1} B[k0:k0+jb, col] (U11 upper with its diagonal, from F).
@@ -565,6 +604,95 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
             return cleanup(e);
     }
     // everything both streams did is ordered before what follows on st
+    if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
+        return cleanup(e);
+    if (last_r >= 0 && (e = cudaStreamWaitEvent(st, evR[last_r & 1], 0)) != cudaSuccess)
+        return cleanup(e);
+    return cleanup(cudaGetLastError());
+}
+
+cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_t* n_host,
+                              int count, int nb, int* err) {
+    int64_t nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, n_host[i]);
+    if (count <= 0 || nmax <= 0) return cudaSuccess;
+    if (nmax > 4 * kPanelThreads || count > 65535) return cudaErrorInvalidValue;
+    const int npanel = (int)((nmax + nb - 1) / nb);
+    cudaError_t e;
+    cudaStream_t hi = nullptr, side = nullptr;
+    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr;
+    auto cleanup = [&](cudaError_t r) {
+        if (evP) cudaEventDestroy(evP);
+        if (evR[0]) cudaEventDestroy(evR[0]);
+        if (evR[1]) cudaEventDestroy(evR[1]);
+        if (evH) cudaEventDestroy(evH);
+        if (side) cudaStreamDestroy(side);
+        if (hi) cudaStreamDestroy(hi);
+        return r;
+    };
+    int prio_lo = 0, prio_hi = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evH, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evR[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&evR[1], cudaEventDisableTiming)) != cudaSuccess)
+        return cleanup(e);
+    if ((e = cudaEventRecord(evP, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(hi, evP, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
+        return cleanup(e);
+    int last_r = -1;
+    for (int k = 0; k < npanel; ++k) {
+        const int k0 = k * nb;
+        // the largest extents over the nodes that still have this panel
+        int64_t rows = 0, rows_below = 0, cols_next = 0, cols_rest = 0;
+        for (int i = 0; i < count; ++i) {
+            int jb, c0, nn;
+            if (k0 >= n_host[i]) continue;
+            rows = std::max(rows, n_host[i] - k0);
+            jb = (int)std::min<int64_t>(nb, n_host[i] - k0);
+            rows_below = std::max(rows_below, n_host[i] - k0 - jb);
+            if (lookahead_cols(n_host[i], k0, nb, 0, &jb, &c0, &nn)) cols_next = std::max<int64_t>(cols_next, nn);
+            if (lookahead_cols(n_host[i], k0, nb, 1, &jb, &c0, &nn)) cols_rest = std::max<int64_t>(cols_rest, nn);
+        }
+        note_launch();
+        if (rows <= kPanelThreads)
+            lu_panel_reg_grouped_kernel<float2, 1><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
+        else if (rows <= 2 * kPanelThreads)
+            lu_panel_reg_grouped_kernel<float2, 2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
+        else
+            lu_panel_reg_grouped_kernel<float2, 4><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(e);
+        if (rows_below <= 0) continue;
+        if (cols_rest > 0) {
+            if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
+                return cleanup(e);
+            dim3 g((unsigned)((cols_rest + kWarpsPerCta - 1) / kWarpsPerCta), count);
+            note_launch();
+            swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, side>>>(nodes, k0, nb, k, 1);
+            if ((e = cgemm_sub_grouped(side, nodes, count, k0, nb, 1, rows_below, cols_rest, err)) !=
+                cudaSuccess)
+                return cleanup(e);
+        }
+        if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
+            return cleanup(e);
+        if (cols_rest > 0) {
+            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return cleanup(e);
+            last_r = k;
+        }
+        if (cols_next > 0) {
+            dim3 g((unsigned)((cols_next + kWarpsPerCta - 1) / kWarpsPerCta), count);
+            note_launch();
+            swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, hi>>>(nodes, k0, nb, k, 0);
+            if ((e = cgemm_sub_grouped(hi, nodes, count, k0, nb, 0, rows_below, cols_next, err)) !=
+                cudaSuccess)
+                return cleanup(e);
+        }
+    }
     if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
         return cleanup(e);

@@ -1,0 +1,88 @@
+"""Grouped factorisation through the C ABI: the node matrices of several
+problems of different orders (one contour each) factored in one launch
+sequence per panel, then each problem solved on its own handle; results
+against QZ and against the same problems factored one by one."""
+import numpy as np
+import pytest
+
+from tests.closed_forms import inside_mask, match_sets, problem_mats, second_companion_eigs
+from workloads import random_pep, start_block
+
+pytestmark = pytest.mark.gpu
+
+# (n, degree, seed): orders that are and are not multiples of the 64-column panel
+CASES = [(130, 3, 21), (256, 2, 5), (200, 3, 8)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1801_09794_gb300 as P
+    P.load_library()
+    return P
+
+
+@pytest.fixture(scope="module")
+def problems():
+    out = []
+    for n, k, seed in CASES:
+        p = random_pep(n, k, seed)
+        lam = second_companion_eigs(problem_mats(p))
+        lam = lam[np.isfinite(lam)]
+        c = lam[np.argmin(np.abs(lam - (0.3 + 0.2j)))]
+        d = np.sort(np.abs(lam - c))
+        r = 0.5 * (d[6] + d[7])                  # 7 inside
+        out.append((p, lam, c, r))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_i8"])
+def test_group_solves_match_qz(lib, problems, prec):
+    hs = [lib.FeastNL(p, prec) for p, _, _, _ in problems]
+    lib.set_contour_group(hs, [c for _, _, c, _ in problems], [r for _, _, _, r in problems],
+                          [r for _, _, _, r in problems], 16)
+    for h, (p, lam_all, c, r) in zip(hs, problems):
+        st, info = h.solve(20, tol=1e-12, maxit=80, X0=start_block(p["n"], 20, 9))
+        lam, X, rr = h.get_eigpairs(inside_only=True)
+        ref = lam_all[inside_mask(lam_all, c, r, r)]
+        assert len(lam) == len(ref) == 7
+        assert match_sets(lam, ref) < 1e-10
+        assert np.all(rr <= 1e-10)
+        h.close()
+
+
+def test_group_factors_match_one_by_one(lib, problems):
+    # same node matrices, same LU arithmetic up to the panel kernel's register
+    # blocking (chosen by the largest order in the launch): node solves agree to
+    # FP32 accuracy, and each problem's eigenpairs agree to 1e-12
+    grouped = [lib.FeastNL(p, "fp32") for p, _, _, _ in problems]
+    lib.set_contour_group(grouped, [c for _, _, c, _ in problems], [r for _, _, _, r in problems],
+                          [r for _, _, _, r in problems], 16)
+    rng = np.random.default_rng(3)
+    for g, (p, _, c, r) in zip(grouped, problems):
+        s = lib.FeastNL(p, "fp32")
+        s.set_contour(c, r, r, 16)
+        R = rng.standard_normal((p["n"], 4)) + 1j * rng.standard_normal((p["n"], 4))
+        for j in (0, 7, 15):
+            y1, y2 = g.node_solve(j, R), s.node_solve(j, R)
+            assert np.linalg.norm(y1 - y2) <= 1e-4 * np.linalg.norm(y2)
+        X0 = start_block(p["n"], 20, 4)
+        g.solve(20, tol=1e-12, maxit=80, X0=X0)
+        s.solve(20, tol=1e-12, maxit=80, X0=X0)
+        l1, _, _ = g.get_eigpairs(inside_only=True)
+        l2, _, _ = s.get_eigpairs(inside_only=True)
+        assert match_sets(l1, l2) < 1e-12
+        s.close()
+        g.close()
+
+
+def test_group_invalid_arguments(lib, problems):
+    p = problems[0][0]
+    a, b = lib.FeastNL(p, "fp32"), lib.FeastNL(p, "fp64")
+    with pytest.raises(lib.FeastError):
+        lib.set_contour_group([a, b], [0.1, 0.1], 0.2, 0.2, 8)        # complex128 factors
+    with pytest.raises(lib.FeastError):
+        lib.set_contour_group([a, a], [0.1, 0.1], 0.2, 0.2, 8)        # same handle twice
+    with pytest.raises(lib.FeastError):
+        lib.set_contour_group([a], [0.1], -0.2, 0.2, 8)               # bad radius
+    a.close()
+    b.close()
