@@ -56,6 +56,10 @@ WORKLOADS = {
     # ~5e-10 eigenvalue error: the solve stops at 1e-12, pairs count at 1e-10
     "slices_n2048": {"gen": "cubic_pep", "n": 2048, "precision": "fp32_i8", "tol": 1e-12,
                      "maxit": 60, "slices": True},
+    # mixed-order batch: cubics n = 256 .. 4096 (complex Gaussian), one circle of
+    # 8 eigenvalues each, factored together, solved side by side
+    "mixed_n": {"gen": "cubic_pep", "precision": "fp32_i8", "tol": 1e-12, "maxit": 60,
+                "mixed": True},
 }
 
 
@@ -91,6 +95,10 @@ def load_workload(name):
     spec = WORKLOADS[name]
     with open(os.path.join(ROOT, "tests", "golden", "contours.json")) as f:
         c = json.load(f)[name]
+    if spec.get("mixed"):
+        problems = [getattr(workloads, spec["gen"])(q["n"], q["n"]) for q in c["problems"]]
+        gold = [np.array([complex(*x) for x in q["eigs_inside"]]) for q in c["problems"]]
+        return spec, c, problems, gold
     problem = getattr(workloads, spec["gen"])(spec["n"], 0)
     if spec.get("slices"):
         gold = [np.array([complex(*x) for x in e]) for e in c["eigs_inside"]]
@@ -661,6 +669,187 @@ def run_slices_reference(args):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------- mixed orders
+def mixed_step(P, hs, c, spec, seed, gold, stream=None):
+    """One step: grouped contours + factorisation of all problems, then their
+    solves side by side (one host thread and one stream per problem)."""
+    import threading
+    qs = c["problems"]
+    P.set_contour_group(hs, [complex(*q["center"]) for q in qs], [q["r"] for q in qs],
+                        [q["r"] for q in qs], c["nc"], c["rule"], stream=stream)
+    res = [None] * len(hs)
+
+    def run(i):
+        st, info = hs[i].solve(c["m0"], tol=spec["tol"], maxit=spec["maxit"], seed=seed,
+                               allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        lam, _, rr = hs[i].get_eigpairs(inside_only=True, vectors=False)
+        q = qs[i]
+        cen = complex(*q["center"])
+        res[i] = (count_good(lam, rr, gold[i], cen, q["r"], q["r"]), info.iters, info.ms_factor)
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(len(hs))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return res
+
+
+def run_mixed(args):
+    """Mixed-order batch: cubics of n = 256 .. 4096, their node matrices
+    factored in one grouped launch sequence, their iterations side by side."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1801_09794_gb300 as P
+    spec, c, problems, gold = load_workload(args.workload)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    hs = []
+    for p in problems:
+        pd = {"n": p["n"], "terms": [dict(t, A=None if t["A"] is None else torch.from_numpy(t["A"]).to(dev))
+                                    for t in p["terms"]]}
+        hs.append(P.FeastNL(pd, spec["precision"]))
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        mixed_step(P, hs, c, spec, args.seed, gold, stream.cuda_stream)
+    # the same factorisations one problem at a time, for comparison
+    one_by_one = 0.0
+    for h, q in zip(hs, c["problems"]):
+        h.set_contour(complex(*q["center"]), q["r"], q["r"], c["nc"], c["rule"])
+        h.solve(c["m0"], tol=spec["tol"], maxit=1, seed=args.seed, allow=(P.FEAST_NL_ENOT_CONVERGED,))
+    for h, q in zip(hs, c["problems"]):
+        h.set_contour(complex(*q["center"]), q["r"], q["r"], c["nc"], c["rule"])
+        _, info = h.solve(c["m0"], tol=spec["tol"], maxit=1, seed=args.seed,
+                          allow=(P.FEAST_NL_ENOT_CONVERGED,))
+        one_by_one += info.ms_factor
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = P.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    goods, fac, iters = [], [], []
+    for _ in range(args.steps):
+        res = mixed_step(P, hs, c, spec, args.seed, gold, stream.cuda_stream)
+        goods.append(sum(r[0] for r in res))
+        fac.append(res[0][2])
+        iters = [r[1] for r in res]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = P.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    for h in hs:
+        h.close()
+    barrier()
+    ms_max = reduce_over_ranks(ms, "max", dev)
+    value = reduce_over_ranks(min(goods), "sum", dev) / (ms_max / 1e3)
+    ns = [q["n"] for q in c["problems"]]
+    lu_flops = c["nc"] * (8.0 / 3.0) * sum(n ** 3 for n in ns)
+    fms = statistics.median(fac)
+    pk = peaks()
+    ach = lu_flops / (fms / 1e3) / 1e12
+    peak, bound, why = phase_peak("lu", spec["precision"], pk, clk.get("sm_mhz"))
+    roof = {"kernel": f"grouped node assembly + LU of {len(ns) * c['nc']} nodes, n = {ns}",
+            "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": why, "ms_per_launch_sequence": fms}
+    e2e = run_mixed_e2e(args, P, torch, problems, spec, c, gold, dev)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64",
+           "data": "synthetic (seeded generator, no dataset)",
+           "config": {"workload": args.workload, "orders": ns, "degree": 3, "nc": c["nc"],
+                      "m0": c["m0"], "count_inside": c["count"], "lu_precision": spec["precision"],
+                      "tol": spec["tol"], "iterations": iters, "eigenpairs_per_step": min(goods),
+                      "ms_factor_grouped": fms, "ms_factor_one_by_one": one_by_one,
+                      "l2": "inputs larger than L2 (A_t %.0f MB)" % (4 * sum(n * n for n in ns) * 16 / 1e6),
+                      "parallelism": f"replicas x{ws}"},
+           "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                      "reasons": clk["reasons"]},
+           "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+           "node_lu_tflops": ach, "peaks": pk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = mixed_cpu_sample(args, problems, spec, c, gold, upto=2)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_mixed_e2e(args, P, torch, problems, spec, c, gold, dev):
+    h2d = sum(t["A"].nbytes for p in problems for t in p["terms"] if t["A"] is not None)
+    steps = max(1, min(args.steps, 3))
+    times, goods = [], []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = [P.FeastNL(p, spec["precision"]) for p in problems]
+        res = mixed_step(P, hs, c, spec, args.seed, gold)
+        for h in hs:
+            h.close()
+        torch.cuda.synchronize()
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+            goods.append(sum(r[0] for r in res))
+    t = reduce_over_ranks(statistics.median(times), "max", dev)
+    g = reduce_over_ranks(min(goods), "sum", dev)
+    return {"value": g / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(16 * 3 * c["m0"] * len(problems)), "s_per_step": t,
+            "steps": steps}
+
+
+def mixed_cpu_sample(args, problems, spec, c, gold, upto=2):
+    """The FP64 oracle on the `upto` smallest problems of the batch (each: its 8
+    node LUs and every iteration)."""
+    from workloads import start_block
+    import oracle as O
+    t_all, good, iters = 0.0, 0, []
+    for i in range(upto):
+        q = c["problems"][i]
+        cen = complex(*q["center"])
+        X0 = start_block(q["n"], c["m0"], args.seed)
+        t0 = time.perf_counter()
+        res = O.nlfeast(problems[i], {"center": cen, "ra": q["r"], "rb": q["r"], "nc": c["nc"],
+                                      "rule": c["rule"]}, c["m0"], X0, tol=spec["tol"],
+                        maxit=spec["maxit"])
+        t_all += time.perf_counter() - t0
+        good += count_good(res["lam"], res["relres"], gold[i], cen, q["r"], q["r"])
+        iters.append(res["iters"])
+    return {"value": good / t_all, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"the {upto} smallest problems (n = {[q['n'] for q in c['problems'][:upto]]}, "
+                      f"{iters} iterations) in {t_all:.1f} s; {good} eigenpairs",
+            "seconds": t_all}
+
+
+def run_mixed_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    spec, c, problems, gold = load_workload(args.workload)
+    w, k = min(args.warmup, 1), min(args.steps, 3)
+    for _ in range(w):
+        mixed_cpu_sample(args, problems, spec, c, gold, upto=2)
+    rs = [mixed_cpu_sample(args, problems, spec, c, gold, upto=2) for _ in range(k)]
+    v = statistics.mean(r["value"] for r in rs)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": k, "warmup": w, "ms_per_step": statistics.mean(r["seconds"] for r in rs) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "orders": [q["n"] for q in c["problems"]],
+                   "nc": c["nc"], "m0": c["m0"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": rs[0]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 # ---------------------------------------------------------------------------- serving
 def serving_stream(num, seed, rate=200.0, n_lo=128, n_hi=2048):
     """Seeded request stream: Poisson arrivals (rate per second); n log-uniform;
@@ -774,6 +963,11 @@ def main():
                               "on the GPU arm only (the oracle has no server)"}))
             return
         run_serving(args)
+    elif WORKLOADS[args.workload].get("mixed"):
+        if args.impl == "reference":
+            run_mixed_reference(args)
+        else:
+            run_mixed(args)
     elif WORKLOADS[args.workload].get("slices"):
         if args.impl == "reference":
             run_slices_reference(args)

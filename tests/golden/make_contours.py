@@ -88,6 +88,9 @@ def main():
     if sys.argv[1:] == ["slices_n2048"]:
         main_slices_only(path)
         return
+    if sys.argv[1:] == ["mixed_n"]:
+        main_mixed_only(path)
+        return
     out = {}
     p1 = config1_qep(256, 0)
     lam1 = brute_force_eigs(p1)
@@ -122,6 +125,7 @@ def main():
         json.dump(out, f, indent=1)
     main_delay_only(path)
     main_slices_only(path)
+    main_mixed_only(path)
 
 
 def main_delay_only(path):
@@ -179,6 +183,39 @@ def main_slices_only(path):
         "method": "shift-invert Arnoldi (24 nearest each disc center) on the first companion "
                   "pencil through one n x n LU per disc"}
     print("C4", len(centers), "discs,", out["slices_n2048"]["count"], "eigenvalues, margin", margin)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+
+
+# mixed-order batch: one cubic with complex Gaussian coefficients per order
+MIXED_ORDERS = (256, 512, 1024, 2048, 4096)
+
+
+def main_mixed_only(path):
+    """Per order n: the circle around the eigenvalue nearest 0.5 + 0.25i (rounded
+    to 3 decimals) holding 8 eigenvalues (radius in the gap after the 8th
+    nearest), and those 8, from the 24 nearest by shift-invert Arnoldi."""
+    with open(path) as f:
+        out = json.load(f)
+    probs = []
+    for n in MIXED_ORDERS:
+        p = cubic_pep(n, n)
+        near = shift_invert_nearest(p, 0.5 + 0.25j, 24)
+        c0 = near[0]
+        center = complex(round(c0.real, 3), round(c0.imag, 3))
+        lam = shift_invert_nearest(p, center, 24)
+        d = np.sort(np.abs(lam - center))
+        r = 0.5 * (d[7] + d[8])
+        gap = (d[8] - d[7]) / r
+        inside = lam[np.abs(lam - center) < r]
+        assert len(inside) == 8 and d[-1] > r
+        probs.append({"n": n, "generator": f"cubic_pep(n={n}, seed={n})",
+                      "center": [center.real, center.imag], "r": float(r), "relative_gap": float(gap),
+                      "eigs_inside": [[x.real, x.imag] for x in sorted(inside, key=lambda v: (v.real, v.imag))]})
+        print("mixed", n, center, r, gap)
+    out["mixed_n"] = {"problems": probs, "nc": 8, "rule": "gl", "m0": 16, "count": 8 * len(probs),
+                      "method": "shift-invert Arnoldi (24 nearest the center) on the first companion "
+                                "pencil through one n x n LU"}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
