@@ -892,8 +892,8 @@ def run_serving(args):
     for q in timed:
         q["t"] -= t0s
 
-    def one_pass(max_active, reqs, paced):
-        srv = P.Server(max_active=max_active, hbm_budget=100 << 30)
+    def one_pass(max_active, reqs, paced, group_limit=None):
+        srv = P.Server(max_active=max_active, hbm_budget=100 << 30, group_limit=group_limit)
         start = time.perf_counter()
         tickets = []
         for q in reqs:
@@ -927,6 +927,7 @@ def run_serving(args):
     one_pass(4, warm, False)                        # warm-up (library load, kernels)
     g1, t1, l1, s1 = one_pass(1, timed, True)
     g4, t4, l4, s4 = one_pass(4, timed, True)
+    gu, tu, lu, su = one_pass(4, timed, True, group_limit=1)     # no grouped factorisation
     want = int(sum(q["count"] for q in timed))
     out = {"metric": "eigenpairs/s under Poisson arrivals (serving)", "value": g4 / t4,
            "unit": "eigenpairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -941,7 +942,10 @@ def run_serving(args):
            "serial": {"value": g1 / t1, "eigenpairs_found": g1, "makespan_s": t1,
                       "latency_ms": {"p50": float(np.percentile(l1, 50)),
                                      "p99": float(np.percentile(l1, 99))}},
-           "max_concurrent_seen": s4["max_concurrent"]}
+           "max_concurrent_seen": s4["max_concurrent"], "max_group_seen": s4["max_group"],
+           "ungrouped": {"value": gu / tu, "eigenpairs_found": gu, "makespan_s": tu,
+                         "latency_ms": {"p50": float(np.percentile(lu, 50)),
+                                        "p99": float(np.percentile(lu, 99))}}}
     print(json.dumps(out), flush=True)
 
 

@@ -206,14 +206,17 @@ int feast_nl_set_contour_group(int32_t count, feast_nl_handle* const* hs, const 
 
 /* ---- serving: continuous batching of independent requests ------------------ */
 /* No counterpart in the paper (its parallelism is over nodes and regions on
- * CPUs).  A request is one whole run of Algorithm 1 (create + set_contour +
+ * CPUs).  A request is one whole run of Algorithm 1 (create + contour +
  * solve) on its own handle and stream.  The server keeps up to max_active
  * requests in flight, admitting them in submission order while the summed
  * device-memory footprint (feast_nl_request_footprint) stays within
  * hbm_budget bytes (a request larger than the budget runs when nothing else
- * does).  Requests in flight overlap on the GPU; each one's arithmetic is the
- * same as when it runs alone.  The caller keeps the term buffers of a request
- * alive until the request is done.  All calls are thread-safe. */
+ * does).  The requests admitted together have their node matrices factored in
+ * one grouped launch sequence (feast_nl_set_contour_group; complex128 factors
+ * and n > 4096 one by one), then each is solved by a worker thread.  Requests
+ * in flight overlap on the GPU; each one's results are the same bits as when
+ * it runs alone.  The caller keeps the term buffers of a request alive until
+ * the request is done.  All calls are thread-safe. */
 typedef struct feast_nl_server feast_nl_server;
 typedef struct {
     int64_t n;
@@ -245,8 +248,13 @@ int feast_nl_server_wait(feast_nl_server* s, uint64_t ticket, feast_nl_info* inf
  * feast_nl_get_eigpairs) and releases the ticket; returns the run's status. */
 int feast_nl_server_fetch(feast_nl_server* s, uint64_t ticket, int32_t capacity, int32_t* m_out,
                           double* lambda, void* X, double* relres, int32_t inside_only);
-/* Largest number of requests seen in flight at once, requests completed. */
-int feast_nl_server_stats(feast_nl_server* s, int32_t* max_concurrent, int64_t* completed);
+/* At most `limit` requests admitted together are factored as one group (1:
+ * every request factored on its own); default 64.  Errors: EINVAL. */
+int feast_nl_server_set_group_limit(feast_nl_server* s, int32_t limit);
+/* Largest number of requests seen in flight at once, requests completed, and
+ * the largest group factored together (any pointer may be NULL). */
+int feast_nl_server_stats(feast_nl_server* s, int32_t* max_concurrent, int64_t* completed,
+                          int32_t* max_group);
 /* Finishes every submitted request, then stops the workers. */
 void feast_nl_server_destroy(feast_nl_server* s);
 

@@ -37,7 +37,7 @@ EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_n
            "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy",
            "feast_nl_slices_create", "feast_nl_slices_solve", "feast_nl_slices_get_eigpairs",
            "feast_nl_slices_graph_launches", "feast_nl_slices_destroy",
-           "feast_nl_set_contour_group"]
+           "feast_nl_set_contour_group", "feast_nl_server_set_group_limit"]
 FEAST_NL_SLICES_NO_GRAPH = 1
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
@@ -110,8 +110,10 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_server_poll.argtypes = [P, U64, ctypes.POINTER(I32)]
     lib.feast_nl_server_wait.argtypes = [P, U64, ctypes.POINTER(feast_nl_info), ctypes.POINTER(D)]
     lib.feast_nl_server_fetch.argtypes = [P, U64, I32, ctypes.POINTER(I32), P, P, P, I32]
-    lib.feast_nl_server_stats.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I64)]
+    lib.feast_nl_server_stats.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I64),
+                                          ctypes.POINTER(I32)]
     lib.feast_nl_server_destroy.argtypes = [P]
+    lib.feast_nl_server_set_group_limit.argtypes = [P, I32]
     lib.feast_nl_server_destroy.restype = None
     lib.feast_nl_slices_create.argtypes = [ctypes.POINTER(P), P, I32, P, P, P, P, I32, I32, P]
     lib.feast_nl_slices_solve.argtypes = [P, I32, D, I32, U64, I32, P]
@@ -330,12 +332,15 @@ def request_footprint(problem, nc, m0, precision="fp32"):
 class Server:
     """Serving loop of the library: requests run concurrently on their own handles."""
 
-    def __init__(self, max_active=4, hbm_budget=64 << 30):
+    def __init__(self, max_active=4, hbm_budget=64 << 30, group_limit=None):
         self.lib = load_library()
         s = ctypes.c_void_p()
         _check(self.lib.feast_nl_server_create(ctypes.byref(s), int(max_active), int(hbm_budget)),
                "feast_nl_server_create")
         self.s = s
+        if group_limit is not None:
+            _check(self.lib.feast_nl_server_set_group_limit(s, int(group_limit)),
+                   "feast_nl_server_set_group_limit")
         self._keep = {}
         self._meta = {}
 
@@ -377,9 +382,10 @@ class Server:
     def stats(self):
         mc = ctypes.c_int32()
         done = ctypes.c_int64()
-        _check(self.lib.feast_nl_server_stats(self.s, ctypes.byref(mc), ctypes.byref(done)),
-               "feast_nl_server_stats")
-        return {"max_concurrent": mc.value, "completed": done.value}
+        mg = ctypes.c_int32()
+        _check(self.lib.feast_nl_server_stats(self.s, ctypes.byref(mc), ctypes.byref(done),
+                                              ctypes.byref(mg)), "feast_nl_server_stats")
+        return {"max_concurrent": mc.value, "completed": done.value, "max_group": mg.value}
 
     def close(self):
         if getattr(self, "s", None):

@@ -55,6 +55,8 @@ def test_alone_and_mixed_give_identical_results(P):
     alone, st1 = _run(P, reqs, 1)
     mixed, st4 = _run(P, reqs, 4)
     assert st1["max_concurrent"] == 1 and st4["max_concurrent"] >= 2
+    # submitted together, the four are admitted together and factored as one group
+    assert st1["max_group"] == 1 and st4["max_group"] >= 2
     for (sa, (la, Xa, ra)), (sm, (lm, Xm, rm)), req in zip(alone, mixed, reqs):
         assert sa == sm == P.FEAST_NL_OK
         assert np.array_equal(la, lm) and np.array_equal(ra, rm) and np.array_equal(Xa, Xm)
@@ -74,5 +76,5 @@ def test_admission_by_footprint(P):
     for t in tickets:
         srv.wait(t)
         srv.fetch(t, vectors=False)
-    assert srv.stats() == {"max_concurrent": 1, "completed": 3}
+    assert srv.stats() == {"max_concurrent": 1, "completed": 3, "max_group": 1}
     srv.close()

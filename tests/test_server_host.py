@@ -31,7 +31,7 @@ def test_footprint_grows_with_size_and_nodes(P):
 
 def test_server_lifecycle_without_requests(P):
     s = P.Server(max_active=3, hbm_budget=1 << 30)
-    assert s.stats() == {"max_concurrent": 0, "completed": 0}
+    assert s.stats() == {"max_concurrent": 0, "completed": 0, "max_group": 0}
     s.close()
 
 
