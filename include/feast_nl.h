@@ -252,7 +252,7 @@ int feast_nl_server_fetch(feast_nl_server* s, uint64_t ticket, int32_t capacity,
  * every request factored on its own); default 64.  Errors: EINVAL. */
 int feast_nl_server_set_group_limit(feast_nl_server* s, int32_t limit);
 /* Largest number of requests seen in flight at once, requests completed, and
- * the largest group factored together (any pointer may be NULL). */
+ * the largest group admitted (and factored) together (any pointer may be NULL). */
 int feast_nl_server_stats(feast_nl_server* s, int32_t* max_concurrent, int64_t* completed,
                           int32_t* max_group);
 /* Finishes every submitted request, then stops the workers. */

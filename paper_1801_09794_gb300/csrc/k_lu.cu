@@ -283,18 +283,26 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_kernel(
 
 // Nodes of different orders in one launch: node blockIdx.x from its
 // descriptor; nodes whose order ends before this panel do nothing.
-// Only the nodes whose remaining rows fall in this variant's class
-// ((ROWS/2) * 1024, ROWS * 1024] take part, the variant a node gets alone.
-template <typename T, int ROWS>
+// Each node runs the rows-per-thread variant it would get in a factorisation
+// of its own (chosen per CTA from its remaining rows, so nodes of every class
+// share the launch).
+template <typename T>
 __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_grouped_kernel(
     const LuNode* __restrict__ nodes, int k0, int nb, int panel_index) {
     const LuNode d = nodes[blockIdx.x];
     if (k0 >= d.n) return;
     const int64_t rows = d.n - k0;
-    if (rows > (int64_t)ROWS * kPanelThreads || rows <= (int64_t)(ROWS / 2) * kPanelThreads) return;
     const int jb = (int)min((int64_t)nb, d.n - k0);
-    panel_reg_body<T, ROWS>(d.n, k0, jb, static_cast<T*>(d.F), d.n, d.piv, d.info,
-                            d.gather + panel_index * 2 * 64, d.gcount + panel_index);
+    T* F = static_cast<T*>(d.F);
+    if (rows <= kPanelThreads)
+        panel_reg_body<T, 1>(d.n, k0, jb, F, d.n, d.piv, d.info, d.gather + panel_index * 2 * 64,
+                             d.gcount + panel_index);
+    else if (rows <= 2 * kPanelThreads)
+        panel_reg_body<T, 2>(d.n, k0, jb, F, d.n, d.piv, d.info, d.gather + panel_index * 2 * 64,
+                             d.gcount + panel_index);
+    else
+        panel_reg_body<T, 4>(d.n, k0, jb, F, d.n, d.piv, d.info, d.gather + panel_index * 2 * 64,
+                             d.gcount + panel_index);
 }
 
 // Column-at-a-time panel in global memory (any n; used above 8192 rows).
@@ -664,26 +672,8 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
             if (lookahead_cols(n_host[i], k0, nb, 0, &jb, &c0, &nn)) cols_next = std::max<int64_t>(cols_next, nn);
             if (lookahead_cols(n_host[i], k0, nb, 1, &jb, &c0, &nn)) cols_rest = std::max<int64_t>(cols_rest, nn);
         }
-        // one launch per rows-per-thread class present (the class a node would
-        // get in a factorisation of its own)
-        bool cls[3] = {false, false, false};
-        for (int i = 0; i < count; ++i) {
-            if (k0 >= n_host[i]) continue;
-            const int64_t r = n_host[i] - k0;
-            cls[r <= kPanelThreads ? 0 : (r <= 2 * kPanelThreads ? 1 : 2)] = true;
-        }
-        if (cls[0]) {
-            note_launch();
-            lu_panel_reg_grouped_kernel<float2, 1><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        }
-        if (cls[1]) {
-            note_launch();
-            lu_panel_reg_grouped_kernel<float2, 2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        }
-        if (cls[2]) {
-            note_launch();
-            lu_panel_reg_grouped_kernel<float2, 4><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        }
+        note_launch();
+        lu_panel_reg_grouped_kernel<float2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
         if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(e);
         if (rows_below <= 0) continue;
         if (cols_rest > 0) {

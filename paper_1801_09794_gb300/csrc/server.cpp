@@ -153,8 +153,6 @@ std::vector<Request*> prepare_group(feast_nl_server* s, const std::vector<Reques
             st = feast_nl_set_contour_group((int32_t)k, hs.data(), cre.data(), cim.data(), ra.data(),
                                             rb.data(), nc.data(), grouped[0]->r.rule, nullptr);
         if (st == FEAST_NL_OK) {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->max_group = std::max(s->max_group, (int)k);
             ok.insert(ok.end(), grouped.begin(), grouped.end());
         } else {
             // one by one, so that a failing request does not take the others down
@@ -164,8 +162,6 @@ std::vector<Request*> prepare_group(feast_nl_server* s, const std::vector<Reques
                 if (st1 != FEAST_NL_OK) { fail_request(q, st1); finish(s, q); }
                 else ok.push_back(q);
             }
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->max_group = std::max(s->max_group, 1);
         }
     }
     return ok;
@@ -196,6 +192,7 @@ void factor_loop(feast_nl_server* s) {
                 q->t_start = now_ms();
                 group.push_back(q);
             }
+            s->max_group = std::max(s->max_group, (int)group.size());
         }
         // the group is prepared on a thread of its own, so that the next group
         // can be taken (and factored on the GPU alongside) while it runs
