@@ -194,6 +194,7 @@ struct Work {
     int splits = 1;
     unsigned char* Qsl = nullptr;   // digit slices of Q' (all contours at once)
     double* Tau = nullptr;          // their column scales
+    unsigned char* Oz = nullptr;    // digit-split workspace of the tall, thin FP64 products
 };
 
 // One contour's view of a NodeSet and a Work, with the stream its per-contour
@@ -207,6 +208,7 @@ struct Disc {
     double2 *Q, *Qt, *X, *R, *W, *G, *Split, *Ahat, *Yred, *Ycat, *G2, *Rinv, *Lam, *Coef, *Fsum;
     double *Nu, *Rnorm, *Relres;
     unsigned char *Red, *Beyn;
+    unsigned char* Oz;              // non-null: tall, thin FP64 products on the tensor cores
     void* Y;
     IterStatus* status;
     int splits;
@@ -279,6 +281,9 @@ struct feast_nl_slices {
 namespace {
 
 constexpr int kMaxSide = 128;
+// subspaces at least this wide take the digit-split path for their tall, thin
+// FP64 products (narrower ones are latency-bound either way)
+constexpr int kOzMinCols = 32;
 
 cudaEvent_t prof_event(feast_nl_handle* h) {
     if (h->pool_used == h->pool.size()) {
@@ -333,7 +338,7 @@ void free_work(Work& wk) {
     dfree(wk.G); dfree(wk.Split); dfree(wk.Ahat); dfree(wk.Yred); dfree(wk.Ycat);
     dfree(wk.G2); dfree(wk.Rinv); dfree(wk.Lam); dfree(wk.Coef); dfree(wk.Fsum);
     dfree(wk.Nu); dfree(wk.Rnorm); dfree(wk.Relres); dfree(wk.Red); dfree(wk.Beyn); dfree(wk.Stage);
-    dfree(wk.Status); dfree(wk.Qsl); dfree(wk.Tau);
+    dfree(wk.Status); dfree(wk.Qsl); dfree(wk.Tau); dfree(wk.Oz);
     wk.nd = 0;
     wk.mcap = 0;
 }
@@ -387,6 +392,10 @@ int alloc_work(const feast_nl_handle* h, Work& wk, int nd, int nc, int m) {
         CK(dalloc(&wk.Qsl, qb));
         CK(cudaMemsetAsync(wk.Qsl, 0, qb, g_alloc_stream));
         CK(dalloc(&wk.Tau, (size_t)M));
+        // one contour with a subspace wide enough for the tensor cores to pay:
+        // X = Q Y, T(X, Lambda) = W Ycat and Q R^{-1} as digit-split products
+        if (nd == 1 && m >= kOzMinCols && ozaki_supported((int64_t)T * m, h->oz_s))
+            CK(dalloc(&wk.Oz, ozaki_general_work_bytes(n, T * m, m, h->oz_s)));
     }
     wk.nd = nd;
     wk.mcap = m;
@@ -433,6 +442,7 @@ Disc disc_view(const feast_nl_handle* h, const NodeSet& ns, const Work& wk, int 
     D.Relres = wk.Relres + (int64_t)d * m;
     D.Red = wk.Red + d * wk.red_bytes;
     D.Beyn = wk.Beyn ? wk.Beyn + d * wk.beyn_bytes : nullptr;
+    D.Oz = (wk.Oz && wk.nd == 1) ? wk.Oz : nullptr;
     D.status = wk.Status + d;
     D.splits = wk.splits;
     return D;
@@ -516,7 +526,11 @@ int orthonormalize(feast_nl_handle* h, Disc D) {
         CK(to_float(D.st, n * m, D.Q, Q32));
         CK(gram_f32(D.st, m, (int)n, Q32, n, D.G2, m, reinterpret_cast<float2*>(D.Split), D.splits));
         CK(chol_inverse(D.st, m, D.G2, 1e-6, D.Rinv, D.status));
-        CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Rinv, m, 0, zero, D.Qt, n, 0, 1));
+        if (D.Oz)
+            CK(ozaki_gemm_general(D.st, n, m, m, D.Q, n, D.Rinv, m, D.Qt, n, h->oz_s, D.Oz,
+                                  &D.status->flags));
+        else
+            CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Rinv, m, 0, zero, D.Qt, n, 0, 1));
         std::swap(D.Q, D.Qt);
     }
     return FEAST_NL_OK;
@@ -545,11 +559,19 @@ int ritz_and_residual(feast_nl_handle* h, const Disc& D, double tol) {
                              D.Yred, D.status));
     }
     Phase ph(h, FEAST_NL_PH_RITZ, D.prof);
-    CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Yred, m, 0, zero, D.X, n, 0, 1));
+    if (D.Oz)
+        CK(ozaki_gemm_general(D.st, n, m, m, D.Q, n, D.Yred, m, D.X, n, h->oz_s, D.Oz,
+                              &D.status->flags));
+    else
+        CK(gemm<double2>(D.st, 0, (int)n, m, m, one, D.Q, n, 0, D.Yred, m, 0, zero, D.X, n, 0, 1));
     CK(column_norms(D.st, n, m, D.X, n, D.Nu));
     CK(ritz_scale(D.st, n, m, T, h->dTerms, D.Lam, D.Nu, D.X, D.Yred, D.Ycat));
-    CK(gemm<double2>(D.st, 0, (int)n, m, T * m, one, D.W, n, 0, D.Ycat, (int64_t)T * m, 0, zero, D.R,
-                     n, 0, 1));
+    if (D.Oz)
+        CK(ozaki_gemm_general(D.st, n, T * m, m, D.W, n, D.Ycat, (int64_t)T * m, D.R, n, h->oz_s,
+                              D.Oz, &D.status->flags));
+    else
+        CK(gemm<double2>(D.st, 0, (int)n, m, T * m, one, D.W, n, 0, D.Ycat, (int64_t)T * m, 0, zero,
+                         D.R, n, 0, 1));
     CK(column_norms(D.st, n, m, D.R, n, D.Rnorm));
     CK(residual_summary(D.st, m, T, h->dTerms, D.Lam, D.Rnorm, D.c_re, D.c_im, D.ra, D.rb, tol,
                         D.Relres, D.status));

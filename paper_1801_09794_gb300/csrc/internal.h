@@ -215,6 +215,15 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, co
                        const double* tau, double2* W, const int* term_slot, int* err,
                        const int* active = nullptr);
 
+// C (M x N) = A (M x K) B (K x N), complex128 column-major (leading dimensions
+// lda, ldb, ldc), FP64-accurate on the BF16 tensor cores (s digit slices of the
+// row-scaled A and column-scaled B); work holds ozaki_general_work_bytes.  For
+// the tall, thin products of the subspace steps (M = n, K and N a few m0).
+size_t ozaki_general_work_bytes(int64_t M, int K, int N, int s);
+cudaError_t ozaki_gemm_general(cudaStream_t st, int64_t M, int K, int N, const double2* A,
+                               int64_t lda, const double2* B, int64_t ldb, double2* C, int64_t ldc,
+                               int s, void* work, int* err);
+
 // ------------------------------------------------------------------ LU (k_lu.cu)
 // One node matrix of a grouped factorisation (orders may differ): F is n x n
 // column-major (leading dimension n) in the LU precision; piv (n), info (1),

@@ -288,14 +288,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
 // digit slices
 // ---------------------------------------------------------------------------
 // sigma_i = 2^e with max_k |A'_ik| < 2^e (1 for a zero row), one thread per row.
-__global__ void row_scale_kernel(int64_t n, const double2* __restrict__ A, double* __restrict__ sigma,
-                                 int64_t Mrows_pad) {
+__global__ void row_scale_kernel(int64_t M, int64_t K, const double2* __restrict__ A, int64_t lda,
+                                 double* __restrict__ sigma, int64_t Mrows_pad) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= Mrows_pad) return;
     double mx = 0.0;
-    if (i < n)
-        for (int64_t k = 0; k < n; ++k) {
-            double2 a = A[i + k * n];
+    if (i < M)
+        for (int64_t k = 0; k < K; ++k) {
+            double2 a = A[i + k * lda];
             mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
         }
     int e = 0;
@@ -313,20 +313,21 @@ __device__ __forceinline__ void digits(double r, int s, float* d) {
     }
 }
 
-// A' slices [slice][Mpad][Kp] (bf16): K index k -> Re A[i,k], n + k -> Im A[i,k].
+// A' slices [slice][Mpad][Kp] (bf16) of an M x K block A (leading dimension
+// lda): K index k -> Re A[i,k], K + k -> Im A[i,k].
 // Block 32 x 8 handles 32 rows x 32 complex columns through shared memory.
-__global__ void split_rows_kernel(int64_t n, int s, const double2* __restrict__ A,
-                                  const double* __restrict__ sigma, __nv_bfloat16* __restrict__ out,
-                                  int64_t slice_stride, int64_t Kp) {
+__global__ void split_rows_kernel(int64_t M, int64_t K, int s, const double2* __restrict__ A,
+                                  int64_t lda, const double* __restrict__ sigma,
+                                  __nv_bfloat16* __restrict__ out, int64_t slice_stride, int64_t Kp) {
     __shared__ float tile[kOzMaxSlices][2][32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
     const int64_t i = i0 + tx;
-    const double inv = (i < n) ? 1.0 / sigma[i] : 0.0;     // exact: sigma is a power of 2
+    const double inv = (i < M) ? 1.0 / sigma[i] : 0.0;     // exact: sigma is a power of 2
     for (int kk = ty; kk < 32; kk += 8) {
         const int64_t k = k0 + kk;
         double2 a = make_double2(0.0, 0.0);
-        if (i < n && k < n) a = A[i + k * n];
+        if (i < M && k < K) a = A[i + k * lda];
         float dr[kOzMaxSlices], di[kOzMaxSlices];
         digits(a.x * inv, s, dr);
         digits(a.y * inv, s, di);
@@ -336,24 +337,25 @@ __global__ void split_rows_kernel(int64_t n, int s, const double2* __restrict__ 
     for (int rr = ty; rr < 32; rr += 8) {
         const int64_t row = i0 + rr;
         const int64_t k = k0 + tx;
-        if (k >= n) continue;
+        if (k >= K) continue;
         for (int p = 0; p < s; ++p) {
             __nv_bfloat16* o = out + p * slice_stride + row * Kp;
             o[k] = __float2bfloat16_rn(tile[p][0][rr][tx]);
-            o[n + k] = __float2bfloat16_rn(tile[p][1][rr][tx]);
+            o[K + k] = __float2bfloat16_rn(tile[p][1][rr][tx]);
         }
     }
 }
 
-// Q' slices for complex column j (rows 2j, 2j+1 of [slice][Npad][Kp]) and tau_j.
-__global__ void split_cols_kernel(int64_t n, int s, const double2* __restrict__ Q,
+// Q' slices for complex column j of a K x N block Q (leading dimension ldq):
+// rows 2j, 2j+1 of [slice][Npad][Kp], and tau_j.
+__global__ void split_cols_kernel(int64_t K, int s, const double2* __restrict__ Q, int64_t ldq,
                                   double* __restrict__ tau, __nv_bfloat16* __restrict__ out,
                                   int64_t slice_stride, int64_t Kp) {
     __shared__ double red[32];
     const int j = blockIdx.x;
-    const double2* q = Q + (int64_t)j * n;
+    const double2* q = Q + (int64_t)j * ldq;
     double mx = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
         mx = fmax(mx, fmax(fabs(q[k].x), fabs(q[k].y)));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -368,7 +370,7 @@ __global__ void split_cols_kernel(int64_t n, int s, const double2* __restrict__ 
     }
     __syncthreads();
     const double inv = 1.0 / red[0];
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
         float dr[kOzMaxSlices], di[kOzMaxSlices];
         digits(q[k].x * inv, s, dr);
         digits(q[k].y * inv, s, di);
@@ -376,9 +378,9 @@ __global__ void split_cols_kernel(int64_t n, int s, const double2* __restrict__ 
             __nv_bfloat16* r0 = out + p * slice_stride + (int64_t)(2 * j) * Kp;
             __nv_bfloat16* r1 = r0 + Kp;
             r0[k] = __float2bfloat16_rn(dr[p]);
-            r0[n + k] = __float2bfloat16_rn(-di[p]);
+            r0[K + k] = __float2bfloat16_rn(-di[p]);
             r1[k] = __float2bfloat16_rn(di[p]);
-            r1[n + k] = __float2bfloat16_rn(dr[p]);
+            r1[K + k] = __float2bfloat16_rn(dr[p]);
         }
     }
 }
@@ -409,11 +411,11 @@ cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, d
     cudaError_t e = cudaMemsetAsync(slices, 0, (size_t)L.a_term * sizeof(__nv_bfloat16), st);
     if (e != cudaSuccess) return e;
     note_launch();
-    row_scale_kernel<<<(unsigned)((L.Mpad + 127) / 128), 128, 0, st>>>(n, A, sigma, L.Mpad);
+    row_scale_kernel<<<(unsigned)((L.Mpad + 127) / 128), 128, 0, st>>>(n, n, A, n, sigma, L.Mpad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
     note_launch();
-    split_rows_kernel<<<g, dim3(32, 8), 0, st>>>(n, s, A, sigma,
+    split_rows_kernel<<<g, dim3(32, 8), 0, st>>>(n, n, s, A, n, sigma,
                                                   static_cast<__nv_bfloat16*>(slices), L.a_slice,
                                                   L.Kp);
     return cudaGetLastError();
@@ -422,7 +424,7 @@ cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, d
 cudaError_t ozaki_split_Q(cudaStream_t st, int64_t n, int m, int s, const double2* Q, double* tau,
                           void* slices, const OzakiLayout& L) {
     note_launch();
-    split_cols_kernel<<<m, 256, 0, st>>>(n, s, Q, tau, static_cast<__nv_bfloat16*>(slices),
+    split_cols_kernel<<<m, 256, 0, st>>>(n, s, Q, n, tau, static_cast<__nv_bfloat16*>(slices),
                                          L.b_slice, L.Kp);
     return cudaGetLastError();
 }
@@ -447,6 +449,84 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, co
         s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,
         sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * mb, mb,
         (int64_t)wterms * n * mb, term_slot, m, err, active);
+    return cudaGetLastError();
+}
+
+// General product on the same kernel: one "term" A (M x K), B (K x N).
+namespace {
+struct OzGeneralLayout {
+    OzakiLayout L;
+    size_t a_bytes, sigma_off, b_off, b_bytes, tau_off, slot_off, total;
+};
+OzGeneralLayout oz_general_layout(int64_t M, int K, int N, int s) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    OzGeneralLayout G;
+    G.L.s = s;
+    G.L.Mpad = (M + kOzM - 1) / kOzM * kOzM;
+    G.L.Kp = (2 * (int64_t)K + kOzBK - 1) / kOzBK * kOzBK;
+    G.L.Npad = (2 * (int64_t)N + kOzN - 1) / kOzN * kOzN;
+    G.L.a_slice = G.L.Mpad * G.L.Kp;
+    G.L.a_term = G.L.a_slice * s;
+    G.L.b_slice = G.L.Npad * G.L.Kp;
+    size_t o = 0;
+    G.a_bytes = (size_t)G.L.a_term * sizeof(__nv_bfloat16);
+    o = al(G.a_bytes);
+    G.sigma_off = o; o = al(o + (size_t)G.L.Mpad * sizeof(double));
+    G.b_off = o;
+    G.b_bytes = (size_t)G.L.b_slice * s * sizeof(__nv_bfloat16);
+    o = al(o + G.b_bytes);
+    G.tau_off = o; o = al(o + (size_t)N * sizeof(double));
+    G.slot_off = o; o = al(o + sizeof(int));
+    G.total = o;
+    return G;
+}
+}  // namespace
+
+size_t ozaki_general_work_bytes(int64_t M, int K, int N, int s) {
+    return oz_general_layout(M, K, N, s).total;
+}
+
+cudaError_t ozaki_gemm_general(cudaStream_t st, int64_t M, int K, int N, const double2* A,
+                               int64_t lda, const double2* B, int64_t ldb, double2* C, int64_t ldc,
+                               int s, void* work, int* err) {
+    if (M <= 0 || K <= 0 || N <= 0) return cudaSuccess;
+    if (!ozaki_supported(K, s)) return cudaErrorInvalidValue;
+    const OzGeneralLayout G = oz_general_layout(M, K, N, s);
+    unsigned char* w = static_cast<unsigned char*>(work);
+    __nv_bfloat16* Asl = reinterpret_cast<__nv_bfloat16*>(w);
+    double* sigma = reinterpret_cast<double*>(w + G.sigma_off);
+    __nv_bfloat16* Bsl = reinterpret_cast<__nv_bfloat16*>(w + G.b_off);
+    double* tau = reinterpret_cast<double*>(w + G.tau_off);
+    int* slot = reinterpret_cast<int*>(w + G.slot_off);
+    // the K padding of both operands must read as zero
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(Asl, 0, G.a_bytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(Bsl, 0, G.b_bytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(slot, 0, sizeof(int), st)) != cudaSuccess)
+        return e;
+    note_launch();
+    row_scale_kernel<<<(unsigned)((G.L.Mpad + 127) / 128), 128, 0, st>>>(M, K, A, lda, sigma, G.L.Mpad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    dim3 g((unsigned)((M + 31) / 32), (unsigned)((K + 31) / 32));
+    split_rows_kernel<<<g, dim3(32, 8), 0, st>>>(M, K, s, A, lda, sigma, Asl, G.L.a_slice, G.L.Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    split_cols_kernel<<<N, 256, 0, st>>>(K, s, B, ldb, tau, Bsl, G.L.b_slice, G.L.Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    static std::atomic<bool> attr_done{false};
+    const int smem = kOzStages * s * (kOzM + kOzN) * kOzBK * 2;
+    if (!attr_done) {
+        e = cudaFuncSetAttribute(ozaki_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kOzStages * kOzMaxSlices * (kOzM + kOzN) * kOzBK * 2);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)(G.L.Npad / kOzN), (unsigned)(G.L.Mpad / kOzM), 1u);
+    note_launch();
+    ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
+        s, (int)M, (int)G.L.Kp, Asl, G.L.a_slice, G.L.a_term, sigma, G.L.Mpad, Bsl, G.L.b_slice,
+        tau, C, ldc, 0, N, 0, slot, N, err, nullptr);
     return cudaGetLastError();
 }
 
