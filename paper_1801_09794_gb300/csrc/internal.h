@@ -293,6 +293,9 @@ cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2*
                              int64_t ldc, int64_t sC, int batch, int* err, int bn = 0,
                              const int* active = nullptr, int group = 1);
 int cgemm_default_bn(int n);
+// tile width of every LU trailing update (uniform and grouped alike, so that a
+// node's factors do not depend on the path)
+constexpr int kLuUpdateBn = 64;
 // The LU's trailing update for grouped nodes (lu_factor_grouped): node z of
 // `nodes`, panel at k0 of width min(nb, n - k0), columns of the look-ahead
 // split `mode`; the grid covers the largest node (max_rows x max_cols).

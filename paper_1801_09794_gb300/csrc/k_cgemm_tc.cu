@@ -312,7 +312,7 @@ cudaError_t launch(cudaStream_t st, int m, int n, int k, const float2* A, int64_
 
 cudaError_t cgemm_sub_grouped(cudaStream_t st, const LuNode* nodes, int count, int k0, int nb,
                               int mode, int64_t max_rows, int64_t max_cols, int* err) {
-    constexpr int BN = 64;
+    constexpr int BN = kLuUpdateBn;
     if (count <= 0 || max_rows <= 0 || max_cols <= 0) return cudaSuccess;
     if (count > 65535) return cudaErrorInvalidValue;
     constexpr int smem = stage_smem<BN>();

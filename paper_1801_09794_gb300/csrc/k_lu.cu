@@ -541,10 +541,11 @@ cudaError_t panel_apply(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_
         (int)ncols, nullptr, 1);
     const int64_t rows = n - k0 - jb;
     if (rows <= 0) return cudaGetLastError();
-    // the 64-column tile whatever the width, as in the grouped factorisation,
-    // so that a node's factors do not depend on which path formed them
+    // the same tile width as the grouped factorisation, so that a node's
+    // factors do not depend on which path formed them
     return update(st, (int)rows, (int)ncols, jb, F + (k0 + jb) + (int64_t)k0 * n, n, strideF,
-                  F + k0 + c0 * n, n, strideF, F + (k0 + jb) + c0 * n, n, strideF, nc, err, 64);
+                  F + k0 + c0 * n, n, strideF, F + (k0 + jb) + c0 * n, n, strideF, nc, err,
+                  kLuUpdateBn);
 }
 
 // Right-looking blocked LU with a look-ahead of one panel: after panel k is
