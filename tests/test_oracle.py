@@ -282,3 +282,44 @@ def test_stored_plain_qep_contour_matches_bruteforce():
     assert len(ins) == w["count"] == 16
     ref = np.array([complex(*x) for x in w["eigs_inside"]])
     assert match_sets(ins, ref) < 1e-11
+
+
+def _near_singular(problem, lam, steps=2, seed=0):
+    """||T(lam) x|| / sum_p |lam|^p ||A_p||_F after inverse iteration from a
+    random start (tiny when lam is an eigenvalue)."""
+    import scipy.linalg as sla
+    mats = problem_mats(problem)
+    T = np.zeros_like(mats[0])
+    for p in range(len(mats) - 1, -1, -1):
+        T = lam * T + mats[p]
+    lu = sla.lu_factor(T)
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(T.shape[0]) + 1j * rng.standard_normal(T.shape[0])
+    for _ in range(steps):
+        x = sla.lu_solve(lu, x)
+        x /= np.linalg.norm(x)
+    scale = sum(abs(lam) ** p * np.linalg.norm(A) for p, A in enumerate(mats))
+    return np.linalg.norm(T @ x) / scale
+
+
+def test_stored_slice_and_mixed_eigenvalues_are_eigenvalues():
+    # a sample of the stored references of the 64-disc and mixed-order
+    # workloads (from the oracle's shift-invert Arnoldi) checked against T itself
+    import json
+    from workloads import cubic_pep
+    with open(os.path.join(GOLD, "contours.json")) as f:
+        g = json.load(f)
+    sl = g["slices_n2048"]
+    p = cubic_pep(2048, 0)
+    picks = [(d, 0) for d in (0, 21, 42, 63) if sl["eigs_inside"][d]]
+    for d, i in picks:
+        lam = complex(*sl["eigs_inside"][d][i])
+        assert abs(lam - complex(*sl["centers"][d])) < sl["r"]
+        assert _near_singular(p, lam) < 1e-13
+        assert _near_singular(p, lam + 1e-3 * sl["r"]) > 1e-9     # the test can fail
+    for q in g["mixed_n"]["problems"]:
+        if q["n"] > 1024:
+            continue
+        pq = cubic_pep(q["n"], q["n"])
+        lam = complex(*q["eigs_inside"][3])
+        assert _near_singular(pq, lam) < 1e-13
