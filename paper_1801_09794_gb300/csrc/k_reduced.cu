@@ -72,7 +72,7 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 }
 
 constexpr int kRedThreads = 1024;
-constexpr int kQrChunk = 29;        // rotations per window in the QR sweep (window <= 32)
+constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (window <= 32)
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
