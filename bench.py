@@ -42,6 +42,10 @@ BEYN_NODES = 256                    # trapezoid nodes of the projected delay pro
 # and its command are under profiles/.  Absent: not captured for this code.
 ROOF_TRAFFIC = {("qep_mixed_n4096", "reduced"): 6 * 2301696}   # 6 iterations per step
 TF32_OVER_BF16 = 1.1 / 2.25
+# arithmetic of the path per node-factor precision
+DTYPES = {"fp64": "c128 (FP64 SIMT LU, solves and products) + f64",
+          "fp32": "c64 (tf32x3 tensor LU) + f64",
+          "fp32_i8": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64"}
 
 WORKLOADS = {
     "qep_mixed_n4096": {"gen": "config2_qep", "n": 4096, "precision": "fp32_i8", "tol": 1e-10,
@@ -348,7 +352,7 @@ def run_gpu(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64",
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[spec["precision"]],
            "data": "synthetic (seeded generator, no dataset)",
            "config": {"workload": args.workload, "n": n, "T": describe_terms(problem), "nc": c["nc"],
                       "m0": m0, "count_inside": c["count"], "lu_precision": spec["precision"],
@@ -958,9 +962,14 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="qep_mixed_n4096")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_i8"], default=None,
+                    help="override the workload's node-factor precision (e.g. fp64: the plain "
+                         "complex128 per-node form, for comparison)")
     ap.add_argument("--no-graph", action="store_true",
                     help="slicing workloads: launch each iteration's kernels one by one")
     args = ap.parse_args()
+    if args.precision and args.workload in WORKLOADS:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], precision=args.precision)
     if args.workload == "serving":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving stream is measured "
