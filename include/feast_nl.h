@@ -327,6 +327,15 @@ int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t feast_nl_launch_count(void);
 
+/* Failure-path self-test (no counterpart in the paper).  Every wait of the
+ * tensor-core kernels on an mbarrier gives up after a bounded number of
+ * cycles, sets bit 4 of the call's status (reported as EDEVICE) and lets the
+ * kernel finish normally, so a lost arrival never hangs the GPU.  This runs
+ * that wait, with a limit of `cycles` (1 .. 2^32), on a barrier that nothing
+ * signals, and returns the status bits it left in *flags_out (16 when the
+ * wait ran out, as it must).  The context stays usable afterwards. */
+int feast_nl_selftest_bounded_wait(int64_t cycles, int32_t* flags_out);
+
 /* ---- allocation-free Gram product --------------------------------------------
  * G = Q^H Q for a device-resident n x m block Q.  The paper has no counterpart:
  * this serves callers that must not touch the CUDA allocator (their device

@@ -37,7 +37,8 @@ EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_n
            "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy",
            "feast_nl_slices_create", "feast_nl_slices_solve", "feast_nl_slices_get_eigpairs",
            "feast_nl_slices_graph_launches", "feast_nl_slices_destroy",
-           "feast_nl_set_contour_group", "feast_nl_server_set_group_limit"]
+           "feast_nl_set_contour_group", "feast_nl_server_set_group_limit",
+           "feast_nl_selftest_bounded_wait"]
 FEAST_NL_SLICES_NO_GRAPH = 1
 PHASES = ["assemble", "lu", "apply", "project", "reduced", "ritz", "solve", "accum", "orth", "io"]
 
@@ -121,6 +122,7 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_slices_graph_launches.argtypes = [P]
     lib.feast_nl_slices_graph_launches.restype = I64
     lib.feast_nl_set_contour_group.argtypes = [I32, P, P, P, P, P, P, I32, P]
+    lib.feast_nl_selftest_bounded_wait.argtypes = [I64, ctypes.POINTER(I32)]
     lib.feast_nl_slices_destroy.argtypes = [P]
     lib.feast_nl_slices_destroy.restype = None
     for name in EXPORTS:

@@ -872,6 +872,30 @@ const char* feast_nl_last_error(void) { return g_last_error.c_str(); }
 
 int64_t feast_nl_launch_count(void) { return (int64_t)launch_count(); }
 
+int feast_nl_selftest_bounded_wait(int64_t cycles, int32_t* flags_out) {
+    g_last_error.clear();
+    if (!flags_out || cycles < 1 || cycles > ((int64_t)1 << 32))
+        return fail(FEAST_NL_EINVAL, "need flags_out and 1 <= cycles <= 2^32");
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rc = [&]() -> int {
+        AllocScope as(st);
+        int* d = nullptr;
+        CK(dalloc(&d, 1));
+        CK(cudaMemsetAsync(d, 0, sizeof(int), st));
+        CK(bounded_wait_probe(st, (long long)cycles, d));
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        dfree(d);
+        *flags_out = h;
+        return FEAST_NL_OK;
+    }();
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
 int feast_nl_set_profiling(feast_nl_handle* h, int32_t on) {
     CKS(validate_handle(h));
     h->prof = on != 0;

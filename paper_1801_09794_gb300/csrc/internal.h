@@ -293,6 +293,8 @@ cudaError_t cgemm_sub_tf32x3(cudaStream_t st, int m, int n, int k, const float2*
                              int64_t ldc, int64_t sC, int batch, int* err, int bn = 0,
                              const int* active = nullptr, int group = 1);
 int cgemm_default_bn(int n);
+// One CTA waits `cycles` on an mbarrier nothing signals, then sets bit 4 of *flags.
+cudaError_t bounded_wait_probe(cudaStream_t st, long long cycles, int* flags);
 // tile width of every LU trailing update (uniform and grouped alike, so that a
 // node's factors do not depend on the path)
 constexpr int kLuUpdateBn = 64;

@@ -333,6 +333,28 @@ cudaError_t cgemm_sub_grouped(cudaStream_t st, const LuNode* nodes, int count, i
     return cudaGetLastError();
 }
 
+namespace {
+// Waits on an mbarrier that nothing arrives at, with the kernels' bounded wait
+// and a caller-chosen limit: the wait must run out, set the error bit and
+// return (the failure path every tensor-core kernel takes on a lost arrival).
+__global__ void bounded_wait_probe_kernel(long long limit, int* __restrict__ flags) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_for(smem_u32(&bar), 0, limit);
+    if (!ok && threadIdx.x == 0) atomicOr(flags, 16);
+}
+}  // namespace
+
+cudaError_t bounded_wait_probe(cudaStream_t st, long long cycles, int* flags) {
+    note_launch();
+    bounded_wait_probe_kernel<<<1, 32, 0, st>>>(cycles, flags);
+    return cudaGetLastError();
+}
+
 int cgemm_default_bn(int n) {
     // the widest tile that wastes the fewest columns (e.g. 48 for 96 right-hand sides)
     int best = 64, waste = ((n + 63) / 64) * 64 - n;

@@ -33,13 +33,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^31 cycles and reports it.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+// Bounded wait: gives up after `limit` cycles and reports it (false).
+__device__ __forceinline__ bool mbar_wait_for(uint32_t addr, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try(addr, parity)) {
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
+}
+// The kernels' wait: ~2^31 cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    return mbar_wait_for(addr, parity, 1ll << 31);
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
