@@ -72,7 +72,7 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 }
 
 constexpr int kRedThreads = 1024;
-constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (window <= 32)
+constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (<= 29)
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
@@ -290,18 +290,19 @@ constexpr int kQrThreads = 256;
 constexpr int kSmallMax = 32;      // active blocks up to this order go to one warp
 constexpr int kSmallLd = 33;       // leading dimension of that dense copy (bank spread)
 
-// G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0)
+// G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0).  Written
+// with selects (no branches) so that a sweep step stays one basic block.
 template <typename R>
 __device__ __forceinline__ void givens(typename cx<R>::type x, typename cx<R>::type y, R& c,
                                        typename cx<R>::type& s) {
     const R nx = cnorm2(x), ny = cnorm2(y);
-    if (ny == (R)0) { c = 1; s.x = 0; s.y = 0; }
-    else if (nx == (R)0) { const R iy = rsqrt(ny); c = 0; s.x = y.x * iy; s.y = -y.y * iy; }
-    else {
-        const R irho = rsqrt(nx + ny), ix = rsqrt(nx);
-        c = nx * ix * irho;                        // |x| / rho
-        s = cscale(ix * irho, x * cconj(y));       // (x/|x|) conj(y) / rho
-    }
+    const R irho = rsqrt(nx + ny), ix = rsqrt(nx), iy = rsqrt(ny);
+    const R f = ix * irho;
+    const typename cx<R>::type xy = x * cconj(y);
+    const bool yz = ny == (R)0, xz = nx == (R)0;
+    c = yz ? (R)1 : (xz ? (R)0 : nx * ix * irho);  // |x| / rho
+    s.x = yz ? (R)0 : (xz ? y.x * iy : f * xy.x);  // (x/|x|) conj(y) / rho
+    s.y = yz ? (R)0 : (xz ? -y.y * iy : f * xy.y);
 }
 
 // Eigenvalues of the ns x ns (ns <= 32) Hessenberg matrix S (column-major, ld
@@ -375,6 +376,85 @@ __device__ int small_hess_eig(typename cx<R>::type* S, int ns, typename cx<R>::t
     }
 #undef SS
     return total;
+}
+
+// One window of a single-shift sweep over the active block l..hi: rotations
+// G_kk, kk = k..k+kb-1 (kb <= 29), one warp.  The matrix must hold the state
+// after rotation k-1 in full; on return it holds the state after rotation
+// k+kb-1 except for what the CTA applies afterwards (the row rotations on the
+// columns right of the window, the column rotations on rows <= kk).
+//
+// Every lane carries the bulge neighbourhood of the current rotation in
+// registers (x = H(kk,kk-1), y = H(kk+1,kk-1) [x = H(l,l) - mu, y = H(l+1,l)
+// for kk = l], P = H(kk,kk), Qv = H(kk+1,kk), U = H(kk,kk+1), D = H(kk+1,kk+1),
+// E = H(kk+2,kk+1)) and computes the rotation itself, so a step's only serial
+// dependence is rotation -> next bulge.  Lane t owns column k-1+t.  At step kk
+// it writes that column's row kk: the final row-rotation value while the
+// column is right of the frontier (it keeps the carry H(kk+1, .) meanwhile),
+// then H(kk,kk+1), H(kk,kk) and the new subdiagonal H(kk,kk-1) as the frontier
+// passes; it hands H(kk+1,kk+2), H(kk+2,kk+2), H(kk+3,kk+2) to all lanes when
+// its column enters the frontier.  A column rotation only has to reach rows
+// kk+1, kk+2 before the next row rotation; on rows <= kk it is deferred.  The
+// bulge slot H(kk+1,kk-1) is not cleared: it is read only as the opening y of
+// the next window, which the closing writes below provide.  Each shared-memory
+// location is read and written by its column's lane only after the opening
+// broadcast reads, so the steps need no warp barrier.
+template <typename R, int KB>
+__device__ __forceinline__ void qr_window(typename cx<R>::type* H, int l, int hi, int k, int kb,
+                                          int w1, typename cx<R>::type mu, R* s_c,
+                                          typename cx<R>::type* s_s) {
+    typedef typename cx<R>::type CT;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x & 31;
+    const CT zero = czero<CT>();
+    CT P = H[PK(k, k)], Qv = H[PK(k + 1, k)];
+    CT x, y;
+    if (k == l) { x = P - mu; y = Qv; }
+    else        { x = H[PK(k, k - 1)]; y = H[PK(k + 1, k - 1)]; }
+    CT U = H[PK(k, k + 1)], D = H[PK(k + 1, k + 1)];
+    CT E = (k + 2 <= hi) ? H[PK(k + 2, k + 1)] : zero;
+    const int col = k - 1 + t;
+    const bool own = col >= l && col <= w1;
+    CT* pc = H + (own ? PK(0, col) : 0);          // pc[i] = H(i, col)
+    CT a = zero, Dl = zero, El = zero;
+    if (own && t >= 3) {
+        a = pc[k];
+        Dl = pc[col];
+        if (col + 1 <= hi) El = pc[col + 1];
+    }
+    __syncwarp();                      // the broadcast reads above come first
+    const int nsteps = KB ? KB : kb;
+#pragma unroll 4
+    for (int r = 0; r < nsteps; ++r) {
+        const int kk = k + r;
+        const bool carry = own && t >= r + 3;
+        const CT h = carry ? pc[kk + 1] : zero;
+        R c;
+        CT s;
+        givens<R>(x, y, c, s);
+        if (t == 0) { s_c[r] = c; s_s[r] = s; }
+        const CT R00 = cscale(c, P) + s * Qv, R10 = cscale(c, Qv) - cconj(s) * P;
+        const CT R01 = cscale(c, U) + s * D, R11 = cscale(c, D) - cconj(s) * U;
+        const CT rho = cscale(c, x) + s * y;
+        const CT out = cscale(c, a) + s * h;
+        const CT val = carry ? out : (t == r + 2 ? R01 : (t == r + 1 ? R00 : rho));
+        if (own && t >= r) pc[kk] = val;
+        if (carry) a = cscale(c, h) - cconj(s) * a;
+        // column rotation kk on rows kk+1, kk+2 (H(kk+2, kk) was zero)
+        x = cscale(c, R10) + cconj(s) * R11;
+        P = cscale(c, R11) - s * R10;
+        y = cconj(s) * E;
+        Qv = cscale(c, E);
+        // column kk+2 (lane r+3) enters the frontier
+        U.x = __shfl_sync(full, a.x, r + 3);  U.y = __shfl_sync(full, a.y, r + 3);
+        D.x = __shfl_sync(full, Dl.x, r + 3); D.y = __shfl_sync(full, Dl.y, r + 3);
+        E.x = __shfl_sync(full, El.x, r + 3); E.y = __shfl_sync(full, El.y, r + 3);
+    }
+    const int kl = k + nsteps - 1;
+    const bool more = kl + 2 <= hi;
+    if (t == nsteps)     { pc[kl + 1] = x; if (more) pc[kl + 2] = y; }
+    if (t == nsteps + 1) { pc[kl + 1] = P; if (more) pc[kl + 2] = Qv; }
+    if (t == nsteps + 2 && more) pc[kl + 1] = a;
 }
 
 // ---------------------------------------------------------------------------
@@ -495,66 +575,45 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
         __syncthreads();
         for (int k = l; k < hi; k += kQrChunk) {
             const int kb = min(kQrChunk, hi - k);
-            const int w0 = (k == l) ? l : k - 1;
             const int w1 = min(k + kb + 1, hi);
             if (warp == 0) {
-                // the window holds at most kQrChunk + 3 <= 32 rows / columns:
-                // one element per lane in each update
-                for (int r = 0; r < kb; ++r) {
-                    const int kk = k + r;
-                    CT x, y;
-                    if (kk == l) { x = HH(l, l) - mu; y = HH(l + 1, l); }
-                    else         { x = HH(kk, kk - 1); y = HH(kk + 1, kk - 1); }
-                    R c;
-                    CT s;
-                    givens<R>(x, y, c, s);
-                    if (lane == 0) { s_c[r] = c; s_s[r] = s; }
-                    const int j = ((kk == l) ? l : kk - 1) + lane;
-                    if (j <= w1) {
-                        CT* h = H + PK(kk, j);
-                        const CT h1 = h[0], h2 = h[1];
-                        h[0] = cscale(c, h1) + s * h2;
-                        h[1] = (j == kk - 1) ? czero<CT>() : cscale(c, h2) - cconj(s) * h1;
-                    }
-                    __syncwarp();
-                    const int i = w0 + lane;
-                    if (i <= min(kk + 2, hi)) {
-                        CT* c0 = H + PK(i, kk);
-                        CT* c1 = H + PK(i, kk + 1);
-                        const CT h1 = *c0, h2 = *c1;
-                        *c0 = cscale(c, h1) + cconj(s) * h2;
-                        *c1 = cscale(c, h2) - s * h1;
-                    }
-                    __syncwarp();
-                }
+                if (kb == kQrChunk) qr_window<R, kQrChunk>(H, l, hi, k, kb, w1, mu, s_c, s_s);
+                else                qr_window<R, 0>(H, l, hi, k, kb, w1, mu, s_c, s_s);
             }
             __syncthreads();
-            // deferred: rows k..k+kb of the columns right of the window, and
-            // columns k..k+kb of the rows above it
-            const int nfc = hi - w1, nfr = w0 - l;
+            // deferred: the window's row rotations on the columns right of it
+            // (rows k..k+kb), its column rotations on the rows above the
+            // frontier (row i takes rotations max(i, k)..k+kb-1)
+            const int nfc = hi - w1, nfr = k + kb - l;
             for (int t = tid; t < nfc + nfr; t += nt) {
                 if (t < nfc) {
-                    const int j = w1 + 1 + t;
-                    CT a = HH(k, j);
+                    CT* col = H + PK(k, w1 + 1 + t);
+                    CT a = col[0];
                     for (int r = 0; r < kb; ++r) {
                         const R c = s_c[r];
                         const CT s = s_s[r];
-                        CT b = HH(k + r + 1, j);
-                        HH(k + r, j) = cscale(c, a) + s * b;
+                        const CT b = col[r + 1];
+                        col[r] = cscale(c, a) + s * b;
                         a = cscale(c, b) - cconj(s) * a;
                     }
-                    HH(k + kb, j) = a;
+                    col[kb] = a;
                 } else {
                     const int i = l + (t - nfc);
-                    CT a = HH(i, k);
-                    for (int r = 0; r < kb; ++r) {
+                    const int r0 = max(i, k) - k;
+                    int cj = k + r0;                  // column of the carry
+                    int off = PK(i, cj);
+                    CT a = H[off];
+                    for (int r = r0; r < kb; ++r) {
                         const R c = s_c[r];
                         const CT s = s_s[r];
-                        CT b = HH(i, k + r + 1);
-                        HH(i, k + r) = cscale(c, a) + cconj(s) * b;
+                        const int off1 = off + cj + 3;   // PK(i, cj + 1)
+                        const CT b = H[off1];
+                        H[off] = cscale(c, a) + cconj(s) * b;
                         a = cscale(c, b) - s * a;
+                        off = off1;
+                        ++cj;
                     }
-                    HH(i, k + kb) = a;
+                    H[off] = a;
                 }
             }
             __syncthreads();
@@ -1357,6 +1416,8 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                                       kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(newton_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024)) != cudaSuccess) return e;
         attr_done = true;
     }
     const BeynLayout L = beyn_layout(m);
@@ -1404,6 +1465,15 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     note_launch();
     newton_kernel<float2><<<m, kNewtonThreads, nsm32, st>>>(
         m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // a pair the FP32-factor Newton did not converge or moved too far: all kept
+    // values refined again from the same starts with FP64 factors (device-side
+    // no-op otherwise), so no Ritz value is left at its FP32 moment estimate
+    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
+                         sizeof(int) * m;
+    note_launch();
+    newton_kernel<double2><<<m, kNewtonThreads, nsm64, st>>>(
+        m, P, lam0, gap, lam, Yred, flag, 2, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
     return cudaGetLastError();
 }
 
