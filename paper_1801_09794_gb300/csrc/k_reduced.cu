@@ -73,6 +73,7 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 
 constexpr int kRedThreads = 1024;
 constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (<= 29)
+static_assert(kQrChunk >= 1 && kQrChunk <= 29, "lane t owns column k-1+t: a window spans kb+3 <= 32 columns");
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;
 
@@ -378,6 +379,12 @@ __device__ int small_hess_eig(typename cx<R>::type* S, int ns, typename cx<R>::t
     return total;
 }
 
+// An integer that orders like the double v (v not NaN; -0 taken as +0).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v + 0.0);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // One window of a single-shift sweep over the active block l..hi: rotations
 // G_kk, kk = k..k+kb-1 (kb <= 29), one warp.  The matrix must hold the state
 // after rotation k-1 in full; on return it holds the state after rotation
@@ -627,31 +634,43 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
     if (tid == 0) status->qr_sweeps = total;
     __syncthreads();
     #undef HH
-    // Step 2: rank by (rho, Re, Im, index); keep the first m0
+    // Step 2: rank by (rho, Re, Im, index); keep the first m0.  Each value's
+    // keys are formed once (rho in FP64 as the ranking defines it) into the
+    // matrix storage, dead now, as integers that order like the doubles; gap[]
+    // is the distance to the nearest other value (found in R, taken in FP64).
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(H);   // 3 per value
     for (int i = tid; i < N; i += nt) {
-        CT e = ev[i];
-        double ex = e.x, ey = e.y;
-        bool fin = isfinite(ex) && isfinite(ey);
-        double rx = (ex - c_re) / ra, ry = (ey - c_im) / rb;
-        double rho = fin ? sqrt(rx * rx + ry * ry) : INFINITY;
-        double kx = fin ? ex : INFINITY, ky = fin ? ey : INFINITY;
-        int rank = 0;
-        double g = INFINITY;
+        const CT e = ev[i];
+        const double ex = e.x, ey = e.y;
+        const bool fin = isfinite(ex) && isfinite(ey);
+        const double rx = (ex - c_re) / ra, ry = (ey - c_im) / rb;
+        key[3 * i] = order_key(fin ? sqrt(rx * rx + ry * ry) : INFINITY);
+        key[3 * i + 1] = order_key(fin ? ex : INFINITY);
+        key[3 * i + 2] = order_key(fin ? ey : INFINITY);
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {
+        const unsigned long long k0 = key[3 * i], k1 = key[3 * i + 1], k2 = key[3 * i + 2];
+        const CT e = ev[i];
+        const bool fin = isfinite(e.x) && isfinite(e.y);
+        int rank = 0, jn = -1;
+        R dn = (R)INFINITY;
         for (int j = 0; j < N; ++j) {
             if (j == i) continue;
-            CT f = ev[j];
-            double fx = f.x, fy = f.y;
-            bool ffin = isfinite(fx) && isfinite(fy);
-            double sx = (fx - c_re) / ra, sy = (fy - c_im) / rb;
-            double rj = ffin ? sqrt(sx * sx + sy * sy) : INFINITY;
-            double jx = ffin ? fx : INFINITY, jy = ffin ? fy : INFINITY;
-            bool less = (rj < rho) || (rj == rho && (jx < kx || (jx == kx && (jy < ky || (jy == ky && j < i)))));
+            const unsigned long long j0 = key[3 * j], j1 = key[3 * j + 1], j2 = key[3 * j + 2];
+            const bool less = j0 < k0 || (j0 == k0 && (j1 < k1 || (j1 == k1 && (j2 < k2 || (j2 == k2 && j < i)))));
             rank += less ? 1 : 0;
-            if (ffin && fin) g = fmin(g, hypot(fx - ex, fy - ey));
+            const CT f = ev[j];
+            if (fin && isfinite(f.x) && isfinite(f.y)) {
+                const R dx = f.x - e.x, dy = f.y - e.y;
+                const R d2 = dx * dx + dy * dy;
+                if (jn < 0 || d2 < dn) { dn = d2; jn = j; }
+            }
         }
         if (rank < m0) {
-            lam0[rank] = make_double2(ex, ey);
-            gap[rank] = g;
+            lam0[rank] = make_double2((double)e.x, (double)e.y);
+            gap[rank] = jn < 0 ? INFINITY
+                               : hypot((double)ev[jn].x - (double)e.x, (double)ev[jn].y - (double)e.y);
         }
     }
 }
