@@ -473,17 +473,19 @@ __device__ __forceinline__ void qr_window(typename cx<R>::type* H, int l, int hi
 // measured: it needs ~2.5x the shifts on these companion matrices, and its
 // FP32 eigenvalues come out too coarse for clustered reduced spectra.)
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool SMEM>
 __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
     int N, int m0, const typename cx<R>::type* __restrict__ C, typename cx<R>::type* Hglobal,
-    int use_smem, double c_re, double c_im, double ra, double rb, double2* __restrict__ lam0,
+    double c_re, double c_im, double ra, double rb, double2* __restrict__ lam0,
     double* __restrict__ gap, const int* redflag, int stage, IterStatus* status) {
     typedef typename cx<R>::type CT;
     if (stage == 2 && !(*redflag & kNeed64)) return;
     extern __shared__ unsigned char smem_raw[];
     CT* ev = reinterpret_cast<CT*>(smem_raw);   // N
     CT* Ssm = ev + N;                            // kSmallLd x kSmallMax
-    CT* H = use_smem ? Ssm + kSmallLd * kSmallMax : Hglobal;
+    // the packed matrix in shared memory when it fits (fixed at compile time, so
+    // the accesses are shared-memory ones), else in the global workspace
+    CT* H = SMEM ? Ssm + kSmallLd * kSmallMax : Hglobal;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
 #define HH(i, j) H[PK(i, j)]
     for (int j = tid; j < N; j += nt)
@@ -895,7 +897,6 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     __shared__ double red[4 * 33];
     __shared__ int s_p;
     const int i = blockIdx.x;
-    const int64_t mm = (int64_t)m * m;
     const double2 l0 = lam0[i];
     double2 l = l0;
     newton_build(m, P, l, T);
@@ -1058,6 +1059,19 @@ __global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2*
 size_t packed_elems(int N) { return (size_t)N * (N + 5) / 2 + 4; }
 constexpr int kMaxSmemPacked = 200 * 1024;
 
+cudaError_t qr_select_attributes() {
+    const int cap = kMaxSmemPacked + 16 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(qr_select_kernel<double, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(qr_select_kernel<double, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
 // Workspace layout, every region 256-byte aligned.
 struct RedLayout {
     size_t c32, lk32, c64, lk64, piv, h32, h64, lam0, gap, flag, total;
@@ -1107,8 +1121,12 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
     size_t smem = fixed + (use_smem ? hbytes : 0);
     note_launch();
-    qr_select_kernel<R><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, use_smem, c_re, c_im, ra, rb, lam0,
-                                              gap, flag, stage, status);
+    if (use_smem)
+        qr_select_kernel<R, true><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb, lam0,
+                                                               gap, flag, stage, status);
+    else
+        qr_select_kernel<R, false><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb, lam0,
+                                                                gap, flag, stage, status);
     return cudaGetLastError();
 }
 
@@ -1122,10 +1140,7 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
     cudaError_t e;
     if (!attr_done) {
-        if ((e = cudaFuncSetAttribute(qr_select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(qr_select_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
+        if ((e = qr_select_attributes()) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(newton_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1431,8 +1446,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                                       cap)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(beyn_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       cap)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(qr_select_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kMaxSmemPacked + 16 * 1024)) != cudaSuccess) return e;
+        if ((e = qr_select_attributes()) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(newton_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(newton_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1475,7 +1489,11 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     const int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
     const size_t qsm = fixed + (use_smem ? hbytes : 0);
     note_launch();
-    qr_select_kernel<float><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, use_smem, c_re, c_im, ra, rb,
+    if (use_smem)
+        qr_select_kernel<float, true><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra, rb,
+                                                                  lam0, gap, flag, 1, status);
+    else
+        qr_select_kernel<float, false><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra, rb,
                                                         lam0, gap, flag, 1, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Newton per kept value (FP32 factor, FP64 residuals), fillers beyond the rank
