@@ -72,6 +72,7 @@ __device__ void eig2x2(typename cx<R>::type a, typename cx<R>::type b, typename 
 }
 
 constexpr int kRedThreads = 1024;
+constexpr size_t kRedSmemCap = 216 * 1024;   // dynamic shared memory cap of the single-CTA kernels
 constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (<= 29)
 static_assert(kQrChunk >= 1 && kQrChunk <= 29, "lane t owns column k-1+t: a window spans kb+3 <= 32 columns");
 // flags word shared by the stages (device memory)
@@ -195,14 +196,24 @@ __global__ void __launch_bounds__(kRedThreads) companion_kernel(
 // ---------------------------------------------------------------------------
 // Householder reduction of C (N x N, in place) to upper Hessenberg form.
 // ---------------------------------------------------------------------------
+// Columns c0..N-1 (those that fit) are held in shared memory for the whole
+// reduction: at step j only columns > j are touched, so from j = c0 on every
+// access is on chip.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename cx<R>::type* __restrict__ C,
-                                                                 const int* redflag, int stage) {
+                                                                 int c0, const int* redflag, int stage) {
     typedef typename cx<R>::type CT;
     if (stage == 2 && !(*redflag & kNeed64)) return;
     extern __shared__ unsigned char smem_raw[];
     CT* sv = reinterpret_cast<CT*>(smem_raw);   // N
     CT* wp = sv + N;                              // G x N partial products
+    CT* S = wp + max(N, (int)blockDim.x);         // columns c0..N-1, N each
+    auto colp = [&](int c) -> CT* { return c >= c0 ? S + (int64_t)(c - c0) * N : C + (int64_t)c * N; };
+    {
+        const int64_t ns = (int64_t)(N - c0) * N;
+        for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) S[e] = C[(int64_t)c0 * N + e];
+        __syncthreads();
+    }
     __shared__ R red[32];
     __shared__ CT s_alpha;
     __shared__ R s_beta;
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
     const int r0 = (N <= nt) ? tid % N : tid, rstep = (N <= nt) ? N : nt;
     for (int j = 0; j + 2 < N; ++j) {
         const int len = N - j - 1;
-        CT* xcol = C + (int64_t)j * N + (j + 1);
+        CT* xcol = colp(j) + (j + 1);
         R s = 0;
         for (int r = tid; r < len; r += nt) s += cnorm2(xcol[r]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
         for (int r = 1 + tid; r < len; r += nt) sv[r] = xcol[r];
         __syncthreads();
         for (int cc = j + 1 + warp; cc < N; cc += nwarps) {
-            CT* col = C + (int64_t)cc * N + (j + 1);
+            CT* col = colp(cc) + (j + 1);
             CT w = czero<CT>();
             for (int r = lane; r < len; r += 32) w = cfma(cconj(sv[r]), col[r], w);
             for (int o = 16; o > 0; o >>= 1) {
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
         for (int r = r0; r < N; r += rstep) {
             CT w = czero<CT>();
             if (g < G)
-                for (int c = g; c < len; c += G) w = cfma(C[r + (int64_t)(j + 1 + c) * N], sv[c], w);
+                for (int c = g; c < len; c += G) w = cfma(colp(j + 1 + c)[r], sv[c], w);
             if (g < G) wp[g * N + r] = w;
         }
         __syncthreads();
@@ -276,12 +287,29 @@ __global__ void __launch_bounds__(kRedThreads) hessenberg_kernel(int N, typename
             for (int q = 0; q < G; ++q) w = w + wp[q * N + r];
             w = cscale(beta, w);
             for (int c = g; c < len; c += G) {
-                CT* p = C + r + (int64_t)(j + 1 + c) * N;
+                CT* p = colp(j + 1 + c) + r;
                 *p = cfms(w, cconj(sv[c]), *p);
             }
         }
         __syncthreads();
     }
+    __syncthreads();
+    const int64_t ns = (int64_t)(N - c0) * N;
+    for (int64_t e = threadIdx.x; e < ns; e += blockDim.x) C[(int64_t)c0 * N + e] = S[e];
+}
+
+// First column the Hessenberg kernel holds in shared memory, and its launch
+// size: as many trailing columns as fit beside the vector and the partial
+// products under the kernels' shared-memory cap.
+template <typename R>
+void hessenberg_launch_shape(int N, int* c0, size_t* smem) {
+    const size_t base = sizeof(typename cx<R>::type) * ((size_t)N + (size_t)max(N, kRedThreads));
+    const size_t cap = kRedSmemCap;
+    const size_t col = sizeof(typename cx<R>::type) * (size_t)N;
+    const size_t fit = base < cap ? (cap - base) / col : 0;
+    const int ncs = (int)min((size_t)N, fit);
+    *c0 = N - ncs;
+    *smem = base + (size_t)ncs * col;
 }
 
 // Packed Hessenberg storage with one bulge row: column j holds rows 0..j+2.
@@ -1061,7 +1089,12 @@ constexpr int kMaxSmemPacked = 200 * 1024;
 
 cudaError_t qr_select_attributes() {
     const int cap = kMaxSmemPacked + 16 * 1024;
+    static_assert(kRedSmemCap <= (size_t)kMaxSmemPacked + 16 * 1024, "one cap for the single-CTA kernels");
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(hessenberg_kernel<float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(hessenberg_kernel<double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(qr_select_kernel<float, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(qr_select_kernel<float, false>,
@@ -1113,8 +1146,10 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     note_launch();
-    const size_t hsm = sizeof(CT) * ((size_t)N + (size_t)max(N, kRedThreads));
-    hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, flag, stage);
+    int c0;
+    size_t hsm;
+    hessenberg_launch_shape<R>(N, &c0, &hsm);
+    hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, c0, flag, stage);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     size_t hbytes = packed_elems(N) * sizeof(CT);
     const size_t fixed = sizeof(CT) * ((size_t)N + kSmallLd * kSmallMax);   // ev, dense block
@@ -1480,9 +1515,11 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     beyn_svd_kernel<<<1, kSvdThreads, svd_smem, st>>>(m, A0, A1, c_re, c_im, ra, B, rank, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // eigenvalues of B (FP32 Hessenberg + QR), ranked by Step 2's rule
-    const size_t hsm = sizeof(float2) * ((size_t)m + (size_t)max(m, kRedThreads));
+    int c0;
+    size_t hsm;
+    hessenberg_launch_shape<float>(m, &c0, &hsm);
     note_launch();
-    hessenberg_kernel<float><<<1, kRedThreads, hsm, st>>>(m, B, flag, 1);
+    hessenberg_kernel<float><<<1, kRedThreads, hsm, st>>>(m, B, c0, flag, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t hbytes = packed_elems(m) * sizeof(float2);
     const size_t fixed = sizeof(float2) * ((size_t)m + kSmallLd * kSmallMax);
