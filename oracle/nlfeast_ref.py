@@ -12,7 +12,7 @@ problems of ``workloads/``.
 Everything is complex128 / float64 on the host, written for readability and
 not for speed: numpy/scipy LAPACK routines (LU, QR, QZ) serve as single steps.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
 
 * Quadrature (Algorithm 1 inputs; Step 4): the contour is
   z(theta) = c + ra*cos(theta) + i*rb*sin(theta), theta in [0, 2*pi)
