@@ -7,8 +7,9 @@ import pytest
 
 import oracle as O
 from tests.closed_forms import (inside_mask, match_sets, load_table1, second_companion_eigs,
-                                problem_mats)
-from workloads import (mass_spring, config1_qep, random_pep, start_block, linear_problem)
+                                problem_mats, family_eigs)
+from workloads import (mass_spring, config1_qep, random_pep, start_block, linear_problem,
+                       closed_form_family)
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -169,6 +170,30 @@ def test_solve_random_pep_matches_bruteforce(lib, k, prec):
     assert len(lam) == len(ref) == 7
     assert match_sets(lam, ref) < 1e-10
     assert np.all(rr <= 1e-10)
+    s.close()
+
+
+def test_solve_max_m0_closed_form(lib):
+    """m0 at its maximum (112) on a quadratic with closed-form eigenvalues
+    (A2 = I, A1 = 0.1 I, A0 = tridiag(-1, 3, -1): lambda = -0.05 +- i sqrt(s - 0.0025)
+    for the tridiagonal's eigenvalues s).  The reduced companion matrix (224 x 224)
+    no longer fits in shared memory: the QR chase runs on the global copy and the
+    Hessenberg reduction keeps only its trailing columns on chip."""
+    n, m0, cnt = 200, 112, 56
+    c, d, a = [0.0, 0.1, 1.0], [1.0, 0.0, 0.0], 3.0
+    p = closed_form_family(n, c, d, a)
+    lam_all = family_eigs(n, c, d, a)
+    cen = -0.05 + 1.6j
+    dist = np.sort(np.abs(lam_all - cen))
+    r = 0.5 * (dist[cnt - 1] + dist[cnt])       # boundary midway between two eigenvalues
+    s = lib.FeastNL(p, "fp32_i8")
+    s.set_contour(cen, r, r, 16, "gl")
+    st, info = s.solve(m0, tol=1e-11, maxit=60, X0=start_block(n, m0, 3))
+    lam, X, rr = s.get_eigpairs(inside_only=True)
+    ref = lam_all[inside_mask(lam_all, cen, r, r)]
+    assert len(lam) == len(ref) == cnt
+    assert match_sets(lam, ref) < 1e-10
+    assert np.all(rr <= 1e-11)
     s.close()
 
 
