@@ -40,7 +40,9 @@ BEYN_NODES = 256                    # trapezoid nodes of the projected delay pro
 # DRAM bytes per step of the dominant phase's kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, phase); the summary
 # and its command are under profiles/.  Absent: not captured for this code.
-ROOF_TRAFFIC = {("qep_mixed_n4096", "reduced"): 6 * 2301696}   # 6 iterations per step
+# DRAM bytes per step of the roofline object, from an ncu capture of the same
+# kernels (none is current: the reduced-stage kernels changed after the last one)
+ROOF_TRAFFIC = {}
 TF32_OVER_BF16 = 1.1 / 2.25
 # arithmetic of the path per node-factor precision
 DTYPES = {"fp64": "c128 (FP64 SIMT LU, solves and products) + f64",
