@@ -431,9 +431,9 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
 // its column enters the frontier.  A column rotation only has to reach rows
 // kk+1, kk+2 before the next row rotation; on rows <= kk it is deferred.  The
 // bulge slot H(kk+1,kk-1) is not cleared: it is read only as the opening y of
-// the next window, which the closing writes below provide.  Each shared-memory
-// location is read and written by its column's lane only after the opening
-// broadcast reads, so the steps need no warp barrier.
+// the next window, which the closing writes below provide.  Each matrix
+// location (shared or global memory) is read and written by its column's lane
+// only after the opening broadcast reads, so the steps need no warp barrier.
 template <typename R, int KB>
 __device__ __forceinline__ void qr_window(typename cx<R>::type* H, int l, int hi, int k, int kb,
                                           int w1, typename cx<R>::type mu, R* s_c,
