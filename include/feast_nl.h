@@ -245,7 +245,10 @@ int feast_nl_server_poll(feast_nl_server* s, uint64_t ticket, int32_t* state);
 int feast_nl_server_wait(feast_nl_server* s, uint64_t ticket, feast_nl_info* info,
                          double* latency_ms);
 /* Copies the kept Ritz pairs of a done request into host buffers (layouts as
- * feast_nl_get_eigpairs) and releases the ticket; returns the run's status. */
+ * feast_nl_get_eigpairs) and releases the ticket; returns the run's status.
+ * EINVAL for an unknown, unfinished or already fetched ticket, and while
+ * another thread is still inside feast_nl_server_wait on the same ticket (the
+ * ticket is released only once no thread waits on it). */
 int feast_nl_server_fetch(feast_nl_server* s, uint64_t ticket, int32_t capacity, int32_t* m_out,
                           double* lambda, void* X, double* relres, int32_t inside_only);
 /* At most `limit` requests admitted together are factored as one group (1:
@@ -346,8 +349,10 @@ int feast_nl_selftest_bounded_wait(int64_t cycles, int32_t* flags_out);
  *   G      : device, complex128, COLUMN-major m x m (leading dimension m), written
  *            in full (G is Hermitian).
  *   stream : cudaStream_t or NULL; the call is asynchronous on that stream.
- * Limits: 1 <= n <= 2^30, 1 <= m, m*m <= 262144 (m <= 512); larger sizes return
- * EINVAL without touching the GPU.  Q and G must be device pointers (EINVAL).
+ * Limits: 1 <= n <= 2^30, n <= ldq <= 2^40, 1 <= m, m*m <= 262144 (m <= 512);
+ * other sizes return EINVAL without touching the GPU.  Q and G must be device
+ * memory of the current device, or managed memory (else EINVAL: the kernel runs
+ * on the current device and must not reach into another GPU's memory).
  * The split-K partial sums live in one static 4 MiB device array that every GPU
  * loading this library holds until the process exits; every call overwrites the
  * partials it reads, so nothing needs clearing, but all calls share that array:

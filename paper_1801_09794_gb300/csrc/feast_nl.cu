@@ -1240,6 +1240,9 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
             for (int i = 0; i < m; ++i)
                 fprintf(stderr, "    %2d  % .12e % .12e  relres %.3e\n", i, lam[i].x, lam[i].y, rr[i]);
         }
+        // a timed-out tensor-core wait (bit 4) or a Ritz value on a node (bit 1)
+        // leaves the iterate invalid: stop now rather than at maxit
+        if (stt.flags & (16 | 2)) break;
         if (it > 1 && stt.n_conv == stt.n_inside) { converged = true; break; }
         if (it == maxit) break;
         CKS(filter_solve(h, h->ns, h->wk, 1, m, h->st, &D.status->flags, true));   // Step 4

@@ -23,10 +23,18 @@
 // three slice pairs each) are therefore accumulated in TMEM over 256-element
 // K chunks (3 * 256 * 127^2 < 2^24) and drained into int32 registers after
 // every chunk, which keeps them exact; levels L >= 5 carry weights <= 2^-35 and
-// are accumulated in FP32 over the whole K (relative effect <= 2^-45).  The
-// dropped pairs (p + q > s + 1) and the truncation remainders are below
-// 2^{-7s} of sigma_i (resp. tau_j) per operand entry; with s = 7 the product is
-// accurate to ~1e-14 relative to |A'| |Q'|.
+// are accumulated in FP32 over the whole K, i.e. K/16 sequential additions
+// into TMEM.  Their rounding error: each level sum has at most 4 digit pairs,
+// so |S_L| <= 4 * 127^2 * K, and K/16 additions at unit roundoff 2^-24 give
+// at most (K/16) 2^-24 |S_L| -- after the level weight, <= 2^-47 K relative to
+// sigma_i tau_j K (the row maximum times the column maximum times K): 5.8e-11
+// at the largest K here (2n = 8192) in the worst case, where every rounding
+// error has the same sign.  With rounding errors of random sign (the usual
+// model) the sum's error grows like sqrt(K/16) instead, ~2^-45 relative to
+// sigma_i tau_j K at any K.  The dropped pairs (p + q > s + 1) and the
+// truncation remainders are below 2^{-7s} of sigma_i (resp. tau_j) per operand
+// entry.  With s = 7 the measured error of the projections at n = 4096,
+// m0 = 96 is ~1e-15 relative (a GPU parity test checks it against FP64).
 //
 // Kernel: one CTA (256 threads) per 128 x 48 tile of W'.  K advances in
 // 16-element stages through a 5-slot cp.async ring (four stages in flight);

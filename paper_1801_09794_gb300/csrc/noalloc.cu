@@ -21,6 +21,9 @@ namespace {
 constexpr int64_t kScratchElems = 262144;
 __device__ __align__(256) double2 g_gram_scratch[kScratchElems];
 
+// Column stride cap: (m - 1) * ldq stays far inside int64 for every m <= 512.
+constexpr int64_t kMaxLd = (int64_t)1 << 40;
+
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
@@ -43,13 +46,17 @@ cudaError_t scratch_for_current_device(void** out) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// True when p is device memory of device dev, or managed memory (reachable from
+// every device).  Device memory of another GPU is rejected: the kernel runs on
+// the current device and would otherwise touch a peer's memory.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int bad(int code, const char* msg) {
@@ -65,8 +72,14 @@ extern "C" int feast_nl_gram_noalloc(int64_t n, int32_t m, const void* Q, int64_
     if ((int64_t)m * m > kScratchElems)
         return bad(FEAST_NL_EINVAL, "m*m exceeds the 262144-element static scratch (m <= 512)");
     if (n > (int64_t)1 << 30 || ldq < n) return bad(FEAST_NL_EINVAL, "need n <= 2^30 and ldq >= n");
-    if (!Q || !G || !on_device(Q) || !on_device(G))
-        return bad(FEAST_NL_EINVAL, "Q and G must be device pointers");
+    if (ldq > kMaxLd) return bad(FEAST_NL_EINVAL, "ldq exceeds 2^40 elements");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bad(FEAST_NL_EDEVICE, "no current CUDA device");
+    }
+    if (!Q || !G || !on_device(Q, dev) || !on_device(G, dev))
+        return bad(FEAST_NL_EINVAL, "Q and G must be device (or managed) memory of the current device");
     void* scratch = nullptr;
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return bad(FEAST_NL_EDEVICE, "cudaGetSymbolAddress of the scratch failed");

@@ -42,6 +42,7 @@ struct Request {
     std::vector<feast_nl_term> terms;   // the caller's terms (buffers stay the caller's)
     int64_t footprint = 0;
     int state = 0;                      // 0 queued, 1 running, 2 done
+    int waiters = 0;                    // threads blocked in feast_nl_server_wait on it
     int status = 0;
     feast_nl_handle* h = nullptr;       // from creation to the end of the solve
     feast_nl_info info{};
@@ -317,7 +318,9 @@ int feast_nl_server_wait(feast_nl_server* s, uint64_t ticket, feast_nl_info* inf
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return FEAST_NL_EINVAL;
     Request* q = it->second.get();
+    ++q->waiters;                       // fetch refuses the ticket while this is non-zero
     s->cv_done.wait(lk, [&] { return q->state == 2; });
+    --q->waiters;
     if (info) *info = q->info;
     if (latency_ms) *latency_ms = q->t_done - q->t_submit;
     return q->status;
@@ -331,6 +334,7 @@ int feast_nl_server_fetch(feast_nl_server* s, uint64_t ticket, int32_t capacity,
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(ticket);
         if (it == s->reqs.end() || it->second->state != 2) return FEAST_NL_EINVAL;
+        if (it->second->waiters > 0) return FEAST_NL_EINVAL;   // another thread still waits on it
         q = std::move(it->second);
         s->reqs.erase(it);
     }
