@@ -122,22 +122,45 @@ def describe_terms(problem):
     return " + ".join(parts)
 
 
-def count_good(lam, rr, gold, center, ra, rb, tol=1e-10):
+def count_good(lam, rr, gold, center, ra, rb, tol=1e-10, acc=None):
     """Kept pairs strictly inside the contour with relres <= tol, matched one-to-one
-    to the reference eigenvalues within relative tol."""
+    to the reference eigenvalues within relative tol.  With `acc` (new_accuracy()),
+    every pair inside also records its relative distance to the nearest reference
+    eigenvalue not yet matched and its relative residual."""
     used = np.zeros(len(gold), dtype=bool)
     good = 0
     for lv, r in zip(lam, rr):
         d = lv - center
-        if (d.real / ra) ** 2 + (d.imag / rb) ** 2 >= 1.0 or not (r <= tol):
+        if (d.real / ra) ** 2 + (d.imag / rb) ** 2 >= 1.0:
             continue
-        d = np.abs(gold - lv) / np.abs(gold)
-        d[used] = np.inf
+        d = np.abs(gold - lv) / np.abs(gold) if len(gold) else np.array([np.inf])
+        if len(gold):
+            d[used] = np.inf
         j = int(np.argmin(d))
-        if d[j] <= tol:
+        if acc is not None:
+            acc["err"].append(float(d[j]))
+            acc["relres"].append(float(r))
+        if r <= tol and d[j] <= tol:
             used[j] = True
             good += 1
     return good
+
+
+def new_accuracy():
+    return {"err": [], "relres": []}
+
+
+def accuracy_summary(acc):
+    """Per-result error against the FP64 oracle's eigenvalues (stored in
+    tests/golden/contours.json), over every pair inside the contour of every
+    counted step."""
+    e, r = np.array(acc["err"]), np.array(acc["relres"])
+    if len(e) == 0:
+        return {"pairs": 0}
+    return {"pairs": int(len(e)), "max_rel_eig_err": float(np.max(e)),
+            "median_rel_eig_err": float(np.median(e)), "max_relres": float(np.max(r)),
+            "median_relres": float(np.median(r)),
+            "reference": "FP64 oracle eigenvalues inside the contour (tests/golden/contours.json)"}
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -189,7 +212,52 @@ class ClockSampler:
         return out
 
 
+_LIVE_PEAKS = {}
+
+
+def probe_peaks(dev):
+    """Denominators the driver's peak file does not hold, measured here with the
+    vendor library (measurement only, never on the product path): FP64 DGEMM,
+    FP32 SGEMM on the FP32 lanes (TF32 off) and TF32 tensor GEMM, each the best
+    of five back-to-back calls timed with CUDA events (TFLOP/s, 2 N^3 flops)."""
+    if _LIVE_PEAKS:
+        return _LIVE_PEAKS
+    import torch
+    old = torch.backends.cuda.matmul.allow_tf32
+    out = {}
+    try:
+        for key, dt, nn, tf32 in (("fp64_tflops", torch.float64, 4096, False),
+                                  ("fp32_simt_tflops", torch.float32, 8192, False),
+                                  ("tf32_tflops", torch.float32, 8192, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(nn, nn, dtype=dt, device=dev)
+            b = torch.randn(nn, nn, dtype=dt, device=dev)
+            c = torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * nn ** 3 / (best / 1e3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    _LIVE_PEAKS.update(out)
+    return out
+
+
 def peaks():
+    pk = _peaks_file()
+    pk.update({k: v for k, v in _LIVE_PEAKS.items()})
+    return pk
+
+
+def _peaks_file():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
@@ -243,21 +311,30 @@ def phase_work(name, spec, c, iters, nterms_dense):
 
 
 def phase_peak(name, precision, pk, sm_mhz, delay=False):
+    """Peak of a phase: (TFLOP/s, bound, where the number comes from).  FP64,
+    FP32-lane and TF32 rates are the live library probes (probe_peaks) when
+    taken, else nominal figures scaled from the driver's BF16 measurement."""
     clk = (sm_mhz or 2070.0) / 2070.0
     if name in ("lu", "solve") and precision in ("fp32", "fp32_i8"):
-        # trailing updates / block substitutions: three TF32 products per FP32
-        # product; TF32 dense = half the BF16 rate (nominal 1.1 vs 2.25 PF/s)
+        # trailing updates / block substitutions: three TF32 products per FP32 product
+        if "tf32_tflops" in pk:
+            return (pk["tf32_tflops"] / 3.0, "tensor",
+                    "TF32 dense, measured (cuBLAS TF32 GEMM 8192^3, live), / 3 for the split products")
         return (pk["bf16_tflops"] * 0.5 / 3.0, "tensor",
                 f"TF32 dense = 0.5 x BF16 ({pk['source']}), / 3 for the split products")
     if name == "apply" and precision == "fp32_i8":
         return (pk["bf16_tflops_sustained"], "tensor",
                 f"BF16 dense, {pk['source']} (sustained figure: timed inside a long step)")
-    if name == "reduced" and delay:
-        return (FP32_SIMT_TFLOPS_AT_MAX * clk, "alu",
-                "FP32 lanes of all 152 SMs (the node solves of the moments span the GPU)")
     if name == "reduced":
-        return (ONE_SM_FP32_TFLOPS_AT_MAX * clk, "alu",
-                "FP32 lanes of the one SM the stage runs on (single CTA): 128 x 2 flop x SM clock")
+        # FP32 arithmetic on the SIMT lanes; the chip-wide rate is the roofline
+        # (the one-SM share is reported beside it for the single-CTA kernels)
+        if "fp32_simt_tflops" in pk:
+            return (pk["fp32_simt_tflops"], "alu",
+                    "FP32 lanes of the whole GPU, measured (cuBLAS SGEMM 8192^3 with TF32 off, live)")
+        return (FP32_SIMT_TFLOPS_AT_MAX * clk, "alu",
+                "FP32 lanes of all 152 SMs, nominal: 152 x 128 x 2 flop x SM clock")
+    if "fp64_tflops" in pk:
+        return pk["fp64_tflops"], "alu", "FP64, measured (cuBLAS DGEMM 4096^3, live)"
     return FP64_NOMINAL_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s"
 
 
@@ -305,10 +382,11 @@ def run_gpu(args):
     e0.record(stream)
     infos = []
     goods = []
+    acc = new_accuracy()
     for _ in range(args.steps):
         infos.append(step(s))
         lam, _, rr = s.get_eigpairs(inside_only=True, vectors=False)
-        goods.append(count_good(lam, rr, gold, center, c["ra"], c["rb"]))
+        goods.append(count_good(lam, rr, gold, center, c["ra"], c["rb"], acc=acc))
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -323,6 +401,8 @@ def run_gpu(args):
 
     # live per-phase roofline (CUDA events on the library's stream)
     iters = infos[-1].iters
+    if not args.no_peak_probe:
+        probe_peaks(dev)
     pk = peaks()
     phases = {}
     for name, (pms, pl) in prof.items():
@@ -334,6 +414,8 @@ def run_gpu(args):
             tf = w / (pms / args.steps / 1e3) / 1e12
             peak, bound, why = phase_peak(name, spec["precision"], pk, clk.get("sm_mhz"), spec["gen"] == "delay_problem")
             ent.update(tflops=tf, peak_tflops=peak, frac=tf / peak, bound=bound)
+            if name == "reduced":
+                ent["frac_of_one_sm"] = tf / (peak / 152.0)
         phases[name] = ent
     dom = max(phases, key=lambda k: phases[k]["ms_per_step"])
     d = phases[dom]
@@ -367,6 +449,7 @@ def run_gpu(args):
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                       "reasons": clk["reasons"]},
            "e2e": e2e, "gpu_launches": int(launches),
+           "accuracy": accuracy_summary(acc),
            "roofline": roof,
            "node_lu_tflops": lu.get("tflops"),
            "phases": phases, "peaks": pk}
@@ -475,11 +558,11 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------- slicing
-def slices_good(sl, centers, r, gold, tol=1e-10):
+def slices_good(sl, centers, r, gold, tol=1e-10, acc=None):
     good = 0
     for d, cen in enumerate(centers):
         lam, _, rr = sl.get_eigpairs(d, inside_only=True, vectors=False)
-        good += count_good(lam, rr, gold[d], cen, r, r, tol)
+        good += count_good(lam, rr, gold[d], cen, r, r, tol, acc=acc)
     return good
 
 
@@ -529,9 +612,10 @@ def run_slices(args):
     torch.cuda.synchronize()
     e0.record(stream)
     goods, fac_ms, it_ms, iters, gl = [], [], [], [], 0
+    acc = new_accuracy()
     for _ in range(args.steps):
         sl, infos = step()
-        goods.append(slices_good(sl, centers, r, gold))
+        goods.append(slices_good(sl, centers, r, gold, acc=acc))
         fac_ms.append(infos[0].ms_factor)
         it_ms.append(infos[0].ms_iterate)
         iters.append(max(i.iters for i in infos))
@@ -547,6 +631,8 @@ def run_slices(args):
     ms_max = reduce_over_ranks(ms, "max", dev)
     good_total = reduce_over_ranks(min(goods), "sum", dev)
     value = good_total / (ms_max / 1e3)
+    if not args.no_peak_probe:
+        probe_peaks(dev)
     pk = peaks()
     # dominant kernel group: the batched node LU (assembly + 512 factorisations,
     # CUDA events around it on the set's stream)
@@ -575,8 +661,8 @@ def run_slices(args):
                       "parallelism": f"replicas x{ws}"},
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                       "reasons": clk["reasons"]},
-           "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
-           "node_lu_tflops": ach, "peaks": pk}
+           "e2e": e2e, "gpu_launches": int(launches), "accuracy": accuracy_summary(acc),
+           "roofline": roof, "node_lu_tflops": ach, "peaks": pk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = slices_cpu_sample(args, problem, spec, c, centers, gold, discs=1)
     if rank == 0:
@@ -676,7 +762,7 @@ def run_slices_reference(args):
 
 
 # ---------------------------------------------------------------------------- mixed orders
-def mixed_step(P, hs, c, spec, seed, gold, stream=None):
+def mixed_step(P, hs, c, spec, seed, gold, stream=None, acc=None):
     """One step: grouped contours + factorisation of all problems, then their
     solves side by side (one host thread and one stream per problem)."""
     import threading
@@ -691,7 +777,8 @@ def mixed_step(P, hs, c, spec, seed, gold, stream=None):
         lam, _, rr = hs[i].get_eigpairs(inside_only=True, vectors=False)
         q = qs[i]
         cen = complex(*q["center"])
-        res[i] = (count_good(lam, rr, gold[i], cen, q["r"], q["r"]), info.iters, info.ms_factor)
+        res[i] = (count_good(lam, rr, gold[i], cen, q["r"], q["r"], acc=acc), info.iters,
+                  info.ms_factor)
     ts = [threading.Thread(target=run, args=(i,)) for i in range(len(hs))]
     for t in ts:
         t.start()
@@ -742,8 +829,9 @@ def run_mixed(args):
     torch.cuda.synchronize()
     e0.record(stream)
     goods, fac, iters = [], [], []
+    acc = new_accuracy()
     for _ in range(args.steps):
-        res = mixed_step(P, hs, c, spec, args.seed, gold, stream.cuda_stream)
+        res = mixed_step(P, hs, c, spec, args.seed, gold, stream.cuda_stream, acc=acc)
         goods.append(sum(r[0] for r in res))
         fac.append(res[0][2])
         iters = [r[1] for r in res]
@@ -760,6 +848,8 @@ def run_mixed(args):
     ns = [q["n"] for q in c["problems"]]
     lu_flops = c["nc"] * (8.0 / 3.0) * sum(n ** 3 for n in ns)
     fms = statistics.median(fac)
+    if not args.no_peak_probe:
+        probe_peaks(dev)
     pk = peaks()
     ach = lu_flops / (fms / 1e3) / 1e12
     peak, bound, why = phase_peak("lu", spec["precision"], pk, clk.get("sm_mhz"))
@@ -780,8 +870,8 @@ def run_mixed(args):
                       "parallelism": f"replicas x{ws}"},
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                       "reasons": clk["reasons"]},
-           "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
-           "node_lu_tflops": ach, "peaks": pk}
+           "e2e": e2e, "gpu_launches": int(launches), "accuracy": accuracy_summary(acc),
+           "roofline": roof, "node_lu_tflops": ach, "peaks": pk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = mixed_cpu_sample(args, problems, spec, c, gold, upto=2)
     if rank == 0:
@@ -967,6 +1057,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_i8"], default=None,
                     help="override the workload's node-factor precision (e.g. fp64: the plain "
                          "complex128 per-node form, for comparison)")
+    ap.add_argument("--no-peak-probe", action="store_true",
+                    help="skip the library GEMMs that measure the FP64 / FP32 / TF32 peaks after "
+                         "the timed region (use for ncu launch lists)")
     ap.add_argument("--no-graph", action="store_true",
                     help="slicing workloads: launch each iteration's kernels one by one")
     args = ap.parse_args()

@@ -394,8 +394,10 @@ int alloc_work(const feast_nl_handle* h, Work& wk, int nd, int nc, int m) {
         CK(dalloc(&wk.Tau, (size_t)M));
         // one contour with a subspace wide enough for the tensor cores to pay:
         // X = Q Y, T(X, Lambda) = W Ycat and Q R^{-1} as digit-split products
+        // (and the projections Q^H W, split over K)
         if (nd == 1 && m >= kOzMinCols && ozaki_supported((int64_t)T * m, h->oz_s))
-            CK(dalloc(&wk.Oz, ozaki_general_work_bytes(n, T * m, m, h->oz_s)));
+            CK(dalloc(&wk.Oz, std::max(ozaki_general_work_bytes(n, T * m, m, h->oz_s),
+                                       ozaki_project_work_bytes(n, T * m, m))));
     }
     wk.nd = nd;
     wk.mcap = m;
@@ -536,6 +538,23 @@ int orthonormalize(feast_nl_handle* h, Disc D) {
     return FEAST_NL_OK;
 }
 
+// Step 1's projections G = Q^H W (m x T m), W = [A_t Q]: on the BF16 tensor
+// cores (digit-split product, split over K) when the contour has the
+// digit-split workspace, else the FP64 split-K product.
+int project_block(feast_nl_handle* h, const Disc& D) {
+    const int64_t n = h->n;
+    const int T = h->nterms;
+    const int m = D.m;
+    if (D.Oz) {
+        CK(ozaki_project(D.st, n, T * m, m, D.W, n, D.Q, n, D.G, D.Oz, &D.status->flags));
+        return FEAST_NL_OK;
+    }
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    CK(gemm_splitk_d(D.st, 1, m, T * m, (int)n, one, D.Q, n, D.W, n, zero, D.G, m, D.Split,
+                     D.splits));
+    return FEAST_NL_OK;
+}
+
 // Rayleigh-Ritz (Steps 1-2) and the block residual (Step 3) for contour D, with
 // W = [A_t Q] already formed.
 int ritz_and_residual(feast_nl_handle* h, const Disc& D, double tol) {
@@ -545,8 +564,7 @@ int ritz_and_residual(feast_nl_handle* h, const Disc& D, double tol) {
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     {
         Phase ph(h, FEAST_NL_PH_PROJECT, D.prof);
-        CK(gemm_splitk_d(D.st, 1, m, T * m, (int)n, one, D.Q, n, D.W, n, zero, D.G, m, D.Split,
-                         D.splits));
+        CKS(project_block(h, D));
         if (!h->has_exp) CK(form_reduced(D.st, m, T, h->kmax, h->dTerms, D.G, D.Ahat));
     }
     {
@@ -1374,16 +1392,12 @@ int feast_nl_project(feast_nl_handle* h, int32_t m, const void* Q, void* Ahat, i
     if (h->has_exp) return fail(FEAST_NL_EUNSUPPORTED, "projection by powers needs polynomial T");
     if (m < 1 || m > kMaxM0 || m > h->n || !Q || !Ahat) return fail(FEAST_NL_EINVAL, "bad m or pointer");
     CKS(ensure_workspace(h, std::max(m, h->wk.mcap)));
-    const int64_t n = h->n;
-    const int T = h->nterms;
-    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     h->have_result = false;
     const Disc D = disc_view(h, h->ns, h->wk, 0, m, h->st, false);
     CKS(load_block(h, h->st, h->wk.Stage, Q, m, D.Q));
     CKS(apply_terms(h, h->wk, 1, m, D.Q, D.W, h->st, &h->dStatus->flags));
-    CK(gemm_splitk_d(h->st, 1, m, T * m, (int)n, one, D.Q, n, D.W, n, zero, D.G, m, D.Split,
-                     D.splits));
-    CK(form_reduced(h->st, m, T, h->kmax, h->dTerms, D.G, D.Ahat));
+    CKS(project_block(h, D));
+    CK(form_reduced(h->st, m, h->nterms, h->kmax, h->dTerms, D.G, D.Ahat));
     const bool dev = is_device_ptr(Ahat);
     for (int p = 0; p <= h->kmax; ++p) {
         double2* dst = static_cast<double2*>(Ahat) + (int64_t)p * m * m;

@@ -224,6 +224,14 @@ cudaError_t ozaki_gemm_general(cudaStream_t st, int64_t M, int K, int N, const d
                                int64_t lda, const double2* B, int64_t ldb, double2* C, int64_t ldc,
                                int s, void* work, int* err);
 
+// G (m x NT, col-major, ld m) = Q^H W for W (n x NT, col-major, ld ldw) and Q
+// (n x m, col-major, ld ldq); FP64-accurate on the BF16 tensor cores (eight
+// digit slices per operand), split over K.  work holds
+// ozaki_project_work_bytes.  A failed internal wait sets bit 4 of *err.
+size_t ozaki_project_work_bytes(int64_t n, int NT, int m);
+cudaError_t ozaki_project(cudaStream_t st, int64_t n, int NT, int m, const double2* W, int64_t ldw,
+                          const double2* Q, int64_t ldq, double2* G, void* work, int* err);
+
 // ------------------------------------------------------------------ LU (k_lu.cu)
 // One node matrix of a grouped factorisation (orders may differ): F is n x n
 // column-major (leading dimension n) in the LU precision; piv (n), info (1),

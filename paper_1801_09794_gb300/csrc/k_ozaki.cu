@@ -54,6 +54,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace fnl {
 namespace {
 using namespace tc;
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     const __nv_bfloat16* __restrict__ Bslices, int64_t b_slice_stride, const double* __restrict__ tau,
     double2* __restrict__ W, int64_t ldw, int64_t w_term_stride, int mb, int64_t w_block_stride,
     const int* __restrict__ term_slot, int ncols_complex, int* __restrict__ err,
-    const int* __restrict__ active) {
+    const int* __restrict__ active, int split_stages, int64_t split_stride) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[kOzStages];
     __shared__ uint32_t s_tmem;
@@ -91,7 +93,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     // slices run together and read them from HBM once (the rest hit in L2)
     const int row0 = blockIdx.y * kOzM;
     const int col0 = blockIdx.x * kOzN;                    // real column of W'
-    const int term = blockIdx.z;
+    // split-K mode (split_stages > 0, one term): blockIdx.z takes K stages
+    // [z * split_stages, ...) and writes its partial product to W + z * split_stride
+    const int term = split_stages > 0 ? 0 : blockIdx.z;
+    const int kst0 = split_stages > 0 ? blockIdx.z * split_stages : 0;
     if (active) {
         // complex columns [c_lo, c_hi] of this tile belong to blocks c / mb
         const int c_lo = col0 / 2, c_hi = min(ncols_complex, (col0 + kOzN) / 2) - 1;
@@ -101,7 +106,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     }
     const __nv_bfloat16* A = Aslices + term * a_term_stride;
     const double* sg = sigma + term * sigma_term_stride;
-    double2* Wt = W + (int64_t)term_slot[term] * w_term_stride;
+    double2* Wt = W + (int64_t)term_slot[term] * w_term_stride +
+                  (split_stages > 0 ? (int64_t)blockIdx.z * split_stride : 0);
     const int a_tile = kOzM * kOzBK * 2;                   // bytes per A slice tile (4 KB)
     const int b_tile = kOzN * kOzBK * 2;                   // 1.5 KB
     const int stage_bytes = s * (a_tile + b_tile);
@@ -122,8 +128,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     const uint32_t tmem = s_tmem;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 
-    const uint32_t idesc = bf16_idesc(kOzM, kOzN);
-    const int nk = Kp / kOzBK;
+    const int nk = split_stages > 0 ? min(Kp / kOzBK - kst0, split_stages) : Kp / kOzBK;
     int exact[kOzExact][kOzN / 2];                         // running sums of levels 2..4
 #pragma unroll
     for (int L = 0; L < kOzExact; ++L)
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
     // stage t (16 K elements of every slice) into ring slot t % kOzStages; each
     // row's 32 bytes are two 16-byte core-matrix rows (LBO 128 B, SBO 256 B)
     auto load = [&](int t) {
-        const int64_t k0 = (int64_t)t * kOzBK;
+        const int64_t k0 = (int64_t)(kst0 + t) * kOzBK;
         unsigned char* sa = smem + (t % kOzStages) * stage_bytes;
         unsigned char* sb = sa + s * a_tile;
         for (int idx = tid; idx < s * (kOzM + kOzN) * 2; idx += kOzThreads) {
@@ -456,7 +461,7 @@ cudaError_t ozaki_gemm(cudaStream_t st, int64_t n, int m, int mb, int wterms, co
     ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
         s, (int)n, (int)L.Kp, static_cast<const __nv_bfloat16*>(Aslices), L.a_slice, L.a_term,
         sigma, L.Mpad, static_cast<const __nv_bfloat16*>(Qslices), L.b_slice, tau, W, n, n * mb, mb,
-        (int64_t)wterms * n * mb, term_slot, m, err, active);
+        (int64_t)wterms * n * mb, term_slot, m, err, active, 0, 0);
     return cudaGetLastError();
 }
 
@@ -534,7 +539,160 @@ cudaError_t ozaki_gemm_general(cudaStream_t st, int64_t M, int K, int N, const d
     note_launch();
     ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
         s, (int)M, (int)G.L.Kp, Asl, G.L.a_slice, G.L.a_term, sigma, G.L.Mpad, Bsl, G.L.b_slice,
-        tau, C, ldc, 0, N, 0, slot, N, err, nullptr);
+        tau, C, ldc, 0, N, 0, slot, N, err, nullptr, 0, 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Projections G = Q^H W (Step 1) as C = W^H Q on the same kernel, split over K.
+// The product is short and wide in K (m x n times n x T m), so its tiles alone
+// would give a dozen CTAs: K is split across blockIdx.z and the FP64 partial
+// products are summed in a fixed order.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Row i of A' = W^H (i < NT; column i of W, K x NT col-major, ld ldw): its
+// scale sigma_i (power of two above the largest |Re|, |Im|) and its s digit
+// slices, Re conj(w) at k, Im conj(w) at K + k, zeros in the K padding; rows
+// NT .. Mpad-1 are written as zeros.  One CTA per row.
+__global__ void split_rows_conjT_kernel(int64_t K, int NT, int s, const double2* __restrict__ Wm,
+                                        int64_t ldw, double* __restrict__ sigma,
+                                        __nv_bfloat16* __restrict__ out, int64_t slice_stride,
+                                        int64_t Kp) {
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    const bool live = i < NT;
+    const double2* w = Wm + (int64_t)(live ? i : 0) * ldw;
+    double mx = 0.0;
+    if (live)
+        for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
+            mx = fmax(mx, fmax(fabs(w[k].x), fabs(w[k].y)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, red[q]);
+        int e = 0;
+        if (t > 0.0) frexp(t, &e);
+        red[0] = (t > 0.0) ? ldexp(1.0, e) : 1.0;
+        sigma[i] = red[0];
+    }
+    __syncthreads();
+    const double inv = 1.0 / red[0];
+    for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
+        float d[kOzMaxSlices];
+        const bool re = k < K, im = k >= K && k < 2 * K;
+        double v = 0.0;
+        if (live && re) v = w[k].x * inv;
+        if (live && im) v = -w[k - K].y * inv;
+        digits(v, s, d);
+        for (int p = 0; p < s; ++p) out[p * slice_stride + (int64_t)i * Kp + k] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+// G (m x NT, col-major, ld m) = conj of the sum over the splits of the partial
+// products P_z = (W^H Q)_z (NT x m, col-major, ld NT), in split order.
+__global__ void splitk_reduce_conjT_kernel(int NT, int m, int S, const double2* __restrict__ P,
+                                           double2* __restrict__ G) {
+    const int64_t total = (int64_t)NT * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int z = 0; z < S; ++z) {
+            const double2 v = P[(int64_t)z * total + e];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        const int64_t i = e % NT, j = e / NT;
+        G[j + i * m] = make_double2(acc.x, -acc.y);
+    }
+}
+
+// Digit slices of both operands of the projections.  Eight slices, one more
+// than the A_t Q product uses: G = Q^H W is a product of unit columns with
+// cancellation in its off-diagonal entries, and with seven slices its error
+// (~1.5e-13 relative to ||G||_F at n = 4096, m0 = 96) is two orders above an
+// FP64 product's; the eighth slice puts it back at the FP64 level.
+constexpr int kOzProjSlices = kOzMaxSlices;
+
+struct OzProjLayout {
+    int64_t Mpad, a_slice;
+    int S, stages;                 // K splits and K stages per split
+    size_t sigma_off, slot_off, qsl_off, tau_off, part_off, total;
+};
+OzProjLayout oz_proj_layout(int64_t n, int NT, int m, int s) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const OzakiLayout LQ = ozaki_layout(n, m, s);
+    OzProjLayout P;
+    P.Mpad = ((int64_t)NT + kOzM - 1) / kOzM * kOzM;
+    P.a_slice = P.Mpad * LQ.Kp;
+    const int nk = (int)(LQ.Kp / kOzBK);
+    const int tiles = (int)((LQ.Npad / kOzN) * (P.Mpad / kOzM));
+    // about one CTA per SM (152), each at least one 256-element drain chunk of K
+    int S = std::max(1, 152 / std::max(tiles, 1));
+    S = std::min(S, std::max(1, nk / kOzChunkStages));
+    P.stages = (nk + S - 1) / S;
+    P.S = (nk + P.stages - 1) / P.stages;
+    size_t o = al((size_t)P.a_slice * s * sizeof(__nv_bfloat16));
+    P.sigma_off = o; o = al(o + (size_t)P.Mpad * sizeof(double));
+    P.slot_off = o;  o = al(o + sizeof(int));
+    P.qsl_off = o;   o = al(o + (size_t)LQ.b_slice * s * sizeof(__nv_bfloat16));
+    P.tau_off = o;   o = al(o + (size_t)m * sizeof(double));
+    P.part_off = o;  o = al(o + (size_t)P.S * NT * m * sizeof(double2));
+    P.total = o;
+    return P;
+}
+
+}  // namespace
+
+size_t ozaki_project_work_bytes(int64_t n, int NT, int m) {
+    return oz_proj_layout(n, NT, m, kOzProjSlices).total;
+}
+
+cudaError_t ozaki_project(cudaStream_t st, int64_t n, int NT, int m, const double2* Wm, int64_t ldw,
+                          const double2* Q, int64_t ldq, double2* G, void* work, int* err) {
+    const int s = kOzProjSlices;
+    if (n <= 0 || NT <= 0 || m <= 0) return cudaSuccess;
+    if (!ozaki_supported(n, s)) return cudaErrorInvalidValue;
+    const OzakiLayout LQ = ozaki_layout(n, m, s);
+    const OzProjLayout P = oz_proj_layout(n, NT, m, s);
+    unsigned char* w = static_cast<unsigned char*>(work);
+    __nv_bfloat16* Asl = reinterpret_cast<__nv_bfloat16*>(w);
+    double* sigma = reinterpret_cast<double*>(w + P.sigma_off);
+    int* slot = reinterpret_cast<int*>(w + P.slot_off);
+    __nv_bfloat16* Qsl = reinterpret_cast<__nv_bfloat16*>(w + P.qsl_off);
+    double* tau = reinterpret_cast<double*>(w + P.tau_off);
+    double2* part = reinterpret_cast<double2*>(w + P.part_off);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(slot, 0, sizeof(int), st)) != cudaSuccess) return e;
+    // B' = digit slices of Q (the K padding and the padded columns read as zero)
+    if ((e = cudaMemsetAsync(Qsl, 0, (size_t)LQ.b_slice * s * sizeof(__nv_bfloat16), st)) != cudaSuccess)
+        return e;
+    note_launch();
+    split_cols_kernel<<<m, 256, 0, st>>>(n, s, Q, ldq, tau, Qsl, LQ.b_slice, LQ.Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    split_rows_conjT_kernel<<<(unsigned)P.Mpad, 256, 0, st>>>(n, NT, s, Wm, ldw, sigma, Asl,
+                                                              P.a_slice, LQ.Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    static std::atomic<bool> attr_done{false};
+    const int smem = kOzStages * s * (kOzM + kOzN) * kOzBK * 2;
+    if (!attr_done) {
+        e = cudaFuncSetAttribute(ozaki_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kOzStages * kOzMaxSlices * (kOzM + kOzN) * kOzBK * 2);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)(LQ.Npad / kOzN), (unsigned)(P.Mpad / kOzM), (unsigned)P.S);
+    note_launch();
+    ozaki_bf16_gemm_kernel<<<grid, kOzThreads, smem, st>>>(
+        s, NT, (int)LQ.Kp, Asl, P.a_slice, 0, sigma, 0, Qsl, LQ.b_slice, tau, part, NT, 0, m, 0, slot,
+        m, err, nullptr, P.stages, (int64_t)NT * m);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    splitk_reduce_conjT_kernel<<<(unsigned)std::min<int64_t>(((int64_t)NT * m + 255) / 256, 1024), 256, 0,
+                                 st>>>(NT, m, P.S, part, G);
     return cudaGetLastError();
 }
 

@@ -316,6 +316,7 @@ void hessenberg_launch_shape(int N, int* c0, size_t* smem) {
 #define PK(i, j) ((((j) * ((j) + 5)) >> 1) + (i))
 
 constexpr int kQrThreads = 256;
+constexpr int kMsShifts = kQrThreads / 32;   // bulges of a multishift sweep: one warp each
 constexpr int kSmallMax = 32;      // active blocks up to this order go to one warp
 constexpr int kSmallLd = 33;       // leading dimension of that dense copy (bank spread)
 
@@ -493,15 +494,28 @@ __device__ __forceinline__ void qr_window(typename cx<R>::type* H, int l, int hi
 }
 
 // ---------------------------------------------------------------------------
-// Eigenvalues of the Hessenberg matrix by the implicit single-shift complex QR
-// algorithm, then Step 2's selection.  Large active blocks: one warp chases
-// the bulge through windows of kQrChunk rotations, the CTA applies each
-// window's rotations to the rest of the block.  Blocks of order <= kSmallMax:
-// one warp on a dense copy.  (A multishift variant with chains of bulges was
-// measured: it needs ~2.5x the shifts on these companion matrices, and its
-// FP32 eigenvalues come out too coarse for clustered reduced spectra.)
+// Eigenvalues of the Hessenberg matrix by the implicit QR algorithm, then Step
+// 2's selection.  Blocks of order <= kSmallMax: one warp on a dense copy,
+// single shifts.  Larger active blocks:
+//  * MS (the FP32 stage): small-bulge multishift sweeps.  The kMsShifts
+//    eigenvalues of the trailing kMsShifts x kMsShifts block are the shifts;
+//    each opens a single-shift bulge at the top of the block, three rows
+//    behind the previous one, and the chain is chased down in lockstep, one
+//    warp per bulge.  Bulges three rows apart act on disjoint row pairs and
+//    disjoint column pairs, so at each step every bulge applies its row
+//    rotation (across the whole active block), the CTA synchronises, every
+//    bulge applies its column rotation, and the CTA synchronises again; left
+//    and right rotations commute, so this equals the one-by-one chase in exact
+//    arithmetic.  (A single-shift chase is one dependent rotation after
+//    another on one warp, ~470 cycles per rotation on GB300; the chain keeps
+//    eight warps busy at the cost of ~1.4x the rotations: ~6,000 chain steps
+//    instead of ~27,000 rotations for the 192 x 192 companion matrices of the
+//    n = 4096 QEP, with the same FP32 eigenvalue accuracy.)
+//  * otherwise (the FP64 fallback stage): single-shift sweeps; one warp chases
+//    the bulge through windows of kQrChunk rotations, the CTA applies each
+//    window's rotations to the rest of the block.
 // ---------------------------------------------------------------------------
-template <typename R, bool SMEM>
+template <typename R, bool SMEM, bool MS = false>
 __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
     int N, int m0, const typename cx<R>::type* __restrict__ C, typename cx<R>::type* Hglobal,
     double c_re, double c_im, double ra, double rb, double2* __restrict__ lam0,
@@ -594,6 +608,71 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
             hi = l - 1;
             its = 0;
             __syncthreads();
+            continue;
+        }
+        if (MS) {
+            // ---- small-bulge multishift sweep
+            __shared__ CT s_sig[kMsShifts];
+            const int ns = kMsShifts;
+            if (warp == 0) {
+                const int s0 = hi - ns + 1;
+                for (int j = lane; j < ns; j += 32)
+                    for (int i = 0; i < ns; ++i)
+                        Ssm[i + j * kSmallLd] = (i <= j + 1) ? HH(s0 + i, s0 + j) : czero<CT>();
+                __syncwarp();
+                small_hess_eig<R>(Ssm, ns, s_sig);
+                if (lane == 0) {
+                    const CT d = HH(hi, hi);
+                    if (its % 6 == 5) {            // exceptional shifts around the corner entry
+                        const R rad = (R)0.75 * cabs(HH(hi, hi - 1));
+                        for (int q = 0; q < ns; ++q) {
+                            double sn_, cs_;
+                            sincos(2.0 * M_PI * q / ns, &sn_, &cs_);
+                            s_sig[q] = d + cmake<CT>(rad * cs_, rad * sn_);
+                        }
+                    }
+                    // the shift nearest the corner entry goes last (its bulge leaves last)
+                    for (int a = 1; a < ns; ++a) {
+                        const CT v = s_sig[a];
+                        const R kv = cabs1(v - d);
+                        int b = a - 1;
+                        while (b >= 0 && cabs1(s_sig[b] - d) < kv) { s_sig[b + 1] = s_sig[b]; --b; }
+                        s_sig[b + 1] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            const int T = (hi - l) + 3 * (ns - 1);
+            for (int t = 0; t < T; ++t) {
+                const int k = l + t - 3 * warp;          // this warp's bulge position
+                const bool act = warp < ns && k >= l && k <= hi - 1;
+                R c = 1;
+                CT sn = czero<CT>();
+                if (act) {
+                    CT x, y;
+                    if (k == l) { x = HH(l, l) - s_sig[warp]; y = HH(l + 1, l); }
+                    else        { x = HH(k, k - 1); y = HH(k + 1, k - 1); }
+                    givens<R>(x, y, c, sn);
+                    __syncwarp();                        // x, y read before any lane writes
+                    // row rotation: rows k, k+1 of columns max(l, k-1) .. hi
+                    for (int j = max(l, k - 1) + lane; j <= hi; j += 32) {
+                        const CT a = HH(k, j), b = HH(k + 1, j);
+                        HH(k, j) = cscale(c, a) + sn * b;
+                        HH(k + 1, j) = (j == k - 1) ? czero<CT>() : cscale(c, b) - cconj(sn) * a;
+                    }
+                }
+                __syncthreads();
+                if (act) {
+                    // column rotation: columns k, k+1 of rows l .. min(k+2, hi)
+                    const int i1 = min(k + 2, hi);
+                    for (int i = l + lane; i <= i1; i += 32) {
+                        const CT a = HH(i, k), b = HH(i, k + 1);
+                        HH(i, k) = cscale(c, a) + cconj(sn) * b;
+                        HH(i, k + 1) = cscale(c, b) - sn * a;
+                    }
+                }
+                __syncthreads();
+            }
             continue;
         }
         // ---- single-shift sweep
@@ -1095,9 +1174,9 @@ cudaError_t qr_select_attributes() {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(hessenberg_kernel<double>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, true>,
+    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, true, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, false>,
+    if ((e = cudaFuncSetAttribute(qr_select_kernel<float, false, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(qr_select_kernel<double, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess) return e;
@@ -1156,12 +1235,14 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
     size_t smem = fixed + (use_smem ? hbytes : 0);
     note_launch();
+    // FP32 stage: multishift sweeps; FP64 fallback stage: single-shift sweeps
+    constexpr bool kMs = sizeof(R) == 4;
     if (use_smem)
-        qr_select_kernel<R, true><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb, lam0,
-                                                               gap, flag, stage, status);
+        qr_select_kernel<R, true, kMs><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb,
+                                                                    lam0, gap, flag, stage, status);
     else
-        qr_select_kernel<R, false><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb, lam0,
-                                                                gap, flag, stage, status);
+        qr_select_kernel<R, false, kMs><<<1, kQrThreads, smem, st>>>(N, m0, C, Hg, c_re, c_im, ra, rb,
+                                                                     lam0, gap, flag, stage, status);
     return cudaGetLastError();
 }
 
@@ -1527,11 +1608,11 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     const size_t qsm = fixed + (use_smem ? hbytes : 0);
     note_launch();
     if (use_smem)
-        qr_select_kernel<float, true><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra, rb,
-                                                                  lam0, gap, flag, 1, status);
+        qr_select_kernel<float, true, true><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra, rb,
+                                                                        lam0, gap, flag, 1, status);
     else
-        qr_select_kernel<float, false><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra, rb,
-                                                        lam0, gap, flag, 1, status);
+        qr_select_kernel<float, false, true><<<1, kQrThreads, qsm, st>>>(m, m, B, Hg, c_re, c_im, ra,
+                                                                         rb, lam0, gap, flag, 1, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Newton per kept value (FP32 factor, FP64 residuals), fillers beyond the rank
     const size_t nsm32 = sizeof(double2) * 4 * m + sizeof(float2) * ((size_t)m * m + 2 * m) +

@@ -90,4 +90,13 @@ def test_delay_n2048_matches_stored_reference(lib):
     assert len(lam) == len(gold) == w["winding_count"]
     assert match_sets(lam, gold) < 1e-10
     assert np.all(rr <= 1e-10)
+    # The iteration count of this workload is set by spurious Ritz values of the
+    # projected problem: the 29 eigenvalues converge within ~5 iterations, but
+    # a Ritz value of Q^H T Q that matches no eigenvalue of T can sit inside C
+    # with a residual near 1e-3 for several iterations, and the test passes
+    # once it leaves (the largest residual then drops from ~1e-3 to ~1e-16 in
+    # one step).  The FP64 oracle takes 6, 6, 17 and 6 iterations from four
+    # start blocks; the GPU path has taken 10 and 14 with different rounding.
+    # Twenty still catches a mixed-precision path that stops converging.
+    assert info.iters <= 20, info.iters
     s.close()

@@ -12,6 +12,13 @@ pytestmark = pytest.mark.gpu
 
 # (n, degree, seed): orders that are and are not multiples of the 64-column panel
 CASES = [(130, 3, 21), (256, 2, 5), (200, 3, 8)]
+# Subspace size: 32 for 7 eigenvalues inside.  With 20, Rayleigh-Ritz on the
+# cubic (60 Ritz values for 20 columns) now and then puts a spurious Ritz value
+# inside the contour whose residual never falls, and the iteration count
+# becomes erratic: the FP64 oracle itself takes 79 iterations on the n = 130
+# problem from this start (6 to over 80 over m0 = 16 .. 28 and three starts),
+# against 4 to 15 with m0 = 32 over six starts for all three problems.
+M0 = 32
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +48,7 @@ def test_group_solves_match_qz(lib, problems, prec):
     lib.set_contour_group(hs, [c for _, _, c, _ in problems], [r for _, _, _, r in problems],
                           [r for _, _, _, r in problems], 16)
     for h, (p, lam_all, c, r) in zip(hs, problems):
-        st, info = h.solve(20, tol=1e-12, maxit=80, X0=start_block(p["n"], 20, 9))
+        st, info = h.solve(M0, tol=1e-12, maxit=80, X0=start_block(p["n"], M0, 9))
         lam, X, rr = h.get_eigpairs(inside_only=True)
         ref = lam_all[inside_mask(lam_all, c, r, r)]
         assert len(lam) == len(ref) == 7
@@ -65,9 +72,9 @@ def test_group_factors_match_one_by_one(lib, problems):
         for j in (0, 7, 15):
             y1, y2 = g.node_solve(j, R), s.node_solve(j, R)
             assert np.array_equal(y1, y2)
-        X0 = start_block(p["n"], 20, 4)
-        g.solve(20, tol=1e-12, maxit=80, X0=X0)
-        s.solve(20, tol=1e-12, maxit=80, X0=X0)
+        X0 = start_block(p["n"], M0, 4)
+        g.solve(M0, tol=1e-12, maxit=80, X0=X0)
+        s.solve(M0, tol=1e-12, maxit=80, X0=X0)
         l1, x1, r1 = g.get_eigpairs(inside_only=True)
         l2, x2, r2 = s.get_eigpairs(inside_only=True)
         assert np.array_equal(l1, l2) and np.array_equal(x1, x2) and np.array_equal(r1, r2)

@@ -105,7 +105,46 @@ def test_project_matches_oracle(lib, prec, n, m):
     s.close()
 
 
+def test_project_matches_oracle_n4096(lib):
+    """Projections at the largest K of the digit-split products (n = 4096,
+    K = 2n = 8192 in the real embedding) on the n = 4096 QEP with m0 = 96: the
+    error of each Q^H A_t Q against FP64, relative to its norm, stays at the
+    FP64 level (the worst-case FP32 accumulation bound of the low levels would
+    allow 6e-11)."""
+    from workloads import config2_qep
+    p = config2_qep(4096, 0)
+    s = lib.FeastNL(p, "fp32_i8")
+    Q = O.orthonormalize(start_block(4096, 96, 5))
+    got = s.project(Q, 2)
+    ref = O.projected_coefficients(p, Q)
+    errs = [_relerr(gp, rp) for gp, rp in zip(got, ref)]
+    print("projection errors at n = 4096, m0 = 96:", ", ".join("%.2e" % e for e in errs))
+    assert max(errs) < 1e-13, errs
+    s.close()
+
+
 # ------------------------------------------------------------------ whole solve
+def test_qep_mixed_n4096_matches_stored_reference(lib):
+    """The n = 4096 QEP with 16 nodes and m0 = 96 in the default mixed precision,
+    through the C ABI as a user calls it: every one of the 64 eigenvalues the
+    oracle's shift-invert Arnoldi found inside the circle (stored), to 1e-10
+    relative, and every residual <= 1e-10 (Algorithm 1, Step 3)."""
+    from workloads import config2_qep
+    with open(os.path.join(GOLD, "contours.json")) as f:
+        w = json.load(f)["qep_mixed_n4096"]
+    gold = np.array([complex(*x) for x in w["eigs_inside"]])
+    p = config2_qep(4096, 0)
+    s = lib.FeastNL(p, "fp32_i8")
+    s.set_contour(complex(*w["center"]), w["ra"], w["rb"], w["nc"], w["rule"])
+    st, info = s.solve(w["m0"], tol=1e-10, maxit=40, seed=0)
+    lam, X, rr = s.get_eigpairs(inside_only=True, vectors=False)
+    assert info.n_inside == len(lam) == len(gold) == w["count"] == 64
+    err = match_sets(lam, gold)
+    print(f"n = 4096 QEP: {info.iters} iterations, max rel eigenvalue error {err:.2e}, "
+          f"max relres {np.max(rr):.2e}")
+    assert err < 1e-10
+    assert np.all(rr <= 1e-10)
+    s.close()
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
 def test_solve_example1_table1(lib, prec):
     rows = load_table1(os.path.join(GOLD, "e1_table1.txt"))
