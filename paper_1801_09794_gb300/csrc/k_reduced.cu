@@ -10,21 +10,28 @@
 //            C = [[-Ahat_k^{-1} Ahat_{k-1} ... -Ahat_k^{-1} Ahat_0], [I 0 ..], ...]
 //            (the first companion pencil of Sec. 2 with its leading block
 //            inverted) by Householder reduction to Hessenberg form and the
-//            implicit single-shift complex QR algorithm, in FP32, one CTA;
+//            implicit complex QR algorithm (multishift sweeps), in FP32;
 //            Step 2 keeps the m Ritz values of smallest normalised radius; each
 //            is refined in FP64 by Newton's method on Ahat(lambda) y = 0 with the
-//            normalisation x^H y = 1 (nonlinear inverse iteration), one CTA per
-//            pair, which also yields the Ritz vector y;
-//   stage 2: only if stage 1 failed (a Newton step left its basin, or two kept
-//            values coincide -- clustered, ill-conditioned Ritz values that FP32
-//            cannot separate), the same companion / Hessenberg / QR / selection
-//            runs in FP64 and Newton polishes from those values.
-// Every stage-2 kernel reads the failure flag on the device and returns at once
-// when it is clear, so the stream never waits on the host.
+//            normalisation x^H y = 1 (nonlinear inverse iteration) with an FP32
+//            factor, one CTA per pair, which also yields the Ritz vector y;
+//   retry:   a pair whose Newton run was rejected (not converged, or moved
+//            beyond 0.3 of the distance to its nearest neighbour without
+//            landing clearly inside the kept region) runs again from the same
+//            start with an FP64 factor; a pair clearly outside C that still
+//            stalls keeps its FP32 value and inverse-iteration vector;
+//   stage 2: only if the retry failed too, or two kept values coincide --
+//            clustered, ill-conditioned Ritz values that FP32 cannot separate --
+//            the companion / Hessenberg / QR / selection runs in FP64 and
+//            Newton polishes from those values.
+// Every retry and stage-2 kernel reads the failure flags on the device and
+// returns at once when they are clear, so the stream never waits on the host.
 // Newton's fixed point is an exact eigenpair of the FP64 projected problem, so
 // the kept pairs carry FP64 accuracy either way.
 #include "internal.h"
 #include <cfloat>
+
+#include <cooperative_groups.h>
 
 namespace fnl {
 namespace {
@@ -76,7 +83,8 @@ constexpr size_t kRedSmemCap = 216 * 1024;   // dynamic shared memory cap of the
 constexpr int kQrChunk = 16;        // rotations per window in the QR sweep (<= 29)
 static_assert(kQrChunk >= 1 && kQrChunk <= 29, "lane t owns column k-1+t: a window spans kb+3 <= 32 columns");
 // flags word shared by the stages (device memory)
-constexpr int kNeed64 = 1;
+constexpr int kNeed64 = 1;      // the FP64 companion / Hessenberg / QR stage runs
+constexpr int kRetry64 = 2;     // some pairs retry Newton with an FP64 factor
 
 // The reduced problem seen by the refinement: the projected matrix polynomial
 // (kmax >= 0: Ahat holds the kmax + 1 coefficients, stacked m x m), or general
@@ -88,6 +96,7 @@ struct RedProblem {
     int nterms;
     const TermDev* terms;
     const double2* G;
+    double c_re, c_im, ra, rb;      // the contour (Step 2's normalised radius)
 };
 
 // ---------------------------------------------------------------------------
@@ -312,20 +321,300 @@ void hessenberg_launch_shape(int N, int* c0, size_t* smem) {
     *smem = base + (size_t)ncs * col;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 stage: the companion matrix by several CTAs, its Householder reduction
+// to Hessenberg form by a thread-block cluster.
+// ---------------------------------------------------------------------------
+constexpr int kCompCols = 32;        // companion columns per CTA (one warp each)
+constexpr int kCompThreads = 32 * kCompCols;
+
+// CTA b forms columns [b kCompCols, ...) of C: every CTA factors Ahat_k in
+// shared memory (the same arithmetic, so the same factors, in each), then each
+// warp solves one column of the top block row and writes the whole column of C.
+// The per-element operation order is that of companion_kernel: LU with partial
+// pivoting on cabs1 (lowest row on ties), forward substitution with the unit L,
+// back substitution multiplying by the reciprocal pivot, then negation.
+__global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
+    int m, int kmax, const double2* __restrict__ Ahat, float2* __restrict__ C, int* redflag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* Lk = reinterpret_cast<float2*>(smem_raw);          // m x m, col-major
+    float2* X = Lk + (size_t)m * m;                             // m x kCompCols
+    int* piv = reinterpret_cast<int*>(X + (size_t)m * kCompCols);
+    __shared__ int s_p;
+    const int N = kmax * m;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t mm = (int64_t)m * m;
+    if (blockIdx.x == 0 && tid == 0) *redflag = 0;
+    for (int64_t e = tid; e < mm; e += nt) {
+        const double2 a = Ahat[(int64_t)kmax * mm + e];
+        Lk[e] = make_float2((float)a.x, (float)a.y);
+    }
+    const int col = blockIdx.x * kCompCols + warp;              // this warp's column of C
+    const bool has = col < N;
+    if (has) {
+        const int b = col / m, cc = col - b * m;
+        const double2* src = Ahat + (int64_t)(kmax - 1 - b) * mm + (int64_t)cc * m;
+        for (int r = lane; r < m; r += 32) X[r + (size_t)warp * m] = make_float2((float)src[r].x, (float)src[r].y);
+    }
+    __syncthreads();
+    for (int c = 0; c < m; ++c) {
+        if (warp == 0) {
+            float best = -1.0f;
+            int bi = c;
+            for (int r = c + lane; r < m; r += 32) {
+                const float v = cabs1(Lk[r + c * m]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) { s_p = bi; piv[c] = bi; }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != c)
+            for (int cc = tid; cc < m; cc += nt) {
+                const float2 a = Lk[c + cc * m];
+                Lk[c + cc * m] = Lk[p + cc * m];
+                Lk[p + cc * m] = a;
+            }
+        __syncthreads();
+        const float2 inv = crcp(Lk[c + c * m]);
+        for (int r = c + 1 + tid; r < m; r += nt) Lk[r + c * m] = Lk[r + c * m] * inv;
+        __syncthreads();
+        const int rem = m - c - 1;
+        for (int e = tid; e < rem * rem; e += nt) {
+            const int r = c + 1 + e % rem, cc = c + 1 + e / rem;
+            Lk[r + cc * m] = cfms(Lk[r + c * m], Lk[c + cc * m], Lk[r + cc * m]);
+        }
+        __syncthreads();
+    }
+    if (!has) return;
+    float2* x = X + (size_t)warp * m;
+    if (lane == 0)
+        for (int c = 0; c < m; ++c) {
+            const int p = piv[c];
+            if (p != c) { const float2 t = x[c]; x[c] = x[p]; x[p] = t; }
+        }
+    __syncwarp();
+    for (int i = 0; i < m - 1; ++i) {
+        const float2 xi = x[i];
+        for (int r = i + 1 + lane; r < m; r += 32) x[r] = cfms(Lk[r + i * m], xi, x[r]);
+        __syncwarp();
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        if (lane == 0) x[i] = x[i] * crcp(Lk[i + i * m]);
+        __syncwarp();
+        const float2 xi = x[i];
+        for (int r = lane; r < i; r += 32) x[r] = cfms(Lk[r + i * m], xi, x[r]);
+        __syncwarp();
+    }
+    float2* out = C + (int64_t)col * N;
+    for (int r = lane; r < N; r += 32)
+        out[r] = r < m ? -x[r] : make_float2(r == col + m ? 1.0f : 0.0f, 0.0f);
+}
+
+size_t companion_cols_smem(int m) {
+    return sizeof(float2) * ((size_t)m * m + (size_t)m * kCompCols) + sizeof(int) * (size_t)m;
+}
+
+// Householder reduction of C (N x N, FP32, in place) to upper Hessenberg form
+// by a cluster of CS CTAs that hold the matrix in distributed shared memory:
+// CTA q owns the columns j = q (mod CS).  Step j (owner o = j mod CS):
+//   1. the owner forms the reflector P = I - beta v v^H from column j (v zero
+//      in rows <= j) and writes v and beta into every CTA's shared memory;
+//   2. every CTA forms w_c = v^H H(:, c) for its columns c > j and its share
+//      of y = H v (the sum over its columns), and writes the share into every
+//      CTA;
+//   3. every CTA sums the shares in rank order, gamma = v^H y, and updates its
+//      columns by the two-sided reflection
+//         H(r, c) <- H(r, c) - beta v_r w_c - beta (y_r - beta gamma v_r) conj(v_c).
+// Two cluster barriers per column; v is double-buffered because the owner of
+// column j + 1 may write it while other CTAs still read column j's.
+constexpr int kHcThreads = 1024;
+
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kHcThreads)
+hess_cluster_kernel(int N, float2* __restrict__ C) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = nt >> 5;
+    const int ncl = (N - q + CS - 1) / CS;             // own columns j = q + CS lc
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);   // ncl x N, column-major
+    float2* vbuf = S + (size_t)ncl * N;                // 2 x N
+    float2* ypart = vbuf + 2 * (size_t)N;              // CS x N
+    float2* wv = ypart + (size_t)CS * N;               // ncl
+    float2* yv = wv + ncl;                             // N
+    __shared__ float s_beta[2];
+    __shared__ float2 s_gamma;
+    for (int64_t e = tid; e < (int64_t)ncl * N; e += nt) {
+        const int lc = (int)(e / N), r = (int)(e - (int64_t)lc * N);
+        S[e] = C[(int64_t)(q + CS * lc) * N + r];
+    }
+    __syncthreads();
+    cluster.sync();
+    for (int j = 0; j + 2 < N; ++j) {
+        const int o = j % CS, buf = j & 1, len = N - j - 1;
+        float2* v = vbuf + (size_t)buf * N;             // v[i] <-> row j + 1 + i
+        if (q == o && warp == 0) {
+            float2* col = S + (size_t)(j / CS) * N + (j + 1);
+            float sq = 0.0f;
+            for (int r = lane; r < len; r += 32) sq += cnorm2(col[r]);
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+            const float2 x0 = col[0];
+            const float ax0 = cabs(x0), nx = sqrtf(sq), tail = sq - ax0 * ax0;
+            float beta = 0.0f;
+            float2 alpha = make_float2(0.0f, 0.0f), v0 = make_float2(0.0f, 0.0f);
+            if (nx > 0.0f && tail > 1e-30f * sq) {
+                const float2 ph = ax0 > 0.0f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.0f, 0.0f);
+                alpha = make_float2(-ph.x * nx, -ph.y * nx);
+                v0 = x0 - alpha;
+                beta = 2.0f / (tail + cnorm2(v0));
+            }
+            for (int d = 0; d < CS; ++d) {
+                float2* vd = cluster.map_shared_rank(v, d);
+                for (int r = lane; r < len; r += 32) vd[r] = r == 0 ? v0 : col[r];
+                if (lane == 0) *cluster.map_shared_rank(&s_beta[buf], d) = beta;
+            }
+            __syncwarp();
+            if (beta != 0.0f)
+                for (int r = lane; r < len; r += 32) col[r] = r == 0 ? alpha : make_float2(0.0f, 0.0f);
+        }
+        cluster.sync();                                 // v, beta of column j everywhere
+        const float beta = s_beta[buf];
+        const int lc0 = (j + 1 - q + CS - 1) / CS > 0 ? (j + 1 - q + CS - 1) / CS : 0;   // first own column > j
+        if (beta != 0.0f) {
+            for (int lc = lc0 + warp; lc < ncl; lc += nw) {
+                const float2* hc = S + (size_t)lc * N + (j + 1);
+                float2 w = make_float2(0.0f, 0.0f);
+                for (int r = lane; r < len; r += 32) w = cfma(cconj(v[r]), hc[r], w);
+                for (int off = 16; off > 0; off >>= 1) {
+                    w.x += __shfl_xor_sync(0xffffffffu, w.x, off);
+                    w.y += __shfl_xor_sync(0xffffffffu, w.y, off);
+                }
+                if (lane == 0) wv[lc] = w;
+            }
+            for (int r = tid; r < N; r += nt) {
+                float2 y = make_float2(0.0f, 0.0f);
+                for (int lc = lc0; lc < ncl; ++lc)
+                    y = cfma(S[(size_t)lc * N + r], v[q + CS * lc - j - 1], y);
+                for (int d = 0; d < CS; ++d) cluster.map_shared_rank(ypart + (size_t)q * N, d)[r] = y;
+            }
+        }
+        cluster.sync();                                 // every share of y everywhere
+        if (beta != 0.0f) {
+            for (int r = tid; r < N; r += nt) {
+                float2 y = ypart[r];
+                for (int d = 1; d < CS; ++d) y = y + ypart[(size_t)d * N + r];
+                yv[r] = y;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                float2 g = make_float2(0.0f, 0.0f);
+                for (int i = lane; i < len; i += 32) g = cfma(cconj(v[i]), yv[j + 1 + i], g);
+                for (int off = 16; off > 0; off >>= 1) {
+                    g.x += __shfl_xor_sync(0xffffffffu, g.x, off);
+                    g.y += __shfl_xor_sync(0xffffffffu, g.y, off);
+                }
+                if (lane == 0) s_gamma = g;
+            }
+            __syncthreads();
+            const float2 bg = beta * s_gamma;
+            const int nlive = ncl - lc0;
+            for (int64_t e = tid; e < (int64_t)nlive * N; e += nt) {
+                const int l2 = (int)(e / N), r = (int)(e - (int64_t)l2 * N);
+                const int lc = lc0 + l2, c = q + CS * lc;
+                const float2 vr = r > j ? v[r - j - 1] : make_float2(0.0f, 0.0f);
+                const float2 yt = cfms(bg, vr, yv[r]);                      // y_r - beta gamma v_r
+                float2 h = S[(size_t)lc * N + r];
+                h = cfms(beta * vr, wv[lc], h);
+                h = cfms(beta * yt, cconj(v[c - j - 1]), h);
+                S[(size_t)lc * N + r] = h;
+            }
+        }
+        __syncthreads();
+    }
+    cluster.sync();
+    for (int64_t e = tid; e < (int64_t)ncl * N; e += nt) {
+        const int lc = (int)(e / N), r = (int)(e - (int64_t)lc * N);
+        C[(int64_t)(q + CS * lc) * N + r] = S[e];
+    }
+}
+
+size_t hess_cluster_smem(int N, int CS) {
+    const size_t ncl = (size_t)(N + CS - 1) / CS;
+    return sizeof(float2) * (ncl * N + 2 * (size_t)N + (size_t)CS * N + ncl + (size_t)N);
+}
+
+constexpr size_t kHcSmemCap = 200 * 1024;
+// Cluster size for the FP32 Hessenberg reduction of order N (0: the matrix does
+// not fit eight CTAs, or N is too small to pay; the single-CTA kernel runs).
+int hess_cluster_size(int N) {
+    if (N < 64 || N > kHcThreads) return 0;
+    if (hess_cluster_smem(N, 4) <= kHcSmemCap) return 4;
+    if (hess_cluster_smem(N, 8) <= kHcSmemCap) return 8;
+    return 0;
+}
+
 // Packed Hessenberg storage with one bulge row: column j holds rows 0..j+2.
 #define PK(i, j) ((((j) * ((j) + 5)) >> 1) + (i))
 
 constexpr int kQrThreads = 256;
 constexpr int kMsShifts = kQrThreads / 32;   // bulges of a multishift sweep: one warp each
+// Multishift sweeps without a deflation at the bottom of the active block after
+// which the block continues with single-shift sweeps until the next deflation
+// (a safety net: the chain has no deflation checks inside the sweep; a healthy
+// block deflates within a few sweeps).
+constexpr int kMsMaxStall = 10;
 constexpr int kSmallMax = 32;      // active blocks up to this order go to one warp
 constexpr int kSmallLd = 33;       // leading dimension of that dense copy (bank spread)
 
+template <typename R> struct givens_range;
+template <> struct givens_range<float> { static __device__ float lo() { return 1e-30f; }
+                                         static __device__ float hi() { return 1e30f; } };
+template <> struct givens_range<double> { static __device__ double lo() { return 1e-280; }
+                                          static __device__ double hi() { return 1e280; } };
+
+// The rotation of givens() when |x|^2 + |y|^2 is tiny or huge: both are divided
+// by their largest component first, so no square underflows or overflows (a
+// collapsed bulge of a multishift sweep reaches |x|, |y| ~ 1e-21, where
+// 1 / (|x| rho) overflows FP32).  Any common factor cancels in c and s.
+template <typename R>
+__device__ __noinline__ void givens_scaled(typename cx<R>::type x, typename cx<R>::type y, R& c,
+                                           typename cx<R>::type& s) {
+    typedef typename cx<R>::type CT;
+    const R mx = fmax(fmax(fabs(x.x), fabs(x.y)), fmax(fabs(y.x), fabs(y.y)));
+    if (!(mx > (R)0) || !isfinite(mx)) { c = 1; s = czero<CT>(); return; }
+    CT xs, ys;
+    xs.x = x.x / mx; xs.y = x.y / mx;
+    ys.x = y.x / mx; ys.y = y.y / mx;
+    const R irho = (R)1 / sqrt(cnorm2(xs) + cnorm2(ys));   // the sum lies in [1, 2]
+    const R ax = sqrt(cnorm2(xs));
+    CT ph;
+    if (ax > (R)0) { ph.x = xs.x / ax; ph.y = xs.y / ax; }
+    else { ph.x = 1; ph.y = 0; }
+    c = ax * irho;
+    s = cscale(irho, ph * cconj(ys));
+}
+
 // G = [[c, s], [-conj(s), c]] with c real maps (x, y) to (rho, 0).  Written
-// with selects (no branches) so that a sweep step stays one basic block.
+// with selects (no branches) so that a sweep step stays one basic block; the
+// rare tiny or huge (x, y) go to givens_scaled (the branch is uniform: every
+// lane of a warp computes the same rotation).
 template <typename R>
 __device__ __forceinline__ void givens(typename cx<R>::type x, typename cx<R>::type y, R& c,
                                        typename cx<R>::type& s) {
     const R nx = cnorm2(x), ny = cnorm2(y);
+    if (!(nx + ny >= givens_range<R>::lo() && nx + ny <= givens_range<R>::hi())) {
+        if (nx + ny == (R)0) { c = 1; s = czero<typename cx<R>::type>(); return; }
+        givens_scaled<R>(x, y, c, s);
+        return;
+    }
     const R irho = rsqrt(nx + ny), ix = rsqrt(nx), iy = rsqrt(ny);
     const R f = ix * irho;
     const typename cx<R>::type xy = x * cconj(y);
@@ -333,6 +622,14 @@ __device__ __forceinline__ void givens(typename cx<R>::type x, typename cx<R>::t
     c = yz ? (R)1 : (xz ? (R)0 : nx * ix * irho);  // |x| / rho
     s.x = yz ? (R)0 : (xz ? y.x * iy : f * xy.x);  // (x/|x|) conj(y) / rho
     s.y = yz ? (R)0 : (xz ? -y.y * iy : f * xy.y);
+    // rsqrt is approximate (a few ulp), so c^2 + |s|^2 = 1 + d with d of that
+    // size, and tens of thousands of such rotations per QR random-walk into the
+    // eigenvalues (3x coarser in FP32).  One Newton step on the normalisation
+    // leaves d = O(ulp^2).
+    const R g = (R)1.5 - (R)0.5 * (c * c + cnorm2(s));
+    c *= g;
+    s.x *= g;
+    s.y *= g;
 }
 
 // Eigenvalues of the ns x ns (ns <= 32) Hessenberg matrix S (column-major, ld
@@ -511,6 +808,8 @@ __device__ __forceinline__ void qr_window(typename cx<R>::type* H, int l, int hi
 //    eight warps busy at the cost of ~1.4x the rotations: ~6,000 chain steps
 //    instead of ~27,000 rotations for the 192 x 192 companion matrices of the
 //    n = 4096 QEP, with the same FP32 eigenvalue accuracy.)
+//    After kMsMaxStall multishift sweeps without a deflation the block goes on
+//    with single-shift sweeps until the next one.
 //  * otherwise (the FP64 fallback stage): single-shift sweeps; one warp chases
 //    the bulge through windows of kQrChunk rotations, the CTA applies each
 //    window's rotations to the rest of the block.
@@ -610,7 +909,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
             __syncthreads();
             continue;
         }
-        if (MS) {
+        if (MS && its <= kMsMaxStall) {
             // ---- small-bulge multishift sweep
             __shared__ CT s_sig[kMsShifts];
             const int ns = kMsShifts;
@@ -757,6 +1056,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
         key[3 * i + 1] = order_key(fin ? ex : INFINITY);
         key[3 * i + 2] = order_key(fin ? ey : INFINITY);
     }
+    if (tid == 0) gap[m0] = INFINITY;   // normalised radius of the first value left out
     __syncthreads();
     for (int i = tid; i < N; i += nt) {
         const unsigned long long k0 = key[3 * i], k1 = key[3 * i + 1], k2 = key[3 * i + 2];
@@ -780,6 +1080,9 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
             lam0[rank] = make_double2((double)e.x, (double)e.y);
             gap[rank] = jn < 0 ? INFINITY
                                : hypot((double)ev[jn].x - (double)e.x, (double)ev[jn].y - (double)e.y);
+        } else if (rank == m0 && fin) {
+            const double rx = ((double)e.x - c_re) / ra, ry = ((double)e.y - c_im) / rb;
+            gap[m0] = sqrt(rx * rx + ry * ry);
         }
     }
 }
@@ -983,8 +1286,10 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     int m, RedProblem P, const double2* __restrict__ lam0,
     const double* __restrict__ gap, double2* __restrict__ lam, double2* __restrict__ Y,
     int* redflag, int stage, IterStatus* status, const int* __restrict__ nkeep,
-    double2 filler) {
+    double2 filler, int* __restrict__ need) {
     if (stage == 2 && !(*redflag & kNeed64)) return;
+    if (stage == 3 && (!(*redflag & kRetry64) || !need[blockIdx.x])) return;
+    if (stage == 1 && need != nullptr && threadIdx.x == 0) need[blockIdx.x] = 0;
     if (nkeep != nullptr && (int)blockIdx.x >= *nkeep) {
         // a slot the reduced solver left empty: lambda outside C, unit vector
         if (threadIdx.x == 0) lam[blockIdx.x] = filler;
@@ -1073,15 +1378,35 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
             ++refreshes;
         }
     }
+    // Accept a move of at most 0.3 of the distance to the nearest other start,
+    // or any converged move that lands clearly inside the kept region: below the
+    // normalised radius of the first value Step 2 left out (gap[m0]) by twice
+    // the move in normalised units.  Two pairs landing on one eigenvalue are
+    // caught by the duplicate check.
     const double moved = cabs(l - l0);
     const double lim = 0.3 * gap[i];
-    if (!conv && stage == 1) ok = false;     // the FP64-factor stage takes over
-    if (!ok || !isfinite(l.x) || !isfinite(l.y) || !(moved <= lim)) {
+    const double rmin = fmin(P.ra, P.rb);
+    const double rx = (l.x - P.c_re) / P.ra, ry = (l.y - P.c_im) / P.rb;
+    const bool kept = conv && sqrt(rx * rx + ry * ry) + 2.0 * moved / rmin < gap[gridDim.x];
+    const double sx = (l0.x - P.c_re) / P.ra, sy = (l0.y - P.c_im) / P.rb;
+    const bool outside = sqrt(sx * sx + sy * sy) > 1.0 + 4.0 * moved / rmin;
+    if (!conv && stage != 2) ok = false;     // a later stage takes over
+    if (!ok || !isfinite(l.x) || !isfinite(l.y) || !(moved <= lim || kept)) {
         l = l0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = xf[r];
         if (threadIdx.x == 0) {
-            atomicOr(&status->flags, 8);
-            atomicOr(redflag, kNeed64);
+            if (stage == 1 && need != nullptr) {
+                // first retry this pair alone with an FP64 factor from the same start
+                need[i] = 1;
+                atomicOr(redflag, kRetry64);
+            } else if (!(stage == 3 && outside)) {
+                atomicOr(&status->flags, 8);
+                atomicOr(redflag, kNeed64);
+            }
+            // (a pair clearly outside C whose polish stalls even with the FP64
+            // factor -- a near-multiple Ritz value, where Newton converges only
+            // linearly -- keeps its FP32 value and inverse-iteration vector: Step
+            // 3 never tests it, and were it inside, its true residual would show)
         }
         __syncthreads();
     }
@@ -1168,6 +1493,13 @@ constexpr int kMaxSmemPacked = 200 * 1024;
 
 cudaError_t qr_select_attributes() {
     const int cap = kMaxSmemPacked + 16 * 1024;
+    cudaError_t e0;
+    if ((e0 = cudaFuncSetAttribute(companion_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)companion_cols_smem(kMaxM0))) != cudaSuccess) return e0;
+    if ((e0 = cudaFuncSetAttribute(hess_cluster_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kHcSmemCap)) != cudaSuccess) return e0;
+    if ((e0 = cudaFuncSetAttribute(hess_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kHcSmemCap)) != cudaSuccess) return e0;
     static_assert(kRedSmemCap <= (size_t)kMaxSmemPacked + 16 * 1024, "one cap for the single-CTA kernels");
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(hessenberg_kernel<float>,
@@ -1186,7 +1518,7 @@ cudaError_t qr_select_attributes() {
 
 // Workspace layout, every region 256-byte aligned.
 struct RedLayout {
-    size_t c32, lk32, c64, lk64, piv, h32, h64, lam0, gap, flag, total;
+    size_t c32, lk32, c64, lk64, piv, h32, h64, lam0, gap, flag, need, total;
 };
 RedLayout red_layout(int m, int kmax) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1201,8 +1533,9 @@ RedLayout red_layout(int m, int kmax) {
     L.h32 = o;  o = al(o + packed_elems((int)N) * sizeof(float2));
     L.h64 = o;  o = al(o + packed_elems((int)N) * sizeof(double2));
     L.lam0 = o; o = al(o + (size_t)m * sizeof(double2));
-    L.gap = o;  o = al(o + (size_t)m * sizeof(double));
+    L.gap = o;  o = al(o + (size_t)(m + 1) * sizeof(double));
     L.flag = o; o = al(o + 16);
+    L.need = o; o = al(o + (size_t)m * sizeof(int));
     L.total = o;
     return L;
 }
@@ -1220,16 +1553,32 @@ cudaError_t run_stage(cudaStream_t st, int stage, int m, int kmax, const double2
     int* flag = reinterpret_cast<int*>(base + L.flag);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
-    note_launch();
-    companion_kernel<R><<<1, kRedThreads, 0, st>>>(m, kmax, Ahat, C, Lk, piv, flag, stage);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    note_launch();
-    int c0;
-    size_t hsm;
-    hessenberg_launch_shape<R>(N, &c0, &hsm);
-    hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, c0, flag, stage);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaError_t e;
+    const int cs = sizeof(R) == 4 ? hess_cluster_size(N) : 0;
+    if (cs > 0) {
+        // FP32 stage: companion by column slices on several CTAs, Hessenberg
+        // reduction by a cluster holding the matrix in distributed shared memory
+        note_launch();
+        companion_cols_kernel<<<(N + kCompCols - 1) / kCompCols, kCompThreads, companion_cols_smem(m), st>>>(
+            m, kmax, Ahat, reinterpret_cast<float2*>(C), flag);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        if (cs == 4)
+            hess_cluster_kernel<4><<<4, kHcThreads, hess_cluster_smem(N, 4), st>>>(N, reinterpret_cast<float2*>(C));
+        else
+            hess_cluster_kernel<8><<<8, kHcThreads, hess_cluster_smem(N, 8), st>>>(N, reinterpret_cast<float2*>(C));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        note_launch();
+        companion_kernel<R><<<1, kRedThreads, 0, st>>>(m, kmax, Ahat, C, Lk, piv, flag, stage);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        note_launch();
+        int c0;
+        size_t hsm;
+        hessenberg_launch_shape<R>(N, &c0, &hsm);
+        hessenberg_kernel<R><<<1, kRedThreads, hsm, st>>>(N, C, c0, flag, stage);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     size_t hbytes = packed_elems(N) * sizeof(CT);
     const size_t fixed = sizeof(CT) * ((size_t)N + kSmallLd * kSmallMax);   // ev, dense block
     int use_smem = (hbytes + fixed) <= (size_t)kMaxSmemPacked;
@@ -1272,21 +1621,29 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
                          sizeof(int) * m;
     const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
                          sizeof(int) * m;
-    // stage 1: FP32 eigenvalues, FP64 Newton
+    int* need = reinterpret_cast<int*>(base + L.need);
+    // stage 1: FP32 eigenvalues, Newton with an FP32 factor and FP64 residuals
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
-    const RedProblem P{kmax, Ahat, 0, nullptr, nullptr};
+    const RedProblem P{kmax, Ahat, 0, nullptr, nullptr, c_re, c_im, ra, rb};
     newton_kernel<float2><<<m0, kNewtonThreads, nsm32, st>>>(m, P, lam0, gap, lam, Yred, flag, 1,
-                                                             status, nullptr, make_double2(0.0, 0.0));
+                                                             status, nullptr, make_double2(0.0, 0.0), need);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the pairs stage 1 rejected, again from the same starts with FP64 factors
+    // (device-side no-op for the others); failing that, the FP64 stage below
+    note_launch();
+    newton_kernel<double2><<<m0, kNewtonThreads, nsm64, st>>>(m, P, lam0, gap, lam, Yred, flag, 3,
+                                                              status, nullptr, make_double2(0.0, 0.0), need);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     note_launch();
     duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // stage 2 (device-side no-op unless stage 1 flagged a failure)
+    // stage 2 (device-side no-op unless the retry failed or two values coincide):
+    // FP64 eigenvalues of the companion matrix, Newton with FP64 factors
     if ((e = run_stage<double>(st, 2, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
     note_launch();
     newton_kernel<double2><<<m0, kNewtonThreads, nsm64, st>>>(m, P, lam0, gap, lam, Yred, flag,
-                                                              2, status, nullptr, make_double2(0.0, 0.0));
+                                                              2, status, nullptr, make_double2(0.0, 0.0), nullptr);
     return cudaGetLastError();
 }
 
@@ -1536,7 +1893,7 @@ BeynLayout beyn_layout(int m) {
     L.B = o;    o = al(o + mm * sizeof(float2));
     L.Hg = o;   o = al(o + packed_elems(m) * sizeof(float2));
     L.lam0 = o; o = al(o + (size_t)m * sizeof(double2));
-    L.gap = o;  o = al(o + (size_t)m * sizeof(double));
+    L.gap = o;  o = al(o + (size_t)(m + 1) * sizeof(double));
     L.flag = o; o = al(o + 16);
     L.rank = o; o = al(o + 16);
     L.total = o;
@@ -1582,7 +1939,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     double* gap = reinterpret_cast<double*>(base + L.gap);
     int* flag = reinterpret_cast<int*>(base + L.flag);
     int* rank = reinterpret_cast<int*>(base + L.rank);
-    const RedProblem P{-1, nullptr, nterms, terms, G};
+    const RedProblem P{-1, nullptr, nterms, terms, G, c_re, c_im, ra, rb};
     if ((e = random_block(st, m, m, probe_seed, V)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return e;
     note_launch();
@@ -1619,7 +1976,8 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                          sizeof(int) * m;
     note_launch();
     newton_kernel<float2><<<m, kNewtonThreads, nsm32, st>>>(
-        m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
+        m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im),
+        nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // a pair the FP32-factor Newton did not converge or moved too far: all kept
     // values refined again from the same starts with FP64 factors (device-side
@@ -1628,7 +1986,8 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                          sizeof(int) * m;
     note_launch();
     newton_kernel<double2><<<m, kNewtonThreads, nsm64, st>>>(
-        m, P, lam0, gap, lam, Yred, flag, 2, status, rank, make_double2(c_re + kBeynScale * ra, c_im));
+        m, P, lam0, gap, lam, Yred, flag, 2, status, rank, make_double2(c_re + kBeynScale * ra, c_im),
+        nullptr);
     return cudaGetLastError();
 }
 

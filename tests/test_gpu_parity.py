@@ -107,10 +107,13 @@ def test_project_matches_oracle(lib, prec, n, m):
 
 def test_project_matches_oracle_n4096(lib):
     """Projections at the largest K of the digit-split products (n = 4096,
-    K = 2n = 8192 in the real embedding) on the n = 4096 QEP with m0 = 96: the
-    error of each Q^H A_t Q against FP64, relative to its norm, stays at the
-    FP64 level (the worst-case FP32 accumulation bound of the low levels would
-    allow 6e-11)."""
+    K = 2n = 8192 in the real embedding) on the n = 4096 QEP with m0 = 96,
+    against FP64.  Seven 7-bit digit slices keep 49 bits of each entry relative
+    to its row's largest entry; the stiffness matrix K has diagonal entries
+    near 50 and off-diagonal entries near 1, so its off-diagonal entries keep
+    ~43 bits in W = K Q: 2^-43 = 1.1e-13 relative, the level measured here.
+    Tolerance 1e-12 (the worst-case FP32 accumulation bound of the low levels
+    would allow 6e-11)."""
     from workloads import config2_qep
     p = config2_qep(4096, 0)
     s = lib.FeastNL(p, "fp32_i8")
@@ -119,7 +122,7 @@ def test_project_matches_oracle_n4096(lib):
     ref = O.projected_coefficients(p, Q)
     errs = [_relerr(gp, rp) for gp, rp in zip(got, ref)]
     print("projection errors at n = 4096, m0 = 96:", ", ".join("%.2e" % e for e in errs))
-    assert max(errs) < 1e-13, errs
+    assert max(errs) < 1e-12, errs
     s.close()
 
 
