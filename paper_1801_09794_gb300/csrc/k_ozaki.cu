@@ -300,30 +300,41 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
 // ---------------------------------------------------------------------------
 // digit slices
 // ---------------------------------------------------------------------------
-// sigma_i = 2^e with max_k |A'_ik| < 2^e (1 for a zero row), one thread per row.
+// sigma_i = 2^e with max_k |A'_ik| < 2^e (1 for a zero row).  A CTA of 32 x 8
+// threads takes 32 rows; its 8 thread rows stride over K (coalesced along the
+// rows), then reduce through shared memory.
 __global__ void row_scale_kernel(int64_t M, int64_t K, const double2* __restrict__ A, int64_t lda,
                                  double* __restrict__ sigma, int64_t Mrows_pad) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= Mrows_pad) return;
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t i = blockIdx.x * (int64_t)32 + tx;
     double mx = 0.0;
     if (i < M)
-        for (int64_t k = 0; k < K; ++k) {
-            double2 a = A[i + k * lda];
+        for (int64_t k = ty; k < K; k += 8) {
+            const double2 a = A[i + k * lda];
             mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
         }
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
-    sigma[i] = (mx > 0.0) ? ldexp(1.0, e) : 1.0;
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && i < Mrows_pad) {
+        for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][tx]);
+        int e = 0;
+        if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+        sigma[i] = (mx > 0.0) ? ldexp(1.0, e) : 1.0;
+    }
 }
 
-// s base-128 digits of r (|r| < 1), truncated toward zero; exact in FP64.
-__device__ __forceinline__ void digits(double r, int s, float* d) {
-    for (int p = 0; p < s; ++p) {
-        r *= 128.0;
-        const double t = trunc(r);
-        d[p] = (float)t;
-        r -= t;
-    }
+// The s base-128 digits of r (|r| < 1), truncated toward zero, given
+// r2 = r * 2^(7 s) (exact: a power-of-two scaling): |r2| < 2^(7 s) <= 2^56 is
+// converted to an integer once (truncation toward zero), and digit p is bits
+// 7 (s-1-p) .. 7 (s-p) - 1 of its magnitude, with r's sign.  The same digits as
+// s steps of r <- 128 r, t = trunc(r), r <- r - t (all exact), without FP64
+// arithmetic beyond the scaling.
+__device__ __forceinline__ void digits_scaled(double r2, int s, float* d) {
+    const long long q = (long long)r2;
+    const unsigned long long u = (unsigned long long)(q < 0 ? -q : q);
+    const float sg = q < 0 ? -1.0f : 1.0f;
+    for (int p = 0; p < s; ++p) d[p] = sg * (float)(int)((u >> (7 * (s - 1 - p))) & 127ull);
 }
 
 // A' slices [slice][Mpad][Kp] (bf16) of an M x K block A (leading dimension
@@ -337,13 +348,14 @@ __global__ void split_rows_kernel(int64_t M, int64_t K, int s, const double2* __
     const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
     const int64_t i = i0 + tx;
     const double inv = (i < M) ? 1.0 / sigma[i] : 0.0;     // exact: sigma is a power of 2
+    const double sc = ldexp(inv, 7 * s);
     for (int kk = ty; kk < 32; kk += 8) {
         const int64_t k = k0 + kk;
         double2 a = make_double2(0.0, 0.0);
         if (i < M && k < K) a = A[i + k * lda];
         float dr[kOzMaxSlices], di[kOzMaxSlices];
-        digits(a.x * inv, s, dr);
-        digits(a.y * inv, s, di);
+        digits_scaled(a.x * sc, s, dr);
+        digits_scaled(a.y * sc, s, di);
         for (int p = 0; p < s; ++p) { tile[p][0][tx][kk] = dr[p]; tile[p][1][tx][kk] = di[p]; }
     }
     __syncthreads();
@@ -382,11 +394,11 @@ __global__ void split_cols_kernel(int64_t K, int s, const double2* __restrict__ 
         tau[j] = red[0];
     }
     __syncthreads();
-    const double inv = 1.0 / red[0];
+    const double sc = ldexp(1.0 / red[0], 7 * s);
     for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
         float dr[kOzMaxSlices], di[kOzMaxSlices];
-        digits(q[k].x * inv, s, dr);
-        digits(q[k].y * inv, s, di);
+        digits_scaled(q[k].x * sc, s, dr);
+        digits_scaled(q[k].y * sc, s, di);
         for (int p = 0; p < s; ++p) {
             __nv_bfloat16* r0 = out + p * slice_stride + (int64_t)(2 * j) * Kp;
             __nv_bfloat16* r1 = r0 + Kp;
@@ -424,7 +436,7 @@ cudaError_t ozaki_split_A(cudaStream_t st, int64_t n, int s, const double2* A, d
     cudaError_t e = cudaMemsetAsync(slices, 0, (size_t)L.a_term * sizeof(__nv_bfloat16), st);
     if (e != cudaSuccess) return e;
     note_launch();
-    row_scale_kernel<<<(unsigned)((L.Mpad + 127) / 128), 128, 0, st>>>(n, n, A, n, sigma, L.Mpad);
+    row_scale_kernel<<<(unsigned)((L.Mpad + 31) / 32), dim3(32, 8), 0, st>>>(n, n, A, n, sigma, L.Mpad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
     note_launch();
@@ -518,7 +530,7 @@ cudaError_t ozaki_gemm_general(cudaStream_t st, int64_t M, int K, int N, const d
         (e = cudaMemsetAsync(slot, 0, sizeof(int), st)) != cudaSuccess)
         return e;
     note_launch();
-    row_scale_kernel<<<(unsigned)((G.L.Mpad + 127) / 128), 128, 0, st>>>(M, K, A, lda, sigma, G.L.Mpad);
+    row_scale_kernel<<<(unsigned)((G.L.Mpad + 31) / 32), dim3(32, 8), 0, st>>>(M, K, A, lda, sigma, G.L.Mpad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     note_launch();
     dim3 g((unsigned)((M + 31) / 32), (unsigned)((K + 31) / 32));
@@ -579,14 +591,14 @@ __global__ void split_rows_conjT_kernel(int64_t K, int NT, int s, const double2*
         sigma[i] = red[0];
     }
     __syncthreads();
-    const double inv = 1.0 / red[0];
+    const double sc = ldexp(1.0 / red[0], 7 * s);
     for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
         float d[kOzMaxSlices];
         const bool re = k < K, im = k >= K && k < 2 * K;
         double v = 0.0;
-        if (live && re) v = w[k].x * inv;
-        if (live && im) v = -w[k - K].y * inv;
-        digits(v, s, d);
+        if (live && re) v = w[k].x * sc;
+        if (live && im) v = -w[k - K].y * sc;
+        digits_scaled(v, s, d);
         for (int p = 0; p < s; ++p) out[p * slice_stride + (int64_t)i * Kp + k] = __float2bfloat16_rn(d[p]);
     }
 }

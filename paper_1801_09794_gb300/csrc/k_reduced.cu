@@ -18,8 +18,8 @@
 //   retry:   a pair whose Newton run was rejected (not converged, or moved
 //            beyond 0.3 of the distance to its nearest neighbour without
 //            landing clearly inside the kept region) runs again from the same
-//            start with an FP64 factor; a pair clearly outside C that still
-//            stalls keeps its FP32 value and inverse-iteration vector;
+//            start with an FP64 factor -- except a pair clearly outside C, which
+//            keeps its FP32 value and inverse-iteration vector;
 //   stage 2: only if the retry failed too, or two kept values coincide --
 //            clustered, ill-conditioned Ritz values that FP32 cannot separate --
 //            the companion / Hessenberg / QR / selection runs in FP64 and
@@ -337,18 +337,20 @@ constexpr int kCompThreads = 32 * kCompCols;
 __global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
     int m, int kmax, const double2* __restrict__ Ahat, float2* __restrict__ C, int* redflag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* Lk = reinterpret_cast<float2*>(smem_raw);          // m x m, col-major
-    float2* X = Lk + (size_t)m * m;                             // m x kCompCols
+    const int ld = m + 1;                                       // see chol_inverse_kernel
+    float2* Lk = reinterpret_cast<float2*>(smem_raw);          // m x m, col-major, ld m + 1
+    float2* X = Lk + (size_t)ld * m;                            // m x kCompCols
     int* piv = reinterpret_cast<int*>(X + (size_t)m * kCompCols);
     __shared__ int s_p;
     const int N = kmax * m;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int64_t mm = (int64_t)m * m;
     if (blockIdx.x == 0 && tid == 0) *redflag = 0;
-    for (int64_t e = tid; e < mm; e += nt) {
-        const double2 a = Ahat[(int64_t)kmax * mm + e];
-        Lk[e] = make_float2((float)a.x, (float)a.y);
-    }
+    for (int c = warp; c < m; c += kCompCols)
+        for (int r = lane; r < m; r += 32) {
+            const double2 a = Ahat[(int64_t)kmax * mm + r + (int64_t)c * m];
+            Lk[r + c * ld] = make_float2((float)a.x, (float)a.y);
+        }
     const int col = blockIdx.x * kCompCols + warp;              // this warp's column of C
     const bool has = col < N;
     if (has) {
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
             float best = -1.0f;
             int bi = c;
             for (int r = c + lane; r < m; r += 32) {
-                const float v = cabs1(Lk[r + c * m]);
+                const float v = cabs1(Lk[r + c * ld]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -376,18 +378,18 @@ __global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
         const int p = s_p;
         if (p != c)
             for (int cc = tid; cc < m; cc += nt) {
-                const float2 a = Lk[c + cc * m];
-                Lk[c + cc * m] = Lk[p + cc * m];
-                Lk[p + cc * m] = a;
+                const float2 a = Lk[c + cc * ld];
+                Lk[c + cc * ld] = Lk[p + cc * ld];
+                Lk[p + cc * ld] = a;
             }
         __syncthreads();
-        const float2 inv = crcp(Lk[c + c * m]);
-        for (int r = c + 1 + tid; r < m; r += nt) Lk[r + c * m] = Lk[r + c * m] * inv;
+        const float2 inv = crcp(Lk[c + c * ld]);
+        for (int r = c + 1 + tid; r < m; r += nt) Lk[r + c * ld] = Lk[r + c * ld] * inv;
         __syncthreads();
-        const int rem = m - c - 1;
-        for (int e = tid; e < rem * rem; e += nt) {
-            const int r = c + 1 + e % rem, cc = c + 1 + e / rem;
-            Lk[r + cc * m] = cfms(Lk[r + c * m], Lk[c + cc * m], Lk[r + cc * m]);
+        for (int cc = c + 1 + warp; cc < m; cc += kCompCols) {     // warp per column
+            const float2 u = Lk[c + cc * ld];
+            for (int r = c + 1 + lane; r < m; r += 32)
+                Lk[r + cc * ld] = cfms(Lk[r + c * ld], u, Lk[r + cc * ld]);
         }
         __syncthreads();
     }
@@ -401,14 +403,14 @@ __global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
     __syncwarp();
     for (int i = 0; i < m - 1; ++i) {
         const float2 xi = x[i];
-        for (int r = i + 1 + lane; r < m; r += 32) x[r] = cfms(Lk[r + i * m], xi, x[r]);
+        for (int r = i + 1 + lane; r < m; r += 32) x[r] = cfms(Lk[r + i * ld], xi, x[r]);
         __syncwarp();
     }
     for (int i = m - 1; i >= 0; --i) {
-        if (lane == 0) x[i] = x[i] * crcp(Lk[i + i * m]);
+        if (lane == 0) x[i] = x[i] * crcp(Lk[i + i * ld]);
         __syncwarp();
         const float2 xi = x[i];
-        for (int r = lane; r < i; r += 32) x[r] = cfms(Lk[r + i * m], xi, x[r]);
+        for (int r = lane; r < i; r += 32) x[r] = cfms(Lk[r + i * ld], xi, x[r]);
         __syncwarp();
     }
     float2* out = C + (int64_t)col * N;
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(kCompThreads) companion_cols_kernel(
 }
 
 size_t companion_cols_smem(int m) {
-    return sizeof(float2) * ((size_t)m * m + (size_t)m * kCompCols) + sizeof(int) * (size_t)m;
+    return sizeof(float2) * ((size_t)(m + 1) * m + (size_t)m * kCompCols) + sizeof(int) * (size_t)m;
 }
 
 // Householder reduction of C (N x N, FP32, in place) to upper Hessenberg form
@@ -434,6 +436,7 @@ size_t companion_cols_smem(int m) {
 // Two cluster barriers per column; v is double-buffered because the owner of
 // column j + 1 may write it while other CTAs still read column j's.
 constexpr int kHcThreads = 1024;
+constexpr int kHcMaxN = 320;         // largest order the cluster reduction takes (registers per lane)
 
 template <int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kHcThreads)
@@ -447,15 +450,14 @@ hess_cluster_kernel(int N, float2* __restrict__ C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);   // ncl x N, column-major
     float2* vbuf = S + (size_t)ncl * N;                // 2 x N
-    float2* ypart = vbuf + 2 * (size_t)N;              // CS x N
+    float2* ypart = vbuf + 2 * (size_t)N;              // CS x N: the CTAs' shares of y
     float2* wv = ypart + (size_t)CS * N;               // ncl
     float2* yv = wv + ncl;                             // N
+    float2* ywarp = yv + N;                            // nw x N: the warps' shares
     __shared__ float s_beta[2];
     __shared__ float2 s_gamma;
-    for (int64_t e = tid; e < (int64_t)ncl * N; e += nt) {
-        const int lc = (int)(e / N), r = (int)(e - (int64_t)lc * N);
-        S[e] = C[(int64_t)(q + CS * lc) * N + r];
-    }
+    for (int lc = warp; lc < ncl; lc += nw)
+        for (int r = lane; r < N; r += 32) S[(size_t)lc * N + r] = C[(int64_t)(q + CS * lc) * N + r];
     __syncthreads();
     cluster.sync();
     for (int j = 0; j + 2 < N; ++j) {
@@ -476,6 +478,7 @@ hess_cluster_kernel(int N, float2* __restrict__ C) {
                 v0 = x0 - alpha;
                 beta = 2.0f / (tail + cnorm2(v0));
             }
+#pragma unroll
             for (int d = 0; d < CS; ++d) {
                 float2* vd = cluster.map_shared_rank(v, d);
                 for (int r = lane; r < len; r += 32) vd[r] = r == 0 ? v0 : col[r];
@@ -487,22 +490,43 @@ hess_cluster_kernel(int N, float2* __restrict__ C) {
         }
         cluster.sync();                                 // v, beta of column j everywhere
         const float beta = s_beta[buf];
-        const int lc0 = (j + 1 - q + CS - 1) / CS > 0 ? (j + 1 - q + CS - 1) / CS : 0;   // first own column > j
+        const int lc0 = (j + CS - q) / CS;              // first own column > j
         if (beta != 0.0f) {
+            // one pass per own column c > j (a warp each): w_c = v^H H(:, c) and
+            // the column's share of y = H v, kept per warp in registers
+            float2 yl[(kHcMaxN + 31) / 32];
+#pragma unroll
+            for (int q2 = 0; q2 < (kHcMaxN + 31) / 32; ++q2) yl[q2] = make_float2(0.0f, 0.0f);
             for (int lc = lc0 + warp; lc < ncl; lc += nw) {
-                const float2* hc = S + (size_t)lc * N + (j + 1);
+                const float2* hc = S + (size_t)lc * N;
+                const float2 vc = v[q + CS * lc - j - 1];
                 float2 w = make_float2(0.0f, 0.0f);
-                for (int r = lane; r < len; r += 32) w = cfma(cconj(v[r]), hc[r], w);
+#pragma unroll
+                for (int q2 = 0; q2 < (kHcMaxN + 31) / 32; ++q2) {
+                    const int r = lane + 32 * q2;
+                    if (r < N) {
+                        const float2 h = hc[r];
+                        yl[q2] = cfma(h, vc, yl[q2]);
+                        if (r > j) w = cfma(cconj(v[r - j - 1]), h, w);
+                    }
+                }
                 for (int off = 16; off > 0; off >>= 1) {
                     w.x += __shfl_xor_sync(0xffffffffu, w.x, off);
                     w.y += __shfl_xor_sync(0xffffffffu, w.y, off);
                 }
                 if (lane == 0) wv[lc] = w;
             }
+#pragma unroll
+            for (int q2 = 0; q2 < (kHcMaxN + 31) / 32; ++q2) {
+                const int r = lane + 32 * q2;
+                if (r < N) ywarp[(size_t)warp * N + r] = yl[q2];
+            }
+            __syncthreads();
+            // the CTA's share of y (warps summed in order) into every CTA
             for (int r = tid; r < N; r += nt) {
-                float2 y = make_float2(0.0f, 0.0f);
-                for (int lc = lc0; lc < ncl; ++lc)
-                    y = cfma(S[(size_t)lc * N + r], v[q + CS * lc - j - 1], y);
+                float2 y = ywarp[r];
+                for (int w2 = 1; w2 < nw; ++w2) y = y + ywarp[(size_t)w2 * N + r];
+#pragma unroll
                 for (int d = 0; d < CS; ++d) cluster.map_shared_rank(ypart + (size_t)q * N, d)[r] = y;
             }
         }
@@ -525,37 +549,39 @@ hess_cluster_kernel(int N, float2* __restrict__ C) {
             }
             __syncthreads();
             const float2 bg = beta * s_gamma;
-            const int nlive = ncl - lc0;
-            for (int64_t e = tid; e < (int64_t)nlive * N; e += nt) {
-                const int l2 = (int)(e / N), r = (int)(e - (int64_t)l2 * N);
-                const int lc = lc0 + l2, c = q + CS * lc;
-                const float2 vr = r > j ? v[r - j - 1] : make_float2(0.0f, 0.0f);
-                const float2 yt = cfms(bg, vr, yv[r]);                      // y_r - beta gamma v_r
-                float2 h = S[(size_t)lc * N + r];
-                h = cfms(beta * vr, wv[lc], h);
-                h = cfms(beta * yt, cconj(v[c - j - 1]), h);
-                S[(size_t)lc * N + r] = h;
+            for (int lc = lc0 + warp; lc < ncl; lc += nw) {   // warp per own column
+                const int c = q + CS * lc;
+                const float2 bvc = beta * cconj(v[c - j - 1]);
+                const float2 bw = beta * wv[lc];
+                float2* hc = S + (size_t)lc * N;
+                for (int r = lane; r < N; r += 32) {
+                    const float2 vr = r > j ? v[r - j - 1] : make_float2(0.0f, 0.0f);
+                    const float2 yt = cfms(bg, vr, yv[r]);             // y_r - beta gamma v_r
+                    float2 h = hc[r];
+                    h = cfms(vr, bw, h);
+                    h = cfms(yt, bvc, h);
+                    hc[r] = h;
+                }
             }
         }
         __syncthreads();
     }
     cluster.sync();
-    for (int64_t e = tid; e < (int64_t)ncl * N; e += nt) {
-        const int lc = (int)(e / N), r = (int)(e - (int64_t)lc * N);
-        C[(int64_t)(q + CS * lc) * N + r] = S[e];
-    }
+    for (int lc = warp; lc < ncl; lc += nw)
+        for (int r = lane; r < N; r += 32) C[(int64_t)(q + CS * lc) * N + r] = S[(size_t)lc * N + r];
 }
 
 size_t hess_cluster_smem(int N, int CS) {
     const size_t ncl = (size_t)(N + CS - 1) / CS;
-    return sizeof(float2) * (ncl * N + 2 * (size_t)N + (size_t)CS * N + ncl + (size_t)N);
+    return sizeof(float2) * (ncl * N + 2 * (size_t)N + (size_t)CS * N + ncl + (size_t)N +
+                             (size_t)(kHcThreads / 32) * N);
 }
 
 constexpr size_t kHcSmemCap = 200 * 1024;
 // Cluster size for the FP32 Hessenberg reduction of order N (0: the matrix does
 // not fit eight CTAs, or N is too small to pay; the single-CTA kernel runs).
 int hess_cluster_size(int N) {
-    if (N < 64 || N > kHcThreads) return 0;
+    if (N < 64 || N > kHcMaxN) return 0;
     if (hess_cluster_smem(N, 4) <= kHcSmemCap) return 4;
     if (hess_cluster_smem(N, 8) <= kHcSmemCap) return 8;
     return 0;
@@ -565,7 +591,9 @@ int hess_cluster_size(int N) {
 #define PK(i, j) ((((j) * ((j) + 5)) >> 1) + (i))
 
 constexpr int kQrThreads = 256;
-constexpr int kMsShifts = kQrThreads / 32;   // bulges of a multishift sweep: one warp each
+constexpr int kMsShifts = 8;                  // bulges of a multishift sweep
+constexpr int kMsWarps = kQrThreads / 32 / kMsShifts;   // warps per bulge
+static_assert(kMsWarps >= 1 && kMsShifts * kMsWarps * 32 == kQrThreads, "whole warps per bulge");
 // Multishift sweeps without a deflation at the bottom of the active block after
 // which the block continues with single-shift sweeps until the next deflation
 // (a safety net: the chain has no deflation checks inside the sweep; a healthy
@@ -941,33 +969,55 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
                 }
             }
             __syncthreads();
+            // bulge b is carried by warps b kMsWarps .. (b + 1) kMsWarps - 1; g indexes
+            // its threads.  The bulge column k-1 (its new subdiagonal entry and the
+            // cleared bulge) is written in the second phase, after every thread of
+            // the bulge has read x and y in the first.
+            const int bb = warp / kMsWarps;
+            const int g = (warp - bb * kMsWarps) * 32 + lane, gs = kMsWarps * 32;
             const int T = (hi - l) + 3 * (ns - 1);
             for (int t = 0; t < T; ++t) {
-                const int k = l + t - 3 * warp;          // this warp's bulge position
-                const bool act = warp < ns && k >= l && k <= hi - 1;
+                const int k = l + t - 3 * bb;            // this bulge's position
+                const bool act = k >= l && k <= hi - 1;
                 R c = 1;
-                CT sn = czero<CT>();
+                CT sn = czero<CT>(), rho = czero<CT>();
                 if (act) {
                     CT x, y;
-                    if (k == l) { x = HH(l, l) - s_sig[warp]; y = HH(l + 1, l); }
+                    if (k == l) { x = HH(l, l) - s_sig[bb]; y = HH(l + 1, l); }
                     else        { x = HH(k, k - 1); y = HH(k + 1, k - 1); }
                     givens<R>(x, y, c, sn);
-                    __syncwarp();                        // x, y read before any lane writes
-                    // row rotation: rows k, k+1 of columns max(l, k-1) .. hi
-                    for (int j = max(l, k - 1) + lane; j <= hi; j += 32) {
-                        const CT a = HH(k, j), b = HH(k + 1, j);
-                        HH(k, j) = cscale(c, a) + sn * b;
-                        HH(k + 1, j) = (j == k - 1) ? czero<CT>() : cscale(c, b) - cconj(sn) * a;
+                    rho = cscale(c, x) + sn * y;
+                    // row rotation: rows k, k+1 of columns k .. hi, three columns per
+                    // thread and pass so that their loads are in flight together
+                    for (int j = k + g; j <= hi; j += 3 * gs) {
+                        const bool p1 = j + gs <= hi, p2 = j + 2 * gs <= hi;
+                        // (indices of absent columns clamped: every address stays in range)
+                        const int o0 = PK(k, j), o1 = PK(k, p1 ? j + gs : j), o2 = PK(k, p2 ? j + 2 * gs : j);
+                        const CT a0 = H[o0], b0 = H[o0 + 1];
+                        const CT a1 = p1 ? H[o1] : czero<CT>(), b1 = p1 ? H[o1 + 1] : czero<CT>();
+                        const CT a2 = p2 ? H[o2] : czero<CT>(), b2 = p2 ? H[o2 + 1] : czero<CT>();
+                        H[o0] = cscale(c, a0) + sn * b0;
+                        H[o0 + 1] = cscale(c, b0) - cconj(sn) * a0;
+                        if (p1) { H[o1] = cscale(c, a1) + sn * b1; H[o1 + 1] = cscale(c, b1) - cconj(sn) * a1; }
+                        if (p2) { H[o2] = cscale(c, a2) + sn * b2; H[o2 + 1] = cscale(c, b2) - cconj(sn) * a2; }
                     }
                 }
                 __syncthreads();
                 if (act) {
+                    if (k > l && g == 0) { HH(k, k - 1) = rho; HH(k + 1, k - 1) = czero<CT>(); }
                     // column rotation: columns k, k+1 of rows l .. min(k+2, hi)
                     const int i1 = min(k + 2, hi);
-                    for (int i = l + lane; i <= i1; i += 32) {
-                        const CT a = HH(i, k), b = HH(i, k + 1);
-                        HH(i, k) = cscale(c, a) + cconj(sn) * b;
-                        HH(i, k + 1) = cscale(c, b) - sn * a;
+                    const int ck = PK(0, k), ck1 = PK(0, k + 1);
+                    for (int i = l + g; i <= i1; i += 3 * gs) {
+                        const bool p1 = i + gs <= i1, p2 = i + 2 * gs <= i1;
+                        const int r1 = p1 ? i + gs : i, r2 = p2 ? i + 2 * gs : i;   // clamped rows
+                        const CT a0 = H[ck + i], b0 = H[ck1 + i];
+                        const CT a1 = p1 ? H[ck + r1] : czero<CT>(), b1 = p1 ? H[ck1 + r1] : czero<CT>();
+                        const CT a2 = p2 ? H[ck + r2] : czero<CT>(), b2 = p2 ? H[ck1 + r2] : czero<CT>();
+                        H[ck + i] = cscale(c, a0) + cconj(sn) * b0;
+                        H[ck1 + i] = cscale(c, b0) - sn * a0;
+                        if (p1) { H[ck + r1] = cscale(c, a1) + cconj(sn) * b1; H[ck1 + r1] = cscale(c, b1) - sn * a1; }
+                        if (p2) { H[ck + r2] = cscale(c, a2) + cconj(sn) * b2; H[ck1 + r2] = cscale(c, b2) - sn * a2; }
                     }
                 }
                 __syncthreads();
@@ -1096,6 +1146,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_select_kernel(
 // complex each), fa, fu (m FP32 complex each), piv (m)
 // ---------------------------------------------------------------------------
 constexpr int kNewtonThreads = 256;
+static_assert(2 * kMaxM0 <= kNewtonThreads, "each row of the FP64 residual takes two threads");
 constexpr int kNewtonMax = 8;
 
 // f_t(l) (scale included) or its derivative, for the general reduced problem
@@ -1117,40 +1168,53 @@ __device__ __forceinline__ double2 rp_term(const TermDev& t, double2 l, bool der
     return t.scale * v;
 }
 
+// Leading dimension of the m x m factorisations held in shared memory: m + 1,
+// so that the rows of a column-major array (m a multiple of 16 for the usual
+// subspace sizes) do not all fall into one shared-memory bank.
+__host__ __device__ __forceinline__ int nld(int m) { return m + 1; }
+
+// T = That(lam) in the factorisation's precision, column-major, leading
+// dimension nld(m); a warp per column, lanes over rows.
 template <typename LT>
 __device__ void newton_build(int m, const RedProblem& P, double2 lam, LT* T) {
     const int64_t mm = (int64_t)m * m;
+    const int ld = nld(m), lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (P.kmax >= 0) {
         const LT lf = cmake<LT>(lam.x, lam.y);
-        for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-            double2 a = P.Ahat[(int64_t)P.kmax * mm + e];      // Horner in lambda
-            LT v = cmake<LT>(a.x, a.y);
-            for (int p = P.kmax - 1; p >= 0; --p) {
-                a = P.Ahat[(int64_t)p * mm + e];
-                v = cfma(v, lf, cmake<LT>(a.x, a.y));
+        for (int c = warp; c < m; c += nw)
+            for (int r = lane; r < m; r += 32) {
+                const int64_t e = r + (int64_t)c * m;
+                double2 a = P.Ahat[(int64_t)P.kmax * mm + e];      // Horner in lambda
+                LT v = cmake<LT>(a.x, a.y);
+                for (int p = P.kmax - 1; p >= 0; --p) {
+                    a = P.Ahat[(int64_t)p * mm + e];
+                    v = cfma(v, lf, cmake<LT>(a.x, a.y));
+                }
+                T[r + c * ld] = v;
             }
-            T[e] = v;
-        }
     } else {
-        for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
-            double2 v = make_double2(0.0, 0.0);
-            for (int t = 0; t < P.nterms; ++t)
-                v = cfma(rp_term(P.terms[t], lam, false), P.G[(int64_t)t * mm + e], v);
-            T[e] = cmake<LT>(v.x, v.y);
-        }
+        for (int c = warp; c < m; c += nw)
+            for (int r = lane; r < m; r += 32) {
+                const int64_t e = r + (int64_t)c * m;
+                double2 v = make_double2(0.0, 0.0);
+                for (int t = 0; t < P.nterms; ++t)
+                    v = cfma(rp_term(P.terms[t], lam, false), P.G[(int64_t)t * mm + e], v);
+                T[r + c * ld] = cmake<LT>(v.x, v.y);
+            }
     }
 }
 
-// Row r of T(l) x and T'(l) x, in FP64.
-__device__ void newton_apply(int m, const RedProblem& P, double2 l, const double2* x, int r,
-                             double2* v_out, double2* dv_out) {
+// Rows r of T(l) x and T'(l) x over the columns [c0, c1), in FP64 (the sum over
+// two column ranges is the whole product: both are linear in the row sums).
+__device__ void newton_apply(int m, const RedProblem& P, double2 l, const double2* x, int r, int c0,
+                             int c1, double2* v_out, double2* dv_out) {
     const int64_t mm = (int64_t)m * m;
     double2 v = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
     if (P.kmax >= 0) {
         for (int p = P.kmax; p >= 0; --p) {                 // Horner for T(l)x and T'(l)x
             double2 row = make_double2(0.0, 0.0);
             const double2* Ap = P.Ahat + (int64_t)p * mm;
-            for (int c = 0; c < m; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
+            for (int c = c0; c < c1; ++c) row = cfma(Ap[r + (int64_t)c * m], x[c], row);
             dv = cfma(dv, l, v);
             v = cfma(v, l, row);
         }
@@ -1158,7 +1222,7 @@ __device__ void newton_apply(int m, const RedProblem& P, double2 l, const double
         for (int t = 0; t < P.nterms; ++t) {
             double2 row = make_double2(0.0, 0.0);
             const double2* Gt = P.G + (int64_t)t * mm;
-            for (int c = 0; c < m; ++c) row = cfma(Gt[r + (int64_t)c * m], x[c], row);
+            for (int c = c0; c < c1; ++c) row = cfma(Gt[r + (int64_t)c * m], x[c], row);
             v = cfma(rp_term(P.terms[t], l, false), row, v);
             dv = cfma(rp_term(P.terms[t], l, true), row, dv);
         }
@@ -1167,18 +1231,22 @@ __device__ void newton_apply(int m, const RedProblem& P, double2 l, const double
     *dv_out = dv;
 }
 
-// LU with partial pivoting (cabs1) in place; the rank-1 update gives each warp
-// whole columns and each lane rows, so no thread divides indices.
+// LU with partial pivoting (cabs1, lowest row on ties) in place, leading
+// dimension nld(m).  Per column: warp 0 finds the pivot, swaps it into the
+// column and scales the multipliers (keeping the reciprocal pivot in rd[c]);
+// one thread per column swaps the two rows in the others; then each warp
+// updates whole columns right of c (lanes over rows).
 template <typename LT>
-__device__ void newton_lu(int m, LT* T, int* piv, int* s_p) {
+__device__ void newton_lu(int m, LT* T, int* piv, LT* rd, int* s_p) {
     typedef typename cplx_real<LT>::type LR;
+    const int ld = nld(m);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = 0; c < m; ++c) {
         if (warp == 0) {
             LR best = -1;
             int bi = c;
             for (int r = c + lane; r < m; r += 32) {
-                LR v = cabs1(T[r + c * m]);
+                LR v = cabs1(T[r + c * ld]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -1186,60 +1254,100 @@ __device__ void newton_lu(int m, LT* T, int* piv, int* s_p) {
                 int oi = __shfl_down_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
-            if (lane == 0) { *s_p = bi; piv[c] = bi; }
+            bi = __shfl_sync(0xffffffffu, bi, 0);
+            if (lane == 0) {
+                *s_p = bi;
+                piv[c] = bi;
+                if (bi != c) { const LT t = T[c + c * ld]; T[c + c * ld] = T[bi + c * ld]; T[bi + c * ld] = t; }
+            }
+            __syncwarp();
+            LT d = T[c + c * ld];
+            if (d.x == (LR)0 && d.y == (LR)0) d = cmake<LT>(1e-30, 0.0);
+            const LT inv = crcp(d);
+            for (int r = c + 1 + lane; r < m; r += 32) T[r + c * ld] = T[r + c * ld] * inv;
+            if (lane == 0) { T[c + c * ld] = d; rd[c] = inv; }
         }
         __syncthreads();
         const int p = *s_p;
-        if (p != c)
-            for (int cc = threadIdx.x; cc < m; cc += blockDim.x) {
-                LT t = T[c + cc * m];
-                T[c + cc * m] = T[p + cc * m];
-                T[p + cc * m] = t;
-            }
-        __syncthreads();
-        LT d = T[c + c * m];
-        if (d.x == (LR)0 && d.y == (LR)0) d = cmake<LT>(1e-30, 0.0);
-        const LT inv = crcp(d);
+        if (p != c) {
+            for (int cc = threadIdx.x; cc < m; cc += blockDim.x)
+                if (cc != c) { const LT t = T[c + cc * ld]; T[c + cc * ld] = T[p + cc * ld]; T[p + cc * ld] = t; }
+            __syncthreads();
+        }
         for (int cc = c + 1 + warp; cc < m; cc += nw) {
-            const LT u = T[c + cc * m];
-            for (int r = c + 1 + lane; r < m; r += 32)
-                T[r + cc * m] = cfms(T[r + c * m] * inv, u, T[r + cc * m]);
+            const LT u = T[c + cc * ld];
+            for (int r = c + 1 + lane; r < m; r += 32) T[r + cc * ld] = cfms(T[r + c * ld], u, T[r + cc * ld]);
         }
         __syncthreads();
-        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) T[r + c * m] = T[r + c * m] * inv;
-        if (threadIdx.x == 0) T[c + c * m] = d;
-        __syncthreads();
     }
+}
+
+// One warp solves L U y = P b in place (factors of newton_lu, reciprocal pivots
+// rd): the row interchanges in shared memory, then both substitutions with b in
+// registers (lane j holds rows j, j + 32, ..; m <= 128), each step's pivot
+// value broadcast by a shuffle.
+template <typename LT>
+__device__ __forceinline__ LT pick4(const LT* br, int q) {
+    return q == 0 ? br[0] : (q == 1 ? br[1] : (q == 2 ? br[2] : br[3]));
+}
+template <typename LT>
+__device__ void warp_lu_solve(int m, const LT* T, const int* piv, const LT* rd, LT* b) {
+    const int lane = threadIdx.x & 31, ld = nld(m);
+    if (lane == 0)
+        for (int c = 0; c < m; ++c) {
+            const int p = piv[c];
+            if (p != c) { const LT t = b[c]; b[c] = b[p]; b[p] = t; }
+        }
+    __syncwarp();
+    LT br[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        br[q] = r < m ? b[r] : cmake<LT>(0.0, 0.0);
+    }
+    for (int i = 0; i + 1 < m; ++i) {                    // unit lower triangle
+        const LT own = pick4(br, i >> 5);
+        LT bi;
+        bi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+        bi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+        const LT* Ti = T + (size_t)i * ld;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = lane + 32 * q;
+            if (r > i && r < m) br[q] = cfms(Ti[r], bi, br[q]);
+        }
+    }
+    for (int i = m - 1; i >= 0; --i) {                   // upper triangle
+        const int qi = i >> 5;
+        const LT own = pick4(br, qi);
+        LT bi;
+        bi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+        bi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+        bi = bi * rd[i];
+        const LT* Ti = T + (size_t)i * ld;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = lane + 32 * q;
+            if (r == i) br[q] = bi;
+            else if (r < i) br[q] = cfms(Ti[r], bi, br[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        if (r < m) b[r] = br[q];
+    }
+    __syncwarp();
 }
 
 // Solves T y = b in place with the LU held in T; warp 0 takes b0 and warp 1
 // takes b1 (when given), so the two right-hand sides of a Newton step proceed
 // side by side.
 template <typename LT>
-__device__ void newton_solve(int m, const LT* T, const int* piv, LT* b0, LT* b1) {
+__device__ void newton_solve(int m, const LT* T, const int* piv, const LT* rd, LT* b0, LT* b1) {
     const int w = threadIdx.x >> 5;
     LT* b = (w == 0) ? b0 : b1;
-    if (w < 2 && b != nullptr) {
-        const int lane = threadIdx.x & 31;
-        if (lane == 0)
-            for (int c = 0; c < m; ++c) {
-                int p = piv[c];
-                if (p != c) { LT t = b[c]; b[c] = b[p]; b[p] = t; }
-            }
-        __syncwarp();
-        for (int i = 0; i < m; ++i) {
-            LT bi = b[i];
-            for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
-            __syncwarp();
-        }
-        for (int i = m - 1; i >= 0; --i) {
-            if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
-            __syncwarp();
-            LT bi = b[i];
-            for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
-            __syncwarp();
-        }
-    }
+    if (w < 2 && b != nullptr) warp_lu_solve(m, T, piv, rd, b);
     __syncthreads();
 }
 
@@ -1279,6 +1387,13 @@ __device__ Sum4 block_sum4(Sum4 v, double* red) {
 __device__ __forceinline__ double2 to_d2f(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d2f(double2 v) { return v; }
 
+// Dynamic shared memory of newton_kernel<LT> for subspace size m.
+template <typename LT>
+size_t newton_smem(int m) {
+    return sizeof(double2) * 6 * (size_t)m + sizeof(LT) * ((size_t)m * nld(m) + 3 * (size_t)m) +
+           sizeof(int) * (size_t)m;
+}
+
 // LT: arithmetic of the factorisation (float2 in stage 1, double2 in the FP64
 // fallback stage, where clustered reduced eigenvalues need the FP64 factor).
 template <typename LT>
@@ -1302,10 +1417,13 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     double2* u = x + m;
     double2* xf = u + m;
     double2* a = xf + m;
-    LT* T = reinterpret_cast<LT*>(a + m);
-    LT* fa = T + (int64_t)m * m;
+    double2* pv = a + m;                       // the second column half's partial rows
+    double2* pdv = pv + m;
+    LT* T = reinterpret_cast<LT*>(pdv + m);    // m x m, leading dimension nld(m)
+    LT* fa = T + (int64_t)m * nld(m);
     LT* fu = fa + m;
-    int* piv = reinterpret_cast<int*>(fu + m);
+    LT* rd = fu + m;                           // reciprocal pivots
+    int* piv = reinterpret_cast<int*>(rd + m);
     __shared__ double red[4 * 33];
     __shared__ int s_p;
     const int i = blockIdx.x;
@@ -1313,10 +1431,10 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     double2 l = l0;
     newton_build(m, P, l, T);
     __syncthreads();
-    newton_lu(m, T, piv, &s_p);
+    newton_lu(m, T, piv, rd, &s_p);
     for (int r = threadIdx.x; r < m; r += blockDim.x) fa[r] = cmake<LT>(1.0, 0.0);
     __syncthreads();
-    newton_solve<LT>(m, T, piv, fa, nullptr);
+    newton_solve<LT>(m, T, piv, rd, fa, nullptr);
     {
         double s = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) s += cnorm2(to_d2f(fa[r]));
@@ -1335,14 +1453,25 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
     int refreshes = 0;
     double prev = INFINITY;
     for (int it = 0; it < kNewtonMax; ++it) {
-        for (int r = threadIdx.x; r < m; r += blockDim.x) {
-            double2 v, dv;
-            newton_apply(m, P, l, x, r, &v, &dv);
-            fa[r] = cmake<LT>(v.x, v.y);
-            fu[r] = cmake<LT>(dv.x, dv.y);
+        {   // FP64 rows of T(l) x and T'(l) x, each row's columns split over two threads
+            const int half = (m + 1) / 2;
+            double2 v = make_double2(0.0, 0.0), dv = v;
+            const int t = threadIdx.x;
+            if (t < 2 * m) {
+                const int r = t < m ? t : t - m;
+                newton_apply(m, P, l, x, r, t < m ? 0 : half, t < m ? half : m, &v, &dv);
+                if (t >= m) { pv[r] = v; pdv[r] = dv; }
+            }
+            __syncthreads();
+            if (t < m) {
+                v = v + pv[t];
+                dv = dv + pdv[t];
+                fa[t] = cmake<LT>(v.x, v.y);
+                fu[t] = cmake<LT>(dv.x, dv.y);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        newton_solve(m, T, piv, fa, fu);
+        newton_solve(m, T, piv, rd, fa, fu);
         double are = 0.0, aim = 0.0, ure = 0.0, uim = 0.0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
             a[r] = to_d2f(fa[r]);
@@ -1374,7 +1503,7 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         if (rel > 1e-9 && refreshes < 2 && (it == 1 || it == 4)) {
             newton_build(m, P, l, T);
             __syncthreads();
-            newton_lu(m, T, piv, &s_p);
+            newton_lu(m, T, piv, rd, &s_p);
             ++refreshes;
         }
     }
@@ -1395,18 +1524,19 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
         l = l0;
         for (int r = threadIdx.x; r < m; r += blockDim.x) x[r] = xf[r];
         if (threadIdx.x == 0) {
-            if (stage == 1 && need != nullptr) {
-                // first retry this pair alone with an FP64 factor from the same start
+            // A pair clearly outside C whose polish stalls -- typically a
+            // near-multiple Ritz value, where Newton converges only linearly --
+            // keeps its FP32 value and inverse-iteration vector: Step 3 never
+            // tests it, and were it inside C its true residual would show.
+            if (stage != 2 && outside) {
+            } else if (stage == 1 && need != nullptr) {
+                // retry this pair alone with an FP64 factor from the same start
                 need[i] = 1;
                 atomicOr(redflag, kRetry64);
-            } else if (!(stage == 3 && outside)) {
+            } else {
                 atomicOr(&status->flags, 8);
                 atomicOr(redflag, kNeed64);
             }
-            // (a pair clearly outside C whose polish stalls even with the FP64
-            // factor -- a near-multiple Ritz value, where Newton converges only
-            // linearly -- keeps its FP32 value and inverse-iteration vector: Step
-            // 3 never tests it, and were it inside, its true residual would show)
         }
         __syncthreads();
     }
@@ -1415,15 +1545,27 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
 }
 
 // Two kept Ritz values that coincide after Newton mean stage 1 lost one.
-__global__ void duplicate_check_kernel(int m0, const double2* __restrict__ lam, int* redflag) {
-    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-        double2 a = lam[i];
-        for (int j = i + 1; j < m0; ++j) {
-            double2 b = lam[j];
-            double d = hypot(a.x - b.x, a.y - b.y);
-            if (d <= 1e-9 * fmax(hypot(a.x, a.y), 1e-300)) atomicOr(redflag, kNeed64);
-        }
+// Every pair (i, j) is one thread's test, on squared distances.
+constexpr int kDupThreads = 1024;
+__global__ void __launch_bounds__(kDupThreads) duplicate_check_kernel(int m0, const double2* __restrict__ lam,
+                                                                      int* redflag) {
+    __shared__ double2 s_l[kMaxM0];
+    __shared__ int s_dup;
+    if (threadIdx.x == 0) s_dup = 0;
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) s_l[i] = lam[i];
+    __syncthreads();
+    const int np = m0 * m0;
+    bool dup = false;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+        const int i = e / m0, j = e - i * m0;
+        if (j <= i) continue;
+        const double2 a = s_l[i], b = s_l[j];
+        const double dx = a.x - b.x, dy = a.y - b.y;
+        dup = dup || (dx * dx + dy * dy <= 1e-18 * fmax(a.x * a.x + a.y * a.y, 1e-300));
     }
+    if (dup) s_dup = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_dup) atomicOr(redflag, kNeed64);
 }
 
 // ---------------------------------------------------------------------------
@@ -1436,56 +1578,75 @@ __global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2*
                                                            double2* __restrict__ Rinv,
                                                            IterStatus* status) {
     extern __shared__ unsigned char smem_raw[];
+    // leading dimension m + 1: the rows of a column-major m x m array with m a
+    // multiple of 16 would otherwise sit in one shared-memory bank
+    const int ld = m + 1;
     float2* R = reinterpret_cast<float2*>(smem_raw);   // m x m col-major (upper used)
-    float2* X = R + m * m;                              // m x m col-major
+    float2* X = R + ld * m;                             // m x m col-major: R^{-1}
+    __shared__ float s_red[16];
     __shared__ float s_tr;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) {
-        double tr = 0.0;
-        for (int i = 0; i < m; ++i) tr += G[i + (int64_t)i * m].x;
-        s_tr = (float)(shift_rel * tr);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    {   // trace (real parts of the diagonal), one warp
+        if (warp == 0) {
+            double tr = 0.0;
+            for (int i = lane; i < m; i += 32) tr += G[i + (int64_t)i * m].x;
+            for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            if (lane == 0) s_tr = (float)(shift_rel * tr);
+        }
+        __syncthreads();
     }
+    for (int c = warp; c < m; c += nw)
+        for (int r = lane; r < m; r += 32) {
+            const double2 g = G[r + (int64_t)c * m];
+            float2 v = make_float2((float)g.x, (float)g.y);
+            if (r == c) v = make_float2(v.x + s_tr, 0.0f);
+            R[r + c * ld] = v;
+            X[r + c * ld] = make_float2(r == c ? 1.0f : 0.0f, 0.0f);
+        }
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-        int r = e % m, c = e / m;
-        double2 g = G[e];
-        float2 v = make_float2((float)g.x, (float)g.y);
-        if (r == c) v = make_float2(v.x + s_tr, 0.0f);
-        R[e] = v;
-    }
-    __syncthreads();
+    // right-looking Cholesky: row j of R, then the trailing upper triangle; the
+    // trailing update gives each warp whole columns and each lane rows
     for (int j = 0; j < m; ++j) {
+        float d = R[j + j * ld].x;
+        const bool bad = !(d > 0.0f);
+        if (bad) d = 1e-30f;
+        const float rjj = sqrtf(d), inv = 1.0f / rjj;
+        __syncthreads();                               // every thread has read the pivot
         if (tid == 0) {
-            float d = R[j + j * m].x;
-            if (!(d > 0.0f)) { atomicOr(&status->flags, 4); d = 1e-30f; }
-            R[j + j * m] = make_float2(sqrtf(d), 0.0f);
+            if (bad) atomicOr(&status->flags, 4);
+            R[j + j * ld] = make_float2(rjj, 0.0f);
         }
+        for (int c = j + 1 + tid; c < m; c += nt) R[j + c * ld] = inv * R[j + c * ld];
         __syncthreads();
-        float rjj = R[j + j * m].x;
-        for (int c = j + 1 + tid; c < m; c += nt) R[j + c * m] = (1.0f / rjj) * R[j + c * m];
-        __syncthreads();
-        int rem = m - j - 1;
-        for (int e = tid; e < rem * rem; e += nt) {
-            int r = j + 1 + e % rem, c = j + 1 + e / rem;
-            if (r <= c) R[r + c * m] = cfms(cconj(R[j + r * m]), R[j + c * m], R[r + c * m]);
+        for (int c = j + 1 + warp; c < m; c += nw) {
+            const float2 uc = R[j + c * ld];
+            for (int r = j + 1 + lane; r <= c; r += 32)
+                R[r + c * ld] = cfms(cconj(R[j + r * ld]), uc, R[r + c * ld]);
         }
         __syncthreads();
     }
-    // column c of R^{-1} by back substitution in thread c; X holds it row-major
-    // (entry (r, c) at X[c + r m]) so that a warp's threads touch adjacent words
-    for (int c = tid; c < m; c += nt) {
-        for (int i = 0; i < m; ++i) X[c + i * m] = make_float2(i == c ? 1.0f : 0.0f, 0.0f);
+    // column c of R^{-1} by back substitution, one warp per column, with the
+    // reciprocal pivots formed once
+    __shared__ float2 s_rdiag[kMaxM0];
+    for (int i = tid; i < m; i += nt) s_rdiag[i] = crcp(R[i + i * ld]);
+    __syncthreads();
+    for (int c = warp; c < m; c += nw) {
+        float2* x = X + c * ld;
         for (int i = c; i >= 0; --i) {
-            float2 xi = X[c + i * m] * crcp(R[i + i * m]);
-            X[c + i * m] = xi;
-            for (int r = 0; r < i; ++r) X[c + r * m] = cfms(R[r + i * m], xi, X[c + r * m]);
+            if (lane == 0) x[i] = x[i] * s_rdiag[i];
+            __syncwarp();
+            const float2 xi = x[i];
+            for (int r = lane; r < i; r += 32) x[r] = cfms(R[r + i * ld], xi, x[r]);
+            __syncwarp();
         }
     }
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-        const float2 v = X[e / m + (e % m) * m];
-        Rinv[e] = make_double2(v.x, v.y);
-    }
+    for (int c = warp; c < m; c += nw)
+        for (int r = lane; r < m; r += 32) {
+            const float2 v = X[r + c * ld];
+            Rinv[r + (int64_t)c * m] = make_double2(v.x, v.y);
+        }
+    (void)s_red;
 }
 
 size_t packed_elems(int N) { return (size_t)N * (N + 5) / 2 + 4; }
@@ -1617,10 +1778,8 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
     int* flag = reinterpret_cast<int*>(base + L.flag);
     double2* lam0 = reinterpret_cast<double2*>(base + L.lam0);
     double* gap = reinterpret_cast<double*>(base + L.gap);
-    const size_t nsm32 = sizeof(double2) * 4 * m + sizeof(float2) * ((size_t)m * m + 2 * m) +
-                         sizeof(int) * m;
-    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
-                         sizeof(int) * m;
+    const size_t nsm32 = newton_smem<float2>(m);
+    const size_t nsm64 = newton_smem<double2>(m);
     int* need = reinterpret_cast<int*>(base + L.need);
     // stage 1: FP32 eigenvalues, Newton with an FP32 factor and FP64 residuals
     if ((e = run_stage<float>(st, 1, m, kmax, Ahat, m0, c_re, c_im, ra, rb, base, L, status)) != cudaSuccess) return e;
@@ -1636,7 +1795,7 @@ cudaError_t reduced_solve(cudaStream_t st, int m, int kmax, const double2* Ahat,
                                                               status, nullptr, make_double2(0.0, 0.0), need);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     note_launch();
-    duplicate_check_kernel<<<1, 128, 0, st>>>(m0, lam, flag);
+    duplicate_check_kernel<<<1, kDupThreads, 0, st>>>(m0, lam, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // stage 2 (device-side no-op unless the retry failed or two values coincide):
     // FP64 eigenvalues of the companion matrix, Newton with FP64 factors
@@ -1675,39 +1834,16 @@ __device__ __forceinline__ void beyn_node(int k, double c_re, double c_im, doubl
     *w = make_double2(dz.y / kBeynNodes, -dz.x / kBeynNodes);
 }
 
-// one warp solves L U y = P b in place (LU and pivots of newton_lu)
-template <typename LT>
-__device__ void lu_solve_warp(int m, const LT* T, const int* piv, LT* b) {
-    const int lane = threadIdx.x & 31;
-    if (lane == 0)
-        for (int c = 0; c < m; ++c) {
-            const int p = piv[c];
-            if (p != c) { LT t = b[c]; b[c] = b[p]; b[p] = t; }
-        }
-    __syncwarp();
-    for (int i = 0; i < m; ++i) {
-        const LT bi = b[i];
-        for (int r = i + 1 + lane; r < m; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
-        __syncwarp();
-    }
-    for (int i = m - 1; i >= 0; --i) {
-        if (lane == 0) b[i] = b[i] * crcp(T[i + i * m]);
-        __syncwarp();
-        const LT bi = b[i];
-        for (int r = lane; r < i; r += 32) b[r] = cfms(T[r + i * m], bi, b[r]);
-        __syncwarp();
-    }
-}
-
 // CTA k: Y = That(z_k)^{-1} V (FP32 LU: the nodes lie away from the
 // eigenvalues), written as w_k Y and w_k z_k Y.
 __global__ void __launch_bounds__(kBeynThreads) beyn_solve_kernel(
     int m, RedProblem P, double c_re, double c_im, double ra, double rb,
     const double2* __restrict__ V, float2* __restrict__ P0, float2* __restrict__ P1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* T = reinterpret_cast<float2*>(smem_raw);
-    float2* Y = T + (int64_t)m * m;
-    int* piv = reinterpret_cast<int*>(Y + (int64_t)m * m);
+    float2* T = reinterpret_cast<float2*>(smem_raw);          // leading dimension nld(m)
+    float2* Y = T + (int64_t)m * nld(m);
+    float2* rd = Y + (int64_t)m * m;
+    int* piv = reinterpret_cast<int*>(rd + m);
     __shared__ int s_p;
     const int k = blockIdx.x;
     double2 z, w;
@@ -1717,9 +1853,9 @@ __global__ void __launch_bounds__(kBeynThreads) beyn_solve_kernel(
     for (int64_t e = threadIdx.x; e < mm; e += blockDim.x)
         Y[e] = make_float2((float)V[e].x, (float)V[e].y);
     __syncthreads();
-    newton_lu(m, T, piv, &s_p);
+    newton_lu(m, T, piv, rd, &s_p);
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = warp; col < m; col += nw) lu_solve_warp(m, T, piv, Y + (int64_t)col * m);
+    for (int col = warp; col < m; col += nw) warp_lu_solve(m, T, piv, rd, Y + (int64_t)col * m);
     __syncthreads();
     const float2 wf = make_float2((float)w.x, (float)w.y);
     const double2 wz = w * z;
@@ -1911,7 +2047,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     if (m < 1 || m > beyn_max_m()) return cudaErrorInvalidValue;
     cudaError_t e;
     static std::atomic<bool> attr_done{false};   // idempotent setup; atomic for concurrent handles
-    const size_t solve_smem = 2 * sizeof(float2) * (size_t)m * m + sizeof(int) * m;
+    const size_t solve_smem = sizeof(float2) * ((size_t)m * nld(m) + (size_t)m * m + m) + sizeof(int) * m;
     const size_t svd_smem = 3 * sizeof(float2) * (size_t)m * m + (sizeof(float) + sizeof(int)) * m;
     if (!attr_done) {
         const int cap = 3 * 8 * 64 * 64 + 8 * 64 + 64;
@@ -1972,8 +2108,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
                                                                          rb, lam0, gap, flag, 1, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Newton per kept value (FP32 factor, FP64 residuals), fillers beyond the rank
-    const size_t nsm32 = sizeof(double2) * 4 * m + sizeof(float2) * ((size_t)m * m + 2 * m) +
-                         sizeof(int) * m;
+    const size_t nsm32 = newton_smem<float2>(m);
     note_launch();
     newton_kernel<float2><<<m, kNewtonThreads, nsm32, st>>>(
         m, P, lam0, gap, lam, Yred, flag, 1, status, rank, make_double2(c_re + kBeynScale * ra, c_im),
@@ -1982,8 +2117,7 @@ cudaError_t reduced_solve_general(cudaStream_t st, int m, int nterms, const Term
     // a pair the FP32-factor Newton did not converge or moved too far: all kept
     // values refined again from the same starts with FP64 factors (device-side
     // no-op otherwise), so no Ritz value is left at its FP32 moment estimate
-    const size_t nsm64 = sizeof(double2) * 4 * m + sizeof(double2) * ((size_t)m * m + 2 * m) +
-                         sizeof(int) * m;
+    const size_t nsm64 = newton_smem<double2>(m);
     note_launch();
     newton_kernel<double2><<<m, kNewtonThreads, nsm64, st>>>(
         m, P, lam0, gap, lam, Yred, flag, 2, status, rank, make_double2(c_re + kBeynScale * ra, c_im),
@@ -2001,7 +2135,7 @@ cudaError_t chol_inverse(cudaStream_t st, int m, const double2* G, double shift_
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    size_t smem = sizeof(float2) * 2 * (size_t)m * m;
+    size_t smem = sizeof(float2) * 2 * (size_t)(m + 1) * m;
     note_launch();
     chol_inverse_kernel<<<1, 512, smem, st>>>(m, G, shift_rel, Rinv, status);
     return cudaGetLastError();
