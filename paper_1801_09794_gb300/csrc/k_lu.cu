@@ -14,14 +14,23 @@
 //              then U12 = L11^{-1} A12 (one warp per column);
 //   3. update: A22 -= L21 U12 (complex64: TF32 tensor cores on split operands,
 //              FP32-accurate; complex128: FP64 SIMT GEMM).
-// Interchanges are never applied to the columns LEFT of a panel: every L block
-// stays in the row order it had when it was formed, and the forward solve
-// applies each panel's interchanges to the right-hand side just before that
-// panel's elimination (the order Gaussian elimination itself uses), which is
-// equivalent to P T = L U and saves the strided row traffic on L.
+//   4. pair swap: for an odd panel k, its gather list applied to the L columns
+//              of panel k - 1 as well, on a third, low-priority stream (nothing
+//              on the critical path reads them), so that panels k - 1 and k form
+//              one block of 2 nb columns whose L carries the row order after
+//              both panels' interchanges -- the factors of a blocked LU with
+//              block size 2 nb.
+// Interchanges are otherwise not applied to the columns left of a block: the
+// forward solve applies each block's two gather lists to the right-hand side
+// just before that block's substitution (the order Gaussian elimination itself
+// uses), equivalent to P T = L U without the strided row traffic on all of L.
+// The solves step through blocks of 2 nb rows (128 for complex64, 64 for
+// complex128): half the dependent steps of per-panel substitution and twice
+// the depth of each tensor-core update.
 #include "internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -440,41 +449,157 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) swap_trsm_grouped_kernel(
                       d.n, c0, ncols);
 }
 
-// B[k0:k0+jb, col] <- U11^{-1} B[k0:k0+jb, col] (U11 upper with its diagonal, from F).
+// ---------------------------------------------------------------------------
+// Interchanges of panel k on the L columns of panel k - 1 (k odd), so that the
+// solves can treat panels k - 1 and k as one block of 2 nb rows.
+// ---------------------------------------------------------------------------
+// One warp applies a gather list (dst <- src rows, at most 128 entries) to one
+// column: every src read before any dst written.
 template <typename T>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) trsm_upper_kernel(
-    int64_t n, int k0, int jb, const T* __restrict__ F, int64_t ld, int64_t strideF, T* B,
-    int64_t ldb, int64_t strideB, int ncols, const int* __restrict__ active, int group) {
-    __shared__ T sU[TriMax<T>::value][TriMax<T>::value + 1];
+__device__ __forceinline__ void gather_rows_warp(const int2* __restrict__ gl, int cnt, T* col) {
+    const int lane = threadIdx.x & 31;
+    T g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        if (e < cnt) g[q] = col[gl[e].y];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        if (e < cnt) col[gl[e].x] = g[q];
+    }
+    __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_cols_kernel(
+    int c0, int ncols, T* F, int64_t ld, int64_t strideF, const int2* __restrict__ gather,
+    const int* __restrict__ gcount, int gstride, int panel_index) {
     const int node = blockIdx.y;
-    if (active && !active[node / group]) return;
+    const int c = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    if (c >= ncols) return;
+    gather_rows_warp(gather + (int64_t)node * gstride + panel_index * 2 * 64,
+                     gcount[(int64_t)node * (gstride / 128) + panel_index],
+                     F + node * strideF + (int64_t)(c0 + c) * ld);
+}
+
+// The same for nodes of different orders: panel k's list on the nb columns of
+// panel k - 1, in every node that has a panel k.
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) swap_cols_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int panel_index) {
+    const LuNode d = nodes[blockIdx.y];
+    if (k0 >= d.n) return;
+    const int c = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    if (c >= nb) return;
+    gather_rows_warp(d.gather + panel_index * 2 * 64, d.gcount[panel_index],
+                     static_cast<T*>(d.F) + (int64_t)(k0 - nb + c) * d.n);
+}
+
+// ---------------------------------------------------------------------------
+// Block substitution step of the solves, one warp per right-hand-side column,
+// on a diagonal block of jb <= SB rows (two panels):
+//   lower (forward): the interchanges of the block's panels, then
+//          B[k0:k0+jb, col] <- L_bb^{-1} B[k0:k0+jb, col] (unit lower);
+//   upper (backward): B[k0:k0+jb, col] <- U_bb^{-1} B[k0:k0+jb, col].
+// The triangle in use is staged in shared memory row-major with row stride
+// SB + 1 (conflict-free for the lanes' rows; the diagonal of U stored
+// inverted); lane l holds rows l, l + 32, l + 64, l + 96 in registers.
+// ---------------------------------------------------------------------------
+constexpr int kBlockWarps = 16;
+
+template <typename T>
+__device__ __forceinline__ T pick_slot(const T* x, int q) {
+    T v = x[0];
+#pragma unroll
+    for (int u = 1; u < 4; ++u)
+        if (u == q) v = x[u];
+    return v;
+}
+
+template <typename T, int SB>
+__global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
+    int k0, int jb, int nb, const T* __restrict__ F, int64_t ld, int64_t strideF,
+    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
+    T* B, int64_t ldb, int64_t strideB, int ncols, int upper, const int* __restrict__ active,
+    int group) {
+    static_assert(SB % 32 == 0 && SB <= 128, "at most four rows per lane");
+    constexpr int Q = SB / 32, LDS = SB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sD = reinterpret_cast<T*>(smem_raw);
+    const int node = blockIdx.y;
+    if (active && !active[node / group]) return;     // a finished contour's nodes
     F += node * strideF;
     B += node * strideB;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < jb * jb; e += blockDim.x) {
-        int r = e % jb, c = e / jb;
-        T v = F[(k0 + r) + (int64_t)(k0 + c) * ld];
-        sU[r][c] = (r == c) ? crcp(v) : v;          // diagonal stored inverted
-    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < jb; c += kBlockWarps)
+        for (int r = lane; r < jb; r += 32) {
+            if (upper ? r > c : r <= c) continue;
+            T v = F[(k0 + r) + (int64_t)(k0 + c) * ld];
+            if (upper && r == c) v = crcp(v);
+            sD[r * LDS + c] = v;
+        }
     __syncthreads();
-    const int cl = blockIdx.x * kWarpsPerCta + warp;
+    const int cl = blockIdx.x * kBlockWarps + warp;
     if (cl >= ncols) return;
     T* col = B + (int64_t)cl * ldb;
-    T x0 = (lane < jb) ? col[k0 + lane] : cmake<T>(0.0, 0.0);
-    T x1 = (lane + 32 < jb) ? col[k0 + lane + 32] : cmake<T>(0.0, 0.0);
-    for (int i = jb - 1; i >= 0; --i) {
-        // x_i <- x_i / U_ii (owner lane), broadcast, eliminate from rows < i
-        if (i < 32) { if (lane == i) x0 = x0 * sU[i][i]; }
-        else        { if (lane == i - 32) x1 = x1 * sU[i][i]; }
-        T src = (i < 32) ? x0 : x1;
-        T xi;
-        xi.x = __shfl_sync(0xffffffffu, src.x, i & 31);
-        xi.y = __shfl_sync(0xffffffffu, src.y, i & 31);
-        if (lane < i) x0 = cfms(sU[lane][i], xi, x0);
-        if (lane + 32 < i) x1 = cfms(sU[lane + 32][i], xi, x1);
+    if (!upper) {
+        const int2* gl = gather + (int64_t)node * gstride + panel_index * 2 * 64;
+        const int* gc = gcount + (int64_t)node * (gstride / 128) + panel_index;
+        gather_rows_warp(gl, gc[0], col);
+        if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
     }
-    if (lane < jb) col[k0 + lane] = x0;
-    if (lane + 32 < jb) col[k0 + lane + 32] = x1;
+    col += k0;
+    T x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        x[q] = (q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
+    }
+    if (!upper) {
+        for (int i = 0; i + 1 < jb; ++i) {
+            const T own = pick_slot(x, i >> 5);
+            T xi;
+            xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+            xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int r = lane + 32 * q;
+                if (r > i && r < jb) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+            }
+        }
+    } else {
+        for (int i = jb - 1; i >= 0; --i) {
+            const T own = pick_slot(x, i >> 5);
+            T xi;
+            xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+            xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+            xi = xi * sD[i * LDS + i];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int r = lane + 32 * q;
+                if (r == i) x[q] = xi;
+                else if (r < i) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r < jb) col[r] = x[q];
+    }
+}
+
+// rows of a solve block: two panels
+template <typename T> struct SolveBlock;
+template <> struct SolveBlock<float2> { static constexpr int value = 128; };
+template <> struct SolveBlock<double2> { static constexpr int value = 64; };
+
+template <typename T>
+constexpr size_t solve_block_smem() {
+    return (size_t)SolveBlock<T>::value * (SolveBlock<T>::value + 1) * sizeof(T);
 }
 
 template <typename T>
@@ -558,44 +683,84 @@ cudaError_t panel_apply(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_
 //   low:   wait P -> apply k to the columns right of panel k+1 -> [R(k)]
 // (the low stream's update of step k-1 covers panel k+1's columns, hence the
 // wait; panel k itself only needs what the high stream did before it).
+// A third stream takes the pair swaps: after odd panel k, once panel k's list
+// exists [P] and the side stream's update of step k - 1 -- the last reader of
+// panel k - 1's L below the panel -- is done [R(k-1)].
+namespace {
+struct FactorStreams {
+    cudaStream_t hi = nullptr, side = nullptr, pair = nullptr;
+    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr, evS = nullptr;
+    ~FactorStreams() {
+        for (cudaEvent_t ev : {evP, evR[0], evR[1], evH, evS})
+            if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t s : {hi, side, pair})       // released once their work completes
+            if (s) cudaStreamDestroy(s);
+    }
+    // all three streams start after everything already queued on st (the assembly)
+    cudaError_t create(cudaStream_t st) {
+        int prio_lo = 0, prio_hi = 0;
+        cudaError_t e;
+        if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&pair, cudaStreamNonBlocking, prio_lo)) != cudaSuccess)
+            return e;
+        for (cudaEvent_t* ev : {&evP, &evR[0], &evR[1], &evH, &evS})
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(evP, st)) != cudaSuccess) return e;
+        for (cudaStream_t s : {hi, side, pair})
+            if ((e = cudaStreamWaitEvent(s, evP, 0)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    // the pair stream waits for panel k (just launched on hi) and for the side
+    // stream's last recorded update
+    cudaError_t pair_after_panel(int last_r) {
+        cudaError_t e;
+        if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(pair, evP, 0)) != cudaSuccess)
+            return e;
+        if (last_r >= 0) return cudaStreamWaitEvent(pair, evR[last_r & 1], 0);
+        return cudaSuccess;
+    }
+    // everything the three streams did is ordered before what follows on st
+    cudaError_t join(cudaStream_t st, int last_r) {
+        cudaError_t e;
+        if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess ||
+            (e = cudaEventRecord(evS, pair)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, evS, 0)) != cudaSuccess)
+            return e;
+        if (last_r >= 0) return cudaStreamWaitEvent(st, evR[last_r & 1], 0);
+        return cudaSuccess;
+    }
+};
+}  // namespace
+
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
                               int* piv, int nc, int* info, int2* gather, int* gcount, int* err) {
     const int gstride = lu_gather_stride(n, nb);
     const int npanel = (int)((n + nb - 1) / nb);
+    if (nb % kWarpsPerCta != 0 || 2 * nb > SolveBlock<T>::value) return cudaErrorInvalidValue;
+    FactorStreams S;
     cudaError_t e;
-    cudaStream_t hi = nullptr, side = nullptr;
-    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr;
-    auto cleanup = [&](cudaError_t r) {
-        if (evP) cudaEventDestroy(evP);
-        if (evR[0]) cudaEventDestroy(evR[0]);
-        if (evR[1]) cudaEventDestroy(evR[1]);
-        if (evH) cudaEventDestroy(evH);
-        if (side) cudaStreamDestroy(side);   // released once their work completes
-        if (hi) cudaStreamDestroy(hi);
-        return r;
-    };
-    int prio_lo = 0, prio_hi = 0;
-    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
-        (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
-        (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evH, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evR[0], cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evR[1], cudaEventDisableTiming)) != cudaSuccess)
-        return cleanup(e);
-    // both streams start after everything already queued on st (the assembly)
-    if ((e = cudaEventRecord(evP, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(hi, evP, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
-        return cleanup(e);
+    if ((e = S.create(st)) != cudaSuccess) return e;
+    cudaStream_t hi = S.hi, side = S.side;
+    cudaEvent_t evP = S.evP, *evR = S.evR;
     int last_r = -1;                              // step whose side update was recorded last
     for (int k = 0; k < npanel; ++k) {
         const int k0 = k * nb;
         const int jb = (int)std::min<int64_t>(nb, n - k0);
         if ((e = launch_panel<T>(hi, n, k0, jb, F, strideF, piv, nc, info, gather, gcount, k,
                                  gstride)) != cudaSuccess)
-            return cleanup(e);
+            return e;
+        if (k & 1) {                              // pair swap: panel k's list on panel k - 1
+            if ((e = S.pair_after_panel(last_r)) != cudaSuccess) return e;
+            note_launch();
+            swap_cols_kernel<T><<<dim3((unsigned)(nb / kWarpsPerCta), nc), 32 * kWarpsPerCta, 0,
+                                  S.pair>>>(k0 - nb, nb, F, n, strideF, gather, gcount, gstride, k);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         const int64_t rest = n - k0 - jb;
         if (rest <= 0) break;
         const int64_t jn = std::min<int64_t>(nb, rest);     // next panel's columns
@@ -603,28 +768,23 @@ cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t 
         if (rr > 0) {
             if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
-                return cleanup(e);
+                return e;
             if ((e = panel_apply<T>(side, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
                                     k0 + jb + jn, rr, err)) != cudaSuccess)
-                return cleanup(e);
+                return e;
         }
         if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
-            return cleanup(e);
+            return e;
         if (rr > 0) {
-            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return cleanup(e);
+            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return e;
             last_r = k;
         }
         if ((e = panel_apply<T>(hi, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
                                 k0 + jb, jn, err)) != cudaSuccess)
-            return cleanup(e);
+            return e;
     }
-    // everything both streams did is ordered before what follows on st
-    if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
-        return cleanup(e);
-    if (last_r >= 0 && (e = cudaStreamWaitEvent(st, evR[last_r & 1], 0)) != cudaSuccess)
-        return cleanup(e);
-    return cleanup(cudaGetLastError());
+    if ((e = S.join(st, last_r)) != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_t* n_host,
@@ -634,31 +794,12 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
     if (count <= 0 || nmax <= 0) return cudaSuccess;
     if (nmax > 4 * kPanelThreads || count > 65535) return cudaErrorInvalidValue;
     const int npanel = (int)((nmax + nb - 1) / nb);
+    if (nb % kWarpsPerCta != 0 || 2 * nb > SolveBlock<float2>::value) return cudaErrorInvalidValue;
+    FactorStreams S;
     cudaError_t e;
-    cudaStream_t hi = nullptr, side = nullptr;
-    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr;
-    auto cleanup = [&](cudaError_t r) {
-        if (evP) cudaEventDestroy(evP);
-        if (evR[0]) cudaEventDestroy(evR[0]);
-        if (evR[1]) cudaEventDestroy(evR[1]);
-        if (evH) cudaEventDestroy(evH);
-        if (side) cudaStreamDestroy(side);
-        if (hi) cudaStreamDestroy(hi);
-        return r;
-    };
-    int prio_lo = 0, prio_hi = 0;
-    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
-        (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
-        (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evP, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evH, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evR[0], cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&evR[1], cudaEventDisableTiming)) != cudaSuccess)
-        return cleanup(e);
-    if ((e = cudaEventRecord(evP, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(hi, evP, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
-        return cleanup(e);
+    if ((e = S.create(st)) != cudaSuccess) return e;
+    cudaStream_t hi = S.hi, side = S.side;
+    cudaEvent_t evP = S.evP, *evR = S.evR;
     int last_r = -1;
     for (int k = 0; k < npanel; ++k) {
         const int k0 = k * nb;
@@ -675,23 +816,30 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
         }
         note_launch();
         lu_panel_reg_grouped_kernel<float2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(e);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (k & 1) {                              // pair swap: panel k's list on panel k - 1
+            if ((e = S.pair_after_panel(last_r)) != cudaSuccess) return e;
+            note_launch();
+            swap_cols_grouped_kernel<float2><<<dim3((unsigned)(nb / kWarpsPerCta), count),
+                                               32 * kWarpsPerCta, 0, S.pair>>>(nodes, k0, nb, k);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         if (rows_below <= 0) continue;
         if (cols_rest > 0) {
             if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
-                return cleanup(e);
+                return e;
             dim3 g((unsigned)((cols_rest + kWarpsPerCta - 1) / kWarpsPerCta), count);
             note_launch();
             swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, side>>>(nodes, k0, nb, k, 1);
             if ((e = cgemm_sub_grouped(side, nodes, count, k0, nb, 1, rows_below, cols_rest, err)) !=
                 cudaSuccess)
-                return cleanup(e);
+                return e;
         }
         if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
-            return cleanup(e);
+            return e;
         if (cols_rest > 0) {
-            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return cleanup(e);
+            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return e;
             last_r = k;
         }
         if (cols_next > 0) {
@@ -700,43 +848,53 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
             swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, hi>>>(nodes, k0, nb, k, 0);
             if ((e = cgemm_sub_grouped(hi, nodes, count, k0, nb, 0, rows_below, cols_next, err)) !=
                 cudaSuccess)
-                return cleanup(e);
+                return e;
         }
     }
-    if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
-        return cleanup(e);
-    if (last_r >= 0 && (e = cudaStreamWaitEvent(st, evR[last_r & 1], 0)) != cudaSuccess)
-        return cleanup(e);
-    return cleanup(cudaGetLastError());
+    if ((e = S.join(st, last_r)) != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int64_t strideF,
                              const int2* gather, const int* gcount, int nc, T* Y, int64_t strideY,
                              int m, int* err, int bn, const int* active, int group) {
+    constexpr int SB = SolveBlock<T>::value;
+    constexpr int smem = (int)solve_block_smem<T>();
+    const int sb = 2 * nb;                        // a block: two panels
+    if (sb > SB) return cudaErrorInvalidValue;
+    static std::atomic<bool> attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        if ((e = cudaFuncSetAttribute(trsm_block_kernel<T, SB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
     const int gstride = lu_gather_stride(n, nb);
-    cudaError_t e;
-    dim3 g((unsigned)((m + kWarpsPerCta - 1) / kWarpsPerCta), nc);
-    for (int64_t k0 = 0, panel = 0; k0 < n; k0 += nb, ++panel) {
-        int jb = (int)((n - k0) < nb ? (n - k0) : nb);
+    dim3 g((unsigned)((m + kBlockWarps - 1) / kBlockWarps), nc);
+    for (int64_t k0 = 0, panel = 0; k0 < n; k0 += sb, panel += 2) {
+        const int jb = (int)std::min<int64_t>(sb, n - k0);
         note_launch();
-        swap_trsm_lower_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(
-            n, (int)k0, jb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, 0, m,
+        trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+            (int)k0, jb, nb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, m, 0,
             active, group);
-        int64_t rest = n - k0 - jb;
+        const int64_t rest = n - k0 - jb;
         if (rest > 0) {
             e = update(st, (int)rest, m, jb, F + (k0 + jb) + k0 * n, n, strideF, Y + k0, n,
                        strideY, Y + k0 + jb, n, strideY, nc, err, bn, active, group);
             if (e != cudaSuccess) return e;
         }
     }
-    int64_t last = ((n - 1) / nb) * nb;
-    for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
-        int jb = (int)((n - k0) < nb ? (n - k0) : nb);
+    const int64_t last = ((n - 1) / sb) * sb;
+    for (int64_t k0 = last; k0 >= 0; k0 -= sb) {
+        const int jb = (int)std::min<int64_t>(sb, n - k0);
         note_launch();
-        trsm_upper_kernel<T><<<g, 32 * kWarpsPerCta, 0, st>>>(n, (int)k0, jb, F, n, strideF, Y, n,
-                                                              strideY, m, active, group);
+        trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+            (int)k0, jb, nb, F, n, strideF, gather, gcount, gstride, 0, Y, n, strideY, m, 1, active,
+            group);
         if (k0 > 0) {
             e = update(st, (int)k0, m, jb, F + k0 * n, n, strideF, Y + k0, n, strideY, Y, n,
                        strideY, nc, err, bn, active, group);
