@@ -28,6 +28,7 @@
 // complex128): half the dependent steps of per-panel substitution and twice
 // the depth of each tensor-core update.
 #include "internal.h"
+#include "tc_common.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -62,13 +63,15 @@ __device__ __forceinline__ void argmax_warp(R& v, int& i) {
 
 // Gather list of a panel's interchanges: the sequential swaps (c, piv[c]),
 // c = k0..k0+jb-1, permute the rows of the set {k0..k0+jb-1} U {piv[c]}; after
-// them row dst[e] holds what row src[e] held before.  One thread, <= 2 jb rows.
-__device__ void panel_gather_list(int k0, int jb, const int* ip, int2* list, int* count) {
-    int rows[128], src[128];
+// them row dst[e] holds what row src[e] held before.  One thread, <= 2 jb <= MAXR
+// rows; ip[c] is the pivot row of column k0 + c.
+template <int MAXR>
+__device__ void gather_list(int k0, int jb, const int* ip, int2* list, int* count) {
+    int rows[MAXR], src[MAXR];
     int cnt = 0;
     for (int c = 0; c < jb; ++c) { rows[cnt] = k0 + c; src[cnt] = k0 + c; ++cnt; }
     for (int c = 0; c < jb; ++c) {
-        const int a = k0 + c, b = ip[k0 + c];
+        const int a = k0 + c, b = ip[c];
         if (a == b) continue;
         int ia = a - k0, ib = -1;
         if (b < k0 + jb) ib = b - k0;
@@ -101,11 +104,16 @@ __device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, 
     __shared__ T s_crow[kMini];     // row being replaced by the pivot row
     __shared__ T s_L11[kMini][kMini];
     __shared__ T s_U[kMini][64];    // U12 rows of the mini-panel (rest of the panel)
+    __shared__ int s_piv[kMini];    // the mini-panel's pivot rows
+    __shared__ int2 s_gl[2 * kMini];
+    __shared__ int s_gc;
+    static_assert(kPanelThreads / 16 >= 64, "a 16-thread group per panel column");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pend = k0 + jb;
-    // panel columns per batch in the in-panel update (as many as the registers
-    // left next to the mini-panel allow at 1024 threads)
-    constexpr int kUpd = (sizeof(T) == 8) ? (ROWS == 4 ? 4 : 8) : (ROWS == 1 ? 4 : 2);
+    // panel columns per batch in the in-panel update: ROWS x kUpd loads in
+    // flight per thread, as many as the registers left next to the mini-panel
+    // allow at 1024 threads
+    constexpr int kUpd = (sizeof(T) == 8) ? 8 / ROWS : (ROWS == 1 ? 4 : 2);
     T v[ROWS][kMini];
 
     for (int mb0 = k0; mb0 < pend; mb0 += kMini) {
@@ -145,6 +153,7 @@ __device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, 
                     if (bi == INT_MAX || bi < col || bi >= n) bi = col;
                     if (!(best > (R)0) && *info1 == 0) *info1 = col + 1;
                     s_p = bi;
+                    s_piv[c] = bi;
                     ip[col] = bi;
                 }
             }
@@ -215,29 +224,39 @@ __device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, 
                 for (int c = 0; c < kMini; ++c) s_L11[r - mb0][c] = v[i][c];
         }
         const int rest0 = mb0 + w, nrest = pend - rest0;   // remaining panel columns
-        const int nleft = mb0 - k0;                        // factored panel columns
+        if (tid == 0) gather_list<2 * kMini>(mb0, w, s_piv, s_gl, &s_gc);
         __syncthreads();
-        // this mini-panel's interchanges on the panel's factored columns, so that the
-        // whole panel ends in the row order of all its interchanges
-        if (tid >= 64 && tid - 64 < nleft) {
-            T* colp = A + (int64_t)(k0 + tid - 64) * ld;
-            for (int c = 0; c < w; ++c) {
-                const int a = mb0 + c, b = ip[a];
-                if (a != b) { T t0 = colp[a]; colp[a] = colp[b]; colp[b] = t0; }
+        const int gcnt = s_gc;
+        // this mini-panel's interchanges on the other panel columns -- factored
+        // ones, so that the whole panel ends in the row order of all its
+        // interchanges, and remaining ones, whose mini-panel rows (the U12 rows
+        // to solve for) go to s_U.  Thread (column jj = tid / 16, slot e =
+        // tid % 16): slots 0..7 read a gather source, slots 8..11 a mini-panel
+        // row; every read lands before any write (one round trip per column).
+        {
+            const int jj = tid >> 4, e = tid & 15;
+            const int cidx = k0 + jj;
+            const bool left = cidx < mb0, rest = cidx >= rest0 && cidx < pend;
+            T* colp = A + (int64_t)cidx * ld;
+            T val = cmake<T>(0.0, 0.0);
+            int dst = -1;
+            if ((left || rest) && e < gcnt) { val = colp[s_gl[e].y]; dst = s_gl[e].x; }
+            if (rest && e >= 2 * kMini && e - 2 * kMini < w)
+                s_U[e - 2 * kMini][cidx - rest0] = colp[mb0 + e - 2 * kMini];
+            __syncthreads();
+            if (dst >= 0) {
+                if (rest && dst < mb0 + w) s_U[dst - mb0][cidx - rest0] = val;
+                else colp[dst] = val;
             }
+            __syncthreads();
         }
         if (nrest > 0) {
-            // interchanges of this mini-panel on the remaining panel columns, then
-            // U12 = L11^{-1} A12: one thread per remaining column
+            // U12 = L11^{-1} A12 on the remaining panel columns, one thread each
             if (tid < nrest) {
                 T* colp = A + (int64_t)(rest0 + tid) * ld;
-                for (int c = 0; c < w; ++c) {
-                    const int a = mb0 + c, b = ip[a];
-                    if (a != b) { T t0 = colp[a]; colp[a] = colp[b]; colp[b] = t0; }
-                }
                 T u[kMini];
 #pragma unroll
-                for (int c = 0; c < kMini; ++c) u[c] = (c < w) ? colp[mb0 + c] : cmake<T>(0.0, 0.0);
+                for (int c = 0; c < kMini; ++c) u[c] = (c < w) ? s_U[c][tid] : cmake<T>(0.0, 0.0);
 #pragma unroll
                 for (int c = 0; c < kMini; ++c)
 #pragma unroll
@@ -251,24 +270,30 @@ __device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, 
             }
             __syncthreads();
             // rank-w update of rows below the mini-panel, remaining panel columns;
-            // kUpd columns at a time so that kUpd loads per row are in flight
+            // per batch of kUpd columns every owned row's loads are issued first
+            for (int j0 = 0; j0 < nrest; j0 += kUpd) {
+                T a[ROWS][kUpd];
 #pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-                const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
-                if (r >= rest0 && r < n) {
-                    T* ar = A + r + (int64_t)rest0 * ld;
-                    for (int j0 = 0; j0 < nrest; j0 += kUpd) {
-                        T a[kUpd];
+                for (int i = 0; i < ROWS; ++i) {
+                    const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+                    const T* ar = A + r + (int64_t)(rest0 + j0) * ld;
 #pragma unroll
-                        for (int q = 0; q < kUpd; ++q)
-                            if (j0 + q < nrest) a[q] = ar[(int64_t)(j0 + q) * ld];
+                    for (int q = 0; q < kUpd; ++q)
+                        a[i][q] = (r >= rest0 && r < n && j0 + q < nrest) ? ar[(int64_t)q * ld]
+                                                                           : cmake<T>(0.0, 0.0);
+                }
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int64_t r = k0 + tid + (int64_t)i * kPanelThreads;
+                    if (r >= rest0 && r < n) {
+                        T* ar = A + r + (int64_t)(rest0 + j0) * ld;
 #pragma unroll
                         for (int q = 0; q < kUpd; ++q) {
                             if (j0 + q < nrest) {
 #pragma unroll
                                 for (int c = 0; c < kMini; ++c)
-                                    if (c < w) a[q] = cfms(v[i][c], s_U[c][j0 + q], a[q]);
-                                ar[(int64_t)(j0 + q) * ld] = a[q];
+                                    if (c < w) a[i][q] = cfms(v[i][c], s_U[c][j0 + q], a[i][q]);
+                                ar[(int64_t)q * ld] = a[i][q];
                             }
                         }
                     }
@@ -277,7 +302,7 @@ __device__ __forceinline__ void panel_reg_body(int64_t n, int k0, int jb, T* A, 
             __syncthreads();
         }
     }
-    if (tid == 0 && gl != nullptr) panel_gather_list(k0, jb, ip, gl, gc);
+    if (tid == 0 && gl != nullptr) gather_list<128>(k0, jb, ip + k0, gl, gc);
 }
 
 template <typename T, int ROWS>
@@ -370,26 +395,49 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_kernel(
         __syncthreads();
     }
     if (tid == 0 && gather != nullptr)
-        panel_gather_list(k0, jb, ip, gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64,
-                          gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
+        gather_list<128>(k0, jb, ip + k0, gather + (int64_t)blockIdx.x * gstride + panel_index * 2 * 64,
+                         gcount + (int64_t)blockIdx.x * (gstride / 128) + panel_index);
 }
 
 // ---------------------------------------------------------------------------
 // Triangular kernels, one warp per right-hand-side column; the jb rows of the
 // diagonal block are spread over the lanes (lane l holds rows l and l + 32).
 // ---------------------------------------------------------------------------
+// One element global -> shared without a register round trip (cp.async; the
+// copies of a whole triangle are in flight together).
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+// Starts the copy of one triangle of the jb x jb diagonal block of F at k0
+// into sD[r * lds + c]: the strictly lower part (upper == 0) or the upper part
+// with the diagonal.  Columns over the CTA's warps, rows over the lanes
+// (coalesced).  Completion: cp.async.wait_all, then a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_triangle(const T* __restrict__ F, int64_t ld, int k0, int jb,
+                                               T* sD, int lds, int upper) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < jb; c += nw) {
+        const T* fc = F + k0 + (int64_t)(k0 + c) * ld;
+        for (int r = upper ? lane : c + 1 + lane; r < (upper ? c + 1 : jb); r += 32)
+            cp_async_elem(sD + r * lds + c, fc + r);
+    }
+}
+
 // Columns [col_begin, col_begin+ncols) of B: the panel's gather list, then
 // B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F).
 template <typename T>
 __device__ __forceinline__ void swap_trsm_body(int k0, int jb, const T* __restrict__ F, int64_t ld,
                                                const int2* __restrict__ gl, int cnt, T* B,
                                                int64_t ldb, int col_begin, int ncols) {
-    __shared__ T sL[TriMax<T>::value][TriMax<T>::value + 1];
+    __shared__ __align__(16) T sL[TriMax<T>::value][TriMax<T>::value + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < jb * jb; e += blockDim.x) {
-        int r = e % jb, c = e / jb;
-        sL[r][c] = F[(k0 + r) + (int64_t)(k0 + c) * ld];
-    }
+    stage_triangle(F, ld, k0, jb, &sL[0][0], TriMax<T>::value + 1, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     const int cl = blockIdx.x * kWarpsPerCta + warp;
     if (cl >= ncols) return;
@@ -534,23 +582,22 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
     F += node * strideF;
     B += node * strideB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = warp; c < jb; c += kBlockWarps)
-        for (int r = lane; r < jb; r += 32) {
-            if (upper ? r > c : r <= c) continue;
-            T v = F[(k0 + r) + (int64_t)(k0 + c) * ld];
-            if (upper && r == c) v = crcp(v);
-            sD[r * LDS + c] = v;
-        }
-    __syncthreads();
+    stage_triangle(F, ld, k0, jb, sD, LDS, upper);
     const int cl = blockIdx.x * kBlockWarps + warp;
-    if (cl >= ncols) return;
     T* col = B + (int64_t)cl * ldb;
-    if (!upper) {
+    if (!upper && cl < ncols) {                   // while the triangle is in flight
         const int2* gl = gather + (int64_t)node * gstride + panel_index * 2 * 64;
         const int* gc = gcount + (int64_t)node * (gstride / 128) + panel_index;
         gather_rows_warp(gl, gc[0], col);
         if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (upper) {                                  // the diagonal, inverted
+        for (int r = threadIdx.x; r < jb; r += blockDim.x) sD[r * LDS + r] = crcp(sD[r * LDS + r]);
+        __syncthreads();
+    }
+    if (cl >= ncols) return;
     col += k0;
     T x[4];
 #pragma unroll
@@ -559,6 +606,7 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
         x[q] = (q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
     }
     if (!upper) {
+#pragma unroll 4
         for (int i = 0; i + 1 < jb; ++i) {
             const T own = pick_slot(x, i >> 5);
             T xi;
@@ -571,6 +619,7 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
             }
         }
     } else {
+#pragma unroll 4
         for (int i = jb - 1; i >= 0; --i) {
             const T own = pick_slot(x, i >> 5);
             T xi;
