@@ -17,19 +17,22 @@
 // A complex64 entry of a column-major A is exactly one (Re, Im) pair of a row
 // of A', and one entry of B fills one pair in each of two rows of B'.
 //
-// CTA: 128 threads and one 128 x BN complex tile of C, held in TMEM as 128
-// lanes x 2 BN FP32 columns.  K advances 8 complex (16 real) entries per stage
-// through a 2-stage shared-memory ring: the threads load a stage, split it and
-// store the four parts (A_hi, A_lo, B_hi, B_lo) in the canonical K-major
-// SWIZZLE_NONE layout (8-row x 16-byte core matrices, the four K core matrices
-// of a row group side by side: LBO 128 B, SBO 512 B); thread 0 issues six
-// MMAs (M = 128, N = 2 BN, K = 8) per stage and commits the stage to its
-// mbarrier, which frees the slot two stages later (two stages rather than
-// three: the kernel is latency-bound, and the smaller ring fits three CTAs per
-// SM instead of two).  The epilogue reads TMEM
-// with lane = row of C and updates C column by column (coalesced along rows).
+// CTA: one 128 x BN complex tile of C, held in TMEM as 128 lanes x 2 BN FP32
+// columns; 160 threads.  K advances 8 complex (16 real) entries per stage
+// through a 2-slot shared-memory ring.  Warps 0-3 load a stage into registers
+// two stages ahead, split it and store the four parts (A_hi, A_lo, B_hi, B_lo)
+// in the canonical K-major SWIZZLE_NONE layout (8-row x 16-byte core
+// matrices, the four K core matrices of a row group side by side: LBO 128 B,
+// SBO 512 B) with 16-byte stores, and count themselves on the slot's full
+// barrier; warp 4's lane 0 issues six MMAs (M = 128, N = 2 BN, K = 8) per full
+// slot and commits them to the slot's empty barrier (its other lanes prefetch
+// the C tile into L2).  No block-wide barrier inside the K loop.  The epilogue
+// reads TMEM with lane = row of C and updates C in groups of 8 columns
+// (coalesced along rows), the next group's loads in flight during the current
+// group's stores.
 #include "internal.h"
 #include "tc_common.cuh"
+
 
 namespace fnl {
 namespace {
@@ -38,7 +41,8 @@ using namespace tc;
 constexpr int kTcM = 128;                      // rows of C per CTA (TMEM lanes)
 constexpr int kTcBK = 8;                       // complex K entries per stage
 constexpr int kTcStages = 2;
-constexpr int kTcThreads = 128;
+constexpr int kTcLoaders = 128;                // loader / epilogue threads (warps 0-3)
+constexpr int kTcThreads = kTcLoaders + 32;     // + the MMA-issuing warp
 constexpr uint32_t kTcTmemCols = 128;
 constexpr int kTcAtile = kTcM * 2 * kTcBK * 4;  // bytes of one A part (8 KB)
 
@@ -68,7 +72,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // One CTA's 128 x BN tile (blockIdx.x, blockIdx.y) of C -= A B for one matrix.
+// Warps 0-3 (the loaders) load, split and store the operand stages and later
+// run the epilogue; warp 4 (one thread) issues the MMAs.  They meet only at
+// mbarriers: full[slot] counts the 128 loader threads' stores of a stage,
+// empty[slot] is the MMAs' commit of that slot, done the commit after the last
+// stage -- no block-wide barrier inside the K loop.  Each loader keeps two
+// stages in registers, so a stage's global loads are issued two stages ahead
+// of its split.
 template <int BN>
 __device__ __forceinline__ void cgemm_body(int m, int n, int k, const float2* __restrict__ A,
                                            int64_t lda, const float2* __restrict__ B, int64_t ldb,
@@ -77,18 +92,23 @@ __device__ __forceinline__ void cgemm_body(int m, int n, int k, const float2* __
     constexpr int NR = 2 * BN;                   // real columns of the tile
     constexpr int kBtile = NR * 2 * kTcBK * 4;   // bytes of one B part
     constexpr int kStage = 2 * kTcAtile + 2 * kBtile;
-    constexpr int kAIt = (kTcM / 16) * (kTcBK / 2) / 4;   // A loads per thread and stage
-    constexpr int kBIt = 2 * (BN / 8) / 4;                 // B loads per thread and stage
+    constexpr int kAP = kTcBK / 2;                         // k pairs of a stage (A items per thread)
+    constexpr int kBIt = (BN / 8 + 3) / 4;                 // B warp steps per warp and stage
     static_assert(BN % 16 == 0 && NR <= 256, "tile width");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[kTcStages];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * kTcM, col0 = blockIdx.y * BN;
+    const int nk = (k + kTcBK - 1) / kTcBK;
 
     if (tid == 0) {
-        for (int q = 0; q < kTcStages; ++q) mbar_init(smem_u32(&mbar[q]), 1);
+        for (int q = 0; q < kTcStages; ++q) {
+            mbar_init(smem_u32(&full[q]), kTcLoaders);
+            mbar_init(smem_u32(&empty[q]), 1);
+        }
+        mbar_init(smem_u32(&done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -101,148 +121,192 @@ __device__ __forceinline__ void cgemm_body(int m, int n, int k, const float2* __
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-
-    // the C tile into L2 while the K loop runs, so that the epilogue's
-    // read-modify-write hits in L2 (up to 9 lines of 128 bytes per column)
-    if (row0 < m) {
-        const int rows = min(kTcM, m - row0);
-        for (int idx = tid; idx < BN * 9; idx += kTcThreads) {
-            const int j = idx / 9, t = idx - j * 9;
-            if (col0 + j >= n) continue;
-            const char* p0 = reinterpret_cast<const char*>(C + row0 + (int64_t)(col0 + j) * ldc);
-            const uintptr_t l0 = reinterpret_cast<uintptr_t>(p0) >> 7;
-            const uintptr_t l1 = (reinterpret_cast<uintptr_t>(p0) + (uintptr_t)rows * 8 - 1) >> 7;
-            if (l0 + t <= l1)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"((l0 + t) << 7));
-        }
-    }
-
-    // A: a warp step covers 16 rows x 2 complex k; lanes 0-7 / 8-15 take the
-    // even / odd k of rows 0-7, lanes 16-31 the same for rows 8-15, so each
-    // 16-lane half stores 128 distinct bytes (no bank conflict).
-    const int a_r = (lane & 7) + 8 * (lane >> 4), a_k = (lane >> 3) & 1;
-    // B: a warp step covers 4 complex k x 8 columns (32 contiguous bytes of a
-    // column per 4 lanes); lanes 16-31 store their odd row first, so every
-    // store instruction covers the 8 row slots of a core matrix.
-    const int b_k = lane & 3, b_j = lane >> 2;
-    const bool b_sw = (lane >> 4) & 1;
-    float2 ra[kAIt], rb[kBIt];
-
-    auto load = [&](int t) {
-        const int k0 = t * kTcBK;
-#pragma unroll
-        for (int q = 0; q < kAIt; ++q) {
-            const int it = warp + 4 * q;
-            const int r = (it & 7) * 16 + a_r, kc = (it >> 3) * 2 + a_k;
-            const int gr = row0 + r, gk = k0 + kc;
-            ra[q] = (gr < m && gk < k) ? __ldg(A + gr + (int64_t)gk * lda) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < kBIt; ++q) {
-            const int it = warp + 4 * q;
-            const int kc = (it & 1) * 4 + b_k, j = (it >> 1) * 8 + b_j;
-            const int gk = k0 + kc, gc = col0 + j;
-            rb[q] = (gk < k && gc < n) ? __ldg(B + gk + (int64_t)gc * ldb) : make_float2(0.f, 0.f);
-        }
-    };
-    auto store = [&](int slot) {
-        unsigned char* ahi = smem + slot * kStage;
-        unsigned char* alo = ahi + kTcAtile;
-        unsigned char* bhi = ahi + 2 * kTcAtile;
-        unsigned char* blo = bhi + kBtile;
-#pragma unroll
-        for (int q = 0; q < kAIt; ++q) {
-            const int it = warp + 4 * q;
-            const uint32_t off = pair_off((it & 7) * 16 + a_r, (it >> 3) * 2 + a_k);
-            const float2 v = ra[q];
-            const float hr = tf32_rn(v.x), hm = tf32_rn(v.y);
-            *reinterpret_cast<float2*>(ahi + off) = make_float2(hr, hm);
-            *reinterpret_cast<float2*>(alo + off) = make_float2(tf32_rn(v.x - hr), tf32_rn(v.y - hm));
-        }
-#pragma unroll
-        for (int q = 0; q < kBIt; ++q) {
-            const int it = warp + 4 * q;
-            const int kc = (it & 1) * 4 + b_k, j = (it >> 1) * 8 + b_j;
-            const float2 v = rb[q];
-            const float hr = tf32_rn(v.x), hm = tf32_rn(v.y);
-            const float lr = tf32_rn(v.x - hr), lm = tf32_rn(v.y - hm);
-            // row 2j: (Re, -Im); row 2j + 1: (Im, Re)
-            const float2 h0 = make_float2(hr, -hm), h1 = make_float2(hm, hr);
-            const float2 l0 = make_float2(lr, -lm), l1 = make_float2(lm, lr);
-            const uint32_t o0 = pair_off(2 * j, kc), o1 = pair_off(2 * j + 1, kc);
-            const uint32_t oA = b_sw ? o1 : o0, oB = b_sw ? o0 : o1;
-            *reinterpret_cast<float2*>(bhi + oA) = b_sw ? h1 : h0;
-            *reinterpret_cast<float2*>(bhi + oB) = b_sw ? h0 : h1;
-            *reinterpret_cast<float2*>(blo + oA) = b_sw ? l1 : l0;
-            *reinterpret_cast<float2*>(blo + oB) = b_sw ? l0 : l1;
-        }
-    };
-
-    const uint32_t idesc = tf32_idesc(kTcM, NR);
-    const int nk = (k + kTcBK - 1) / kTcBK;
     bool ok = true;
-    int issued = 0;
-    load(0);
-    for (int t = 0; t < nk; ++t) {
-        const int slot = t % kTcStages;
-        if (t >= kTcStages) ok = mbar_wait(smem_u32(&mbar[slot]), ((t / kTcStages) - 1) & 1);
-        ok = __syncthreads_and(ok);                // uniform exit on a timeout
-        if (!ok) break;
-        store(slot);
-        if (t + 1 < nk) load(t + 1);              // in flight while the MMAs run
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(smem + slot * kStage);
+
+    if (warp == kTcLoaders / 32) {
+        if (lane == 0) {                             // MMA issuer
+            const uint32_t idesc = tf32_idesc(kTcM, NR);
+            int t = 0;
+            for (; t < nk; ++t) {
+                const int slot = t % kTcStages;
+                if (!mbar_wait(smem_u32(&full[slot]), (t / kTcStages) & 1)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = smem_u32(smem + slot * kStage);
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {       // two K = 8 (32-byte) steps
-                const uint64_t ah = smem_desc(base + ks * 256, 128, 512);
-                const uint64_t al = smem_desc(base + kTcAtile + ks * 256, 128, 512);
-                const uint64_t bh = smem_desc(base + 2 * kTcAtile + ks * 256, 128, 512);
-                const uint64_t bl = smem_desc(base + 2 * kTcAtile + kBtile + ks * 256, 128, 512);
-                mma_tf32(tmem, al, bh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-                mma_tf32(tmem, ah, bl, idesc, 1u);
-                mma_tf32(tmem, ah, bh, idesc, 1u);
+                for (int ks = 0; ks < 2; ++ks) {     // two K = 8 (32-byte) steps
+                    const uint64_t ah = smem_desc(base + ks * 256, 128, 512);
+                    const uint64_t al = smem_desc(base + kTcAtile + ks * 256, 128, 512);
+                    const uint64_t bh = smem_desc(base + 2 * kTcAtile + ks * 256, 128, 512);
+                    const uint64_t bl = smem_desc(base + 2 * kTcAtile + kBtile + ks * 256, 128, 512);
+                    mma_tf32(tmem, al, bh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(tmem, ah, bl, idesc, 1u);
+                    mma_tf32(tmem, ah, bh, idesc, 1u);
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&empty[slot]))
+                    : "memory");
             }
+            // all MMAs issued have completed once `done` arrives (also on the
+            // timeout path, so that TMEM is read or released only after them)
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar[slot]))
+                    smem_u32(&done))
                 : "memory");
+            if (!mbar_wait(smem_u32(&done), 0) || t < nk) ok = false;
+        } else if (row0 < m) {
+            // the other lanes: the C tile into L2 while the K loop runs (up to 9
+            // lines of 128 bytes per column)
+            const int rows = min(kTcM, m - row0);
+            for (int idx = lane - 1; idx < BN * 9; idx += 31) {
+                const int j = idx / 9, t9 = idx - j * 9;
+                if (col0 + j >= n) continue;
+                const char* p0 = reinterpret_cast<const char*>(C + row0 + (int64_t)(col0 + j) * ldc);
+                const uintptr_t l0 = reinterpret_cast<uintptr_t>(p0) >> 7;
+                const uintptr_t l1 = (reinterpret_cast<uintptr_t>(p0) + (uintptr_t)rows * 8 - 1) >> 7;
+                if (l0 + t9 <= l1) asm volatile("prefetch.global.L2 [%0];" ::"l"((l0 + t9) << 7));
+            }
         }
-        ++issued;
+    } else {
+        // Every smem store writes one 16-byte row chunk of a core matrix: two
+        // complex k (a k pair) of one row of A' or B'.
+        // A: warp w takes rows 32 w + lane and, per item, the k pair p; the 8
+        // lanes of a store phase hold 8 consecutive rows of one core matrix
+        // (distinct 16-byte bank groups), and each load reads 32 consecutive rows.
+        // B: a warp step covers 16 columns x 2 k pairs: lane = 8 jg + 4 psel + jo
+        // takes column 4 jg + jo of its 16 and pair psel; it writes rows 2j and
+        // 2j + 1 of B', the psel = 1 lanes the odd row first, so that each store
+        // phase covers the 8 row slots of a core matrix.
+        const int b_jo = lane & 3, b_ps = (lane >> 2) & 1, b_jg = lane >> 3;
+        const int gr = row0 + warp * 32 + lane;
+        // a k pair of B is 16-byte aligned when B is and its columns are an even number of entries apart
+        const bool b_pair = ((reinterpret_cast<uintptr_t>(B) & 15) == 0) && ((ldb & 1) == 0);
+        float2 ra0[2 * kAP], rb0[2 * kBIt], ra1[2 * kAP], rb1[2 * kBIt];
+
+        auto load = [&](int t, float2* ra, float2* rb) {
+            const int k0 = t * kTcBK;
+#pragma unroll
+            for (int p = 0; p < kAP; ++p) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int gk = k0 + 2 * p + h;
+                    ra[2 * p + h] = (gr < m && gk < k) ? __ldg(A + gr + (int64_t)gk * lda)
+                                                       : make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kBIt; ++q) {
+                const int it = warp + 4 * q;           // warp step: column chunk it >> 1, pairs 2 (it & 1)
+                const int j = (it >> 1) * 16 + 4 * b_jg + b_jo, pp = (it & 1) * 2 + b_ps;
+                const int gc = col0 + j, gk = k0 + 2 * pp;
+                const float2* bp = B + gk + (int64_t)gc * ldb;
+                if (b_pair && it < BN / 8 && gk + 1 < k && gc < n) {   // the k pair in one 16-byte load
+                    const float4 w = __ldg(reinterpret_cast<const float4*>(bp));
+                    rb[2 * q] = make_float2(w.x, w.y);
+                    rb[2 * q + 1] = make_float2(w.z, w.w);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        rb[2 * q + h] = (it < BN / 8 && gk + h < k && gc < n) ? __ldg(bp + h)
+                                                                              : make_float2(0.f, 0.f);
+                }
+            }
+        };
+        auto store = [&](int slot, const float2* ra, const float2* rb) {
+            unsigned char* ahi = smem + slot * kStage;
+            unsigned char* alo = ahi + kTcAtile;
+            unsigned char* bhi = ahi + 2 * kTcAtile;
+            unsigned char* blo = bhi + kBtile;
+            const int r = warp * 32 + lane;
+#pragma unroll
+            for (int p = 0; p < kAP; ++p) {
+                const uint32_t off = pair_off(r, 2 * p);
+                const float2 v0 = ra[2 * p], v1 = ra[2 * p + 1];
+                const float h0 = tf32_rn(v0.x), h1 = tf32_rn(v0.y), h2 = tf32_rn(v1.x), h3 = tf32_rn(v1.y);
+                *reinterpret_cast<float4*>(ahi + off) = make_float4(h0, h1, h2, h3);
+                *reinterpret_cast<float4*>(alo + off) =
+                    make_float4(tf32_rn(v0.x - h0), tf32_rn(v0.y - h1), tf32_rn(v1.x - h2), tf32_rn(v1.y - h3));
+            }
+#pragma unroll
+            for (int q = 0; q < kBIt; ++q) {
+                const int it = warp + 4 * q;
+                if (it >= BN / 8) break;
+                const int j = (it >> 1) * 16 + 4 * b_jg + b_jo, pp = (it & 1) * 2 + b_ps;
+                const float2 v0 = rb[2 * q], v1 = rb[2 * q + 1];
+                const float r0 = tf32_rn(v0.x), i0 = tf32_rn(v0.y), r1 = tf32_rn(v1.x), i1 = tf32_rn(v1.y);
+                const float lr0 = tf32_rn(v0.x - r0), li0 = tf32_rn(v0.y - i0);
+                const float lr1 = tf32_rn(v1.x - r1), li1 = tf32_rn(v1.y - i1);
+                // row 2j: (Re, -Im) per k; row 2j + 1: (Im, Re)
+                const float4 he = make_float4(r0, -i0, r1, -i1), ho = make_float4(i0, r0, i1, r1);
+                const float4 le = make_float4(lr0, -li0, lr1, -li1), lo = make_float4(li0, lr0, li1, lr1);
+                const uint32_t oe = pair_off(2 * j, 2 * pp), oo = pair_off(2 * j + 1, 2 * pp);
+                const uint32_t o1 = b_ps ? oo : oe, o2 = b_ps ? oe : oo;
+                *reinterpret_cast<float4*>(bhi + o1) = b_ps ? ho : he;
+                *reinterpret_cast<float4*>(bhi + o2) = b_ps ? he : ho;
+                *reinterpret_cast<float4*>(blo + o1) = b_ps ? lo : le;
+                *reinterpret_cast<float4*>(blo + o2) = b_ps ? le : lo;
+            }
+        };
+        // stage t: wait until its slot's previous MMAs are done, split the
+        // registers into it, count this thread on full[slot], then load stage t + 2
+        auto step = [&](int t, float2* ra, float2* rb) {
+            const int slot = t % kTcStages;
+            bool w = true;
+            if (t >= kTcStages) w = mbar_wait(smem_u32(&empty[slot]), ((t / kTcStages) - 1) & 1);
+            if (!__all_sync(0xffffffffu, w)) return false;   // warp-uniform exit on a timeout
+            store(slot, ra, rb);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&full[slot]));
+            if (t + 2 < nk) load(t + 2, ra, rb);
+            return true;
+        };
+        load(0, ra0, rb0);
+        if (nk > 1) load(1, ra1, rb1);
+        for (int t = 0; t < nk; t += 2) {            // two register sets, used in turn
+            if (!step(t, ra0, rb0)) { ok = false; break; }
+            if (t + 1 < nk && !step(t + 1, ra1, rb1)) { ok = false; break; }
+        }
+        // the accumulator is complete once `done` has arrived
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&done), 0))) ok = false;
     }
-    // all MMAs complete once the last committed stage has arrived (also on the
-    // timeout path, so that TMEM is released only after its writers finished)
-    bool done = true;
-    if (issued > 0)
-        done = mbar_wait(smem_u32(&mbar[(issued - 1) % kTcStages]), ((issued - 1) / kTcStages) & 1);
-    ok = __syncthreads_and(ok && done);
+    ok = __syncthreads_and(ok);
     if (!ok && tid == 0) atomicOr(err, 16);
-    if (ok && issued > 0) {
+    if (ok && warp < kTcLoaders / 32) {
+        // epilogue: C -= accumulator, 8 complex columns per group; the next
+        // group's C loads are issued before this group's stores
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = row0 + warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const bool live = row < m;
+        constexpr int kGroups = NR / 16;
+        float2 cv[8], cn[8];
+        auto cload = [&](int g, float2* dst) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = col0 + g * 8 + jj;
+                if (live && j < n) dst[jj] = C[row + (int64_t)j * ldc];
+            }
+        };
+        cload(0, cv);
 #pragma unroll 1
-        for (int g = 0; g < NR / 32; ++g) {        // 16 complex columns per group
-            uint32_t v[32];
+        for (int g = 0; g < kGroups; g += 2) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) tmem_ld8(taddr + (uint32_t)(g * 32 + c * 8), v + c * 8);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < m) {
-                float2 cv[16];
+            for (int h = 0; h < 2; ++h) {            // groups g (cv) and g + 1 (cn)
+                const int gg = g + h;
+                if (gg >= kGroups) break;
+                float2* cur = h ? cn : cv;
+                float2* nxt = h ? cv : cn;
+                if (gg + 1 < kGroups) cload(gg + 1, nxt);
+                uint32_t v[16];
+                tmem_ld8(taddr + (uint32_t)(gg * 16), v);
+                tmem_ld8(taddr + (uint32_t)(gg * 16 + 8), v + 8);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = col0 + g * 16 + jj;
-                    if (j < n) cv[jj] = C[row + (int64_t)j * ldc];
-                }
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = col0 + g * 16 + jj;
-                    if (j < n)
-                        C[row + (int64_t)j * ldc] =
-                            make_float2(cv[jj].x - __uint_as_float(v[2 * jj]),
-                                        cv[jj].y - __uint_as_float(v[2 * jj + 1]));
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = col0 + gg * 8 + jj;
+                    if (live && j < n)
+                        C[row + (int64_t)j * ldc] = make_float2(cur[jj].x - __uint_as_float(v[2 * jj]),
+                                                                cur[jj].y - __uint_as_float(v[2 * jj + 1]));
                 }
             }
         }
