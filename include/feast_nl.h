@@ -323,6 +323,15 @@ enum feast_nl_phase {
  * on the handle's stream. */
 int feast_nl_set_profiling(feast_nl_handle* h, int32_t on);
 
+/* Iteration graph of feast_nl_solve (on by default): from the second
+ * iteration on, Steps 4, 5 and 1-3 of Algorithm 1 (node solves, accumulation,
+ * orthonormalisation, A_t Q, Rayleigh-Ritz, residual test) are captured once
+ * per solve as one CUDA graph and replayed; the host reads only the residual
+ * summary between replays.  Results are bit-identical with and without the
+ * graph.  Per-phase profiling (feast_nl_set_profiling) and the trace output
+ * run the iteration eagerly.  on: nonzero = use the graph. */
+int feast_nl_set_iteration_graph(feast_nl_handle* h, int32_t on);
+
 /* Totals since the last feast_nl_set_profiling: device milliseconds and kernel
  * launches per phase (arrays of nphases entries, host memory, may be NULL). */
 int feast_nl_get_profile(feast_nl_handle* h, int32_t nphases, double* ms, int64_t* launches);

@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": FEAST_NL_FP64, "fp32": FEAST_NL_FP32, "fp32_i8": FEAST_NL_
 EXPORTS = ["feast_nl_create", "feast_nl_set_contour", "feast_nl_solve", "feast_nl_get_eigpairs",
            "feast_nl_get_nodes", "feast_nl_node_solve", "feast_nl_filter_apply",
            "feast_nl_project", "feast_nl_destroy", "feast_nl_strerror", "feast_nl_last_error",
-           "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_launch_count",
+           "feast_nl_set_profiling", "feast_nl_get_profile", "feast_nl_set_iteration_graph", "feast_nl_launch_count",
            "feast_nl_gram_noalloc", "feast_nl_request_footprint", "feast_nl_server_create",
            "feast_nl_server_submit", "feast_nl_server_poll", "feast_nl_server_wait",
            "feast_nl_server_fetch", "feast_nl_server_stats", "feast_nl_server_destroy",
@@ -100,6 +100,7 @@ def load_library(path=LIB_PATH):
     lib.feast_nl_last_error.argtypes = []
     lib.feast_nl_last_error.restype = ctypes.c_char_p
     lib.feast_nl_set_profiling.argtypes = [P, I32]
+    lib.feast_nl_set_iteration_graph.argtypes = [P, I32]
     lib.feast_nl_get_profile.argtypes = [P, I32, P, P]
     lib.feast_nl_launch_count.argtypes = []
     lib.feast_nl_launch_count.restype = ctypes.c_int64
@@ -250,6 +251,11 @@ class FeastNL:
 
     def set_profiling(self, on=True):
         _check(self.lib.feast_nl_set_profiling(self.h, int(bool(on))), "feast_nl_set_profiling")
+
+    def set_iteration_graph(self, on=True):
+        """Replay Steps 4, 5, 1-3 as one captured CUDA graph from the second iteration on."""
+        _check(self.lib.feast_nl_set_iteration_graph(self.h, int(bool(on))),
+               "feast_nl_set_iteration_graph")
 
     def get_profile(self):
         """{phase: (device ms, launches)} accumulated since set_profiling."""

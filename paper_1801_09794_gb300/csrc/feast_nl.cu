@@ -242,6 +242,7 @@ struct feast_nl_handle {
     // optional per-phase device timing
     struct Mark { int phase; cudaEvent_t a, b; uint64_t l0, l1; };
     bool prof = false;
+    bool iter_graph = true;         // feast_nl_set_iteration_graph
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
@@ -914,6 +915,12 @@ int feast_nl_selftest_bounded_wait(int64_t cycles, int32_t* flags_out) {
     return rc;
 }
 
+int feast_nl_set_iteration_graph(feast_nl_handle* h, int32_t on) {
+    CKS(validate_handle(h));
+    h->iter_graph = on != 0;
+    return FEAST_NL_OK;
+}
+
 int feast_nl_set_profiling(feast_nl_handle* h, int32_t on) {
     CKS(validate_handle(h));
     h->prof = on != 0;
@@ -1238,12 +1245,58 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
     int it = 0;
     bool converged = false;
     IterStatus stt{};
-    for (it = 1; it <= maxit; ++it) {
+    // Steps 4, 5 and 1-3 of the next iteration, as launched eagerly
+    auto filter_then_ritz = [&]() -> int {
+        CKS(filter_solve(h, h->ns, h->wk, 1, m, h->st, &D.status->flags, true));   // Step 4
+        CKS(filter_accumulate(h, D));
+        CKS(orthonormalize(h, D));                              // Step 5
         {
             Phase ph(h, FEAST_NL_PH_APPLY);
             CKS(apply_terms(h, h->wk, 1, m, D.Q, D.W, h->st, &D.status->flags));
         }
-        CKS(ritz_and_residual(h, D, tol));                      // Steps 1-3
+        return ritz_and_residual(h, D, tol);                    // Steps 1-3
+    };
+    // ... or as one captured graph, replayed (not with per-phase events or the trace)
+    const bool use_graph = h->iter_graph && !h->prof && !trace_enabled();
+    cudaGraphExec_t exec = nullptr;
+    int64_t per_iter = 0;
+    struct ExecGuard {
+        cudaGraphExec_t* e;
+        ~ExecGuard() { if (*e) cudaGraphExecDestroy(*e); }
+    } exec_guard{&exec};
+    auto capture = [&]() -> int {
+        if (h->precision != FEAST_NL_FP64)      // tune the node solves before the capture
+            lu_solve_pick_bn(h->st, h->n, lu_block_size<float2>(), static_cast<const float2*>(h->ns.dF),
+                             h->n * h->n, h->ns.dGather, h->ns.dGcount, h->ns.nc,
+                             static_cast<float2*>(h->wk.Y), h->n * m, m, &D.status->flags);
+        cudaGraph_t graph = nullptr;
+        const uint64_t l0 = launch_count();
+        CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+        const int rc2 = filter_then_ritz();
+        const cudaError_t ec = cudaStreamEndCapture(h->st, &graph);
+        if (rc2 != FEAST_NL_OK) { if (graph) cudaGraphDestroy(graph); return rc2; }
+        CK(ec);
+        per_iter = (int64_t)(launch_count() - l0);
+        note_launch(-(int)per_iter);          // captured, not launched: counted at each replay
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+        return FEAST_NL_OK;
+    };
+    for (it = 1; it <= maxit; ++it) {
+        if (it == 1) {
+            {
+                Phase ph(h, FEAST_NL_PH_APPLY);
+                CKS(apply_terms(h, h->wk, 1, m, D.Q, D.W, h->st, &D.status->flags));
+            }
+            CKS(ritz_and_residual(h, D, tol));                  // Steps 1-3
+        } else if (use_graph) {
+            if (!exec) CKS(capture());
+            CK(cudaGraphLaunch(exec, h->st));
+            note_launch((int)per_iter);       // the graph's kernels count as this library's launches
+        } else {
+            CKS(filter_then_ritz());
+        }
         CK(cudaMemcpyAsync(h->hStatus.get(), D.status, sizeof(IterStatus), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
         stt = *h->hStatus;
@@ -1263,9 +1316,6 @@ int feast_nl_solve(feast_nl_handle* h, int32_t m0, double tol, int32_t maxit, ui
         if (stt.flags & (16 | 2)) break;
         if (it > 1 && stt.n_conv == stt.n_inside) { converged = true; break; }
         if (it == maxit) break;
-        CKS(filter_solve(h, h->ns, h->wk, 1, m, h->st, &D.status->flags, true));   // Step 4
-        CKS(filter_accumulate(h, D));
-        CKS(orthonormalize(h, D));                              // Step 5
     }
     CK(cudaEventRecord(h->ev1, h->st));
     CK(cudaEventSynchronize(h->ev1));

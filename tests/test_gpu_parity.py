@@ -192,6 +192,30 @@ def test_solve_plain_qep_matches_oracle(lib, prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
+def test_iteration_graph_equals_eager(lib, prec):
+    # the captured iteration replays exactly the launches of the eager loop
+    with open(os.path.join(GOLD, "contours.json")) as f:
+        w = json.load(f)["qep_plain_n256"]
+    p = config1_qep(256, 0)
+    c = complex(*w["center"])
+    X0 = start_block(256, 24, 0)
+    out = []
+    for graph in (False, True, False):        # the first run fills the solve autotuner's cache
+        s = lib.FeastNL(p, prec)
+        s.set_iteration_graph(graph)
+        s.set_contour(c, w["ra"], w["rb"], 8, "gl")
+        l0 = lib.launch_count()
+        st, info = s.solve(24, tol=1e-10, maxit=60, X0=X0)
+        launches = lib.launch_count() - l0
+        lam, X, rr = s.get_eigpairs(inside_only=True)
+        out.append((info.iters, launches, lam, X, rr))
+        s.close()
+    (i1, n1, l1, x1, r1), (i2, n2, l2, x2, r2) = out[1:]
+    assert i1 == i2 and i1 > 2 and n1 == n2
+    assert np.array_equal(l1, l2) and np.array_equal(x1, x2) and np.array_equal(r1, r2)
+
+
 @pytest.mark.parametrize("k,prec", [(3, "fp64"), (3, "fp32"), (1, "fp32"), (3, "fp32_i8")])
 def test_solve_random_pep_matches_bruteforce(lib, k, prec):
     n = 130 if k > 1 else 150
