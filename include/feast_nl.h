@@ -53,9 +53,16 @@ extern "C" {
 /* ---- enums --------------------------------------------------------------- */
 enum feast_nl_fkind { FEAST_NL_POW = 0, FEAST_NL_EXP = 1 };
 
-/* Arithmetic of the node factorisations and solves (Step 4).  The block residual
- * T(X, Lambda), the projections Q^H A_t Q, the reduced problem and the
- * orthonormalisation are FP64-accurate in every mode.
+/* Arithmetic of the node factorisations and solves (Step 4).  In every mode the
+ * block residual T(X, Lambda) and the projections Q^H A_t Q are FP64-accurate,
+ * and so are the kept Ritz pairs: the reduced problem's eigenvalues are located
+ * in FP32 (Hessenberg reduction and QR of the companion matrix), then every kept
+ * pair is refined by Newton's method with FP64 residuals until it is an
+ * eigenpair of the FP64 projected problem (with an FP64 factor, or the whole
+ * stage in FP64, when the FP32 start does not converge).  The
+ * orthonormalisation (Steps 0, 5) is two Cholesky-QR passes with the Gram
+ * matrix and its Cholesky factor in FP32 and Q R^{-1} formed FP64-accurately:
+ * Step 1 depends only on span(Q), which this keeps to FP64 rounding.
  *   FEAST_NL_FP64  : LU and solves in FP64.
  *   FEAST_NL_FP32  : LU and solves in FP32 (complex64).  The filter is a
  *                    residual inverse iteration (Sec. 4.2), so solve errors scale
@@ -146,7 +153,10 @@ int feast_nl_set_contour(feast_nl_handle* h, double c_re, double c_im, double ra
  * (e.g. the delay problem T = -lambda I + A0 + A1 e^{-tau lambda}), the paper
  * names no reduced solver: the projected problem is solved by the first two
  * contour moments of its inverse (Beyn's method) on the contour scaled by 1.5
- * (256 trapezoid nodes, FP64), then Newton per pair; slots the moments leave
+ * (256 trapezoid nodes; FP32 node LUs, moments summed in FP64 in a fixed order,
+ * FP32 SVD with the rank cut at 1e-5 sigma_1, above FP32 noise), then Newton per
+ * pair with FP64 residuals (FP64 factor when the FP32 one does not converge),
+ * which makes each kept pair FP64-accurate; slots the moments leave
  * empty hold lambda = c + 1.5 ra (outside C) and are never tested.  There
  * m0 <= 64.
  * Returns OK, ENOT_CONVERGED, ETOO_MANY, ESINGULAR_NODE, EINVAL, ENOMEM,
