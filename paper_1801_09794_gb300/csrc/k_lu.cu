@@ -35,7 +35,11 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <climits>
+#include <cstdlib>
+
+#include <cooperative_groups.h>
 
 namespace fnl {
 namespace {
@@ -337,6 +341,305 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_grouped_kernel(
     else
         panel_reg_body<T, 4>(d.n, k0, jb, F, d.n, d.piv, d.info, d.gather + panel_index * 2 * 64,
                              d.gcount + panel_index);
+}
+
+// ---------------------------------------------------------------------------
+// Panel factorisation spread over a thread-block cluster (complex64).
+// ---------------------------------------------------------------------------
+// The CL CTAs of one cluster share one node's panel: thread g = rank * NT + tid
+// of the cluster owns rows k0 + g + i * CL * NT (i < ROWS), so every row has
+// one owner thread and one owner CTA.  Per column, each CTA reduces its own
+// rows to one pivot candidate and stores it -- value, row and the row's four
+// mini-panel entries -- into a slot of every CTA's shared memory
+// (distributed shared memory), the owner of the diagonal row stores that row
+// too, and one cluster barrier later every CTA picks the same pivot and holds
+// both rows it needs for the interchange and the rank-1 update.  The slots
+// alternate between two buffers by column parity, so a CTA that runs ahead
+// into the next column cannot overwrite a slot another CTA is still reading
+// (it has to pass that CTA at the barrier first).  The pivot row as chosen at
+// column c is the final row c of the mini-panel (later steps only touch rows
+// below it), so the L11 block needs no exchange of its own.
+// A mini-panel's interchanges on the other panel columns take one more
+// cluster barrier (every read before any write, as in the one-CTA panel);
+// each moved row is written by its owner CTA, so every later access to a row
+// in global memory is made by the CTA that wrote it or after a barrier.
+// Per element the operations and their order are those of the one-CTA panel
+// (same pivot rule: first row of maximal cabs1; same scaling and rank-1 and
+// rank-w updates), so the factors are the same bits whatever CL and ROWS are.
+namespace cg = cooperative_groups;
+constexpr int kClusterMax = 8;       // portable cluster size
+constexpr int kClusterThreads = 512;
+
+template <typename T>
+struct PanelCand {
+    typename cplx_real<T>::type v;   // cabs1 of the candidate (-1: none)
+    int i;                           // its row (INT_MAX: none)
+    T row[kMini];                    // its mini-panel entries
+};
+
+template <typename T, int ROWS>
+__device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T* A, int64_t ld,
+                                                   int* ip, int* info1, int2* gl, int* gc) {
+    typedef typename cplx_real<T>::type R;
+    constexpr int NT = kClusterThreads, NW = NT / 32;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int G = CL * NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = rank * NT + tid;
+    __shared__ PanelCand<T> s_cand[2][kClusterMax];
+    __shared__ T s_crow[2][kMini];
+    __shared__ PanelCand<T> s_wc[NW];
+    __shared__ T s_L11[kMini][kMini];
+    __shared__ T s_U[kMini][64];
+    __shared__ T s_gval[2 * kMini][64];
+    __shared__ int s_piv[kMini];
+    __shared__ int2 s_gl[2 * kMini];
+    __shared__ int s_gc;
+    const int pend = k0 + jb;
+    constexpr int kUpd = ROWS == 1 ? 8 : 4;
+    T v[ROWS][kMini];
+
+    for (int mb0 = k0; mb0 < pend; mb0 += kMini) {
+        const int w = min(kMini, pend - mb0);
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int64_t r = k0 + g + (int64_t)i * G;
+#pragma unroll
+            for (int c = 0; c < kMini; ++c)
+                v[i][c] = (r < n && c < w) ? A[r + (int64_t)(mb0 + c) * ld] : cmake<T>(0.0, 0.0);
+        }
+        for (int c = 0; c < w; ++c) {
+            const int col = mb0 + c, par = col & 1;
+            // this thread's candidate among its rows >= col
+            R best = (R)-1;
+            int bi = INT_MAX, bslot = 0;
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int64_t r = k0 + g + (int64_t)i * G;
+                T x = v[i][0];
+#pragma unroll
+                for (int cc = 1; cc < kMini; ++cc) if (cc == c) x = v[i][cc];
+                if (r >= col && r < n) {
+                    R a = cabs1(x);
+                    if (a > best) { best = a; bi = (int)r; bslot = i; }
+                }
+            }
+            R wb = best;
+            int wi = bi;
+            argmax_warp(wb, wi);
+            wi = __shfl_sync(0xffffffffu, wi, 0);
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (wi != INT_MAX && bi == wi) {          // this lane holds the warp's candidate row
+                PanelCand<T>& e = s_wc[warp];
+                e.v = wb;
+                e.i = wi;
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i)
+                    if (i == bslot)
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) e.row[cc] = v[i][cc];
+            }
+            if (lane == 0 && wi == INT_MAX) { s_wc[warp].v = (R)-1; s_wc[warp].i = INT_MAX; }
+            // the diagonal row, for the interchange
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                if (k0 + g + (int64_t)i * G == col) {
+                    for (int d = 0; d < CL; ++d) {
+                        T* dst = cl.map_shared_rank(&s_crow[par][0], d);
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) dst[cc] = v[i][cc];
+                    }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const R cv = lane < NW ? s_wc[lane].v : (R)-1;
+                const int ci = lane < NW ? s_wc[lane].i : INT_MAX;
+                R rv = cv;
+                int ri = ci;
+                argmax_warp(rv, ri);
+                ri = __shfl_sync(0xffffffffu, ri, 0);
+                const unsigned m = __ballot_sync(0xffffffffu, lane < NW && ci == ri);
+                const int src = m ? __ffs(m) - 1 : 0;
+                if (lane < CL) {
+                    PanelCand<T>* dst = cl.map_shared_rank(&s_cand[par][rank], lane);
+                    *dst = s_wc[src];
+                }
+            }
+            cl.sync();
+            // every thread combines the CL candidates the same way
+            R pb = (R)-1;
+            int p = INT_MAX, wd = -1;
+            for (int d = 0; d < CL; ++d) {
+                const R vd = s_cand[par][d].v;
+                const int id = s_cand[par][d].i;
+                if (vd > pb || (vd == pb && id < p)) { pb = vd; p = id; wd = d; }
+            }
+            const bool found = !(p == INT_MAX || p < col || p >= n);
+            if (!found) p = col;
+            T prow[kMini];
+#pragma unroll
+            for (int cc = 0; cc < kMini; ++cc)
+                prow[cc] = found ? s_cand[par][wd].row[cc] : s_crow[par][cc];
+            if (tid == 0) {
+                s_piv[c] = p;
+#pragma unroll
+                for (int cc = 0; cc < kMini; ++cc) s_L11[c][cc] = prow[cc];
+                if (rank == 0) {
+                    if (!(pb > (R)0) && *info1 == 0) *info1 = col + 1;
+                    ip[col] = p;
+                }
+            }
+            if (p != col) {
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int64_t r = k0 + g + (int64_t)i * G;
+                    if (r == col) {
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) v[i][cc] = prow[cc];
+                    } else if (r == p) {
+#pragma unroll
+                        for (int cc = 0; cc < kMini; ++cc) v[i][cc] = s_crow[par][cc];
+                    }
+                }
+            }
+            T piv_v = prow[0];
+#pragma unroll
+            for (int cc = 1; cc < kMini; ++cc) if (cc == c) piv_v = prow[cc];
+            const T inv = crcp(piv_v);
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int64_t r = k0 + g + (int64_t)i * G;
+                if (r > col && r < n) {
+                    T l = cmake<T>(0.0, 0.0);
+#pragma unroll
+                    for (int cc = 0; cc < kMini; ++cc) if (cc == c) { l = v[i][cc] * inv; v[i][cc] = l; }
+#pragma unroll
+                    for (int cc = 0; cc < kMini; ++cc)
+                        if (cc > c && cc < w) v[i][cc] = cfms(l, prow[cc], v[i][cc]);
+                }
+            }
+        }
+        // the factored mini-panel back to memory (own rows)
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int64_t r = k0 + g + (int64_t)i * G;
+            if (r < n)
+#pragma unroll
+                for (int c = 0; c < kMini; ++c)
+                    if (c < w) A[r + (int64_t)(mb0 + c) * ld] = v[i][c];
+        }
+        const int rest0 = mb0 + w, nrest = pend - rest0;
+        if (tid == 0) gather_list<2 * kMini>(mb0, w, s_piv, s_gl, &s_gc);
+        __syncthreads();
+        const int gcnt = s_gc;
+        // reads: (a) the mini-panel rows of the remaining columns after the
+        // interchanges (every CTA, for its own copy of U12); (b) the moved
+        // entries of the other panel columns whose destination row this CTA owns
+        for (int it = tid; it < w * nrest; it += NT) {
+            const int j = it / nrest, cr = it - j * nrest;
+            int src = mb0 + j;
+            for (int e = 0; e < gcnt; ++e)
+                if (s_gl[e].x == mb0 + j) src = s_gl[e].y;
+            s_U[j][cr] = __ldcg(A + src + (int64_t)(rest0 + cr) * ld);
+        }
+        for (int it = tid; it < gcnt * jb; it += NT) {
+            const int e = it / jb, cj = it - e * jb, cidx = k0 + cj;
+            const int dst = s_gl[e].x;
+            const bool left = cidx < mb0, rest = cidx >= rest0;
+            if ((left || (rest && dst >= mb0 + w)) &&
+                (int)(((int64_t)(dst - k0) % G) / NT) == rank)
+                s_gval[e][cj] = __ldcg(A + s_gl[e].y + (int64_t)cidx * ld);
+        }
+        cl.sync();                                  // every read before any write
+        for (int it = tid; it < gcnt * jb; it += NT) {
+            const int e = it / jb, cj = it - e * jb, cidx = k0 + cj;
+            const int dst = s_gl[e].x;
+            const bool left = cidx < mb0, rest = cidx >= rest0;
+            if ((left || (rest && dst >= mb0 + w)) &&
+                (int)(((int64_t)(dst - k0) % G) / NT) == rank)
+                A[dst + (int64_t)cidx * ld] = s_gval[e][cj];
+        }
+        __syncthreads();
+        if (nrest > 0) {
+            // U12 = L11^{-1} A12 on the remaining panel columns (every CTA)
+            if (tid < nrest) {
+                T u[kMini];
+#pragma unroll
+                for (int c = 0; c < kMini; ++c) u[c] = (c < w) ? s_U[c][tid] : cmake<T>(0.0, 0.0);
+#pragma unroll
+                for (int c = 0; c < kMini; ++c)
+#pragma unroll
+                    for (int r2 = c + 1; r2 < kMini; ++r2)
+                        if (r2 < w) u[r2] = cfms(s_L11[r2][c], u[c], u[r2]);
+#pragma unroll
+                for (int c = 0; c < kMini; ++c) s_U[c][tid] = u[c];
+            }
+            __syncthreads();
+            // the U12 rows go to memory from the CTA that owns them
+            for (int it = tid; it < w * nrest; it += NT) {
+                const int j = it / nrest, cr = it - j * nrest;
+                if ((int)(((int64_t)(mb0 + j - k0) % G) / NT) == rank)
+                    A[mb0 + j + (int64_t)(rest0 + cr) * ld] = s_U[j][cr];
+            }
+            // rank-w update of the own rows below the mini-panel
+            for (int j0 = 0; j0 < nrest; j0 += kUpd) {
+                T a[ROWS][kUpd];
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int64_t r = k0 + g + (int64_t)i * G;
+                    const T* ar = A + r + (int64_t)(rest0 + j0) * ld;
+#pragma unroll
+                    for (int q = 0; q < kUpd; ++q)
+                        a[i][q] = (r >= rest0 && r < n && j0 + q < nrest) ? ar[(int64_t)q * ld]
+                                                                           : cmake<T>(0.0, 0.0);
+                }
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int64_t r = k0 + g + (int64_t)i * G;
+                    if (r >= rest0 && r < n) {
+                        T* ar = A + r + (int64_t)(rest0 + j0) * ld;
+#pragma unroll
+                        for (int q = 0; q < kUpd; ++q) {
+                            if (j0 + q < nrest) {
+#pragma unroll
+                                for (int c = 0; c < kMini; ++c)
+                                    if (c < w) a[i][q] = cfms(v[i][c], s_U[c][j0 + q], a[i][q]);
+                                ar[(int64_t)q * ld] = a[i][q];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (rank == 0 && tid == 0 && gl != nullptr) gather_list<128>(k0, jb, ip + k0, gl, gc);
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kClusterThreads, 1) lu_panel_cluster_kernel(
+    int64_t n, int k0, int jb, float2* F, int64_t ld, int64_t strideF, int* piv, int* info,
+    int2* gather, int* gcount, int panel_index, int gstride) {
+    const int node = blockIdx.y;
+    panel_cluster_body<float2, ROWS>(
+        n, k0, jb, F + node * strideF, ld, piv + (int64_t)node * n, info + node,
+        gather ? gather + (int64_t)node * gstride + panel_index * 2 * 64 : nullptr,
+        gcount + (int64_t)node * (gstride / 128) + panel_index);
+}
+
+// Nodes of different orders: cluster blockIdx.y is node blockIdx.y; a node
+// whose order ends before this panel returns (the whole cluster at once).
+template <int ROWS>
+__global__ void __launch_bounds__(kClusterThreads, 1) lu_panel_cluster_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int panel_index) {
+    const LuNode d = nodes[blockIdx.y];
+    if (k0 >= d.n) return;
+    const int jb = (int)min((int64_t)nb, d.n - k0);
+    panel_cluster_body<float2, ROWS>(d.n, k0, jb, static_cast<float2*>(d.F), d.n, d.piv, d.info,
+                                     d.gather + panel_index * 2 * 64, d.gcount + panel_index);
 }
 
 // Column-at-a-time panel in global memory (any n; used above 8192 rows).
@@ -651,12 +954,62 @@ constexpr size_t solve_block_smem() {
     return (size_t)SolveBlock<T>::value * (SolveBlock<T>::value + 1) * sizeof(T);
 }
 
+// Cluster shape of a complex64 panel of `rows` rows: CL CTAs of 512 threads,
+// ROWS rows per thread.  Taller panels spread over more CTAs, one per
+// FEAST_NL_PANEL_ROWS_PER_CTA rows (default 1024, measured best of 300, 512
+// and 1024 on the n = 4096 QEP: node LU 50.2, 47.0 and 46.3 ms against 54.3
+// with every panel on one CTA; 0 keeps every panel on one CTA); false when
+// one CTA takes the panel.  The factors do not depend on it.
+constexpr int64_t kPanelRowsPerCta = 1024;
+bool panel_cluster_shape(int64_t rows, int* cl, int* rows_per_thread) {
+    const char* e = getenv("FEAST_NL_PANEL_ROWS_PER_CTA");
+    const int64_t rpc = e ? atoll(e) : kPanelRowsPerCta;
+    if (rpc <= 0 || rows <= rpc || rows > 2 * kClusterMax * kClusterThreads) return false;
+    int c = (int)std::min<int64_t>(kClusterMax, (rows + rpc - 1) / rpc);
+    int r = (int)((rows + (int64_t)c * kClusterThreads - 1) / ((int64_t)c * kClusterThreads));
+    if (r > 2) { c = kClusterMax; r = 2; }
+    *cl = c;
+    *rows_per_thread = r;
+    return true;
+}
+
+// launch with a cluster of cl CTAs along x (one cluster per node row of the grid)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_clustered(void (*kernel)(KArgs...), int cl, int ny, cudaStream_t st,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl, (unsigned)ny, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T>
 cudaError_t launch_panel(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_t strideF,
                          int* piv, int nc, int* info, int2* gather, int* gcount, int panel,
                          int gstride) {
     const int64_t rows = n - k0;
     note_launch();
+    if constexpr (sizeof(T) == 8) {
+        int cl = 0, rt = 0;
+        if (panel_cluster_shape(rows, &cl, &rt)) {
+            float2* F32 = reinterpret_cast<float2*>(F);
+            const int64_t ld = n;
+            if (rt == 1)
+                return launch_clustered(lu_panel_cluster_kernel<1>, cl, nc, st, n, k0, jb, F32, ld,
+                                        strideF, piv, info, gather, gcount, panel, gstride);
+            return launch_clustered(lu_panel_cluster_kernel<2>, cl, nc, st, n, k0, jb, F32, ld,
+                                    strideF, piv, info, gather, gcount, panel, gstride);
+        }
+    }
     if (rows <= kPanelThreads)
         lu_panel_reg_kernel<T, 1><<<nc, kPanelThreads, 0, st>>>(n, k0, jb, F, n, strideF, piv, info,
                                                                 gather, gcount, panel, gstride);
@@ -864,8 +1217,13 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
             if (lookahead_cols(n_host[i], k0, nb, 1, &jb, &c0, &nn)) cols_rest = std::max<int64_t>(cols_rest, nn);
         }
         note_launch();
-        lu_panel_reg_grouped_kernel<float2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int pcl = 0, prt = 0;
+        if (panel_cluster_shape(rows, &pcl, &prt))
+            e = prt == 1 ? launch_clustered(lu_panel_cluster_grouped_kernel<1>, pcl, count, hi, nodes, k0, nb, k)
+                         : launch_clustered(lu_panel_cluster_grouped_kernel<2>, pcl, count, hi, nodes, k0, nb, k);
+        else
+            lu_panel_reg_grouped_kernel<float2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
+        if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
         if (k & 1) {                              // pair swap: panel k's list on panel k - 1
             if ((e = S.pair_after_panel(last_r)) != cudaSuccess) return e;
             note_launch();

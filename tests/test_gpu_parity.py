@@ -69,6 +69,26 @@ def test_node_solve_matches_oracle(lib, prec, n):
     s.close()
 
 
+@pytest.mark.parametrize("n", [1500, 4096])
+def test_panel_cluster_factors_bit_identical(lib, n, monkeypatch):
+    """A complex64 panel spread over a cluster of CTAs (several shapes) gives
+    the same factors, bit for bit, as the panel on one CTA: the node solves
+    through them agree exactly."""
+    p = random_pep(n, 2, seed=11)
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((n, 24)) + 1j * rng.standard_normal((n, 24))
+    out = {}
+    for rpc in ("0", "512", "1024", "300"):
+        monkeypatch.setenv("FEAST_NL_PANEL_ROWS_PER_CTA", rpc)
+        s = lib.FeastNL(p, "fp32")
+        s.set_contour(0.05 + 0.1j, 0.6, 0.6, 4, "gl")
+        out[rpc] = [s.node_solve(j, R) for j in range(4)]
+        s.close()
+    for rpc in ("512", "1024", "300"):
+        for j in range(4):
+            assert np.array_equal(out[rpc][j], out["0"][j]), (rpc, j)
+
+
 # ------------------------------------------------------------------ Step 4 and Step 1 pieces
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_i8"])
 def test_filter_apply_matches_oracle(lib, prec):
