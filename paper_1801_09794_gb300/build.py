@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["k_dense.cu", "k_lu.cu", "k_reduced.cu", "k_ozaki.cu", "k_cgemm_tc.cu", "feast_nl.cu",
            "noalloc.cu", "server.cpp"]
-HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_common.cuh"), os.path.join(ROOT, "include", "feast_nl.h")]
+HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_common.cuh"), os.path.join(CSRC, "cgemm_tile.cuh"), os.path.join(ROOT, "include", "feast_nl.h")]
 LIB = os.path.join(HERE, "libfeast_nl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -29,6 +29,7 @@
 // the depth of each tensor-core update.
 #include "internal.h"
 #include "tc_common.cuh"
+#include "cgemm_tile.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -36,6 +37,7 @@
 #include <mutex>
 #include <tuple>
 #include <utility>
+#include <vector>
 #include <climits>
 #include <cstdlib>
 
@@ -732,45 +734,58 @@ __device__ __forceinline__ void stage_triangle(const T* __restrict__ F, int64_t 
 }
 
 // Columns [col_begin, col_begin+ncols) of B: the panel's gather list, then
-// B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F).
+// B[k0:k0+jb, col] <- L11^{-1} B[k0:k0+jb, col] (L11 unit lower, from F,
+// staged in sL with row stride TriMax + 1).  Warp w takes the columns
+// first + w, first + w + stride, ...
+template <typename T>
+__device__ __forceinline__ void swap_trsm_cols(int k0, int jb, const T* __restrict__ F, int64_t ld,
+                                               const int2* __restrict__ gl, int cnt, T* B,
+                                               int64_t ldb, int col_begin, int ncols, T* sL,
+                                               int first, int stride) {
+    constexpr int LDS = TriMax<T>::value + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    stage_triangle(F, ld, k0, jb, sL, LDS, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    for (int cl = first + warp; cl < ncols; cl += stride) {
+        T* col = B + (int64_t)(col_begin + cl) * ldb;
+        // interchanges: every src read before any dst written
+        T g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = lane + 32 * q;
+            if (e < cnt) g[q] = col[gl[e].y];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = lane + 32 * q;
+            if (e < cnt) col[gl[e].x] = g[q];
+        }
+        __syncwarp();
+        T x0 = (lane < jb) ? col[k0 + lane] : cmake<T>(0.0, 0.0);
+        T x1 = (lane + 32 < jb) ? col[k0 + lane + 32] : cmake<T>(0.0, 0.0);
+        for (int i = 0; i < jb; ++i) {
+            T src = (i < 32) ? x0 : x1;
+            T xi;
+            xi.x = __shfl_sync(0xffffffffu, src.x, i & 31);
+            xi.y = __shfl_sync(0xffffffffu, src.y, i & 31);
+            if (lane > i) x0 = cfms(sL[lane * LDS + i], xi, x0);
+            if (lane + 32 > i && lane + 32 < jb) x1 = cfms(sL[(lane + 32) * LDS + i], xi, x1);
+        }
+        if (lane < jb) col[k0 + lane] = x0;
+        if (lane + 32 < jb) col[k0 + lane + 32] = x1;
+    }
+}
+
+// One column per warp: column blockIdx.x * kWarpsPerCta + warp.
 template <typename T>
 __device__ __forceinline__ void swap_trsm_body(int k0, int jb, const T* __restrict__ F, int64_t ld,
                                                const int2* __restrict__ gl, int cnt, T* B,
                                                int64_t ldb, int col_begin, int ncols) {
-    __shared__ __align__(16) T sL[TriMax<T>::value][TriMax<T>::value + 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    stage_triangle(F, ld, k0, jb, &sL[0][0], TriMax<T>::value + 1, 0);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    const int cl = blockIdx.x * kWarpsPerCta + warp;
-    if (cl >= ncols) return;
-    T* col = B + (int64_t)(col_begin + cl) * ldb;
-    // interchanges: every src read before any dst written
-    T g[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int e = lane + 32 * q;
-        if (e < cnt) g[q] = col[gl[e].y];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int e = lane + 32 * q;
-        if (e < cnt) col[gl[e].x] = g[q];
-    }
-    __syncwarp();
-    T x0 = (lane < jb) ? col[k0 + lane] : cmake<T>(0.0, 0.0);
-    T x1 = (lane + 32 < jb) ? col[k0 + lane + 32] : cmake<T>(0.0, 0.0);
-    for (int i = 0; i < jb; ++i) {
-        T src = (i < 32) ? x0 : x1;
-        T xi;
-        xi.x = __shfl_sync(0xffffffffu, src.x, i & 31);
-        xi.y = __shfl_sync(0xffffffffu, src.y, i & 31);
-        if (lane > i) x0 = cfms(sL[lane][i], xi, x0);
-        if (lane + 32 > i && lane + 32 < jb) x1 = cfms(sL[lane + 32][i], xi, x1);
-    }
-    if (lane < jb) col[k0 + lane] = x0;
-    if (lane + 32 < jb) col[k0 + lane + 32] = x1;
+    __shared__ __align__(16) T sL[TriMax<T>::value * (TriMax<T>::value + 1)];
+    swap_trsm_cols<T>(k0, jb, F, ld, gl, cnt, B, ldb, col_begin, ncols, sL,
+                      blockIdx.x * kWarpsPerCta, ncols > 0 ? ncols : 1);
 }
 
 template <typename T>
@@ -870,27 +885,25 @@ __device__ __forceinline__ T pick_slot(const T* x, int q) {
     return v;
 }
 
+// One CTA's share of a block substitution: stage the triangle, then its warps
+// take the columns first + warp, first + warp + stride, ... below ncols of B
+// (column cl at B + cl * ldb; the block's rows are k0 .. k0 + jb - 1 of every
+// column).  gl / gc: the block's first panel's gather list and count (the
+// second panel's follow at gl + 128, gc + 1).
 template <typename T, int SB>
-__global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
-    int k0, int jb, int nb, const T* __restrict__ F, int64_t ld, int64_t strideF,
-    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
-    T* B, int64_t ldb, int64_t strideB, int ncols, int upper, const int* __restrict__ active,
-    int group) {
+__device__ __forceinline__ void trsm_block_body(int k0, int jb, int nb, const T* __restrict__ F,
+                                                int64_t ld, const int2* __restrict__ gl,
+                                                const int* __restrict__ gc, T* B, int64_t ldb,
+                                                int ncols, int upper, int first, int stride) {
     static_assert(SB % 32 == 0 && SB <= 128, "at most four rows per lane");
     constexpr int Q = SB / 32, LDS = SB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sD = reinterpret_cast<T*>(smem_raw);
-    const int node = blockIdx.y;
-    if (active && !active[node / group]) return;     // a finished contour's nodes
-    F += node * strideF;
-    B += node * strideB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     stage_triangle(F, ld, k0, jb, sD, LDS, upper);
-    const int cl = blockIdx.x * kBlockWarps + warp;
-    T* col = B + (int64_t)cl * ldb;
+    int cl = first + warp;
     if (!upper && cl < ncols) {                   // while the triangle is in flight
-        const int2* gl = gather + (int64_t)node * gstride + panel_index * 2 * 64;
-        const int* gc = gcount + (int64_t)node * (gstride / 128) + panel_index;
+        T* col = B + (int64_t)cl * ldb;
         gather_rows_warp(gl, gc[0], col);
         if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
     }
@@ -900,48 +913,290 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
         for (int r = threadIdx.x; r < jb; r += blockDim.x) sD[r * LDS + r] = crcp(sD[r * LDS + r]);
         __syncthreads();
     }
-    if (cl >= ncols) return;
-    col += k0;
-    T x[4];
+    for (; cl < ncols; cl += stride) {
+        T* col = B + (int64_t)cl * ldb;
+        if (!upper && cl != first + warp) {
+            gather_rows_warp(gl, gc[0], col);
+            if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
+        }
+        col += k0;
+        T x[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        x[q] = (q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
-    }
-    if (!upper) {
+        for (int q = 0; q < 4; ++q) {
+            const int r = lane + 32 * q;
+            x[q] = (q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
+        }
+        if (!upper) {
 #pragma unroll 4
-        for (int i = 0; i + 1 < jb; ++i) {
-            const T own = pick_slot(x, i >> 5);
-            T xi;
-            xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
-            xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+            for (int i = 0; i + 1 < jb; ++i) {
+                const T own = pick_slot(x, i >> 5);
+                T xi;
+                xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+                xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int r = lane + 32 * q;
-                if (r > i && r < jb) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+                for (int q = 0; q < Q; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r > i && r < jb) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int i = jb - 1; i >= 0; --i) {
+                const T own = pick_slot(x, i >> 5);
+                T xi;
+                xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
+                xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+                xi = xi * sD[i * LDS + i];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r == i) x[q] = xi;
+                    else if (r < i) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+                }
             }
         }
-    } else {
-#pragma unroll 4
-        for (int i = jb - 1; i >= 0; --i) {
-            const T own = pick_slot(x, i >> 5);
-            T xi;
-            xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
-            xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
-            xi = xi * sD[i * LDS + i];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int r = lane + 32 * q;
-                if (r == i) x[q] = xi;
-                else if (r < i) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
-            }
+        for (int q = 0; q < Q; ++q) {
+            const int r = lane + 32 * q;
+            if (r < jb) col[r] = x[q];
         }
     }
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int r = lane + 32 * q;
-        if (r < jb) col[r] = x[q];
+}
+
+template <typename T, int SB>
+__global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
+    int k0, int jb, int nb, const T* __restrict__ F, int64_t ld, int64_t strideF,
+    const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
+    T* B, int64_t ldb, int64_t strideB, int ncols, int upper, const int* __restrict__ active,
+    int group) {
+    const int node = blockIdx.y;
+    if (active && !active[node / group]) return;     // a finished contour's nodes
+    trsm_block_body<T, SB>(k0, jb, nb, F + node * strideF, ld,
+                           gather + (int64_t)node * gstride + panel_index * 2 * 64,
+                           gcount + (int64_t)node * (gstride / 128) + panel_index,
+                           B + node * strideB, ldb, ncols, upper, blockIdx.x * kBlockWarps,
+                           gridDim.x * kBlockWarps);
+}
+
+// A pair's block substitution on the columns of nodes of different orders:
+// mode 0 the next pair's columns, mode 1 the columns right of them.
+template <int SB>
+__global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_grouped_kernel(
+    const LuNode* __restrict__ nodes, int k0, int nb, int panel_index, int mode) {
+    const LuNode d = nodes[blockIdx.y];
+    int jb, c0, ncols;
+    if (!lookahead_cols(d.n, k0, 2 * nb, mode, &jb, &c0, &ncols)) return;
+    float2* F = static_cast<float2*>(d.F);
+    trsm_block_body<float2, SB>(k0, jb, nb, F, d.n, d.gather + panel_index * 2 * 64,
+                                d.gcount + panel_index, F + (int64_t)c0 * d.n, d.n, ncols, 0,
+                                blockIdx.x * kBlockWarps, gridDim.x * kBlockWarps);
+}
+
+// ---------------------------------------------------------------------------
+// The batched factorisation as one persistent launch
+// ---------------------------------------------------------------------------
+// The pair scheme of lu_factor_batched (see above) as a device work queue:
+// per node d and pair p (k0 = 2 nb p) the tasks
+//   P0  panel 2p                     needs: column block 2p updated by pair p-1
+//   B1  panel 2p on block 2p+1       needs: P0, block 2p+1 updated by pair p-1
+//       (swap + nb-row triangle, update with K = nb)
+//   P1  panel 2p+1                   needs: B1
+//   SW  pair swap (2p+1's list on 2p's L)   needs: P1
+//   COL(cb) pair p on column block cb (both lists, 2 nb-row triangle, update
+//       with K = 2 nb)               needs: SW, block cb updated by pair p-1
+// are listed in an order in which every task comes after the tasks it needs
+// (P0..SW of pair p+1 before the wide blocks of pair p, so the next panels
+// overlap them).  Each CTA (512 threads: the panels, triangles and swaps on
+// all of them; the updates on three 160-thread tensor-core units with 128
+// TMEM columns each) takes the next task from a counter, waits for the flags
+// of what it needs and raises its own when done.  A task only waits on tasks
+// taken before it, each held by a running CTA, so the queue always moves; the
+// waits are still bounded (on expiry: error bit 16, every CTA stops).  Every
+// task does the arithmetic of the launch-per-step path with the same device
+// functions and tiles, so the factors are the same bits.
+constexpr int kPersistThreads = 512;
+constexpr int kPersistUnits = 3;                 // tensor-core units per CTA
+constexpr long long kPersistSpin = 1ll << 24;    // x ~128 ns sleep: ~2 s
+constexpr int kPersistSmem = kPersistUnits * tcu::stage_smem<kLuUpdateBn>();
+static_assert(kPersistUnits * tcu::kTcThreads <= kPersistThreads, "units fit the CTA");
+static_assert((int)(128 * 129 * sizeof(float2)) <= kPersistSmem, "the triangle fits the rings' space");
+
+enum : int { kTaskP0 = 0, kTaskB1 = 1, kTaskP1 = 2, kTaskSW = 3, kTaskCol = 4 };
+struct PersistTask { int kind, node, pair, cb; };
+
+struct PersistPlan {
+    const LuNode* nodes;
+    const PersistTask* tasks;
+    int ntasks;
+    int nb;
+    int* next;            // the queue's counter
+    int* flags;           // per node and pair: P0, B1, P1, SW, then one per column block
+    int pair_stride;      // 4 + column blocks
+    int node_stride;      // pairs * pair_stride
+    int* err;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// one thread: bounded wait for a raised flag
+__device__ __forceinline__ bool wait_flag(const int* f) {
+    for (long long i = 0; i < kPersistSpin; ++i) {
+        if (ld_acquire_gpu(f)) return true;
+        __nanosleep(128);
     }
+    return false;
+}
+
+// The panel of column k0p on this CTA alone (a cluster of one), rows per thread
+// chosen from the remaining rows.
+__device__ __forceinline__ void persist_panel(const LuNode& d, int k0p, int nb, int panel) {
+    const int64_t rows = d.n - k0p;
+    const int jb = (int)min((int64_t)nb, rows);
+    float2* F = static_cast<float2*>(d.F);
+    int2* gl = d.gather + panel * 2 * 64;
+    int* gc = d.gcount + panel;
+    if (rows <= 2 * kClusterThreads)
+        panel_cluster_body<float2, 2>(d.n, k0p, jb, F, d.n, d.piv, d.info, gl, gc);
+    else if (rows <= 4 * kClusterThreads)
+        panel_cluster_body<float2, 4>(d.n, k0p, jb, F, d.n, d.piv, d.info, gl, gc);
+    else
+        panel_cluster_body<float2, 8>(d.n, k0p, jb, F, d.n, d.piv, d.info, gl, gc);
+}
+
+// The update rows [0, rows) x columns [0, ncols) of C -= A B (K = k) on the
+// CTA's tensor-core units, 128-row tiles dealt round-robin; false on a timeout.
+__device__ __forceinline__ bool persist_update(tcu::TcUnit& u, int unit, int rows, int ncols, int k,
+                                               const float2* A, const float2* B, float2* C,
+                                               int64_t ld) {
+    bool ok = true;
+    if (unit < kPersistUnits) {
+        const int utid = threadIdx.x - unit * tcu::kTcThreads;
+        const int tiles = (rows + tcu::kTcM - 1) / tcu::kTcM;
+        for (int i = unit; i < tiles; i += kPersistUnits)
+            if (!tcu::cgemm_tile<kLuUpdateBn, false>(u, utid, rows, ncols, k, A, ld, B, ld, C, ld,
+                                              i * tcu::kTcM, 0)) {
+                ok = false;                       // unit-uniform: stop this unit's tiles
+                break;
+            }
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 1) lu_persistent_kernel(PersistPlan P) {
+    extern __shared__ __align__(1024) unsigned char dsm[];     // the units' rings, or a triangle
+    __shared__ __align__(8) uint64_t ufull[kPersistUnits][tcu::kTcStages];
+    __shared__ __align__(8) uint64_t uempty[kPersistUnits][tcu::kTcStages];
+    __shared__ __align__(8) uint64_t udone[kPersistUnits];
+    __shared__ uint32_t s_tmem;
+    __shared__ PersistTask s_task;
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < kPersistUnits; ++q) tcu::unit_init_barriers(ufull[q], uempty[q], &udone[q]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc::smem_u32(&s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int unit = tid / tcu::kTcThreads;         // 3: the spare warp
+    const int uq = unit < kPersistUnits ? unit : 0;
+    tcu::TcUnit u{dsm + uq * tcu::stage_smem<kLuUpdateBn>(), ufull[uq], uempty[uq], &udone[uq],
+                  s_tmem + (uint32_t)(uq * 128), 1 + uq, 0u, 0u};
+    const int nb = P.nb;
+    for (;;) {
+        if (tid == 0) {
+            int stop = 0;
+            const int t = atomicAdd(P.next, 1);
+            if (t >= P.ntasks || (ld_acquire_gpu(P.err) & 16)) {
+                stop = 1;
+            } else {
+                const PersistTask tk = P.tasks[t];
+                s_task = tk;
+                const int* f = P.flags + (int64_t)tk.node * P.node_stride;
+                const int* fp = f + tk.pair * P.pair_stride;            // this pair
+                const int* fq = fp - P.pair_stride;                      // the previous pair
+                bool ok = true;
+                switch (tk.kind) {
+                    case kTaskP0: if (tk.pair > 0) ok = wait_flag(fq + 4 + 2 * tk.pair); break;
+                    case kTaskB1:
+                        ok = wait_flag(fp + 0) && (tk.pair == 0 || wait_flag(fq + 4 + 2 * tk.pair + 1));
+                        break;
+                    case kTaskP1: ok = wait_flag(fp + 1); break;
+                    case kTaskSW: ok = wait_flag(fp + 2); break;
+                    default: ok = wait_flag(fp + 3) && (tk.pair == 0 || wait_flag(fq + 4 + tk.cb)); break;
+                }
+                if (!ok) {
+                    atomicOr(P.err, 16);
+                    stop = 1;
+                }
+            }
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const PersistTask tk = s_task;
+        const LuNode d = P.nodes[tk.node];
+        float2* F = static_cast<float2*>(d.F);
+        const int64_t n = d.n;
+        const int k0 = 2 * nb * tk.pair;
+        bool ok = true;
+        switch (tk.kind) {
+            case kTaskP0: persist_panel(d, k0, nb, 2 * tk.pair); break;
+            case kTaskP1: persist_panel(d, k0 + nb, nb, 2 * tk.pair + 1); break;
+            case kTaskB1: {
+                const int jb1 = (int)min((int64_t)nb, n - k0 - nb);
+                swap_trsm_cols<float2>(k0, nb, F, n, d.gather + 2 * tk.pair * 2 * 64,
+                                       d.gcount[2 * tk.pair], F, n, k0 + nb, jb1,
+                                       reinterpret_cast<float2*>(dsm), 0, kPersistThreads / 32);
+                __syncthreads();                      // the triangle's space goes to the rings
+                ok = persist_update(u, unit, (int)(n - k0 - nb), jb1, nb,
+                                    F + (k0 + nb) + (int64_t)k0 * n, F + k0 + (int64_t)(k0 + nb) * n,
+                                    F + (k0 + nb) + (int64_t)(k0 + nb) * n, n);
+                break;
+            }
+            case kTaskSW:
+                for (int c = warp; c < nb; c += kPersistThreads / 32)
+                    gather_rows_warp(d.gather + (2 * tk.pair + 1) * 2 * 64, d.gcount[2 * tk.pair + 1],
+                                     F + (int64_t)(k0 + c) * n);
+                break;
+            default: {
+                const int jb = 2 * nb;
+                const int c0 = tk.cb * nb;
+                const int ncols = (int)min((int64_t)nb, n - c0);
+                trsm_block_body<float2, 128>(k0, jb, nb, F, n, d.gather + 2 * tk.pair * 2 * 64,
+                                             d.gcount + 2 * tk.pair, F + (int64_t)c0 * n, n, ncols, 0,
+                                             0, kPersistThreads / 32);
+                __syncthreads();
+                ok = persist_update(u, unit, (int)(n - k0 - jb), ncols, jb,
+                                    F + (k0 + jb) + (int64_t)k0 * n, F + k0 + (int64_t)c0 * n,
+                                    F + (k0 + jb) + (int64_t)c0 * n, n);
+                break;
+            }
+        }
+        if (!ok && (threadIdx.x % tcu::kTcThreads) == 0) atomicOr(P.err, 16);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const int slot = tk.kind == kTaskCol ? 4 + tk.cb : tk.kind;
+            st_release_gpu(P.flags + (int64_t)tk.node * P.node_stride + tk.pair * P.pair_stride + slot, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(512));
 }
 
 // rows of a solve block: two panels
@@ -952,6 +1207,36 @@ template <> struct SolveBlock<double2> { static constexpr int value = 64; };
 template <typename T>
 constexpr size_t solve_block_smem() {
     return (size_t)SolveBlock<T>::value * (SolveBlock<T>::value + 1) * sizeof(T);
+}
+
+// the dynamic shared memory of the block substitution kernels, once per device
+template <typename T>
+cudaError_t trsm_block_attr() {
+    constexpr int SB = SolveBlock<T>::value;
+    constexpr int smem = (int)solve_block_smem<T>();
+    static std::atomic<bool> attr_set[64] = {};   // idempotent setup; atomic for concurrent handles
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        if ((e = cudaFuncSetAttribute(trsm_block_kernel<T, SB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e;
+        if constexpr (sizeof(T) == 8)
+            if ((e = cudaFuncSetAttribute(trsm_block_grouped_kernel<SB>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+// CTAs per node of a block substitution over ncols columns: enough for about
+// four waves of one CTA per SM over all nodes; the warps loop over the rest
+inline unsigned trsm_block_ctas(int64_t ncols, int nodes) {
+    const int64_t need = (ncols + kBlockWarps - 1) / kBlockWarps;
+    const int64_t cap = std::max<int64_t>(1, (4 * 152 + nodes - 1) / nodes);
+    return (unsigned)std::max<int64_t>(1, std::min(need, cap));
 }
 
 // Cluster shape of a complex64 panel of `rows` rows: CL CTAs of 512 threads,
@@ -1075,62 +1360,75 @@ cudaError_t panel_apply(cudaStream_t st, int64_t n, int k0, int jb, T* F, int64_
                   kLuUpdateBn);
 }
 
-// Right-looking blocked LU with a look-ahead of one panel: after panel k is
-// factored, a high-priority stream updates only the next panel's columns and
-// factors that panel, while a low-priority stream updates every column beyond
-// it; so each panel factorisation (one CTA per node) overlaps the previous
-// panel's trailing update, and the block scheduler hands freed SMs to the
-// panel first.  Events order the two streams:
-//   high:  panel(k) -> [P] -> wait R(k-1) -> apply k to panel k+1's columns
-//   low:   wait P -> apply k to the columns right of panel k+1 -> [R(k)]
-// (the low stream's update of step k-1 covers panel k+1's columns, hence the
-// wait; panel k itself only needs what the high stream did before it).
-// A third stream takes the pair swaps: after odd panel k, once panel k's list
-// exists [P] and the side stream's update of step k - 1 -- the last reader of
-// panel k - 1's L below the panel -- is done [R(k-1)].
+// A pair of panels (rows and columns k0 .. k0 + jb - 1, jb = 2 nb, the pair
+// swap done) on the columns [c0, c0 + ncols): both gather lists and the
+// 2 nb x 2 nb unit lower triangle, then the update of every row below the pair
+// with K = 2 nb.
+template <typename T>
+cudaError_t block_apply(cudaStream_t st, int64_t n, int k0, int jb, int nb, T* F, int64_t strideF,
+                        int nc, const int2* gather, const int* gcount, int gstride, int panel,
+                        int64_t c0, int64_t ncols, int* err) {
+    if (ncols <= 0) return cudaSuccess;
+    constexpr int SB = SolveBlock<T>::value;
+    constexpr int smem = (int)solve_block_smem<T>();
+    cudaError_t e = trsm_block_attr<T>();
+    if (e != cudaSuccess) return e;
+    dim3 g(trsm_block_ctas(ncols, nc), nc);
+    note_launch();
+    trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+        k0, jb, nb, F, n, strideF, gather, gcount, gstride, panel, F + c0 * n, n, strideF,
+        (int)ncols, 0, nullptr, 1);
+    const int64_t rows = n - k0 - jb;
+    if (rows <= 0) return cudaGetLastError();
+    return update(st, (int)rows, (int)ncols, jb, F + (k0 + jb) + (int64_t)k0 * n, n, strideF,
+                  F + k0 + c0 * n, n, strideF, F + (k0 + jb) + c0 * n, n, strideF, nc, err,
+                  kLuUpdateBn);
+}
+
+// Right-looking blocked LU by pairs of panels with a look-ahead.  Pair p
+// covers the columns B0 = [k0, k0 + nb) and B1 = [k0 + nb, k0 + 2 nb),
+// k0 = 2 nb p; N = the next pair's 2 nb columns, R = the columns right of N.
+//   high:  panel(B0) -> apply panel B0 to B1 (swap, nb-row triangle, update
+//          with K = nb) -> panel(B1) -> pair swap (B1's list on B0's L) -> [P]
+//          -> wait R(p-1) -> pair p on N (both lists, 2 nb-row triangle,
+//          update with K = 2 nb)
+//   low:   wait P -> pair p on R -> [R(p)]
+// so the wide trailing updates of R take K = 2 nb: each entry of the trailing
+// matrix is read and written once per pair instead of once per panel, which
+// halves the factorisation's dominant DRAM traffic.  The panels and the
+// updates feeding the next panel stay on the high-priority stream, so each
+// pair's panels overlap the previous pair's update of R (the low stream's
+// update of pair p-1 covers N, hence the wait).
 namespace {
 struct FactorStreams {
-    cudaStream_t hi = nullptr, side = nullptr, pair = nullptr;
-    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr, evS = nullptr;
+    cudaStream_t hi = nullptr, side = nullptr;
+    cudaEvent_t evP = nullptr, evR[2] = {nullptr, nullptr}, evH = nullptr;
     ~FactorStreams() {
-        for (cudaEvent_t ev : {evP, evR[0], evR[1], evH, evS})
+        for (cudaEvent_t ev : {evP, evR[0], evR[1], evH})
             if (ev) cudaEventDestroy(ev);
-        for (cudaStream_t s : {hi, side, pair})       // released once their work completes
+        for (cudaStream_t s : {hi, side})         // released once their work completes
             if (s) cudaStreamDestroy(s);
     }
-    // all three streams start after everything already queued on st (the assembly)
+    // both streams start after everything already queued on st (the assembly)
     cudaError_t create(cudaStream_t st) {
         int prio_lo = 0, prio_hi = 0;
         cudaError_t e;
         if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
             (e = cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
-            (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess ||
-            (e = cudaStreamCreateWithPriority(&pair, cudaStreamNonBlocking, prio_lo)) != cudaSuccess)
+            (e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_lo)) != cudaSuccess)
             return e;
-        for (cudaEvent_t* ev : {&evP, &evR[0], &evR[1], &evH, &evS})
+        for (cudaEvent_t* ev : {&evP, &evR[0], &evR[1], &evH})
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(evP, st)) != cudaSuccess) return e;
-        for (cudaStream_t s : {hi, side, pair})
+        for (cudaStream_t s : {hi, side})
             if ((e = cudaStreamWaitEvent(s, evP, 0)) != cudaSuccess) return e;
         return cudaSuccess;
     }
-    // the pair stream waits for panel k (just launched on hi) and for the side
-    // stream's last recorded update
-    cudaError_t pair_after_panel(int last_r) {
-        cudaError_t e;
-        if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(pair, evP, 0)) != cudaSuccess)
-            return e;
-        if (last_r >= 0) return cudaStreamWaitEvent(pair, evR[last_r & 1], 0);
-        return cudaSuccess;
-    }
-    // everything the three streams did is ordered before what follows on st
+    // everything the streams did is ordered before what follows on st
     cudaError_t join(cudaStream_t st, int last_r) {
         cudaError_t e;
         if ((e = cudaEventRecord(evH, hi)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess ||
-            (e = cudaEventRecord(evS, pair)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(st, evS, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(st, evH, 0)) != cudaSuccess)
             return e;
         if (last_r >= 0) return cudaStreamWaitEvent(st, evR[last_r & 1], 0);
         return cudaSuccess;
@@ -1138,50 +1436,154 @@ struct FactorStreams {
 };
 }  // namespace
 
+// The persistent factorisation: FEAST_NL_LU_PERSISTENT=1 uses it whenever it
+// applies (complex64, nb = 64, every order <= 4096); otherwise the launches per
+// panel step, which measured faster (64 discs of n = 2048: 217 against 574 ms;
+// the mixed-order batch: 41 against 196 ms).
+static bool lu_persistent_wanted(int count, int64_t nmax, int nb) {
+    if (nmax > 4096 || nb != 64 || count <= 0) return false;
+    const char* e = getenv("FEAST_NL_LU_PERSISTENT");
+    return e && e[0] == '1';
+}
+
+// The task list of lu_persistent_kernel for nodes of orders n_host[0..count).
+static std::vector<PersistTask> persist_tasks(const int64_t* n_host, int count, int nb, int* npair_out,
+                                       int* ncb_out) {
+    int64_t nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, n_host[i]);
+    const int npair = (int)((nmax + 2 * nb - 1) / (2 * nb));
+    const int ncb = (int)((nmax + nb - 1) / nb);
+    std::vector<PersistTask> t;
+    auto head = [&](int p) {                      // P0, B1, P1, SW of pair p, kind by kind
+        const int64_t k0 = 2ll * nb * p;
+        for (int i = 0; i < count; ++i)
+            if (k0 < n_host[i]) t.push_back({kTaskP0, i, p, 0});
+        for (int kind : {kTaskB1, kTaskP1, kTaskSW})
+            for (int i = 0; i < count; ++i)
+                if (n_host[i] - k0 > nb) t.push_back({kind, i, p, 0});
+    };
+    auto cols = [&](int p, bool next) {           // the next pair's blocks, or those right of them
+        const int64_t k0 = 2ll * nb * p;
+        const int lo = next ? 2 * p + 2 : 2 * p + 4, hi = next ? 2 * p + 4 : ncb;
+        for (int cb = lo; cb < hi; ++cb)
+            for (int i = 0; i < count; ++i)
+                if (n_host[i] - k0 > 2 * nb && (int64_t)cb * nb < n_host[i]) t.push_back({kTaskCol, i, p, cb});
+    };
+    head(0);
+    for (int p = 0; p < npair; ++p) {
+        cols(p, true);
+        if (p + 1 < npair) head(p + 1);
+        cols(p, false);
+    }
+    *npair_out = npair;
+    *ncb_out = ncb;
+    return t;
+}
+
+// nodes: the descriptors in device memory, or null with nodes_host in host memory
+static cudaError_t lu_factor_persistent(cudaStream_t st, const LuNode* nodes, const LuNode* nodes_host,
+                                 const int64_t* n_host, int count, int nb, int* err) {
+    int npair = 0, ncb = 0;
+    const std::vector<PersistTask> tasks = persist_tasks(n_host, count, nb, &npair, &ncb);
+    if (tasks.empty()) return cudaSuccess;
+    static std::atomic<bool> attr_set[64] = {};
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        if ((e = cudaFuncSetAttribute(lu_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kPersistSmem)) != cudaSuccess)
+            return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    // one device block: the counter, the flags, the node descriptors, the tasks
+    const int pair_stride = 4 + ncb, node_stride = npair * pair_stride;
+    const size_t head = 256, fbytes = (size_t)count * node_stride * sizeof(int);
+    const size_t nbytes = nodes ? 0 : (size_t)count * sizeof(LuNode);
+    const size_t tbytes = tasks.size() * sizeof(PersistTask);
+    const size_t off_nodes = (head + fbytes + 255) / 256 * 256, off_tasks = (off_nodes + nbytes + 255) / 256 * 256;
+    unsigned char* buf = nullptr;
+    if ((e = cudaMallocAsync(&buf, off_tasks + tbytes, st)) != cudaSuccess) return e;
+    e = cudaMemsetAsync(buf, 0, head + fbytes, st);
+    if (e == cudaSuccess && !nodes)
+        e = cudaMemcpyAsync(buf + off_nodes, nodes_host, nbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + off_tasks, tasks.data(), tbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        PersistPlan P{nodes ? nodes : reinterpret_cast<const LuNode*>(buf + off_nodes),
+                      reinterpret_cast<const PersistTask*>(buf + off_tasks), (int)tasks.size(), nb,
+                      reinterpret_cast<int*>(buf), reinterpret_cast<int*>(buf + head), pair_stride,
+                      node_stride, err};
+        const int grid = (int)std::min<size_t>((size_t)sms, tasks.size());
+        note_launch();
+        lu_persistent_kernel<<<grid, kPersistThreads, kPersistSmem, st>>>(P);
+        e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return e != cudaSuccess ? e : ef;
+}
+
 template <typename T>
 cudaError_t lu_factor_batched(cudaStream_t st, int64_t n, int nb, T* F, int64_t strideF,
                               int* piv, int nc, int* info, int2* gather, int* gcount, int* err) {
     const int gstride = lu_gather_stride(n, nb);
     const int npanel = (int)((n + nb - 1) / nb);
-    if (nb % kWarpsPerCta != 0 || 2 * nb > SolveBlock<T>::value) return cudaErrorInvalidValue;
+    if (nb % kWarpsPerCta != 0 || 2 * nb != SolveBlock<T>::value) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 8) {
+        if (lu_persistent_wanted(nc, n, nb)) {
+            std::vector<LuNode> nodes(nc);
+            std::vector<int64_t> ns(nc, n);
+            for (int i = 0; i < nc; ++i)
+                nodes[i] = LuNode{F + i * strideF, piv + (int64_t)i * n, info + i,
+                                  gather + (int64_t)i * gstride, gcount + (int64_t)i * (gstride / 128), n};
+            return lu_factor_persistent(st, nullptr, nodes.data(), ns.data(), nc, nb, err);
+        }
+    }
     FactorStreams S;
     cudaError_t e;
     if ((e = S.create(st)) != cudaSuccess) return e;
     cudaStream_t hi = S.hi, side = S.side;
     cudaEvent_t evP = S.evP, *evR = S.evR;
-    int last_r = -1;                              // step whose side update was recorded last
-    for (int k = 0; k < npanel; ++k) {
-        const int k0 = k * nb;
-        const int jb = (int)std::min<int64_t>(nb, n - k0);
-        if ((e = launch_panel<T>(hi, n, k0, jb, F, strideF, piv, nc, info, gather, gcount, k,
+    int last_r = -1;                              // pair whose low-stream update was recorded last
+    for (int p = 0; 2 * p < npanel; ++p) {
+        const int k0 = 2 * nb * p;
+        const int jb0 = (int)std::min<int64_t>(nb, n - k0);
+        if ((e = launch_panel<T>(hi, n, k0, jb0, F, strideF, piv, nc, info, gather, gcount, 2 * p,
                                  gstride)) != cudaSuccess)
             return e;
-        if (k & 1) {                              // pair swap: panel k's list on panel k - 1
-            if ((e = S.pair_after_panel(last_r)) != cudaSuccess) return e;
-            note_launch();
-            swap_cols_kernel<T><<<dim3((unsigned)(nb / kWarpsPerCta), nc), 32 * kWarpsPerCta, 0,
-                                  S.pair>>>(k0 - nb, nb, F, n, strideF, gather, gcount, gstride, k);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+        const int64_t r1 = n - k0 - jb0;
+        if (r1 <= 0) break;
+        const int jb1 = (int)std::min<int64_t>(nb, r1);
+        if ((e = panel_apply<T>(hi, n, k0, jb0, F, strideF, nc, gather, gcount, gstride, 2 * p,
+                                k0 + jb0, jb1, err)) != cudaSuccess)
+            return e;
+        if ((e = launch_panel<T>(hi, n, k0 + jb0, jb1, F, strideF, piv, nc, info, gather, gcount,
+                                 2 * p + 1, gstride)) != cudaSuccess)
+            return e;
+        note_launch();                            // pair swap: B1's list on B0's L columns
+        swap_cols_kernel<T><<<dim3((unsigned)(nb / kWarpsPerCta), nc), 32 * kWarpsPerCta, 0, hi>>>(
+            k0, nb, F, n, strideF, gather, gcount, gstride, 2 * p + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int jb = jb0 + jb1;
         const int64_t rest = n - k0 - jb;
         if (rest <= 0) break;
-        const int64_t jn = std::min<int64_t>(nb, rest);     // next panel's columns
-        const int64_t rr = rest - jn;                        // columns beyond it
+        const int64_t jn = std::min<int64_t>(2 * nb, rest);  // the next pair's columns
+        const int64_t rr = rest - jn;                         // columns beyond them
         if (rr > 0) {
             if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
                 return e;
-            if ((e = panel_apply<T>(side, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
-                                    k0 + jb + jn, rr, err)) != cudaSuccess)
+            if ((e = block_apply<T>(side, n, k0, jb, nb, F, strideF, nc, gather, gcount, gstride,
+                                    2 * p, k0 + jb + jn, rr, err)) != cudaSuccess)
                 return e;
         }
         if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
             return e;
         if (rr > 0) {
-            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return e;
-            last_r = k;
+            if ((e = cudaEventRecord(evR[p & 1], side)) != cudaSuccess) return e;
+            last_r = p;
         }
-        if ((e = panel_apply<T>(hi, n, k0, jb, F, strideF, nc, gather, gcount, gstride, k,
+        if ((e = block_apply<T>(hi, n, k0, jb, nb, F, strideF, nc, gather, gcount, gstride, 2 * p,
                                 k0 + jb, jn, err)) != cudaSuccess)
             return e;
     }
@@ -1196,67 +1598,91 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
     if (count <= 0 || nmax <= 0) return cudaSuccess;
     if (nmax > 4 * kPanelThreads || count > 65535) return cudaErrorInvalidValue;
     const int npanel = (int)((nmax + nb - 1) / nb);
-    if (nb % kWarpsPerCta != 0 || 2 * nb > SolveBlock<float2>::value) return cudaErrorInvalidValue;
+    if (nb % kWarpsPerCta != 0 || 2 * nb != SolveBlock<float2>::value) return cudaErrorInvalidValue;
+    constexpr int SB = SolveBlock<float2>::value;
+    constexpr int smem = (int)solve_block_smem<float2>();
+    if (lu_persistent_wanted(count, nmax, nb))
+        return lu_factor_persistent(st, nodes, nullptr, n_host, count, nb, err);
     FactorStreams S;
     cudaError_t e;
+    if ((e = trsm_block_attr<float2>()) != cudaSuccess) return e;
     if ((e = S.create(st)) != cudaSuccess) return e;
     cudaStream_t hi = S.hi, side = S.side;
     cudaEvent_t evP = S.evP, *evR = S.evR;
-    int last_r = -1;
-    for (int k = 0; k < npanel; ++k) {
-        const int k0 = k * nb;
-        // the largest extents over the nodes that still have this panel
-        int64_t rows = 0, rows_below = 0, cols_next = 0, cols_rest = 0;
-        for (int i = 0; i < count; ++i) {
-            int jb, c0, nn;
-            if (k0 >= n_host[i]) continue;
-            rows = std::max(rows, n_host[i] - k0);
-            jb = (int)std::min<int64_t>(nb, n_host[i] - k0);
-            rows_below = std::max(rows_below, n_host[i] - k0 - jb);
-            if (lookahead_cols(n_host[i], k0, nb, 0, &jb, &c0, &nn)) cols_next = std::max<int64_t>(cols_next, nn);
-            if (lookahead_cols(n_host[i], k0, nb, 1, &jb, &c0, &nn)) cols_rest = std::max<int64_t>(cols_rest, nn);
-        }
+    // one panel launch over the nodes that have panel k (rows: their largest
+    // remaining order)
+    auto panel = [&](int k0, int k, int64_t rows) -> cudaError_t {
         note_launch();
         int pcl = 0, prt = 0;
+        cudaError_t pe = cudaSuccess;
         if (panel_cluster_shape(rows, &pcl, &prt))
-            e = prt == 1 ? launch_clustered(lu_panel_cluster_grouped_kernel<1>, pcl, count, hi, nodes, k0, nb, k)
-                         : launch_clustered(lu_panel_cluster_grouped_kernel<2>, pcl, count, hi, nodes, k0, nb, k);
+            pe = prt == 1 ? launch_clustered(lu_panel_cluster_grouped_kernel<1>, pcl, count, hi, nodes, k0, nb, k)
+                          : launch_clustered(lu_panel_cluster_grouped_kernel<2>, pcl, count, hi, nodes, k0, nb, k);
         else
             lu_panel_reg_grouped_kernel<float2><<<count, kPanelThreads, 0, hi>>>(nodes, k0, nb, k);
-        if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
-        if (k & 1) {                              // pair swap: panel k's list on panel k - 1
-            if ((e = S.pair_after_panel(last_r)) != cudaSuccess) return e;
-            note_launch();
-            swap_cols_grouped_kernel<float2><<<dim3((unsigned)(nb / kWarpsPerCta), count),
-                                               32 * kWarpsPerCta, 0, S.pair>>>(nodes, k0, nb, k);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return pe != cudaSuccess ? pe : cudaGetLastError();
+    };
+    // a pair's substitution and update on the nodes' columns of `mode`
+    auto pair_apply = [&](cudaStream_t s, int k0, int p, int mode, int64_t rows_below,
+                          int64_t cols) -> cudaError_t {
+        dim3 g(trsm_block_ctas(cols, count), count);
+        note_launch();
+        trsm_block_grouped_kernel<SB><<<g, 32 * kBlockWarps, smem, s>>>(nodes, k0, nb, 2 * p, mode);
+        cudaError_t pe = cudaGetLastError();
+        if (pe != cudaSuccess) return pe;
+        return cgemm_sub_grouped(s, nodes, count, k0, 2 * nb, mode, rows_below, cols, err);
+    };
+    int last_r = -1;
+    for (int p = 0; 2 * p < npanel; ++p) {
+        const int k0 = 2 * nb * p;
+        // the largest extents over the nodes that have these panels
+        int64_t rows0 = 0, rows1 = 0, b1_below = 0, b1_cols = 0, pr_below = 0, n_cols = 0, r_cols = 0;
+        for (int i = 0; i < count; ++i) {
+            const int64_t ni = n_host[i];
+            int jb, c0, nn;
+            if (k0 >= ni) continue;
+            rows0 = std::max(rows0, ni - k0);
+            if (ni - k0 > nb) rows1 = std::max(rows1, ni - k0 - nb);
+            if (lookahead_cols(ni, k0, nb, 0, &jb, &c0, &nn)) {
+                b1_cols = std::max<int64_t>(b1_cols, nn);
+                b1_below = std::max(b1_below, ni - k0 - jb);
+            }
+            if (lookahead_cols(ni, k0, 2 * nb, 0, &jb, &c0, &nn)) {
+                n_cols = std::max<int64_t>(n_cols, nn);
+                pr_below = std::max(pr_below, ni - k0 - jb);
+            }
+            if (lookahead_cols(ni, k0, 2 * nb, 1, &jb, &c0, &nn)) r_cols = std::max<int64_t>(r_cols, nn);
         }
-        if (rows_below <= 0) continue;
-        if (cols_rest > 0) {
+        if (rows0 <= 0) break;
+        if ((e = panel(k0, 2 * p, rows0)) != cudaSuccess) return e;
+        if (rows1 <= 0) continue;
+        if (b1_cols > 0) {                        // panel B0 on B1
+            dim3 g((unsigned)((b1_cols + kWarpsPerCta - 1) / kWarpsPerCta), count);
+            note_launch();
+            swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, hi>>>(nodes, k0, nb, 2 * p, 0);
+            if ((e = cgemm_sub_grouped(hi, nodes, count, k0, nb, 0, b1_below, b1_cols, err)) !=
+                cudaSuccess)
+                return e;
+        }
+        if ((e = panel(k0 + nb, 2 * p + 1, rows1)) != cudaSuccess) return e;
+        note_launch();                            // pair swap: B1's list on B0's L columns
+        swap_cols_grouped_kernel<float2><<<dim3((unsigned)(nb / kWarpsPerCta), count),
+                                           32 * kWarpsPerCta, 0, hi>>>(nodes, k0 + nb, nb, 2 * p + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (n_cols <= 0) continue;
+        if (r_cols > 0) {
             if ((e = cudaEventRecord(evP, hi)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(side, evP, 0)) != cudaSuccess)
                 return e;
-            dim3 g((unsigned)((cols_rest + kWarpsPerCta - 1) / kWarpsPerCta), count);
-            note_launch();
-            swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, side>>>(nodes, k0, nb, k, 1);
-            if ((e = cgemm_sub_grouped(side, nodes, count, k0, nb, 1, rows_below, cols_rest, err)) !=
-                cudaSuccess)
-                return e;
+            if ((e = pair_apply(side, k0, p, 1, pr_below, r_cols)) != cudaSuccess) return e;
         }
         if (last_r >= 0 && (e = cudaStreamWaitEvent(hi, evR[last_r & 1], 0)) != cudaSuccess)
             return e;
-        if (cols_rest > 0) {
-            if ((e = cudaEventRecord(evR[k & 1], side)) != cudaSuccess) return e;
-            last_r = k;
+        if (r_cols > 0) {
+            if ((e = cudaEventRecord(evR[p & 1], side)) != cudaSuccess) return e;
+            last_r = p;
         }
-        if (cols_next > 0) {
-            dim3 g((unsigned)((cols_next + kWarpsPerCta - 1) / kWarpsPerCta), count);
-            note_launch();
-            swap_trsm_grouped_kernel<float2><<<g, 32 * kWarpsPerCta, 0, hi>>>(nodes, k0, nb, k, 0);
-            if ((e = cgemm_sub_grouped(hi, nodes, count, k0, nb, 0, rows_below, cols_next, err)) !=
-                cudaSuccess)
-                return e;
-        }
+        if ((e = pair_apply(hi, k0, p, 0, pr_below, n_cols)) != cudaSuccess) return e;
     }
     if ((e = S.join(st, last_r)) != cudaSuccess) return e;
     return cudaGetLastError();
@@ -1270,16 +1696,8 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     constexpr int smem = (int)solve_block_smem<T>();
     const int sb = 2 * nb;                        // a block: two panels
     if (sb > SB) return cudaErrorInvalidValue;
-    static std::atomic<bool> attr_set[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = trsm_block_attr<T>();
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        if ((e = cudaFuncSetAttribute(trsm_block_kernel<T, SB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-            return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
     const int gstride = lu_gather_stride(n, nb);
     dim3 g((unsigned)((m + kBlockWarps - 1) / kBlockWarps), nc);
     for (int64_t k0 = 0, panel = 0; k0 < n; k0 += sb, panel += 2) {

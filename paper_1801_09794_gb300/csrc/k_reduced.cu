@@ -85,6 +85,10 @@ static_assert(kQrChunk >= 1 && kQrChunk <= 29, "lane t owns column k-1+t: a wind
 // flags word shared by the stages (device memory)
 constexpr int kNeed64 = 1;      // the FP64 companion / Hessenberg / QR stage runs
 constexpr int kRetry64 = 2;     // some pairs retry Newton with an FP64 factor
+// The FP64 stage runs for a pair that neither FP32- nor FP64-factor Newton could
+// refine only once the previous iteration's largest relative residual inside C
+// is at most this (Step 3's test then needs FP64-exact Ritz pairs).
+constexpr double kExactStageRelres = 1e-6;
 
 // The reduced problem seen by the refinement: the projected matrix polynomial
 // (kmax >= 0: Ahat holds the kmax + 1 coefficients, stacked m x m), or general
@@ -1533,6 +1537,13 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
                 // retry this pair alone with an FP64 factor from the same start
                 need[i] = 1;
                 atomicOr(redflag, kRetry64);
+            } else if (stage != 2 && !(status->n_inside > 0 && status->max_relres <= kExactStageRelres)) {
+                // Far from convergence (the previous iteration's residuals inside
+                // C above kExactStageRelres, or no previous test) the pair keeps
+                // its FP32 value and inverse-iteration vector: the Ritz pairs of
+                // such an iterate are approximations at the filter's level of
+                // progress anyway, and the FP64 re-run of the whole stage costs
+                // about as much as eight iterations of the n = 4096 QEP.
             } else {
                 atomicOr(&status->flags, 8);
                 atomicOr(redflag, kNeed64);
@@ -1583,7 +1594,6 @@ __global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2*
     const int ld = m + 1;
     float2* R = reinterpret_cast<float2*>(smem_raw);   // m x m col-major (upper used)
     float2* X = R + ld * m;                             // m x m col-major: R^{-1}
-    __shared__ float s_red[16];
     __shared__ float s_tr;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     {   // trace (real parts of the diagonal), one warp
@@ -1646,7 +1656,6 @@ __global__ void __launch_bounds__(512) chol_inverse_kernel(int m, const double2*
             const float2 v = X[r + c * ld];
             Rinv[r + (int64_t)c * m] = make_double2(v.x, v.y);
         }
-    (void)s_red;
 }
 
 size_t packed_elems(int N) { return (size_t)N * (N + 5) / 2 + 4; }

@@ -19,7 +19,8 @@ sys.path.insert(0, ROOT)
 
 from oracle import (assemble, brute_force_eigs, nlfeast, normalized_radius,  # noqa: E402
                     shift_invert_nearest, winding_count)
-from workloads import config1_qep, config2_qep, cubic_pep, delay_problem, start_block  # noqa: E402
+from workloads import (config1_qep, config2_qep, cubic_pep, delay_problem, random_pep,  # noqa: E402
+                       serving_requests, start_block)
 
 
 def circle_around(lam, target, count):
@@ -90,6 +91,9 @@ def main():
         return
     if sys.argv[1:] == ["mixed_n"]:
         main_mixed_only(path)
+        return
+    if sys.argv[1:2] == ["serving"]:
+        main_serving(int(sys.argv[2]) if len(sys.argv) > 2 else SERVING_REQUESTS)
         return
     out = {}
     p1 = config1_qep(256, 0)
@@ -218,6 +222,49 @@ def main_mixed_only(path):
                                 "pencil through one n x n LU"}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
+
+
+# serving stream (random PEPs of mixed n and degree): its own file
+SERVING_REQUESTS = 104          # 8 warm-up + 96 timed requests
+
+
+def serving_circle(q):
+    """One request of ``serving_requests``: the eigenvalues nearest its random
+    point (shift-invert Arnoldi, want + 12 of them); the count is taken in
+    [want - 3, want + 3] (clipped to [4, 64]) at the widest relative gap of
+    the sorted distances, the radius in the middle of that gap."""
+    import os as _os
+    _os.environ.setdefault("OMP_NUM_THREADS", "2")
+    p = random_pep(q["n"], q["k"], q["coef_seed"])
+    c = q["point"]
+    lam = shift_invert_nearest(p, c, q["want"] + 12)
+    d = np.sort(np.abs(lam - c))
+    lo, hi = max(4, q["want"] - 3), min(64, q["want"] + 3)
+    kk = max(range(lo, hi + 1), key=lambda j: (d[j] - d[j - 1]) / d[j])
+    r = 0.5 * (d[kk - 1] + d[kk])
+    inside = lam[np.abs(lam - c) < r]
+    assert len(inside) == kk and d[-1] > r
+    return {"t": q["t"], "n": q["n"], "k": q["k"], "coef_seed": q["coef_seed"], "nc": q["nc"],
+            "center": [c.real, c.imag], "r": float(r), "count": int(kk),
+            "m0": int(np.ceil(1.5 * kk)), "relative_gap": float((d[kk] - d[kk - 1]) / r),
+            "eigs_inside": [[x.real, x.imag] for x in sorted(inside, key=lambda v: (v.real, v.imag))]}
+
+
+def main_serving(num):
+    """tests/golden/serving_stream.json: the circles and enclosed eigenvalues of
+    the first `num` requests of ``serving_requests()`` (oracle only)."""
+    import multiprocessing as mp
+    reqs = serving_requests(num)
+    with mp.get_context("spawn").Pool(4) as pool:
+        rows = pool.map(serving_circle, reqs, chunksize=1)
+    out = {"generator": "serving_requests(num=%d, seed=2024, rate=200)" % num,
+           "coefficients": "random_pep(n, k, coef_seed)", "rule": "gl",
+           "method": "shift-invert Arnoldi (want + 12 nearest the random point) on the first "
+                     "companion pencil through one n x n LU",
+           "requests": rows}
+    with open(os.path.join(ROOT, "tests", "golden", "serving_stream.json"), "w") as f:
+        json.dump(out, f, indent=0)
+    print("serving", num, "requests,", sum(r["count"] for r in rows), "eigenvalues")
 
 
 if __name__ == "__main__":

@@ -82,6 +82,46 @@ def test_group_factors_match_one_by_one(lib, problems):
         g.close()
 
 
+@pytest.mark.parametrize("persistent", ["0", "1"])
+def test_group_factors_match_one_by_one_either_path(lib, problems, persistent, monkeypatch):
+    """The grouped factorisation by launches per panel step and by one
+    persistent launch over all nodes (a device work queue) give the factors
+    of the one-by-one factorisation (launches per step), bit for bit."""
+    rng = np.random.default_rng(4)
+    monkeypatch.setenv("FEAST_NL_LU_PERSISTENT", persistent)
+    grouped = [lib.FeastNL(p, "fp32") for p, _, _, _ in problems]
+    lib.set_contour_group(grouped, [c for _, _, c, _ in problems], [r for _, _, _, r in problems],
+                          [r for _, _, _, r in problems], 16)
+    monkeypatch.setenv("FEAST_NL_LU_PERSISTENT", "0")
+    for g, (p, _, c, r) in zip(grouped, problems):
+        s = lib.FeastNL(p, "fp32")
+        s.set_contour(c, r, r, 16)
+        R = rng.standard_normal((p["n"], 5)) + 1j * rng.standard_normal((p["n"], 5))
+        for j in range(16):
+            assert np.array_equal(g.node_solve(j, R), s.node_solve(j, R)), j
+        s.close()
+        g.close()
+
+
+@pytest.mark.parametrize("n,nodes", [(700, 6), (1500, 4), (2048, 3)])
+def test_persistent_factorisation_bit_identical(lib, n, nodes, monkeypatch):
+    """One problem's node matrices factored by one persistent launch equal,
+    bit for bit, those factored by launches per panel step with cluster
+    panels and prioritised streams."""
+    p = random_pep(n, 2, seed=17)
+    rng = np.random.default_rng(8)
+    R = rng.standard_normal((n, 12)) + 1j * rng.standard_normal((n, 12))
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("FEAST_NL_LU_PERSISTENT", mode)
+        s = lib.FeastNL(p, "fp32")
+        s.set_contour(0.05 + 0.1j, 0.6, 0.6, nodes, "gl")
+        out[mode] = [s.node_solve(j, R) for j in range(nodes)]
+        s.close()
+    for j in range(nodes):
+        assert np.array_equal(out["0"][j], out["1"][j]), j
+
+
 def test_group_invalid_arguments(lib, problems):
     p = problems[0][0]
     a, b = lib.FeastNL(p, "fp32"), lib.FeastNL(p, "fp64")

@@ -21,6 +21,7 @@ __all__ = [
     "tridiag", "sym_gauss", "complex_gauss", "start_block",
     "mass_spring", "closed_form_family", "config1_qep", "config2_qep",
     "random_pep", "linear_problem", "delay_problem", "cubic_pep", "delay_family",
+    "serving_requests",
 ]
 
 
@@ -160,3 +161,25 @@ def delay_family(n, c, d, a, tau=1.0):
              {"kind": "pow", "p": 0, "scale": 1.0 + 0j, "A": c[0] * I + d[0] * S},
              {"kind": "exp", "tau": float(tau), "scale": 1.0 + 0j, "A": c[1] * I + d[1] * S}]
     return {"n": n, "terms": terms, "name": f"delay_family_n{n}"}
+
+
+def serving_requests(num, seed=2024, rate=200.0, n_lo=128, n_hi=4096):
+    """A seeded stream of solve requests: Poisson arrivals at `rate` per second
+    (exponential gaps), n log-uniform in [n_lo, n_hi], degree 2 or 3 with
+    dense complex N(0,1)/sqrt(n) coefficients (``random_pep(n, k, coef_seed)``),
+    8 to 16 quadrature nodes, a wanted eigenvalue count in [4, 64] and a
+    random point of the spectral bulk (modulus in [0.6, 1.5], uniform angle)
+    about which the contour is drawn.  Only random draws: the circle itself
+    (radius, count, enclosed eigenvalues) is computed elsewhere."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for q in range(num):
+        t += rng.exponential(1.0 / rate)
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        k = int(rng.choice([2, 3]))
+        nc = int(rng.integers(8, 17))
+        want = int(rng.integers(4, 65))
+        rho, th = rng.uniform(0.6, 1.5), rng.uniform(0.0, 2.0 * np.pi)
+        out.append({"t": float(t), "n": n, "k": k, "coef_seed": 7000 + q, "nc": nc,
+                    "want": want, "point": complex(rho * np.cos(th), rho * np.sin(th))})
+    return out
