@@ -37,12 +37,15 @@ FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (vector and tensor), nominal
 FP32_SIMT_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 lanes x FMA x 2.07 GHz
 ONE_SM_FP32_TFLOPS_AT_MAX = 128 * 2 * 2.070e9 / 1e12        # one SM
 BEYN_NODES = 256                    # trapezoid nodes of the projected delay problem's moments
-# DRAM bytes per step of the dominant phase's kernels from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, phase); the summary
-# and its command are under profiles/.  Absent: not captured for this code.
-# DRAM bytes per step of the roofline object, from an ncu capture of the same
-# kernels (none is current: the reduced-stage kernels changed after the last one)
-ROOF_TRAFFIC = {}
+# DRAM bytes per launch of a phase's kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over the phase's launches in one ncu capture of
+# the same code, divided by those launches), keyed by (workload, phase); the
+# summaries and their commands are under profiles/.  Absent: not captured.
+ROOF_TRAFFIC = {
+    # node LU of the n = 4096 QEP, 16 nodes: 62.45 GB over 282 launches
+    # (profiles/lu_dram_qep_n4096.md)
+    ("qep_mixed_n4096", "lu"): 221.4e6,
+}
 TF32_OVER_BF16 = 1.1 / 2.25
 # arithmetic of the path per node-factor precision
 DTYPES = {"fp64": "c128 (FP64 SIMT LU, solves and products) + f64",

@@ -4,6 +4,8 @@
 #include "../../include/feast_nl.h"
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -294,12 +296,17 @@ cudaEvent_t prof_event(feast_nl_handle* h) {
     }
     return h->pool[h->pool_used++];
 }
+// NVTX range names of the phases (host ranges around each phase's launches,
+// for a timeline tool; no cost without one attached)
+const char* const kPhaseNames[FEAST_NL_NPHASES] = {"assemble", "lu", "apply", "project", "reduced",
+                                                  "ritz", "solve", "accum", "orth", "io"};
 // Scoped device-time measurement of one phase on the handle's stream (no-op
-// unless profiling is on and the caller asks for it).
+// unless profiling is on and the caller asks for it), inside an NVTX range.
 struct Phase {
     feast_nl_handle* h;
     int idx = -1;
     Phase(feast_nl_handle* hh, int phase, bool on = true) : h(hh) {
+        nvtxRangePushA(kPhaseNames[phase]);
         if (!on || !h->prof) return;
         cudaEvent_t a = prof_event(h), b = prof_event(h);
         if (!a || !b) return;
@@ -308,6 +315,7 @@ struct Phase {
         idx = (int)h->marks.size() - 1;
     }
     ~Phase() {
+        nvtxRangePop();
         if (idx < 0) return;
         cudaEventRecord(h->marks[idx].b, h->st);
         h->marks[idx].l1 = launch_count();

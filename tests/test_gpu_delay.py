@@ -96,7 +96,9 @@ def test_delay_n2048_matches_stored_reference(lib):
     # with a residual near 1e-3 for several iterations, and the test passes
     # once it leaves (the largest residual then drops from ~1e-3 to ~1e-16 in
     # one step).  The FP64 oracle takes 6, 6, 17 and 6 iterations from four
-    # start blocks; the GPU path has taken 10 and 14 with different rounding.
-    # Twenty still catches a mixed-precision path that stops converging.
-    assert info.iters <= 20, info.iters
+    # start blocks (9 on the GPU host's Arm cores from the bench's start); the
+    # GPU path takes 7 (it has taken 10 and 14 with earlier rounding).  The
+    # bound is the oracle's 9 plus two: a mixed-precision path that converges
+    # more slowly than the FP64 algorithm fails here.
+    assert info.iters <= 11, info.iters
     s.close()
