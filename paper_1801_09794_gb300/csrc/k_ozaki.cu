@@ -37,14 +37,15 @@
 // m0 = 96 is ~1e-15 relative (a GPU parity test checks it against FP64).
 //
 // Kernel: one CTA (256 threads) per 128 x 48 tile of W'.  K advances in
-// 16-element stages through a 5-slot cp.async ring (four stages in flight);
+// 16-element stages through a 5-slot cp.async ring (loads three stages ahead,
+// the MMAs of two stages queued behind them);
 // thread 0 issues tcgen05.mma.kind::f16 (M = 128, K = 16) once per A slice p
 // against the B slices q = 0 .. s-1-p side by side (N = 48 per slice, at most
 // five per instruction), with D placed so that slice q's columns fall on
 // level p + q's TMEM region (nine MMAs per K step instead of 28, which cuts
 // the shared-memory reads of A that bound the small-N products), and commits
 // each stage to the slot's mbarrier, which releases the slot for the stage
-// four ahead.  Warps w
+// five ahead.  Warps w
 // and w + 4 read TMEM lanes 32 (w mod 4) .. and split the 48 columns.  Operand
 // tiles use the canonical K-major layout without swizzle: 8-row x 16-byte core
 // matrices (128 bytes), the two K chunks of a row group side by side
@@ -64,12 +65,19 @@ constexpr int kOzM = 128;          // rows of W' per CTA (TMEM lanes)
 constexpr int kOzN = 48;           // columns of W' per CTA
 constexpr int kOzBK = 16;          // K elements (32 bytes) per stage
 constexpr int kOzStages = 5;       // shared-memory ring depth
+// Stages loaded ahead of the one being multiplied, and stages of MMAs left
+// queued while a slot is refilled: kOzLead + kOzMmaAhead = kOzStages, so the
+// refilled slot is the one the MMAs of stage t - kOzMmaAhead have released.
+constexpr int kOzLead = 3;
+constexpr int kOzMmaAhead = kOzStages - kOzLead;
 constexpr int kOzGroup = 5;        // B slices per MMA (N = 5 x 48 <= 256)
 constexpr int kOzThreads = 256;
 constexpr int kOzMaxSlices = 8;
 constexpr int kOzExact = 3;        // levels drained exactly (L = 2..4)
 constexpr int kOzChunkStages = 16; // 16 x 16 = 256 K elements between drains
 constexpr uint32_t kTmemCols = 512;
+// cp.async items (16 bytes) of a stage per thread, at most
+constexpr int kOzLoadIters = (kOzMaxSlices * (kOzM + kOzN) * 2 + kOzThreads - 1) / kOzThreads;
 
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
@@ -135,43 +143,55 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
 #pragma unroll
         for (int c = 0; c < kOzN / 2; ++c) exact[L][c] = 0;
     // stage t (16 K elements of every slice) into ring slot t % kOzStages; each
-    // row's 32 bytes are two 16-byte core-matrix rows (LBO 128 B, SBO 256 B)
-    auto load = [&](int t) {
-        const int64_t k0 = (int64_t)(kst0 + t) * kOzBK;
-        unsigned char* sa = smem + (t % kOzStages) * stage_bytes;
-        unsigned char* sb = sa + s * a_tile;
-        for (int idx = tid; idx < s * (kOzM + kOzN) * 2; idx += kOzThreads) {
-            const int chunk = idx & 1;                     // 16-byte K chunk (8 elements)
-            const int r = idx >> 1;
-            int p, rr;
-            const __nv_bfloat16* src;
-            unsigned char* dst;
+    // row's 32 bytes are two 16-byte core-matrix rows (LBO 128 B, SBO 256 B).
+    // A thread's copies are the same (slice, row, chunk) items at every stage,
+    // so their source rows and shared-memory offsets are formed once here and
+    // a stage only adds its K offset.
+    const int nitems = s * (kOzM + kOzN) * 2;
+    const __nv_bfloat16* lsrc[kOzLoadIters];
+    uint32_t ldst[kOzLoadIters];
+#pragma unroll
+    for (int j = 0; j < kOzLoadIters; ++j) {
+        const int idx = tid + j * kOzThreads;
+        const int chunk = idx & 1;                         // 16-byte K chunk (8 elements)
+        const int r = idx >> 1;
+        int p = 0, rr = 0;
+        uint32_t base = 0;
+        const __nv_bfloat16* src = A;
+        if (idx < nitems) {
             if (r < s * kOzM) {
                 p = r / kOzM;
                 rr = r - p * kOzM;
-                src = A + p * a_slice_stride + (int64_t)(row0 + rr) * Kp + k0 + chunk * 8;
-                dst = sa + p * a_tile;
+                src = A + p * a_slice_stride + (int64_t)(row0 + rr) * Kp + chunk * 8;
+                base = (uint32_t)(p * a_tile);
             } else {
                 const int r2 = r - s * kOzM;
                 p = r2 / kOzN;
                 rr = r2 - p * kOzN;
-                src = Bslices + p * b_slice_stride + (int64_t)(col0 + rr) * Kp + k0 + chunk * 8;
-                dst = sb + p * b_tile;
+                src = Bslices + p * b_slice_stride + (int64_t)(col0 + rr) * Kp + chunk * 8;
+                base = (uint32_t)(s * a_tile + p * b_tile);
             }
-            dst += ((rr >> 3) * 2 + chunk) * 128 + (rr & 7) * 16;
-            cp_async16(smem_u32(dst), src);
         }
+        lsrc[j] = src;
+        ldst[j] = base + (uint32_t)(((rr >> 3) * 2 + chunk) * 128 + (rr & 7) * 16);
+    }
+    auto load = [&](int t) {
+        const int64_t k0 = (int64_t)(kst0 + t) * kOzBK;
+        const uint32_t sbase = smem_u32(smem + (t % kOzStages) * stage_bytes);
+#pragma unroll
+        for (int j = 0; j < kOzLoadIters; ++j)
+            if (tid + j * kOzThreads < nitems) cp_async16(sbase + ldst[j], lsrc[j] + k0);
     };
     bool ok = true;
     int issued = 0;                                        // stages committed to MMA
-    // prologue: kOzStages - 1 stages in flight (one commit group each)
-    for (int t = 0; t < kOzStages - 1; ++t) {
+    // prologue: kOzLead stages in flight (one commit group each)
+    for (int t = 0; t < kOzLead; ++t) {
         if (t < nk) load(t);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (int t = 0; t < nk && ok; ++t) {
         const int slot = t % kOzStages;
-        asm volatile("cp.async.wait_group %0;" ::"n"(kOzStages - 2) : "memory");   // stage t landed
+        asm volatile("cp.async.wait_group %0;" ::"n"(kOzLead - 1) : "memory");   // stage t landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -202,12 +222,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
                 : "memory");
         }
         ++issued;
-        // refill the slot of stage t - 1 with stage t + kOzStages - 1 once the
-        // MMAs of stage t - 1 are done (those of stage t are already queued)
-        if (t >= 1) ok = mbar_wait(smem_u32(&mbar[(t - 1) % kOzStages]), ((t - 1) / kOzStages) & 1);
+        // refill the slot of stage t - kOzMmaAhead with stage t + kOzLead once the
+        // MMAs of that stage are done (those of the stages after it stay queued)
+        if (t >= kOzMmaAhead)
+            ok = mbar_wait(smem_u32(&mbar[(t - kOzMmaAhead) % kOzStages]),
+                           ((t - kOzMmaAhead) / kOzStages) & 1);
         ok = __syncthreads_and(ok);                          // uniform exit on a timeout
         if (!ok) break;
-        if (t + kOzStages - 1 < nk) load(t + kOzStages - 1);
+        if (t + kOzLead < nk) load(t + kOzLead);
         asm volatile("cp.async.commit_group;" ::: "memory");
         // ---- end of a 256-element chunk (or of K): drain the exact levels
         if ((t % kOzChunkStages) == kOzChunkStages - 1 || t == nk - 1) {
