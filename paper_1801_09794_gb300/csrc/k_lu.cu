@@ -371,15 +371,19 @@ __global__ void __launch_bounds__(kPanelThreads) lu_panel_reg_grouped_kernel(
 namespace cg = cooperative_groups;
 constexpr int kClusterMax = 8;       // portable cluster size
 constexpr int kClusterThreads = 512;
+// mini-panel width of the cluster panels: 8 columns halve the passes over the
+// rest of the panel (the per-element operations and their order are those of
+// 4-column mini-panels, so the factors are unchanged)
+constexpr int kClusterMini = 8;
 
-template <typename T>
+template <typename T, int MINI>
 struct PanelCand {
     typename cplx_real<T>::type v;   // cabs1 of the candidate (-1: none)
     int i;                           // its row (INT_MAX: none)
-    T row[kMini];                    // its mini-panel entries
+    T row[MINI];                     // its mini-panel entries
 };
 
-template <typename T, int ROWS>
+template <typename T, int ROWS, int MINI = kMini>
 __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T* A, int64_t ld,
                                                    int* ip, int* info1, int2* gl, int* gc) {
     typedef typename cplx_real<T>::type R;
@@ -390,26 +394,26 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
     const int G = CL * NT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = rank * NT + tid;
-    __shared__ PanelCand<T> s_cand[2][kClusterMax];
-    __shared__ T s_crow[2][kMini];
-    __shared__ PanelCand<T> s_wc[NW];
-    __shared__ T s_L11[kMini][kMini];
-    __shared__ T s_U[kMini][64];
-    __shared__ T s_gval[2 * kMini][64];
-    __shared__ int s_piv[kMini];
-    __shared__ int2 s_gl[2 * kMini];
+    __shared__ PanelCand<T, MINI> s_cand[2][kClusterMax];
+    __shared__ T s_crow[2][MINI];
+    __shared__ PanelCand<T, MINI> s_wc[NW];
+    __shared__ T s_L11[MINI][MINI];
+    __shared__ T s_U[MINI][64];
+    __shared__ T s_gval[2 * MINI][64];
+    __shared__ int s_piv[MINI];
+    __shared__ int2 s_gl[2 * MINI];
     __shared__ int s_gc;
     const int pend = k0 + jb;
     constexpr int kUpd = ROWS == 1 ? 8 : 4;
-    T v[ROWS][kMini];
+    T v[ROWS][MINI];
 
-    for (int mb0 = k0; mb0 < pend; mb0 += kMini) {
-        const int w = min(kMini, pend - mb0);
+    for (int mb0 = k0; mb0 < pend; mb0 += MINI) {
+        const int w = min(MINI, pend - mb0);
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             const int64_t r = k0 + g + (int64_t)i * G;
 #pragma unroll
-            for (int c = 0; c < kMini; ++c)
+            for (int c = 0; c < MINI; ++c)
                 v[i][c] = (r < n && c < w) ? A[r + (int64_t)(mb0 + c) * ld] : cmake<T>(0.0, 0.0);
         }
         for (int c = 0; c < w; ++c) {
@@ -422,7 +426,7 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                 const int64_t r = k0 + g + (int64_t)i * G;
                 T x = v[i][0];
 #pragma unroll
-                for (int cc = 1; cc < kMini; ++cc) if (cc == c) x = v[i][cc];
+                for (int cc = 1; cc < MINI; ++cc) if (cc == c) x = v[i][cc];
                 if (r >= col && r < n) {
                     R a = cabs1(x);
                     if (a > best) { best = a; bi = (int)r; bslot = i; }
@@ -434,14 +438,14 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
             wi = __shfl_sync(0xffffffffu, wi, 0);
             wb = __shfl_sync(0xffffffffu, wb, 0);
             if (wi != INT_MAX && bi == wi) {          // this lane holds the warp's candidate row
-                PanelCand<T>& e = s_wc[warp];
+                PanelCand<T, MINI>& e = s_wc[warp];
                 e.v = wb;
                 e.i = wi;
 #pragma unroll
                 for (int i = 0; i < ROWS; ++i)
                     if (i == bslot)
 #pragma unroll
-                        for (int cc = 0; cc < kMini; ++cc) e.row[cc] = v[i][cc];
+                        for (int cc = 0; cc < MINI; ++cc) e.row[cc] = v[i][cc];
             }
             if (lane == 0 && wi == INT_MAX) { s_wc[warp].v = (R)-1; s_wc[warp].i = INT_MAX; }
             // the diagonal row, for the interchange
@@ -451,7 +455,7 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                     for (int d = 0; d < CL; ++d) {
                         T* dst = cl.map_shared_rank(&s_crow[par][0], d);
 #pragma unroll
-                        for (int cc = 0; cc < kMini; ++cc) dst[cc] = v[i][cc];
+                        for (int cc = 0; cc < MINI; ++cc) dst[cc] = v[i][cc];
                     }
                 }
             }
@@ -466,7 +470,7 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                 const unsigned m = __ballot_sync(0xffffffffu, lane < NW && ci == ri);
                 const int src = m ? __ffs(m) - 1 : 0;
                 if (lane < CL) {
-                    PanelCand<T>* dst = cl.map_shared_rank(&s_cand[par][rank], lane);
+                    PanelCand<T, MINI>* dst = cl.map_shared_rank(&s_cand[par][rank], lane);
                     *dst = s_wc[src];
                 }
             }
@@ -481,14 +485,14 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
             }
             const bool found = !(p == INT_MAX || p < col || p >= n);
             if (!found) p = col;
-            T prow[kMini];
+            T prow[MINI];
 #pragma unroll
-            for (int cc = 0; cc < kMini; ++cc)
+            for (int cc = 0; cc < MINI; ++cc)
                 prow[cc] = found ? s_cand[par][wd].row[cc] : s_crow[par][cc];
             if (tid == 0) {
                 s_piv[c] = p;
 #pragma unroll
-                for (int cc = 0; cc < kMini; ++cc) s_L11[c][cc] = prow[cc];
+                for (int cc = 0; cc < MINI; ++cc) s_L11[c][cc] = prow[cc];
                 if (rank == 0) {
                     if (!(pb > (R)0) && *info1 == 0) *info1 = col + 1;
                     ip[col] = p;
@@ -500,16 +504,16 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                     const int64_t r = k0 + g + (int64_t)i * G;
                     if (r == col) {
 #pragma unroll
-                        for (int cc = 0; cc < kMini; ++cc) v[i][cc] = prow[cc];
+                        for (int cc = 0; cc < MINI; ++cc) v[i][cc] = prow[cc];
                     } else if (r == p) {
 #pragma unroll
-                        for (int cc = 0; cc < kMini; ++cc) v[i][cc] = s_crow[par][cc];
+                        for (int cc = 0; cc < MINI; ++cc) v[i][cc] = s_crow[par][cc];
                     }
                 }
             }
             T piv_v = prow[0];
 #pragma unroll
-            for (int cc = 1; cc < kMini; ++cc) if (cc == c) piv_v = prow[cc];
+            for (int cc = 1; cc < MINI; ++cc) if (cc == c) piv_v = prow[cc];
             const T inv = crcp(piv_v);
 #pragma unroll
             for (int i = 0; i < ROWS; ++i) {
@@ -517,9 +521,9 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                 if (r > col && r < n) {
                     T l = cmake<T>(0.0, 0.0);
 #pragma unroll
-                    for (int cc = 0; cc < kMini; ++cc) if (cc == c) { l = v[i][cc] * inv; v[i][cc] = l; }
+                    for (int cc = 0; cc < MINI; ++cc) if (cc == c) { l = v[i][cc] * inv; v[i][cc] = l; }
 #pragma unroll
-                    for (int cc = 0; cc < kMini; ++cc)
+                    for (int cc = 0; cc < MINI; ++cc)
                         if (cc > c && cc < w) v[i][cc] = cfms(l, prow[cc], v[i][cc]);
                 }
             }
@@ -530,11 +534,11 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
             const int64_t r = k0 + g + (int64_t)i * G;
             if (r < n)
 #pragma unroll
-                for (int c = 0; c < kMini; ++c)
+                for (int c = 0; c < MINI; ++c)
                     if (c < w) A[r + (int64_t)(mb0 + c) * ld] = v[i][c];
         }
         const int rest0 = mb0 + w, nrest = pend - rest0;
-        if (tid == 0) gather_list<2 * kMini>(mb0, w, s_piv, s_gl, &s_gc);
+        if (tid == 0) gather_list<2 * MINI>(mb0, w, s_piv, s_gl, &s_gc);
         __syncthreads();
         const int gcnt = s_gc;
         // reads: (a) the mini-panel rows of the remaining columns after the
@@ -568,16 +572,16 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
         if (nrest > 0) {
             // U12 = L11^{-1} A12 on the remaining panel columns (every CTA)
             if (tid < nrest) {
-                T u[kMini];
+                T u[MINI];
 #pragma unroll
-                for (int c = 0; c < kMini; ++c) u[c] = (c < w) ? s_U[c][tid] : cmake<T>(0.0, 0.0);
+                for (int c = 0; c < MINI; ++c) u[c] = (c < w) ? s_U[c][tid] : cmake<T>(0.0, 0.0);
 #pragma unroll
-                for (int c = 0; c < kMini; ++c)
+                for (int c = 0; c < MINI; ++c)
 #pragma unroll
-                    for (int r2 = c + 1; r2 < kMini; ++r2)
+                    for (int r2 = c + 1; r2 < MINI; ++r2)
                         if (r2 < w) u[r2] = cfms(s_L11[r2][c], u[c], u[r2]);
 #pragma unroll
-                for (int c = 0; c < kMini; ++c) s_U[c][tid] = u[c];
+                for (int c = 0; c < MINI; ++c) s_U[c][tid] = u[c];
             }
             __syncthreads();
             // the U12 rows go to memory from the CTA that owns them
@@ -607,7 +611,7 @@ __device__ __forceinline__ void panel_cluster_body(int64_t n, int k0, int jb, T*
                         for (int q = 0; q < kUpd; ++q) {
                             if (j0 + q < nrest) {
 #pragma unroll
-                                for (int c = 0; c < kMini; ++c)
+                                for (int c = 0; c < MINI; ++c)
                                     if (c < w) a[i][q] = cfms(v[i][c], s_U[c][j0 + q], a[i][q]);
                                 ar[(int64_t)q * ld] = a[i][q];
                             }
@@ -626,7 +630,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lu_panel_cluster_kernel(
     int64_t n, int k0, int jb, float2* F, int64_t ld, int64_t strideF, int* piv, int* info,
     int2* gather, int* gcount, int panel_index, int gstride) {
     const int node = blockIdx.y;
-    panel_cluster_body<float2, ROWS>(
+    panel_cluster_body<float2, ROWS, kClusterMini>(
         n, k0, jb, F + node * strideF, ld, piv + (int64_t)node * n, info + node,
         gather ? gather + (int64_t)node * gstride + panel_index * 2 * 64 : nullptr,
         gcount + (int64_t)node * (gstride / 128) + panel_index);
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lu_panel_cluster_grouped_k
     const LuNode d = nodes[blockIdx.y];
     if (k0 >= d.n) return;
     const int jb = (int)min((int64_t)nb, d.n - k0);
-    panel_cluster_body<float2, ROWS>(d.n, k0, jb, static_cast<float2*>(d.F), d.n, d.piv, d.info,
+    panel_cluster_body<float2, ROWS, kClusterMini>(d.n, k0, jb, static_cast<float2*>(d.F), d.n, d.piv, d.info,
                                      d.gather + panel_index * 2 * 64, d.gcount + panel_index);
 }
 
