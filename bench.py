@@ -45,6 +45,9 @@ ROOF_TRAFFIC = {
     # node LU of the n = 4096 QEP, 16 nodes: 62.45 GB over 282 launches
     # (profiles/lu_dram_qep_n4096.md)
     ("qep_mixed_n4096", "lu"): 221.4e6,
+    # reduced stage (companion order 192): 2.11 MB over the 10 launches of one
+    # iteration (profiles/reduced_stage_dram_m96.md)
+    ("qep_mixed_n4096", "reduced"): 0.211e6,
 }
 TF32_OVER_BF16 = 1.1 / 2.25
 # arithmetic of the path per node-factor precision

@@ -1466,11 +1466,14 @@ static std::vector<PersistTask> persist_tasks(const int64_t* n_host, int count, 
             for (int i = 0; i < count; ++i)
                 if (n_host[i] - k0 > nb) t.push_back({kind, i, p, 0});
     };
-    auto cols = [&](int p, bool next) {           // the next pair's blocks, or those right of them
+    // the next pair's blocks, or those right of them, node by node: the tasks
+    // running together then share one node's L21 block in L2 (ordered block
+    // by block over the nodes, each task re-read its own node's L21 from DRAM)
+    auto cols = [&](int p, bool next) {
         const int64_t k0 = 2ll * nb * p;
         const int lo = next ? 2 * p + 2 : 2 * p + 4, hi = next ? 2 * p + 4 : ncb;
-        for (int cb = lo; cb < hi; ++cb)
-            for (int i = 0; i < count; ++i)
+        for (int i = 0; i < count; ++i)
+            for (int cb = lo; cb < hi; ++cb)
                 if (n_host[i] - k0 > 2 * nb && (int64_t)cb * nb < n_host[i]) t.push_back({kTaskCol, i, p, cb});
     };
     head(0);
