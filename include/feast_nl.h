@@ -312,6 +312,22 @@ int feast_nl_slices_get_eigpairs(feast_nl_slices* s, int32_t disc, int32_t capac
 int64_t feast_nl_slices_graph_launches(feast_nl_slices* s);
 void feast_nl_slices_destroy(feast_nl_slices* s);
 
+/* ---- environment ------------------------------------------------------------ */
+/* Read by the library at the calls named; none changes a result's bits except
+ * where stated.
+ *   FEAST_NL_TRACE=1                : every iteration's kept Ritz values, residuals
+ *                                     and status on stderr (solve runs eagerly).
+ *   FEAST_NL_PANEL_ROWS_PER_CTA=r   : complex64 LU panels taller than r rows are
+ *                                     factored by a cluster of up to 8 CTAs, one per
+ *                                     r rows (default 1024; 0 = one CTA per panel).
+ *                                     Same factors for every r.
+ *   FEAST_NL_LU_PERSISTENT=1        : the complex64 factorisation of set_contour,
+ *                                     feast_nl_set_contour_group and the slicing
+ *                                     set (orders <= 4096) runs as one persistent
+ *                                     launch over all nodes instead of launches per
+ *                                     panel step.  Same factors; slower on the
+ *                                     measured workloads, so off by default. */
+
 /* ---- measurement ------------------------------------------------------------ */
 /* Phases of the path, for feast_nl_get_profile. */
 enum feast_nl_phase {
