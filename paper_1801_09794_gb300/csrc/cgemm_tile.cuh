@@ -97,12 +97,13 @@ __device__ __forceinline__ void unit_init_barriers(uint64_t* full, uint64_t* emp
 // split.  Returns false (on every thread of the unit) when a wait timed out;
 // the tile is then not written.
 // Operand loads: through the read-only path when A and B stay unchanged for
-// the whole launch (NC), else L2-coherent (a persistent kernel that changes
-// the matrix between its tasks).
+// the whole launch (NC), else as ordinary cached loads (ld.global.ca), which a
+// persistent kernel that changes the matrix between its tasks may use after
+// its acquire of the producing task's flag.
 template <bool NC, typename V>
 __device__ __forceinline__ V ld_operand(const V* p) {
     if constexpr (NC) return __ldg(p);
-    else return __ldcg(p);
+    else return __ldca(p);
 }
 
 template <int BN, bool NC = true>
