@@ -38,7 +38,9 @@
 //
 // Kernel: one CTA (256 threads) per 128 x 48 tile of W'.  K advances in
 // 16-element stages through a 5-slot cp.async ring (loads three stages ahead,
-// the MMAs of two stages queued behind them);
+// the MMAs of two stages queued behind them; one block barrier per stage,
+// after which the stage's copies have all landed and the slot to refill is
+// free);
 // thread 0 issues tcgen05.mma.kind::f16 (M = 128, K = 16) once per A slice p
 // against the B slices q = 0 .. s-1-p side by side (N = 48 per slice, at most
 // five per instruction), with D placed so that slice q's columns fall on
@@ -193,7 +195,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
         const int slot = t % kOzStages;
         asm volatile("cp.async.wait_group %0;" ::"n"(kOzLead - 1) : "memory");   // stage t landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        // the slot refilled below with stage t + kOzLead is the one the MMAs of
+        // stage t - kOzMmaAhead read: wait for them here, so that one barrier
+        // per stage covers both (every copy of stage t landed, the slot free)
+        if (t >= kOzMmaAhead && t + kOzLead < nk)
+            ok = mbar_wait(smem_u32(&mbar[(t - kOzMmaAhead) % kOzStages]),
+                           ((t - kOzMmaAhead) / kOzStages) & 1);
+        ok = __syncthreads_and(ok);                          // uniform exit on a timeout
+        if (!ok) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
@@ -222,13 +231,6 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_bf16_gemm_kernel(
                 : "memory");
         }
         ++issued;
-        // refill the slot of stage t - kOzMmaAhead with stage t + kOzLead once the
-        // MMAs of that stage are done (those of the stages after it stay queued)
-        if (t >= kOzMmaAhead)
-            ok = mbar_wait(smem_u32(&mbar[(t - kOzMmaAhead) % kOzStages]),
-                           ((t - kOzMmaAhead) / kOzStages) & 1);
-        ok = __syncthreads_and(ok);                          // uniform exit on a timeout
-        if (!ok) break;
         if (t + kOzLead < nk) load(t + kOzLead);
         asm volatile("cp.async.commit_group;" ::: "memory");
         // ---- end of a 256-element chunk (or of K): drain the exact levels
