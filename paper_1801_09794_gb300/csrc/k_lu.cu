@@ -890,11 +890,14 @@ __device__ __forceinline__ T pick_slot(const T* x, int q) {
 }
 
 // One CTA's share of a block substitution: stage the triangle, then its warps
-// take the columns first + warp, first + warp + stride, ... below ncols of B
-// (column cl at B + cl * ldb; the block's rows are k0 .. k0 + jb - 1 of every
-// column).  gl / gc: the block's first panel's gather list and count (the
-// second panel's follow at gl + 128, gc + 1).
-template <typename T, int SB>
+// take the column groups first + warp, first + warp + stride, ... (group g =
+// columns g NC .. g NC + NC - 1 below ncols of B; column cl at B + cl * ldb;
+// the block's rows are k0 .. k0 + jb - 1 of every column).  A warp solves the
+// NC columns of a group together, so each triangle entry it reads from shared
+// memory serves NC columns; per column the operations and their order are
+// those of a one-column solve.  gl / gc: the block's first panel's gather list
+// and count (the second panel's follow at gl + 128, gc + 1).
+template <typename T, int SB, int NC>
 __device__ __forceinline__ void trsm_block_body(int k0, int jb, int nb, const T* __restrict__ F,
                                                 int64_t ld, const int2* __restrict__ gl,
                                                 const int* __restrict__ gc, T* B, int64_t ldb,
@@ -905,69 +908,104 @@ __device__ __forceinline__ void trsm_block_body(int k0, int jb, int nb, const T*
     T* sD = reinterpret_cast<T*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     stage_triangle(F, ld, k0, jb, sD, LDS, upper);
-    int cl = first + warp;
-    if (!upper && cl < ncols) {                   // while the triangle is in flight
-        T* col = B + (int64_t)cl * ldb;
-        gather_rows_warp(gl, gc[0], col);
-        if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
-    }
+    int grp = first + warp;
+    auto gather_group = [&](int g) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int cl = g * NC + c;
+            if (cl < ncols) {
+                T* col = B + (int64_t)cl * ldb;
+                gather_rows_warp(gl, gc[0], col);
+                if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
+            }
+        }
+    };
+    if (!upper && grp * NC < ncols) gather_group(grp);    // while the triangle is in flight
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (upper) {                                  // the diagonal, inverted
         for (int r = threadIdx.x; r < jb; r += blockDim.x) sD[r * LDS + r] = crcp(sD[r * LDS + r]);
         __syncthreads();
     }
-    for (; cl < ncols; cl += stride) {
-        T* col = B + (int64_t)cl * ldb;
-        if (!upper && cl != first + warp) {
-            gather_rows_warp(gl, gc[0], col);
-            if (jb > nb) gather_rows_warp(gl + 2 * 64, gc[1], col);
-        }
-        col += k0;
-        T x[4];
+    for (; grp * NC < ncols; grp += stride) {
+        if (!upper && grp != first + warp) gather_group(grp);
+        T x[NC][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r = lane + 32 * q;
-            x[q] = (q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
+        for (int c = 0; c < NC; ++c) {
+            const int cl = grp * NC + c;
+            const T* col = B + (int64_t)min(cl, ncols - 1) * ldb + k0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = lane + 32 * q;
+                x[c][q] = (cl < ncols && q < Q && r < jb) ? col[r] : cmake<T>(0.0, 0.0);
+            }
         }
         if (!upper) {
-#pragma unroll 4
+#pragma unroll 2
             for (int i = 0; i + 1 < jb; ++i) {
-                const T own = pick_slot(x, i >> 5);
-                T xi;
-                xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
-                xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
+                T xi[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const T own = pick_slot(x[c], i >> 5);
+                    xi[c].x = __shfl_sync(0xffffffffu, own.x, i & 31);
+                    xi[c].y = __shfl_sync(0xffffffffu, own.y, i & 31);
+                }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const int r = lane + 32 * q;
-                    if (r > i && r < jb) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+                    if (r > i && r < jb) {
+                        const T l = sD[r * LDS + i];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) x[c][q] = cfms(l, xi[c], x[c][q]);
+                    }
                 }
             }
         } else {
-#pragma unroll 4
+#pragma unroll 2
             for (int i = jb - 1; i >= 0; --i) {
-                const T own = pick_slot(x, i >> 5);
-                T xi;
-                xi.x = __shfl_sync(0xffffffffu, own.x, i & 31);
-                xi.y = __shfl_sync(0xffffffffu, own.y, i & 31);
-                xi = xi * sD[i * LDS + i];
+                const T dinv = sD[i * LDS + i];
+                T xi[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const T own = pick_slot(x[c], i >> 5);
+                    xi[c].x = __shfl_sync(0xffffffffu, own.x, i & 31);
+                    xi[c].y = __shfl_sync(0xffffffffu, own.y, i & 31);
+                    xi[c] = xi[c] * dinv;
+                }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const int r = lane + 32 * q;
-                    if (r == i) x[q] = xi;
-                    else if (r < i) x[q] = cfms(sD[r * LDS + i], xi, x[q]);
+                    if (r == i) {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) x[c][q] = xi[c];
+                    } else if (r < i) {
+                        const T u = sD[r * LDS + i];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) x[c][q] = cfms(u, xi[c], x[c][q]);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int r = lane + 32 * q;
-            if (r < jb) col[r] = x[q];
+        for (int c = 0; c < NC; ++c) {
+            const int cl = grp * NC + c;
+            if (cl < ncols) {
+                T* col = B + (int64_t)cl * ldb + k0;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r < jb) col[r] = x[c][q];
+                }
+            }
         }
     }
 }
 
-template <typename T, int SB>
+// NC: columns per warp (1 for the solves' right-hand sides, where the chain
+// of a column is the latency to hide; kLuTrsmCols for the factorisation's
+// trailing columns, where the triangle's shared-memory reads bound)
+constexpr int kLuTrsmCols = 4;
+template <typename T, int SB, int NC>
 __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
     int k0, int jb, int nb, const T* __restrict__ F, int64_t ld, int64_t strideF,
     const int2* __restrict__ gather, const int* __restrict__ gcount, int gstride, int panel_index,
@@ -975,7 +1013,7 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
     int group) {
     const int node = blockIdx.y;
     if (active && !active[node / group]) return;     // a finished contour's nodes
-    trsm_block_body<T, SB>(k0, jb, nb, F + node * strideF, ld,
+    trsm_block_body<T, SB, NC>(k0, jb, nb, F + node * strideF, ld,
                            gather + (int64_t)node * gstride + panel_index * 2 * 64,
                            gcount + (int64_t)node * (gstride / 128) + panel_index,
                            B + node * strideB, ldb, ncols, upper, blockIdx.x * kBlockWarps,
@@ -984,14 +1022,14 @@ __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_kernel(
 
 // A pair's block substitution on the columns of nodes of different orders:
 // mode 0 the next pair's columns, mode 1 the columns right of them.
-template <int SB>
+template <int SB, int NC>
 __global__ void __launch_bounds__(32 * kBlockWarps) trsm_block_grouped_kernel(
     const LuNode* __restrict__ nodes, int k0, int nb, int panel_index, int mode) {
     const LuNode d = nodes[blockIdx.y];
     int jb, c0, ncols;
     if (!lookahead_cols(d.n, k0, 2 * nb, mode, &jb, &c0, &ncols)) return;
     float2* F = static_cast<float2*>(d.F);
-    trsm_block_body<float2, SB>(k0, jb, nb, F, d.n, d.gather + panel_index * 2 * 64,
+    trsm_block_body<float2, SB, NC>(k0, jb, nb, F, d.n, d.gather + panel_index * 2 * 64,
                                 d.gcount + panel_index, F + (int64_t)c0 * d.n, d.n, ncols, 0,
                                 blockIdx.x * kBlockWarps, gridDim.x * kBlockWarps);
 }
@@ -1179,7 +1217,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) lu_persistent_kernel(Persi
                 const int jb = 2 * nb;
                 const int c0 = tk.cb * nb;
                 const int ncols = (int)min((int64_t)nb, n - c0);
-                trsm_block_body<float2, 128>(k0, jb, nb, F, n, d.gather + 2 * tk.pair * 2 * 64,
+                trsm_block_body<float2, 128, kLuTrsmCols>(k0, jb, nb, F, n, d.gather + 2 * tk.pair * 2 * 64,
                                              d.gcount + 2 * tk.pair, F + (int64_t)c0 * n, n, ncols, 0,
                                              0, kPersistThreads / 32);
                 __syncthreads();
@@ -1223,11 +1261,13 @@ cudaError_t trsm_block_attr() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        if ((e = cudaFuncSetAttribute(trsm_block_kernel<T, SB>,
+        if ((e = cudaFuncSetAttribute(trsm_block_kernel<T, SB, 1>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(trsm_block_kernel<T, SB, kLuTrsmCols>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
             return e;
         if constexpr (sizeof(T) == 8)
-            if ((e = cudaFuncSetAttribute(trsm_block_grouped_kernel<SB>,
+            if ((e = cudaFuncSetAttribute(trsm_block_grouped_kernel<SB, kLuTrsmCols>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
                 return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
@@ -1235,10 +1275,11 @@ cudaError_t trsm_block_attr() {
     return cudaSuccess;
 }
 
-// CTAs per node of a block substitution over ncols columns: enough for about
-// four waves of one CTA per SM over all nodes; the warps loop over the rest
-inline unsigned trsm_block_ctas(int64_t ncols, int nodes) {
-    const int64_t need = (ncols + kBlockWarps - 1) / kBlockWarps;
+// CTAs per node of a block substitution over `groups` column groups (one per
+// warp at a time): enough for about four waves of one CTA per SM over all
+// nodes; the warps loop over the rest
+inline unsigned trsm_block_ctas(int64_t groups, int nodes) {
+    const int64_t need = (groups + kBlockWarps - 1) / kBlockWarps;
     const int64_t cap = std::max<int64_t>(1, (4 * 152 + nodes - 1) / nodes);
     return (unsigned)std::max<int64_t>(1, std::min(need, cap));
 }
@@ -1377,9 +1418,9 @@ cudaError_t block_apply(cudaStream_t st, int64_t n, int k0, int jb, int nb, T* F
     constexpr int smem = (int)solve_block_smem<T>();
     cudaError_t e = trsm_block_attr<T>();
     if (e != cudaSuccess) return e;
-    dim3 g(trsm_block_ctas(ncols, nc), nc);
+    dim3 g(trsm_block_ctas((ncols + kLuTrsmCols - 1) / kLuTrsmCols, nc), nc);
     note_launch();
-    trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+    trsm_block_kernel<T, SB, kLuTrsmCols><<<g, 32 * kBlockWarps, smem, st>>>(
         k0, jb, nb, F, n, strideF, gather, gcount, gstride, panel, F + c0 * n, n, strideF,
         (int)ncols, 0, nullptr, 1);
     const int64_t rows = n - k0 - jb;
@@ -1632,9 +1673,10 @@ cudaError_t lu_factor_grouped(cudaStream_t st, const LuNode* nodes, const int64_
     // a pair's substitution and update on the nodes' columns of `mode`
     auto pair_apply = [&](cudaStream_t s, int k0, int p, int mode, int64_t rows_below,
                           int64_t cols) -> cudaError_t {
-        dim3 g(trsm_block_ctas(cols, count), count);
+        dim3 g(trsm_block_ctas((cols + kLuTrsmCols - 1) / kLuTrsmCols, count), count);
         note_launch();
-        trsm_block_grouped_kernel<SB><<<g, 32 * kBlockWarps, smem, s>>>(nodes, k0, nb, 2 * p, mode);
+        trsm_block_grouped_kernel<SB, kLuTrsmCols><<<g, 32 * kBlockWarps, smem, s>>>(nodes, k0, nb,
+                                                                                     2 * p, mode);
         cudaError_t pe = cudaGetLastError();
         if (pe != cudaSuccess) return pe;
         return cgemm_sub_grouped(s, nodes, count, k0, 2 * nb, mode, rows_below, cols, err);
@@ -1710,7 +1752,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     for (int64_t k0 = 0, panel = 0; k0 < n; k0 += sb, panel += 2) {
         const int jb = (int)std::min<int64_t>(sb, n - k0);
         note_launch();
-        trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+        trsm_block_kernel<T, SB, 1><<<g, 32 * kBlockWarps, smem, st>>>(
             (int)k0, jb, nb, F, n, strideF, gather, gcount, gstride, (int)panel, Y, n, strideY, m, 0,
             active, group);
         const int64_t rest = n - k0 - jb;
@@ -1724,7 +1766,7 @@ cudaError_t lu_solve_batched(cudaStream_t st, int64_t n, int nb, const T* F, int
     for (int64_t k0 = last; k0 >= 0; k0 -= sb) {
         const int jb = (int)std::min<int64_t>(sb, n - k0);
         note_launch();
-        trsm_block_kernel<T, SB><<<g, 32 * kBlockWarps, smem, st>>>(
+        trsm_block_kernel<T, SB, 1><<<g, 32 * kBlockWarps, smem, st>>>(
             (int)k0, jb, nb, F, n, strideF, gather, gcount, gstride, 0, Y, n, strideY, m, 1, active,
             group);
         if (k0 > 0) {
