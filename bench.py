@@ -42,9 +42,9 @@ BEYN_NODES = 256                    # trapezoid nodes of the projected delay pro
 # the same code, divided by those launches), keyed by (workload, phase); the
 # summaries and their commands are under profiles/.  Absent: not captured.
 ROOF_TRAFFIC = {
-    # node LU of the n = 4096 QEP, 16 nodes: 62.42 GB over 282 launches
+    # node LU of the n = 4096 QEP, 16 nodes: 62.87 GB over 282 launches
     # (profiles/lu_dram_qep_n4096.md)
-    ("qep_mixed_n4096", "lu"): 221.3e6,
+    ("qep_mixed_n4096", "lu"): 222.9e6,
     # reduced stage (companion order 192): 2.11 MB over the 10 launches of one
     # iteration (profiles/reduced_stage_dram_m96.md)
     ("qep_mixed_n4096", "reduced"): 0.211e6,
