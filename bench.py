@@ -287,7 +287,7 @@ def _peaks_file():
 DIGIT_SLICES = 7      # FEAST_NL_FP32_I8: digit slices per operand of A_t Q
 
 
-def phase_work(name, spec, c, iters, nterms_dense):
+def phase_work(name, spec, c, iters, nterms_dense, nterms_sliced=None):
     """Flops of one phase over one solve: algorithmic (4M complex counting), except
     the digit-split A_t Q, which counts the BF16 tensor-core flops it executes
     (s(s+1)/2 slice products of the real-embedded n x 2n x 2 m0 GEMM per term),
@@ -300,7 +300,9 @@ def phase_work(name, spec, c, iters, nterms_dense):
     if name == "apply":
         if spec["precision"] == "fp32_i8":
             pairs = DIGIT_SLICES * (DIGIT_SLICES + 1) // 2
-            return iters * nterms_dense * pairs * 2.0 * n * (2 * n) * (2 * m0)
+            # diagonal terms are applied as diagonal scalings, without slices
+            ns = nterms_dense if nterms_sliced is None else nterms_sliced
+            return iters * ns * pairs * 2.0 * n * (2 * n) * (2 * m0)
         return iters * nterms_dense * 8.0 * n * n * m0
     if name == "solve":
         return (iters - 1) * nc * 8.0 * n * n * m0
@@ -367,6 +369,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     s = P.FeastNL(pdev, spec["precision"], stream=stream.cuda_stream)
     nterms_dense = sum(1 for t in problem["terms"] if t["A"] is not None)
+    # a dense term with nothing off its diagonal takes the library's diagonal path
+    nterms_sliced = sum(1 for t in problem["terms"] if t["A"] is not None
+                        and np.count_nonzero(t["A"]) != np.count_nonzero(np.diag(t["A"])))
 
     def step(h):
         h.set_contour(center, c["ra"], c["rb"], c["nc"], c["rule"])
@@ -419,7 +424,7 @@ def run_gpu(args):
     for name, (pms, pl) in prof.items():
         if pms <= 0:
             continue
-        w = phase_work(name, spec, c, iters, nterms_dense)
+        w = phase_work(name, spec, c, iters, nterms_dense, nterms_sliced)
         ent = {"ms_per_step": pms / prof_steps, "launches_per_step": pl / prof_steps}
         if w is not None:
             tf = w / (pms / prof_steps / 1e3) / 1e12

@@ -236,7 +236,11 @@ struct feast_nl_handle {
     int oz_s = 0;
     unsigned char* dAsl = nullptr;  // nA x s slices of A'
     double* dSigma = nullptr;       // nA x Mpad row scales
-    int* dSlot = nullptr;           // dense index -> term index
+    int* dSlot = nullptr;           // sliced index -> term index
+    int nsl = 0;                    // dense terms with digit slices
+    // dense terms that are diagonal (exact zeros off the diagonal): their
+    // products A_t Q are diagonal scalings (term index, diagonal on the device)
+    std::vector<std::pair<int, double2*>> diag_terms;
     // results of the last solve
     bool have_result = false;
     int m_last = 0;
@@ -501,11 +505,15 @@ int apply_terms(const feast_nl_handle* h, const Work& wk, int nd, int m, const d
     const int M = nd * m;
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     if (h->oz_s > 0 && h->nA > 0) {
-        // all dense terms and all contours at once on the BF16 tensor cores
-        const OzakiLayout L = ozaki_layout(n, M, h->oz_s);
-        CK(ozaki_split_Q(st, n, M, h->oz_s, Q, wk.Tau, wk.Qsl, L));
-        CK(ozaki_gemm(st, n, M, m, T, L, h->nA, h->dAsl, h->dSigma, wk.Qsl, wk.Tau, W, h->dSlot, err,
-                      active));
+        // all sliced dense terms and all contours at once on the BF16 tensor
+        // cores; diagonal terms as diagonal scalings (FP64 products)
+        if (h->nsl > 0) {
+            const OzakiLayout L = ozaki_layout(n, M, h->oz_s);
+            CK(ozaki_split_Q(st, n, M, h->oz_s, Q, wk.Tau, wk.Qsl, L));
+            CK(ozaki_gemm(st, n, M, m, T, L, h->nsl, h->dAsl, h->dSigma, wk.Qsl, wk.Tau, W, h->dSlot,
+                          err, active));
+        }
+        for (const auto& dt : h->diag_terms) CK(diag_times(st, n, m, nd, T, dt.first, dt.second, Q, W));
         CK(copy_identity_terms(st, n, m, nd, T, h->dTerms, Q, W));
         return FEAST_NL_OK;
     }
@@ -959,6 +967,8 @@ void feast_nl_destroy(feast_nl_handle* h) {
     dfree(h->dAsl);
     dfree(h->dSigma);
     dfree(h->dSlot);
+    for (auto& dt : h->diag_terms) dfree(dt.second);
+    h->diag_terms.clear();
     dfree(h->dTerms);
     dfree(h->dStatus);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
@@ -1035,22 +1045,18 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
     if (precision == FEAST_NL_FP32_I8 && h->nA > 0 && ozaki_supported(n, kOzakiSlices)) {
         h->oz_s = kOzakiSlices;
         const OzakiLayout L = ozaki_layout(n, 1, h->oz_s);
-        std::vector<int> slot;
-        for (int t = 0; t < nterms; ++t)
-            if (h->terms[t].aidx >= 0) slot.push_back(t);
         if ((e = dalloc(&h->dAsl, (size_t)(L.a_term * h->nA) * ozaki_elem_bytes())) != cudaSuccess ||
             (e = dalloc(&h->dSigma, (size_t)(L.Mpad * h->nA))) != cudaSuccess ||
-            (e = dalloc(&h->dSlot, slot.size())) != cudaSuccess ||
-            (e = cudaMemcpyAsync(h->dSlot, slot.data(), sizeof(int) * slot.size(),
-                                 cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(h->st)) != cudaSuccess)
+            (e = dalloc(&h->dSlot, (size_t)h->nA)) != cudaSuccess)
             return cleanup(fail_cuda(e, "allocation of digit slices", __LINE__));
     }
     // copy the coefficients in, transposed to column-major
     double2* stage = nullptr;
     double2 *v = nullptr, *u = nullptr, *gw = nullptr;
     double* nrm = nullptr;
-    auto free_tmp = [&]() { dfree(stage); dfree(v); dfree(u); dfree(gw); dfree(nrm); };
+    int* dflag = nullptr;
+    std::vector<int> slot;                    // sliced index -> term index
+    auto free_tmp = [&]() { dfree(stage); dfree(v); dfree(u); dfree(gw); dfree(nrm); dfree(dflag); };
     bool need_stage = false;
     for (int t = 0; t < nterms; ++t)
         if (terms[t].A && !terms[t].on_device) need_stage = true;
@@ -1059,7 +1065,8 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         return cleanup(fail_cuda(e, "staging allocation", __LINE__));
     }
     if ((e = dalloc(&v, (size_t)n)) != cudaSuccess || (e = dalloc(&u, (size_t)n)) != cudaSuccess ||
-        (e = dalloc(&gw, (size_t)n * 32)) != cudaSuccess || (e = dalloc(&nrm, 2)) != cudaSuccess) {
+        (e = dalloc(&gw, (size_t)n * 32)) != cudaSuccess || (e = dalloc(&nrm, 2)) != cudaSuccess ||
+        (e = dalloc(&dflag, 1)) != cudaSuccess) {
         free_tmp();
         return cleanup(fail_cuda(e, "allocation", __LINE__));
     }
@@ -1078,11 +1085,28 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         }
         if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "transpose of A", __LINE__)); }
         if (h->oz_s > 0) {
-            const OzakiLayout L = ozaki_layout(n, 1, h->oz_s);
-            const int a = h->terms[t].aidx;
-            e = ozaki_split_A(h->st, n, h->oz_s, dst, h->dSigma + (int64_t)a * L.Mpad,
-                              h->dAsl + (int64_t)a * L.a_term * ozaki_elem_bytes(), L);
-            if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "digit split of A", __LINE__)); }
+            // a diagonal term's product A_t Q is a diagonal scaling: no slices
+            int hflag = 0;
+            e = cudaMemsetAsync(dflag, 0, sizeof(int), h->st);
+            if (e == cudaSuccess) e = offdiag_nonzero(h->st, n, dst, n, dflag);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "diagonal test", __LINE__)); }
+            if (!hflag) {
+                double2* dg = nullptr;
+                if ((e = dalloc(&dg, (size_t)n)) == cudaSuccess) {
+                    h->diag_terms.push_back({t, dg});
+                    e = extract_diagonal(h->st, n, dst, n, dg);
+                }
+                if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "diagonal of A", __LINE__)); }
+            } else {
+                const OzakiLayout L = ozaki_layout(n, 1, h->oz_s);
+                const int a = h->nsl++;
+                slot.push_back(t);
+                e = ozaki_split_A(h->st, n, h->oz_s, dst, h->dSigma + (int64_t)a * L.Mpad,
+                                  h->dAsl + (int64_t)a * L.a_term * ozaki_elem_bytes(), L);
+                if (e != cudaSuccess) { free_tmp(); return cleanup(fail_cuda(e, "digit split of A", __LINE__)); }
+            }
         }
         if (!tt.on_device) {
             // the staging buffer is reused by the next term
@@ -1104,6 +1128,12 @@ int feast_nl_create(feast_nl_handle** out, int64_t n, int32_t nterms, const feas
         h->terms[t].norm = std::sqrt(s);
     }
     free_tmp();
+    if (h->oz_s > 0 && !slot.empty()) {
+        e = cudaMemcpyAsync(h->dSlot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice,
+                            h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return cleanup(fail_cuda(e, "copy of the slice slots", __LINE__));
+    }
     std::vector<TermDev> td(nterms);
     for (int t = 0; t < nterms; ++t) {
         const HostTerm& ht = h->terms[t];

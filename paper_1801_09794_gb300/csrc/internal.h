@@ -181,6 +181,13 @@ cudaError_t to_double(cudaStream_t st, int64_t cnt, const T* src, double2* dst);
 cudaError_t set_identity(cudaStream_t st, int m, double2* Y, double* ones);
 // identity terms of W (layout of ozaki_gemm, nd blocks of m columns): slot t of
 // block b <- Q_b
+// Diagonal coefficient terms: *flag <- 1 when A (n x n, column-major) has a
+// nonzero off-diagonal entry; d <- diag(A); W block t of each of the nd
+// contours <- diag(d) Q_d (Q: nd blocks of n x m, W: nd blocks of nterms).
+cudaError_t offdiag_nonzero(cudaStream_t st, int64_t n, const double2* A, int64_t lda, int* flag);
+cudaError_t extract_diagonal(cudaStream_t st, int64_t n, const double2* A, int64_t lda, double2* d);
+cudaError_t diag_times(cudaStream_t st, int64_t n, int m, int nd, int nterms, int t, const double2* d,
+                       const double2* Q, double2* W);
 cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nd, int nterms,
                                 const TermDev* terms, const double2* Q, double2* W);
 

@@ -713,6 +713,33 @@ __global__ void form_reduced_kernel(int m, int nterms, int kmax, const TermDev* 
     }
     Ahat[e] = v;
 }
+// flag <- 1 when some off-diagonal entry of the n x n column-major A is
+// nonzero (exact test)
+__global__ void offdiag_nonzero_kernel(int64_t n, const double2* __restrict__ A, int64_t lda,
+                                       int* flag) {
+    bool nz = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, j = e / n;
+        const double2 a = A[i + j * lda];
+        nz = nz || (i != j && (a.x != 0.0 || a.y != 0.0));
+    }
+    if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1;
+}
+__global__ void diagonal_kernel(int64_t n, const double2* __restrict__ A, int64_t lda,
+                                double2* __restrict__ d) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = A[i + i * lda];
+}
+// W block t of every contour d <- diag(dg) Q_d (FP64 products, rounded once)
+__global__ void diag_times_kernel(int64_t n, int64_t nm, int nterms, int t,
+                                  const double2* __restrict__ dg, const double2* __restrict__ Q,
+                                  double2* __restrict__ W) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nm) return;
+    const int d = blockIdx.y;
+    W[(int64_t)d * nterms * nm + (int64_t)t * nm + e] = dg[e % n] * Q[d * nm + e];
+}
 __global__ void copy_identity_kernel(int64_t nm, int nterms, const TermDev* __restrict__ terms,
                                      const double2* __restrict__ Q, double2* __restrict__ W) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -762,6 +789,24 @@ cudaError_t form_reduced(cudaStream_t st, int m, int nterms, int kmax, const Ter
     note_launch();
     form_reduced_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, nterms, kmax, terms, G,
                                                                       Ahat);
+    return cudaGetLastError();
+}
+cudaError_t offdiag_nonzero(cudaStream_t st, int64_t n, const double2* A, int64_t lda, int* flag) {
+    note_launch();
+    offdiag_nonzero_kernel<<<1216, 256, 0, st>>>(n, A, lda, flag);
+    return cudaGetLastError();
+}
+cudaError_t extract_diagonal(cudaStream_t st, int64_t n, const double2* A, int64_t lda, double2* d) {
+    note_launch();
+    diagonal_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A, lda, d);
+    return cudaGetLastError();
+}
+cudaError_t diag_times(cudaStream_t st, int64_t n, int m, int nd, int nterms, int t, const double2* dg,
+                       const double2* Q, double2* W) {
+    const int64_t nm = n * m;
+    note_launch();
+    dim3 g((unsigned)((nm + 255) / 256), (unsigned)nd);
+    diag_times_kernel<<<g, 256, 0, st>>>(n, nm, nterms, t, dg, Q, W);
     return cudaGetLastError();
 }
 cudaError_t copy_identity_terms(cudaStream_t st, int64_t n, int m, int nd, int nterms,

@@ -125,6 +125,36 @@ def test_project_matches_oracle(lib, prec, n, m):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32_i8", "fp32"])
+def test_project_with_diagonal_terms(lib, prec):
+    """Dense coefficients that are diagonal (a non-identity mass matrix) take
+    the diagonal-scaling path for A_t Q in the digit-split precision; the
+    projections and a whole solve still match the oracle."""
+    n, m = 300, 24
+    rng = np.random.default_rng(21)
+    p = random_pep(n, 2, seed=9)
+    p["terms"][2]["A"] = np.diag(1.0 + 0.1 * rng.uniform(size=n)).astype(np.complex128)
+    p["terms"][0]["A"] = np.diag(rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    s = lib.FeastNL(p, prec)
+    Q = O.orthonormalize(start_block(n, m, 3))
+    got = s.project(Q, 2)
+    ref = O.projected_coefficients(p, Q)
+    for gp, rp in zip(got, ref):
+        assert _relerr(gp, rp) < 1e-13
+    lam_all = O.brute_force_eigs(p)
+    lam_all = lam_all[np.isfinite(lam_all)]
+    c = lam_all[np.argmin(np.abs(lam_all - 0.3j))]
+    d = np.sort(np.abs(lam_all - c))
+    r = 0.5 * (d[5] + d[6])
+    s.set_contour(c, r, r, 16, "gl")
+    s.solve(32, tol=1e-12, maxit=60, X0=start_block(n, 32, 4), allow=(lib.FEAST_NL_ENOT_CONVERGED,))
+    lam, _, rr = s.get_eigpairs(inside_only=True)
+    want = lam_all[np.abs(lam_all - c) < r]
+    assert len(lam) == len(want) == 6
+    assert match_sets(lam, want) < 1e-10 and np.all(rr <= 1e-10)
+    s.close()
+
+
 def test_project_matches_oracle_n4096(lib):
     """Projections at the largest K of the digit-split products (n = 4096,
     K = 2n = 8192 in the real embedding) on the n = 4096 QEP with m0 = 96,
