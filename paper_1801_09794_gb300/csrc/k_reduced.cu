@@ -1533,17 +1533,18 @@ __global__ void __launch_bounds__(kNewtonThreads) newton_kernel(
             // keeps its FP32 value and inverse-iteration vector: Step 3 never
             // tests it, and were it inside C its true residual would show.
             if (stage != 2 && outside) {
-            } else if (stage == 1 && need != nullptr) {
-                // retry this pair alone with an FP64 factor from the same start
-                need[i] = 1;
-                atomicOr(redflag, kRetry64);
             } else if (stage != 2 && !(status->n_inside > 0 && status->max_relres <= kExactStageRelres)) {
                 // Far from convergence (the previous iteration's residuals inside
                 // C above kExactStageRelres, or no previous test) the pair keeps
                 // its FP32 value and inverse-iteration vector: the Ritz pairs of
                 // such an iterate are approximations at the filter's level of
-                // progress anyway, and the FP64 re-run of the whole stage costs
-                // about as much as eight iterations of the n = 4096 QEP.
+                // progress anyway, and neither an FP64-factor retry nor the FP64
+                // re-run of the whole stage (about as much as eight iterations of
+                // the n = 4096 QEP) would change that.
+            } else if (stage == 1 && need != nullptr) {
+                // retry this pair alone with an FP64 factor from the same start
+                need[i] = 1;
+                atomicOr(redflag, kRetry64);
             } else {
                 atomicOr(&status->flags, 8);
                 atomicOr(redflag, kNeed64);
