@@ -55,24 +55,22 @@ DTYPES = {"fp64": "c128 (FP64 SIMT LU, solves and products) + f64",
           "fp32": "c64 (tf32x3 tensor LU) + f64",
           "fp32_i8": "c64 (tf32x3 tensor LU) + bf16-split f64 products + f64"}
 
-WORKLOADS = {
-    "qep_mixed_n4096": {"gen": "config2_qep", "n": 4096, "precision": "fp32_i8", "tol": 1e-10,
-                        "maxit": 40},
-    "qep_plain_n256": {"gen": "config1_qep", "n": 256, "precision": "fp64", "tol": 1e-10,
-                       "maxit": 60},
-    # non-polynomial T = -lambda I + A0 + A1 exp(-lambda), ellipse 2:1 at -0.9
-    "delay_n2048": {"gen": "delay_problem", "n": 2048, "precision": "fp32_i8", "tol": 1e-10,
-                    "maxit": 40},
-    # spectrum slicing: random cubic, 64 discs of an 8 x 8 grid, 8 nodes each; its
-    # eigenvalues are non-normal (condition ~5), so relres 1e-10 alone leaves
-    # ~5e-10 eigenvalue error: the solve stops at 1e-12, pairs count at 1e-10
-    "slices_n2048": {"gen": "cubic_pep", "n": 2048, "precision": "fp32_i8", "tol": 1e-12,
-                     "maxit": 60, "slices": True},
-    # mixed-order batch: cubics n = 256 .. 4096 (complex Gaussian), one circle of
-    # 8 eigenvalues each, factored together, solved side by side
-    "mixed_n": {"gen": "cubic_pep", "precision": "fp32_i8", "tol": 1e-12, "maxit": 60,
-                "mixed": True},
-}
+
+def load_configs():
+    """The workloads, one JSON file each under configs/ (generator, n, seed,
+    node-factor precision, tolerance, iteration cap; the contour, m0 and the
+    reference eigenvalues are in tests/golden/contours.json)."""
+    out = {}
+    d = os.path.join(ROOT, "configs")
+    for f in sorted(os.listdir(d)):
+        if f.endswith(".json"):
+            with open(os.path.join(d, f)) as fh:
+                spec = json.load(fh)
+            out[spec["workload"]] = spec
+    return out
+
+
+WORKLOADS = load_configs()
 
 
 # ---------------------------------------------------------------------------- ranks
@@ -111,7 +109,7 @@ def load_workload(name):
         problems = [getattr(workloads, spec["gen"])(q["n"], q["n"]) for q in c["problems"]]
         gold = [np.array([complex(*x) for x in q["eigs_inside"]]) for q in c["problems"]]
         return spec, c, problems, gold
-    problem = getattr(workloads, spec["gen"])(spec["n"], 0)
+    problem = getattr(workloads, spec["gen"])(spec["n"], spec["seed"])
     if spec.get("slices"):
         gold = [np.array([complex(*x) for x in e]) for e in c["eigs_inside"]]
     else:
