@@ -379,13 +379,18 @@ def factor_nodes(problem, z):
 
 
 def filter_update(lus, z, omega, X, lam, R):
-    """Step 4: Q = sum_j omega_j (X - T(z_j)^{-1} T(X, Lambda)) (z_j I - Lambda)^{-1}."""
+    """Step 4: Q = sum_j omega_j (X - T(z_j)^{-1} T(X, Lambda)) (z_j I - Lambda)^{-1}.
+
+    lus[j] is either T(z_j)'s LU factors (scipy's ``lu_factor`` pair) or a
+    callable R -> T(z_j)^{-1} R; the callable form lets a test substitute an
+    inexact solve (Sec. 4.2 reads the filter as residual inverse iteration,
+    which tolerates one)."""
     Q = np.zeros_like(X)
     for lu, zj, wj in zip(lus, z, omega):
         d = zj - lam
         if np.any(d == 0):
             raise SingularNode("Ritz value on a quadrature node")
-        Yj = sla.lu_solve(lu, R)
+        Yj = lu(R) if callable(lu) else sla.lu_solve(lu, R)
         Q += (X - Yj) * (wj / d)[None, :]
     return Q
 
