@@ -49,7 +49,11 @@ def test_nodes_match_oracle(lib, rule, nc):
 
 # ------------------------------------------------------------------ node LU + solve
 @pytest.mark.parametrize("prec,n", [("fp64", 150), ("fp32", 150), ("fp64", 33), ("fp32", 200),
-                                    ("fp64", 1), ("fp32", 65), ("fp32", 1), ("fp32", 700)])
+                                    ("fp64", 1), ("fp32", 65), ("fp32", 1), ("fp32", 700),
+                                    # odd orders: one ragged panel, a ragged pair, and
+                                    # a first panel taller than one CTA's 1024 rows
+                                    ("fp32", 3), ("fp32", 17), ("fp64", 127), ("fp32", 127),
+                                    ("fp32", 1027)])
 def test_node_solve_matches_oracle(lib, prec, n):
     p = random_pep(n, 2, seed=3)
     c, ra = 0.05 + 0.1j, 0.6
