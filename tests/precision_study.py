@@ -22,8 +22,10 @@ each with 0, 1 or 2 refinement sweeps Y <- Y + LU^{-1}(R - T(z_j) Y), whose
 residual is formed in FP64.  The right-hand side enters the low-precision
 solves rounded to complex64 and the solution returns as complex128.
 
-    python tests/precision_study.py                 # n = 4096 QEP, 16 nodes, m0 = 96
-    python tests/precision_study.py --workload qep_plain_n256
+    python tests/precision_study.py --modes fp64,tf32 --sweeps 0,1
+        # n = 4096 QEP, 16 nodes, m0 = 96: ~1 to 40 minutes per (mode, sweeps)
+        # on 8 cores (the emulated TF32 factorisations and FP64 sweeps dominate)
+    python tests/precision_study.py --workload qep_plain_n256     # seconds
 
 Test infrastructure: this file calls the oracle and numpy only.
 """
