@@ -80,3 +80,23 @@ def test_match_count_takes_each_reference_eigenvalue_once():
     # relative; the last misses the residual bar
     assert bench.match_count(lam, rr, ref) == 1
     assert bench.match_count(lam, rr, np.array([])) == 0
+
+
+def test_reference_arm_prints_one_complete_json_line(capsys):
+    """`bench.py --impl reference` on the n = 256 QEP (one FP64 oracle solve):
+    one JSON line with the contract's keys, all 16 pairs counted."""
+    import argparse
+    import json
+    import bench
+    bench.run_reference(argparse.Namespace(workload="qep_plain_n256", seed=0, warmup=0, steps=1))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["value"] > 0 and abs(d["value"] - 16 / (d["ms_per_step"] / 1e3)) < 1e-6 * d["value"]
+    assert d["config"]["workload"] == "qep_plain_n256"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
