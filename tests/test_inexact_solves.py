@@ -111,3 +111,14 @@ def test_planted_non_residual_filter_stalls_at_solve_precision(monkeypatch):
     r = _solve(problem, contour, g["m0"], X0, O.term_norms(problem), "tf32", 0)
     assert not r["converged"]
     assert min(r["history"][1:]) > 1e-8
+
+
+def test_found_counts_reference_pairs_per_iteration():
+    """The study's per-iteration count: a reference eigenvalue is found when a
+    Ritz value with relres <= tol lies within tol (relative) of it."""
+    ref = np.array([1.0 + 1.0j, 2.0 + 0.0j])
+    trace = [(np.array([1.0 + 1.0j, 2.0 + 1e-6j]), np.array([1e-12, 1e-12])),   # 2+1e-6i too far
+             (np.array([1.0 + 1.0j, 2.0 + 0.0j]), np.array([1e-9, 1e-12])),     # 1+1i residual too big
+             (np.array([1.0 + 1.0j, 2.0 + 0.0j]), np.array([1e-12, 1e-12]))]
+    assert S.found(trace, ref) == [1, 1, 2]
+    assert S.found([(np.array([]), np.array([]))], ref) == [0]
